@@ -1,0 +1,377 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, a brute-force enumeration, finite differences, a special case that
+reduces to a textbook routine, or an independently written loop.  A plausible
+slip in the oracle (dropped term, wrong sign or index, transposed operand)
+fails at least one of them.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle.altgdmin_lrs as O
+from lrsgen import GaussianInstance, FourierInstance
+
+
+def rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+# ------------------------------------------------------------ HardThreshold --
+
+def _ht_bruteforce(v, rho):
+    """Max sum |v_i|^2 over index sets of size rho; ties -> lexicographically
+    smallest sorted index tuple."""
+    n = len(v)
+    best, best_set = -1.0, None
+    for S in itertools.combinations(range(n), rho):
+        val = float(np.sum(np.abs(v[list(S)]) ** 2))
+        if val > best + 1e-300 or (val == best and S < best_set):
+            best, best_set = val, S
+    return np.array(best_set, dtype=np.int64)
+
+
+@pytest.mark.parametrize("rho", [0, 1, 2, 3, 6, 7])
+def test_hard_threshold_matches_bruteforce_with_ties(rho):
+    g = rng(rho)
+    for trial in range(30):
+        v = g.choice([-3.0, -2.0, -1.0, 0.0, 1.0, 2.0, 3.0], size=7)   # many ties
+        if trial % 3 == 0:
+            v = g.standard_normal(7)
+        idx, vals, _ = O.hard_threshold(v[None], rho)
+        np.testing.assert_array_equal(idx[0], _ht_bruteforce(v, rho))
+        np.testing.assert_array_equal(vals[0], v[idx[0]])
+
+
+def test_hard_threshold_complex_uses_modulus():
+    v = np.array([3 + 4j, -6.0, 0.1j, 5j, -4 - 3j])
+    idx, _, _ = O.hard_threshold(v[None], 3)
+    # |v| = 5, 6, 0.1, 5, 5 -> 6 (idx1) then the three 5s keep the two lowest: 0, 3
+    np.testing.assert_array_equal(idx[0], [0, 1, 3])
+
+
+# --------------------------------------------------------------------- IHT --
+
+def test_iht_identity_operator_one_step_is_hard_threshold_of_z():
+    """M = I, s = 0: g = -z, mu = 1 on any support, so s = HT(z) exactly."""
+    g = rng(1)
+    n, rho = 12, 4
+    z = g.standard_normal((3, n))
+    I = lambda s: s
+    s, idx, _ = O.iht(z, I, I, rho, 1, np.zeros_like(z))
+    hidx, hval, _ = O.hard_threshold(z, rho)
+    np.testing.assert_array_equal(idx, hidx)
+    np.testing.assert_array_equal(s, O.densify(hidx, hval, n))
+
+
+def test_iht_step_is_exact_line_search_on_support():
+    """mu minimises ||M(s - mu g_G) - z||^2 over mu (G = current support)."""
+    from scipy.optimize import minimize_scalar
+    g = rng(2)
+    m, n, rho = 9, 15, 3
+    Mm = g.standard_normal((m, n))
+    z = g.standard_normal(m)
+    G = np.array([1, 6, 11])
+    s0 = np.zeros(n)
+    s0[G] = g.standard_normal(3)
+    M = lambda s: s @ Mm.T
+    MH = lambda u: u @ Mm
+    s1, idx1, _ = O.iht(z[None], M, MH, rho, 1, s0[None], idx0=G[None])
+    grad = Mm.T @ (Mm @ s0 - z)
+    gG = np.zeros(n)
+    gG[G] = grad[G]
+    phi = lambda mu: float(np.sum((Mm @ (s0 - mu * gG) - z) ** 2))
+    mu_star = minimize_scalar(phi, bracket=(0.0, 1e-3), tol=1e-14).x
+    i = idx1[0][np.argmax(np.abs(grad[idx1[0]]))]
+    mu_oracle = (s0[i] - s1[0, i]) / grad[i]
+    assert abs(mu_oracle - mu_star) <= 1e-6 * abs(mu_star)
+
+
+def test_iht_invariant_to_operator_scaling():
+    g = rng(3)
+    K, m, n, rho = 4, 10, 20, 3
+    Mm = g.standard_normal((K, m, n))
+    z = g.standard_normal((K, m))
+    res = []
+    for c in (1.0, 37.5):
+        M = lambda s, c=c: ((c * Mm) @ s[:, :, None])[:, :, 0]
+        MH = lambda u, c=c: (u[:, None, :] @ (c * Mm))[:, 0, :]
+        s, idx, _ = O.iht(c * z, M, MH, rho, 5, np.zeros((K, n)))
+        res.append((s, idx))
+    np.testing.assert_array_equal(res[0][1], res[1][1])
+    np.testing.assert_allclose(res[0][0], res[1][0], rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------------- LS --
+
+def test_ls_step_is_pseudoinverse_closed_form():
+    """b = (A U)^dagger v with M^dagger := (M^T M)^{-1} M^T (Section I-A)."""
+    g = rng(4)
+    W = g.standard_normal((6, 30, 4))
+    v = g.standard_normal((6, 30))
+    b = O.pinv_apply(W, v)
+    for k in range(6):
+        b_def = np.linalg.solve(W[k].T @ W[k], W[k].T @ v[k])
+        b_lsq = np.linalg.lstsq(W[k], v[k], rcond=None)[0]
+        np.testing.assert_allclose(b[k], b_def, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(b[k], b_lsq, rtol=1e-12, atol=1e-12)
+        assert np.max(np.abs(W[k].T @ (v[k] - W[k] @ b[k]))) < 1e-11
+
+
+def test_projector_and_projected_problem():
+    """P_perp idempotent and symmetric; M = P_perp A; z - M s = P_perp(y - A s)."""
+    g = rng(5)
+    m, n, r = 12, 25, 3
+    A = g.standard_normal((1, m, n))
+    U = np.linalg.qr(g.standard_normal((n, r)))[0]
+    W = A @ U
+    P = O.projector_perp(W)[0]
+    np.testing.assert_allclose(P @ P, P, atol=1e-13)
+    np.testing.assert_allclose(P, P.T, atol=1e-13)
+    np.testing.assert_allclose(P @ W[0], 0, atol=1e-12)
+    y = g.standard_normal(m)
+    s = np.zeros(n)
+    s[[2, 9]] = [1.5, -2.0]
+    Wp = np.linalg.pinv(W[0])
+    z = y - W[0] @ (Wp @ y)
+    Mm = A[0] - W[0] @ (Wp @ A[0])
+    np.testing.assert_allclose(Mm, P @ A[0], atol=1e-12)
+    np.testing.assert_allclose(z - Mm @ s, P @ (y - A[0] @ s), atol=1e-12)
+
+
+# ---------------------------------------------------------------- gradient --
+
+def _cost(op, U, B, S, Y):
+    X = (U @ B).T + S
+    return float(np.sum(np.abs(Y - op.A(X)) ** 2))
+
+
+def test_gradient_matches_central_differences_real():
+    """Paper's grad_U f is the derivative of f/2 (Section II-A)."""
+    g = rng(6)
+    q, m, n, r = 5, 9, 12, 2
+    op = O.GaussianOperator(g.standard_normal((q, m, n)))
+    U, B = g.standard_normal((n, r)), g.standard_normal((r, q))
+    S = np.zeros((q, n))
+    S[:, 3] = 2.0
+    Y = g.standard_normal((q, m))
+    G = O.gradient_U(op, U, B, S, Y)
+    h = 1e-6
+    FD = np.zeros_like(U)
+    for i in range(n):
+        for j in range(r):
+            E = np.zeros_like(U)
+            E[i, j] = h
+            FD[i, j] = (_cost(op, U + E, B, S, Y) - _cost(op, U - E, B, S, Y)) / (2 * h) / 2
+    assert np.linalg.norm(G - FD) <= 1e-7 * np.linalg.norm(FD)
+
+
+def test_gradient_matches_central_differences_fourier_complex():
+    g = rng(7)
+    nx = ny = 4
+    q, m, r = 3, 7, 2
+    masks = np.stack([np.sort(g.choice(16, m, replace=False)) for _ in range(q)])
+    op = O.FourierOperator(masks, nx, ny)
+    U = g.standard_normal((16, r)) + 1j * g.standard_normal((16, r))
+    B = g.standard_normal((r, q)) + 1j * g.standard_normal((r, q))
+    S = np.zeros((q, 16), complex)
+    S[:, 5] = 1 - 2j
+    Y = g.standard_normal((q, m)) + 1j * g.standard_normal((q, m))
+    G = O.gradient_U(op, U, B, S, Y)
+    h = 1e-6
+    FD = np.zeros_like(U)
+    for i in range(16):
+        for j in range(r):
+            E = np.zeros_like(U)
+            E[i, j] = h
+            dre = (_cost(op, U + E, B, S, Y) - _cost(op, U - E, B, S, Y)) / (2 * h)
+            dim = (_cost(op, U + 1j * E, B, S, Y) - _cost(op, U - 1j * E, B, S, Y)) / (2 * h)
+            FD[i, j] = (dre + 1j * dim) / 2
+    assert np.linalg.norm(G - FD) <= 1e-7 * np.linalg.norm(FD)
+
+
+# ---------------------------------------------------------------------- QR --
+
+def _gram_schmidt(Z):
+    Q = np.zeros_like(Z)
+    for j in range(Z.shape[1]):
+        v = Z[:, j].copy()
+        for i in range(j):
+            v -= np.vdot(Q[:, i], v) * Q[:, i]
+        for i in range(j):                      # second pass (re-orthogonalise)
+            v -= np.vdot(Q[:, i], v) * Q[:, i]
+        Q[:, j] = v / np.linalg.norm(v)
+    return Q
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_qr_positive_is_the_unique_q_factor(cplx):
+    g = rng(8)
+    Z = g.standard_normal((50, 5)) + (1j * g.standard_normal((50, 5)) if cplx else 0)
+    Q, R = O.qr_positive(Z)
+    np.testing.assert_allclose(Q.conj().T @ Q, np.eye(5), atol=1e-13)
+    np.testing.assert_allclose(Q @ R, Z, atol=1e-12)
+    np.testing.assert_allclose(np.tril(R, -1), 0, atol=1e-14)
+    d = np.diag(R)
+    assert np.all(np.abs(d.imag) < 1e-14) and np.all(d.real > 0)
+    np.testing.assert_allclose(Q, _gram_schmidt(Z), atol=1e-12)
+
+
+# --------------------------------------------------------- spectral init --
+
+def test_top_r_left_singular_vectors_match_eigh():
+    g = rng(9)
+    L0 = g.standard_normal((40, 25)) @ np.diag(np.linspace(5, 0.1, 25)) @ \
+        np.linalg.qr(g.standard_normal((25, 25)))[0]
+    U, _ = O.top_r_left(L0, 3)
+    w, V = np.linalg.eigh(L0 @ L0.T)
+    Ve = V[:, np.argsort(w)[::-1][:3]]
+    cosines = np.linalg.svd(U.T @ Ve, compute_uv=False)
+    assert np.all(np.abs(cosines - 1) < 1e-10)
+    lam = np.sort(w)[::-1][:3]
+    np.testing.assert_allclose(L0 @ (L0.T @ U), U * lam[None, :], atol=1e-9)
+
+
+# --------------------------------------------------------- special cases --
+
+def _altgdmin_lrccs(A, Y, r, T, c_eta=0.14):
+    """Independent AltGDmin for the S* = 0 problem (LRCCS) written from its
+    definition: spectral init from [A_k^T y_k], then b_k by least squares,
+    the U-gradient, a frozen step from the first gradient and a QR."""
+    q, m, n = A.shape
+    L0 = np.stack([A[k].T @ Y[k] for k in range(q)], axis=1)
+    U = np.linalg.svd(L0)[0][:, :r]
+    Xs = []
+    eta = None
+    for t in range(T):
+        B = np.stack([np.linalg.lstsq(A[k] @ U, Y[k], rcond=None)[0] for k in range(q)], axis=1)
+        G = sum(np.outer(A[k].T @ (A[k] @ (U @ B[:, k]) - Y[k]), B[:, k]) for k in range(q))
+        if eta is None:
+            eta = c_eta / np.linalg.norm(G, 2)
+        U = _gram_schmidt(U - eta * G)
+        Xs.append(U @ B)
+    return Xs
+
+
+def test_rho_zero_reduces_to_altgdmin_lrccs():
+    inst = GaussianInstance(n=30, q=25, r=2, m=12, rho=0, seed=21, y_float64=True)
+    A, Y = inst.A.astype(np.float64), inst.Y
+    T = 6
+    st, log = O.run_alg1(O.GaussianOperator(A), Y, 2, 0, T, keep=tuple(range(T + 1)))
+    ref = _altgdmin_lrccs(A, Y, 2, T)
+    for t in range(1, T + 1):
+        # X_t of the oracle is (U_t, B_t): the LRCCS loop logs U_{t} B_t too.
+        np.testing.assert_allclose(log.X[t], ref[t - 1], rtol=0, atol=1e-10 * np.abs(ref[t - 1]).max())
+    assert np.all(st.S == 0)
+
+
+def test_exact_recovery_tiny_noiseless_m_ge_n():
+    inst = GaussianInstance(n=16, q=16, r=2, m=20, rho=1, seed=22, y_float64=True)
+    st, log = O.run_alg1(O.GaussianOperator(inst.A), inst.Y, 2, 1, 300, Xstar=inst.Xstar)
+    assert log.err[-1] < 1e-12
+
+
+def test_exact_recovery_identity_operator_robust_pca_case():
+    inst = GaussianInstance(n=24, q=24, r=2, m=24, rho=1, seed=23, y_float64=True,
+                            identity_A=True)
+    st, log = O.run_alg1(O.GaussianOperator(inst.A), inst.Y, 2, 1, 260, Xstar=inst.Xstar)
+    assert log.err[-1] < 1e-10
+
+
+# ----------------------------------------------------------------- Fourier --
+
+def test_fourier_operator_equals_direct_dft_rows():
+    nx, ny, m = 8, 4, 11
+    g = rng(10)
+    masks = np.sort(g.choice(nx * ny, m, replace=False))[None]
+    op = O.FourierOperator(masks, nx, ny)
+    x = g.standard_normal(nx * ny) + 1j * g.standard_normal(nx * ny)
+    X = x.reshape(nx, ny)
+    direct = []
+    for row in masks[0]:
+        kx, ky = divmod(row, ny)
+        ph = np.exp(-2j * np.pi * (kx * np.arange(nx)[:, None] / nx + ky * np.arange(ny)[None, :] / ny))
+        direct.append(np.sum(X * ph) / np.sqrt(nx * ny))
+    np.testing.assert_allclose(op.A(x[None])[0], direct, atol=1e-12)
+    Aexp = op.explicit()[0]
+    np.testing.assert_allclose(Aexp @ Aexp.conj().T, np.eye(m), atol=1e-12)   # A A^H = I
+    v = g.standard_normal(m) + 1j * g.standard_normal(m)
+    np.testing.assert_allclose(op.AH(v[None])[0], Aexp.conj().T @ v, atol=1e-12)
+    full = O.FourierOperator(np.arange(nx * ny)[None], nx, ny)
+    assert abs(np.linalg.norm(full.A(x[None])) - np.linalg.norm(x)) < 1e-12   # Parseval
+
+
+def test_fourier_iteration_uses_same_algebra_as_explicit_matrices():
+    """One Fourier iteration (operator form) equals the same step done with the
+    explicit DFT-row matrices through the Gaussian (explicit-matrix) path."""
+    inst = FourierInstance(nx=4, ny=4, q=6, r=2, m=10, rho=2, seed=24, s_law="S1",
+                           mask_law="uniform", b_law="gauss")
+    opF = O.FourierOperator(inst.masks, 4, 4)
+    Y = inst.Y.astype(np.complex128)
+
+    class Explicit(O.GaussianOperator):
+        def __init__(self, M):
+            self.M = M
+            self.q, self.m, self.n = M.shape
+            self.complex = True
+
+        def subset(self, ks):
+            return Explicit(self.M[ks])
+
+        def AH(self, V):
+            return (V[:, None, :] @ self.M.conj())[:, 0, :]
+
+    opE = Explicit(opF.explicit())
+    st1, _, _, _ = O.init_alg1(opF, Y, 2, 2)
+    st2, _, _, _ = O.init_alg1(opE, Y, 2, 2)
+    np.testing.assert_allclose(st1.U @ st1.B, st2.U @ st2.B, atol=1e-10)
+    m1, g1 = O.iterate_alg1(opF, Y, st1, 2)
+    # the explicit path through iterate_alg1 forms M_k = A_k - W W^dagger A_k
+    m2, g2 = O.iterate_alg1(opE, Y, st2, 2)
+    np.testing.assert_allclose(st1.U @ st1.B + st1.S.T, st2.U @ st2.B + st2.S.T, atol=1e-9)
+
+
+# ------------------------------------------------------ paper-printed values --
+
+def _table1():
+    import os
+    rows = []
+    p = os.path.join(os.path.dirname(__file__), "golden", "table1_fourier_altgdmin_lps.txt")
+    for line in open(p):
+        if line.strip() and not line.startswith("#"):
+            m, e = line.split()
+            rows.append((int(m), float(e)))
+    return dict(rows)
+
+
+def test_table1_fourier_trend():
+    """Table 1 (Fourier, n = q = 400, r = 4, rho = 2, rho_max = 5, T = 10).
+
+    The paper's frame shape, mask law and Monte Carlo spread are not printed,
+    so this is a statistical pin on one seeded run (20 x 20 frames, uniform
+    random DFT rows): the error must fall from the m = 40 level to the small
+    values the table prints for m >= 150.
+    """
+    paper = _table1()
+    errs = {}
+    for m in (40, 150):
+        inst = FourierInstance(nx=20, ny=20, q=400, r=4, m=m, rho=2, seed=31, s_law="S1",
+                               mask_law="uniform", b_law="gauss")
+        _, log = O.run_alg1(O.FourierOperator(inst.masks, 20, 20), inst.Y, 4, 5, 10,
+                            Xstar=inst.Xstar)
+        errs[m] = log.err[-1]
+    assert errs[150] < 10 * max(paper[150], 1e-4)
+    assert errs[40] > 10 * errs[150]
+    assert errs[40] < 1.0
+
+
+@pytest.mark.slow
+def test_fig1_gaussian_converges_for_small_rho():
+    """Fig. 1: n = q = 600, m = 80, r = 4, rho = 2, rho_max = 7, S1 law (alpha = 6),
+    T = 200: the error reaches the floor set by the float32-stored y."""
+    inst = GaussianInstance(n=600, q=600, r=4, m=80, rho=2, seed=11, s_law="S1")
+    _, log = O.run_alg1(O.GaussianOperator(inst.A), inst.Y.astype(np.float64), 4, 7, 120,
+                        Xstar=inst.Xstar, chunk=200)
+    assert log.err[-1] < 1e-6
