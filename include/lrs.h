@@ -1,0 +1,181 @@
+/*
+ * lrs.h - C ABI of the GB300 AltGDmin-LR+S solver (liblrs.so).
+ *
+ * Problem (arXiv 2311.03824, Section I-A): recover the n x q matrix
+ * X* = L* + S*, L* = U* B* of rank r, S* with rho nonzeros per column, from
+ * per-column measurements y_k = A_k x*_k (k = 0..q-1), A_k m x n.  A_k is a
+ * dense Gaussian matrix or a row subset of the unitary 2D DFT (Section I-A,
+ * "random Fourier matrix"; Section I-A notes the 2D-DFT case of dynamic MRI).
+ * The solver runs Algorithm 1 (AltGDmin-L+S, Section II) with Algorithm 2
+ * (IHT, Section II-D) entirely in CUDA kernels on one GPU.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an lrs_status; nothing throws or aborts across the ABI.
+ *    lrs_last_error() returns a thread-local message for the last failure.
+ *  - Handle states: CREATED -> MEASURED (lrs_set_measurements) ->
+ *    INITIALISED (lrs_init) -> ITERATING (lrs_iterate).  A call made in the
+ *    wrong state returns LRS_ERR_STATE and changes nothing.
+ *  - The handle owns all device memory it allocates; lrs_destroy frees it.
+ *    Inputs are copied into the handle's own layout during the call that
+ *    receives them (host or device pointers); the caller may free them after
+ *    that call returns.  Outputs go to caller-owned buffers.
+ *  - All kernels run on the stream given in lrs_options.stream (a
+ *    cudaStream_t; NULL = the legacy default stream).  Calls that return host
+ *    data synchronise that stream.
+ *  - Matrices are column-major unless stated: "m x q column-major" means
+ *    element (i, k) at offset i + k*m, i.e. each column is contiguous.
+ */
+#ifndef LRS_H_
+#define LRS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lrs_ctx* lrs_t;
+
+typedef enum {
+  LRS_OK = 0,
+  LRS_ERR_ARG = 1,          /* invalid argument (sizes, pointers, options)     */
+  LRS_ERR_STATE = 2,        /* call made in the wrong handle state             */
+  LRS_ERR_OOM = 3,          /* device or host allocation failed                */
+  LRS_ERR_CUDA = 4,         /* a CUDA runtime call failed                      */
+  LRS_ERR_NUMERICAL = 5,    /* non-SPD r x r Gram (LS step / QR) or NaN/Inf    */
+  LRS_ERR_TIMEOUT = 6,      /* a bounded device wait or a request timed out    */
+  LRS_ERR_UNSUPPORTED = 7   /* valid input this build does not handle          */
+} lrs_status;
+
+typedef enum {
+  LRS_OP_GAUSSIAN = 0,      /* dense A_k, i.i.d. N(0,1) in the paper           */
+  LRS_OP_DFT2D_MASK = 1     /* A_k x = (F2 x)[Omega_k], F2 unitary 2D DFT      */
+} lrs_op_kind;
+
+typedef enum {
+  LRS_A_FP32 = 0,           /* A_k kept in float32 (the exact operator)        */
+  LRS_A_BF16 = 1,           /* A_k kept in bfloat16                            */
+  LRS_A_FP8_HI = 2,         /* e4m3 hi with one float32 scale per row          */
+  LRS_A_FP8_HILO = 3        /* e4m3 hi + e4m3 lo of the remainder, row scale   */
+} lrs_a_dtype;
+
+/* Options.  A zero-initialised struct selects the paper's defaults
+ * (Algorithm 1 and Section II-F): tau0 = 10, tau = 3, T = 200, c_eta = 0.14,
+ * rho_max = rho, float32 A_k. */
+typedef struct {
+  int32_t tau0;             /* IHT sweeps in the initialisation (0 -> 10)      */
+  int32_t tau;              /* IHT sweeps per GDmin iteration (0 -> 3)         */
+  int32_t T;                /* iterations run by lrs_solve (0 -> 200)          */
+  double c_eta;             /* eta = c_eta / ||grad_U f(U0,B1,S1)||_2 (0 -> 0.14) */
+  int32_t rho_max;          /* entries HardThreshold keeps (0 -> rho)          */
+  int32_t nx, ny;           /* DFT frame: n = nx*ny, both powers of two        */
+  lrs_a_dtype a_dtype;      /* storage of A_k for the sweeps                   */
+  int32_t refine_every;     /* low-precision A_k: exact-operator refinement of
+                               the residual every this many iterations (0 -> 1) */
+  int32_t cluster;          /* Gaussian sweep: CTAs per column (0 -> autotune) */
+  int32_t power_iters;      /* cap on subspace iterations in lrs_init (0 -> 300) */
+  double power_tol;         /* stop when ||(I - U_old U_old^T) U||_F < tol (0 -> 1e-6) */
+  int32_t use_graph;        /* 1: replay steady-state iterations as a CUDA graph */
+  void* stream;             /* cudaStream_t for every launch (NULL = default)  */
+  uint64_t seed;            /* seed of the subspace-iteration start            */
+  int32_t profile;          /* 1: time each phase of lrs_iterate with CUDA events */
+} lrs_options;
+
+/* Create a solver for one problem (Section I-A sizes).
+ * n, m, q >= 1; 1 <= r <= 16 and r <= min(m, n); 0 <= rho <= n; for
+ * LRS_OP_DFT2D_MASK, opt->nx * opt->ny == n with both powers of two (m may
+ * exceed n only for the Gaussian operator's special cases; for the DFT
+ * m <= n).  opt may be NULL (paper defaults).  On success *out holds a new
+ * handle in state CREATED.  Errors: LRS_ERR_ARG, LRS_ERR_OOM, LRS_ERR_CUDA. */
+lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho,
+                      lrs_op_kind kind, const lrs_options* opt, lrs_t* out);
+
+/* Give the measurements y_k and the operator (Section I-A: y_k = A_k x*_k).
+ *  y:         m x q column-major; float for GAUSSIAN, interleaved complex64
+ *             (re, im float pairs) for DFT2D_MASK.
+ *  A_or_mask: GAUSSIAN: q consecutive m x n row-major float blocks (A_k
+ *             element (i, j) at offset k*m*n + i*n + j).
+ *             DFT2D_MASK: q x m int32 row indices, column k (m consecutive
+ *             values) lists the kept DFT rows kx*ny + ky of frame k, each in
+ *             [0, n) and strictly ascending.
+ *  mem_kind:  0 = host pointers, 1 = device pointers.  Either way the data is
+ *             copied (and re-laid-out) before the call returns.
+ * State: CREATED or later (re-measuring resets the handle to MEASURED).
+ * Errors: LRS_ERR_ARG (NULL pointer, bad mem_kind, mask out of range or not
+ * ascending), LRS_ERR_STATE, LRS_ERR_OOM, LRS_ERR_CUDA. */
+lrs_status lrs_set_measurements(lrs_t h, const void* y, const void* A_or_mask,
+                                int32_t mem_kind);
+
+/* Initialisation of Algorithm 1: s_k = IHT(y_k, A_k, rho, tau0, 0),
+ * L0 = [A_k^T (y_k - A_k s_k)], U0 = top-r left singular subspace of L0
+ * (subspace iteration with Cholesky-QR2 to power_tol), b_k = (A_k U0)^+ (y_k -
+ * A_k s_k).  State: MEASURED or later -> INITIALISED.
+ * Errors: LRS_ERR_STATE, LRS_ERR_NUMERICAL (non-SPD Gram, NaN), LRS_ERR_CUDA. */
+lrs_status lrs_init(lrs_t h);
+
+/* Run `iters` GDmin iterations of Algorithm 1 (t continues from the last
+ * call): P_perp-projected IHT for s_k (tau sweeps), LS for b_k,
+ * grad = sum_k A_k^T (A_k(U b_k + s_k) - y_k) b_k^T, eta from the t = 1
+ * gradient (spectral norm), U <- Q(U - eta grad) by Cholesky-QR2.
+ * err_log: NULL, or a host array of `iters` doubles that receives
+ * ||X_t - X_ref||_F / ||X_ref||_F after each iteration (needs
+ * lrs_set_reference).  State: INITIALISED or ITERATING -> ITERATING.
+ * Errors: LRS_ERR_ARG (iters < 0, err_log without reference), LRS_ERR_STATE,
+ * LRS_ERR_NUMERICAL (column id in lrs_last_error), LRS_ERR_CUDA. */
+lrs_status lrs_iterate(lrs_t h, int32_t iters, double* err_log);
+
+/* lrs_init followed by lrs_iterate(h, T, NULL).  State: MEASURED or later. */
+lrs_status lrs_solve(lrs_t h);
+
+/* Copy out the current factors (Algorithm 1, Output: x_k = U b_k + s_k).
+ *  U:     n x r column-major (float, or complex64 for DFT2D_MASK), or NULL
+ *  B:     r x q column-major (same type), or NULL
+ *  S_idx: rho_max x q column-major int32, each column ascending, or NULL
+ *  S_val: rho_max x q column-major values matching S_idx, or NULL
+ * mem_kind: 0 = host buffers (the call synchronises the stream), 1 = device.
+ * State: INITIALISED or ITERATING.  Errors: LRS_ERR_STATE, LRS_ERR_ARG,
+ * LRS_ERR_CUDA. */
+lrs_status lrs_get(lrs_t h, void* U, void* B, int32_t* S_idx, void* S_val,
+                   int32_t mem_kind);
+
+/* Restore a state written by lrs_get (same layouts, host or device), so that
+ * a run can be resumed: t is the number of iterations already done and eta
+ * the frozen step size (ignored when t == 0).  State: MEASURED or later ->
+ * INITIALISED (t == 0) or ITERATING.  Errors: LRS_ERR_ARG, LRS_ERR_STATE,
+ * LRS_ERR_CUDA. */
+lrs_status lrs_set_state(lrs_t h, const void* U, const void* B,
+                         const int32_t* S_idx, const void* S_val, int32_t t,
+                         double eta, int32_t mem_kind);
+
+/* Frozen step size eta and the number of iterations done so far. */
+lrs_status lrs_get_progress(lrs_t h, double* eta, int32_t* t);
+
+/* Reference X* (n x q column-major, float or complex64, host or device) for
+ * the error log of lrs_iterate (Section III error metric
+ * ||X* - X||_F / ||X*||_F).  The data is copied.  Errors: LRS_ERR_ARG,
+ * LRS_ERR_STATE, LRS_ERR_OOM, LRS_ERR_CUDA. */
+lrs_status lrs_set_reference(lrs_t h, const void* Xref, int32_t mem_kind);
+
+/* Device time accumulated by lrs_iterate since the previous call, measured
+ * with CUDA events on the handle's stream when lrs_options.profile = 1
+ * (tracing aid; Algorithm 1 phases):
+ *   out[0] ms in the per-column sweep kernel (IHT, LS, gradient terms)
+ *   out[1] ms in the column reduction of the gradient
+ *   out[2] ms in the step size and Cholesky-QR2 of U
+ *   out[3] number of iterations timed
+ * The counters restart at zero after the call.  Errors: LRS_ERR_ARG,
+ * LRS_ERR_CUDA. */
+lrs_status lrs_phase_times(lrs_t h, double* out4);
+
+/* Release every resource of the handle (NULL is accepted). */
+lrs_status lrs_destroy(lrs_t h);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* lrs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LRS_H_ */

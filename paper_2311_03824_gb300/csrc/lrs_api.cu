@@ -1,0 +1,608 @@
+// C ABI of the solver (include/lrs.h): argument checks, the handle state
+// machine, device memory of one problem, and the launch sequence of
+// Algorithm 1 (initialisation, then GDmin iterations) on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lrs.h"
+#include "lrs_internal.h"
+
+using namespace lrs;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lrs_status fail(lrs_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define CUDA_TRY(expr)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      return fail(e_ == cudaErrorMemoryAllocation ? LRS_ERR_OOM : LRS_ERR_CUDA,     \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));              \
+    }                                                                               \
+  } while (0)
+
+enum State { kCreated = 0, kMeasured = 1, kInitialised = 2, kIterating = 3 };
+
+constexpr int kThreads = 256;
+
+}  // namespace
+
+struct lrs_ctx {
+  int64_t n = 0, m = 0, q = 0;
+  int r = 0, rho_true = 0, rho = 0;
+  lrs_op_kind kind = LRS_OP_GAUSSIAN;
+  lrs_options opt{};
+  cudaStream_t stream = nullptr;
+  State state = kCreated;
+  int t = 0;
+  GaussLayout L{};
+  int resident = 1;
+  // device buffers
+  float* A = nullptr;      // slab layout
+  float* y = nullptr;      // q x m
+  float* U = nullptr;      // n x r row-major
+  float* Bk = nullptr;     // q x r
+  int* S_idx = nullptr;    // q x rho
+  float* S_val = nullptr;  // q x rho
+  float* H = nullptr;      // q x n
+  float* grad = nullptr;   // n x r
+  float* Z = nullptr;      // n x r
+  float* U2 = nullptr;     // n x r (subspace iteration)
+  float* P = nullptr;      // q x r
+  double* part = nullptr;  // nblk x r x r
+  double* small = nullptr;
+  double* eta = nullptr;   // device scalar
+  int* err = nullptr;      // {code, column}
+  float* Xref = nullptr;   // q x n (error log)
+  double* errpart = nullptr;
+  int nblk = 0;
+  // graph of one steady-state iteration
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  // phase timing (profile = 1): 4 events per iteration
+  std::vector<cudaEvent_t> ev;
+  double phase_ms[3] = {0, 0, 0};
+  int64_t phase_iters = 0;
+};
+
+namespace {
+
+GlobalWork gw(lrs_ctx* h) {
+  GlobalWork g;
+  g.n = static_cast<int>(h->n);
+  g.q = static_cast<int>(h->q);
+  g.r = h->r;
+  g.grad = h->grad;
+  g.part = h->part;
+  g.small = h->small;
+  g.Z = h->Z;
+  g.nblk = h->nblk;
+  return g;
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Pick the cluster size (CTAs per column) and the slab shape.
+void choose_layout(lrs_ctx* h) {
+  int max_optin = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (max_optin <= 0) max_optin = 232448;
+  auto shape = [&](int cs) {
+    GaussLayout L{};
+    L.n = static_cast<int>(h->n);
+    L.m = static_cast<int>(h->m);
+    L.q = static_cast<int>(h->q);
+    L.r = h->r;
+    L.rho = h->rho;
+    L.cs = cs;
+    const int64_t w = (h->n + cs - 1) / cs;
+    L.ns = static_cast<int>((w + 3) / 4 * 4);
+    int pad = L.ns;
+    while (pad % 32 != 4) pad += 4;
+    L.ns_pad = pad;
+    return L;
+  };
+  auto valid = [&](const GaussLayout& L) {
+    return static_cast<int64_t>(L.cs - 1) * L.ns < h->n;
+  };
+  const int forced = h->opt.cluster;
+  const int cands[5] = {1, 2, 4, 8, 16};
+  if (forced > 0) {
+    h->L = shape(forced);
+    h->resident = sweep_smem_bytes(h->L, 1, kThreads) <= static_cast<size_t>(max_optin);
+    return;
+  }
+  // prefer >= 2 resident CTAs per SM, then any resident shape, else stream
+  for (int pass = 0; pass < 2; ++pass) {
+    const size_t lim = pass == 0 ? 112 * 1024 : static_cast<size_t>(max_optin);
+    for (int cs : cands) {
+      GaussLayout L = shape(cs);
+      if (!valid(L)) continue;
+      if (sweep_smem_bytes(L, 1, kThreads) <= lim) {
+        h->L = L;
+        h->resident = 1;
+        return;
+      }
+    }
+  }
+  GaussLayout L = shape(8);
+  if (!valid(L)) L = shape(1);
+  h->L = L;
+  h->resident = 0;
+}
+
+lrs_status check_device_error(lrs_ctx* h, const char* where) {
+  int e[2] = {0, 0};
+  CUDA_TRY(cudaMemcpyAsync(e, h->err, sizeof(e), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (e[0] == 0) return LRS_OK;
+  CUDA_TRY(cudaMemsetAsync(h->err, 0, 2 * sizeof(int), h->stream));
+  const char* what = e[0] == kErrNotSPD  ? "r x r Gram matrix not positive definite"
+                     : e[0] == kErrNaN   ? "NaN/Inf in the iteration"
+                     : e[0] == kErrTimeout ? "bounded device wait expired"
+                                           : "device error";
+  std::string msg = std::string(where) + ": " + what;
+  if (e[1] >= 0) msg += " (column " + std::to_string(e[1]) + ")";
+  return fail(e[0] == kErrTimeout ? LRS_ERR_TIMEOUT : LRS_ERR_NUMERICAL, msg);
+}
+
+lrs_status launch_sweep(lrs_ctx* h, int mode, int tau) {
+  SweepArgs a{};
+  a.L = h->L;
+  a.mode = mode;
+  a.tau = tau;
+  a.A = h->A;
+  a.y = h->y;
+  a.U = h->U;
+  a.S_idx = h->S_idx;
+  a.S_val = h->S_val;
+  a.B = h->Bk;
+  a.H = h->H;
+  a.err = h->err;
+  a.resident = h->resident;
+  CUDA_TRY(sweep_launch(a, kThreads, h->stream));
+  return LRS_OK;
+}
+
+// One GDmin iteration (Algorithm 1): sweep, gradient, eta at t = 1, QR.
+// With `evs` (4 events) the phase boundaries are recorded on the stream.
+lrs_status enqueue_iteration(lrs_ctx* h, bool first, cudaEvent_t* evs = nullptr) {
+  if (evs) CUDA_TRY(cudaEventRecord(evs[0], h->stream));
+  lrs_status st = launch_sweep(h, kModeIter, h->opt.tau);
+  if (st != LRS_OK) return st;
+  if (evs) CUDA_TRY(cudaEventRecord(evs[1], h->stream));
+  GlobalWork g = gw(h);
+  CUDA_TRY(grad_reduce(g, h->H, h->Bk, h->stream));
+  if (evs) CUDA_TRY(cudaEventRecord(evs[2], h->stream));
+  if (first) CUDA_TRY(eta_from_grad(g, h->opt.c_eta, h->eta, h->stream));
+  CUDA_TRY(qr_step(g, h->U, h->eta, h->err, h->stream));
+  if (evs) CUDA_TRY(cudaEventRecord(evs[3], h->stream));
+  return LRS_OK;
+}
+
+__global__ void err_kernel(int n, int q, int r, int rho, const float* U, const float* Bk,
+                           const int* S_idx, const float* S_val, const float* Xref,
+                           double* out) {
+  __shared__ double sd[8], sr[8];
+  const int k = blockIdx.x;
+  double d2 = 0.0, r2 = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    float x = 0.f;
+    for (int l = 0; l < r; ++l) x = fmaf(U[static_cast<size_t>(j) * r + l], Bk[static_cast<size_t>(k) * r + l], x);
+    for (int e = 0; e < rho; ++e)
+      if (S_idx[static_cast<size_t>(k) * rho + e] == j) x += S_val[static_cast<size_t>(k) * rho + e];
+    const double xr = Xref[static_cast<size_t>(k) * n + j];
+    d2 += (x - xr) * (x - xr);
+    r2 += xr * xr;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sd[threadIdx.x >> 5] = d2;
+    sr[threadIdx.x >> 5] = r2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += sd[w]; b += sr[w]; }
+    out[2 * k] = a;
+    out[2 * k + 1] = b;
+  }
+}
+
+lrs_status error_now(lrs_ctx* h, double* out) {
+  err_kernel<<<static_cast<unsigned>(h->q), 256, 0, h->stream>>>(
+      static_cast<int>(h->n), static_cast<int>(h->q), h->r, h->rho, h->U, h->Bk, h->S_idx,
+      h->S_val, h->Xref, h->errpart);
+  CUDA_TRY(cudaGetLastError());
+  std::vector<double> p(2 * h->q);
+  CUDA_TRY(cudaMemcpyAsync(p.data(), h->errpart, p.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  double a = 0, b = 0;
+  for (int64_t k = 0; k < h->q; ++k) { a += p[2 * k]; b += p[2 * k + 1]; }
+  *out = b > 0 ? std::sqrt(a / b) : 0.0;
+  return LRS_OK;
+}
+
+__global__ void transpose_kernel(const float* in, float* out, int rows, int cols) {
+  // out[c*rows + r] = in[r*cols + c]
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < rows * cols) {
+    const int rr = t / cols, cc = t - rr * cols;
+    out[static_cast<size_t>(cc) * rows + rr] = in[t];
+  }
+}
+
+// Deterministic start of the subspace iteration: splitmix64 + Box-Muller.
+std::vector<float> start_block(int64_t n, int r, uint64_t seed) {
+  std::vector<float> v(static_cast<size_t>(n) * r);
+  uint64_t s = seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+  auto next = [&]() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  for (size_t i = 0; i < v.size(); i += 2) {
+    const double u1 = ((next() >> 11) + 1.0) * 0x1.0p-53;
+    const double u2 = (next() >> 11) * 0x1.0p-53;
+    const double rad = std::sqrt(-2.0 * std::log(u1));
+    v[i] = static_cast<float>(rad * std::cos(6.283185307179586 * u2));
+    if (i + 1 < v.size()) v[i + 1] = static_cast<float>(rad * std::sin(6.283185307179586 * u2));
+  }
+  return v;
+}
+
+template <typename T>
+lrs_status dalloc(T** p, size_t count) {
+  if (count == 0) count = 1;
+  CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)));
+  return LRS_OK;
+}
+
+void free_all(lrs_ctx* h) {
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  h->ev.clear();
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->gexec = nullptr;
+  h->graph = nullptr;
+  void* ps[] = {h->A, h->y, h->U, h->Bk, h->S_idx, h->S_val, h->H, h->grad, h->Z,
+                h->U2, h->P, h->part, h->small, h->eta, h->err, h->Xref, h->errpart};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lrs_last_error(void) { return g_last_error.c_str(); }
+
+lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, lrs_op_kind kind,
+                      const lrs_options* opt, lrs_t* out) {
+  if (!out) return fail(LRS_ERR_ARG, "lrs_create: out is NULL");
+  *out = nullptr;
+  if (n < 1 || m < 1 || q < 1) return fail(LRS_ERR_ARG, "lrs_create: n, m, q must be >= 1");
+  if (r < 1 || r > 16 || r > std::min(m, n))
+    return fail(LRS_ERR_ARG, "lrs_create: need 1 <= r <= min(16, m, n)");
+  if (rho < 0 || rho > n) return fail(LRS_ERR_ARG, "lrs_create: need 0 <= rho <= n");
+  if (n >= (int64_t(1) << 30) || m >= (int64_t(1) << 30) || q >= (int64_t(1) << 30))
+    return fail(LRS_ERR_ARG, "lrs_create: sizes must be < 2^30");
+  if (kind != LRS_OP_GAUSSIAN && kind != LRS_OP_DFT2D_MASK)
+    return fail(LRS_ERR_ARG, "lrs_create: unknown operator kind");
+  lrs_options o{};
+  if (opt) o = *opt;
+  if (kind == LRS_OP_DFT2D_MASK) {
+    if (!is_pow2(o.nx) || !is_pow2(o.ny) || int64_t(o.nx) * o.ny != n)
+      return fail(LRS_ERR_ARG, "lrs_create: DFT frames need nx, ny powers of two, nx*ny = n");
+    if (m > n) return fail(LRS_ERR_ARG, "lrs_create: DFT needs m <= n");
+    return fail(LRS_ERR_UNSUPPORTED, "lrs_create: the DFT operator is not built into this library");
+  }
+  if (o.tau0 < 0 || o.tau < 0 || o.T < 0 || o.rho_max < 0 || o.c_eta < 0 || o.cluster < 0 ||
+      o.power_iters < 0 || o.refine_every < 0)
+    return fail(LRS_ERR_ARG, "lrs_create: negative option");
+  if (o.cluster != 0 && o.cluster != 1 && o.cluster != 2 && o.cluster != 4 && o.cluster != 8 &&
+      o.cluster != 16)
+    return fail(LRS_ERR_ARG, "lrs_create: cluster must be 0, 1, 2, 4, 8 or 16");
+  if (o.a_dtype != LRS_A_FP32)
+    return fail(LRS_ERR_UNSUPPORTED, "lrs_create: only float32 A_k storage is built in");
+  if (o.tau0 == 0) o.tau0 = 10;
+  if (o.tau == 0) o.tau = 3;
+  if (o.T == 0) o.T = 200;
+  if (o.c_eta == 0) o.c_eta = 0.14;
+  if (o.rho_max == 0) o.rho_max = rho;
+  if (o.rho_max > n) return fail(LRS_ERR_ARG, "lrs_create: rho_max > n");
+  if (o.power_iters == 0) o.power_iters = 300;
+  if (o.power_tol == 0) o.power_tol = 1e-6;
+  if (o.refine_every == 0) o.refine_every = 1;
+
+  lrs_ctx* h = new lrs_ctx();
+  h->n = n;
+  h->m = m;
+  h->q = q;
+  h->r = r;
+  h->rho_true = rho;
+  h->rho = o.rho_max;
+  h->kind = kind;
+  h->opt = o;
+  h->stream = static_cast<cudaStream_t>(o.stream);
+  choose_layout(h);
+  if (o.cluster > 0 && (int64_t(h->L.cs) - 1) * h->L.ns >= n) {
+    delete h;
+    return fail(LRS_ERR_ARG, "lrs_create: cluster size too large for n");
+  }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  h->nblk = std::max(1, std::min<int>(nsm > 0 ? nsm : 148, static_cast<int>((n + 63) / 64)));
+  const size_t per_col = static_cast<size_t>(h->L.cs) * h->L.m * h->L.ns_pad;
+  lrs_status st = LRS_OK;
+  if ((st = dalloc(&h->A, per_col * q)) || (st = dalloc(&h->y, size_t(m) * q)) ||
+      (st = dalloc(&h->U, size_t(n) * r)) || (st = dalloc(&h->Bk, size_t(q) * r)) ||
+      (st = dalloc(&h->S_idx, size_t(q) * h->rho)) || (st = dalloc(&h->S_val, size_t(q) * h->rho)) ||
+      (st = dalloc(&h->H, size_t(q) * n)) || (st = dalloc(&h->grad, size_t(n) * r)) ||
+      (st = dalloc(&h->Z, size_t(n) * r)) || (st = dalloc(&h->U2, size_t(n) * r)) ||
+      (st = dalloc(&h->P, size_t(q) * r)) || (st = dalloc(&h->part, size_t(h->nblk) * r * r)) ||
+      (st = dalloc(&h->small, 4 * 16 * 16 + 64)) || (st = dalloc(&h->eta, 1)) ||
+      (st = dalloc(&h->err, 2)) || (st = dalloc(&h->errpart, 2 * size_t(q)))) {
+    std::string msg = g_last_error;
+    free_all(h);
+    delete h;
+    return fail(st, "lrs_create: " + msg);
+  }
+  cudaError_t e = sweep_prepare(h->L, kThreads);
+  if (e == cudaSuccess) e = cudaMemset(h->err, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->S_idx, 0, sizeof(int) * size_t(q) * std::max(1, h->rho));
+  if (e == cudaSuccess) e = cudaMemset(h->S_val, 0, sizeof(float) * size_t(q) * std::max(1, h->rho));
+  if (e != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return fail(LRS_ERR_CUDA, std::string("lrs_create: ") + cudaGetErrorString(e));
+  }
+  if (sweep_max_active_clusters(h->L, h->resident, kThreads) <= 0) {
+    free_all(h);
+    delete h;
+    return fail(LRS_ERR_UNSUPPORTED, "lrs_create: sweep kernel shape cannot be scheduled");
+  }
+  *out = h;
+  return LRS_OK;
+}
+
+lrs_status lrs_set_measurements(lrs_t h, const void* y, const void* A_or_mask, int32_t mem_kind) {
+  if (!h || !y || !A_or_mask) return fail(LRS_ERR_ARG, "lrs_set_measurements: NULL argument");
+  if (mem_kind != 0 && mem_kind != 1)
+    return fail(LRS_ERR_ARG, "lrs_set_measurements: mem_kind must be 0 or 1");
+  const cudaMemcpyKind kin = mem_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CUDA_TRY(cudaMemcpyAsync(h->y, y, sizeof(float) * h->m * h->q, kin, h->stream));
+  // A: row-major blocks -> slab layout, in chunks of columns
+  const size_t col_elems = static_cast<size_t>(h->m) * h->n;
+  int64_t chunk = std::max<int64_t>(1, (int64_t(256) << 20) / (int64_t)(col_elems * 4));
+  chunk = std::min<int64_t>(chunk, h->q);
+  float* tmp = nullptr;
+  if (mem_kind == 0) CUDA_TRY(cudaMalloc(&tmp, sizeof(float) * col_elems * chunk));
+  for (int64_t k0 = 0; k0 < h->q; k0 += chunk) {
+    const int64_t kc = std::min(chunk, h->q - k0);
+    const float* src = static_cast<const float*>(A_or_mask) + k0 * col_elems;
+    if (mem_kind == 0) {
+      cudaError_t e = cudaMemcpyAsync(tmp, src, sizeof(float) * col_elems * kc,
+                                      cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = repack_gauss(h->L, tmp, static_cast<int>(k0), static_cast<int>(kc), h->A, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) {
+        cudaFree(tmp);
+        return fail(LRS_ERR_CUDA, std::string("lrs_set_measurements: ") + cudaGetErrorString(e));
+      }
+    } else {
+      CUDA_TRY(repack_gauss(h->L, src, static_cast<int>(k0), static_cast<int>(kc), h->A, h->stream));
+    }
+  }
+  if (tmp) cudaFree(tmp);
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  h->state = kMeasured;
+  h->t = 0;
+  return LRS_OK;
+}
+
+lrs_status lrs_init(lrs_t h) {
+  if (!h) return fail(LRS_ERR_ARG, "lrs_init: NULL handle");
+  if (h->state < kMeasured) return fail(LRS_ERR_STATE, "lrs_init: no measurements");
+  GlobalWork g = gw(h);
+  // s_k = IHT(y_k, A_k, rho, tau0, 0); L0 column k = A_k^T (y_k - A_k s_k) -> H
+  lrs_status st = launch_sweep(h, kModeInit, h->opt.tau0);
+  if (st) return st;
+  // U0: top-r left singular subspace of L0 (= H^T) by subspace iteration
+  std::vector<float> U0 = start_block(h->n, h->r, h->opt.seed + 1);
+  CUDA_TRY(cudaMemcpyAsync(h->U2, U0.data(), sizeof(float) * U0.size(), cudaMemcpyHostToDevice,
+                           h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  CUDA_TRY(cholqr2(g, h->U2, h->U, h->err, h->stream));
+  double* D = h->small + 2 * 16 * 16;
+  const int r = h->r;
+  for (int it = 0; it < h->opt.power_iters; ++it) {
+    CUDA_TRY(project_cols(g, h->H, h->U, h->P, h->stream));      // P = L0^T U
+    CUDA_TRY(grad_reduce(g, h->H, h->P, h->stream));             // grad = L0 P
+    CUDA_TRY(cudaMemcpyAsync(h->U2, h->U, sizeof(float) * h->n * r, cudaMemcpyDeviceToDevice,
+                             h->stream));
+    CUDA_TRY(cholqr2(g, h->grad, h->U, h->err, h->stream));      // U = Q(L0 L0^T U)
+    if ((it % 5) == 4 || it + 1 == h->opt.power_iters) {
+      // subspace change ||(I - U_old U_old^T) U||_F
+      CUDA_TRY(subspace_change(g, h->U2, h->U, D, D + 16 * 16, h->stream));
+      double chg2 = 0.0;
+      CUDA_TRY(cudaMemcpyAsync(&chg2, D + 16 * 16, sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
+      CUDA_TRY(cudaStreamSynchronize(h->stream));
+      if (std::sqrt(std::max(0.0, chg2)) < h->opt.power_tol) break;
+    }
+  }
+  // b_k = (A_k U0)^+ (y_k - A_k s_k)
+  st = launch_sweep(h, kModeLS, 0);
+  if (st) return st;
+  st = check_device_error(h, "lrs_init");
+  if (st) return st;
+  h->state = kInitialised;
+  h->t = 0;
+  return LRS_OK;
+}
+
+lrs_status lrs_iterate(lrs_t h, int32_t iters, double* err_log) {
+  if (!h) return fail(LRS_ERR_ARG, "lrs_iterate: NULL handle");
+  if (iters < 0) return fail(LRS_ERR_ARG, "lrs_iterate: iters < 0");
+  if (h->state < kInitialised) return fail(LRS_ERR_STATE, "lrs_iterate: call lrs_init first");
+  if (err_log && !h->Xref) return fail(LRS_ERR_ARG, "lrs_iterate: err_log needs lrs_set_reference");
+  const bool prof = h->opt.profile != 0;
+  if (prof) {
+    while (h->ev.size() < 4 * static_cast<size_t>(iters)) {
+      cudaEvent_t e;
+      CUDA_TRY(cudaEventCreate(&e));
+      h->ev.push_back(e);
+    }
+  }
+  for (int i = 0; i < iters; ++i) {
+    const bool first = (h->t == 0);
+    cudaEvent_t* evs = prof ? &h->ev[4 * static_cast<size_t>(i)] : nullptr;
+    if (!first && h->opt.use_graph && h->stream && !prof) {
+      if (!h->gexec) {
+        CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        lrs_status st = enqueue_iteration(h, false);
+        cudaGraph_t gph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->stream, &gph);
+        if (st) return st;
+        CUDA_TRY(e);
+        h->graph = gph;
+        CUDA_TRY(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+      }
+      CUDA_TRY(cudaGraphLaunch(h->gexec, h->stream));
+    } else {
+      lrs_status st = enqueue_iteration(h, first, evs);
+      if (st) return st;
+    }
+    h->t += 1;
+    if (err_log) {
+      lrs_status st = error_now(h, &err_log[i]);
+      if (st) return st;
+    }
+  }
+  h->state = kIterating;
+  if (prof && iters > 0) {
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < iters; ++i) {
+      float a = 0, b = 0, c = 0;
+      cudaEvent_t* evs = &h->ev[4 * static_cast<size_t>(i)];
+      CUDA_TRY(cudaEventElapsedTime(&a, evs[0], evs[1]));
+      CUDA_TRY(cudaEventElapsedTime(&b, evs[1], evs[2]));
+      CUDA_TRY(cudaEventElapsedTime(&c, evs[2], evs[3]));
+      h->phase_ms[0] += a;
+      h->phase_ms[1] += b;
+      h->phase_ms[2] += c;
+    }
+    h->phase_iters += iters;
+  }
+  return check_device_error(h, "lrs_iterate");
+}
+
+lrs_status lrs_solve(lrs_t h) {
+  lrs_status st = lrs_init(h);
+  if (st) return st;
+  return lrs_iterate(h, h->opt.T, nullptr);
+}
+
+lrs_status lrs_get(lrs_t h, void* U, void* B, int32_t* S_idx, void* S_val, int32_t mem_kind) {
+  if (!h) return fail(LRS_ERR_ARG, "lrs_get: NULL handle");
+  if (mem_kind != 0 && mem_kind != 1) return fail(LRS_ERR_ARG, "lrs_get: mem_kind must be 0 or 1");
+  if (h->state < kInitialised) return fail(LRS_ERR_STATE, "lrs_get: no iterate yet");
+  const cudaMemcpyKind kout = mem_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (U) {
+    const int tot = static_cast<int>(h->n) * h->r;
+    transpose_kernel<<<(tot + 255) / 256, 256, 0, h->stream>>>(h->U, h->Z, static_cast<int>(h->n), h->r);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(U, h->Z, sizeof(float) * tot, kout, h->stream));
+  }
+  if (B) CUDA_TRY(cudaMemcpyAsync(B, h->Bk, sizeof(float) * h->q * h->r, kout, h->stream));
+  if (S_idx && h->rho)
+    CUDA_TRY(cudaMemcpyAsync(S_idx, h->S_idx, sizeof(int) * h->q * h->rho, kout, h->stream));
+  if (S_val && h->rho)
+    CUDA_TRY(cudaMemcpyAsync(S_val, h->S_val, sizeof(float) * h->q * h->rho, kout, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return LRS_OK;
+}
+
+lrs_status lrs_set_state(lrs_t h, const void* U, const void* B, const int32_t* S_idx,
+                         const void* S_val, int32_t t, double eta, int32_t mem_kind) {
+  if (!h || !U || !B || (h->rho && (!S_idx || !S_val)))
+    return fail(LRS_ERR_ARG, "lrs_set_state: NULL argument");
+  if (mem_kind != 0 && mem_kind != 1) return fail(LRS_ERR_ARG, "lrs_set_state: bad mem_kind");
+  if (t < 0) return fail(LRS_ERR_ARG, "lrs_set_state: t < 0");
+  if (h->state < kMeasured) return fail(LRS_ERR_STATE, "lrs_set_state: no measurements");
+  const cudaMemcpyKind kin = mem_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const int tot = static_cast<int>(h->n) * h->r;
+  CUDA_TRY(cudaMemcpyAsync(h->Z, U, sizeof(float) * tot, kin, h->stream));
+  transpose_kernel<<<(tot + 255) / 256, 256, 0, h->stream>>>(h->Z, h->U, h->r, static_cast<int>(h->n));
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(h->Bk, B, sizeof(float) * h->q * h->r, kin, h->stream));
+  if (h->rho) {
+    CUDA_TRY(cudaMemcpyAsync(h->S_idx, S_idx, sizeof(int) * h->q * h->rho, kin, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->S_val, S_val, sizeof(float) * h->q * h->rho, kin, h->stream));
+  }
+  CUDA_TRY(cudaMemcpyAsync(h->eta, &eta, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  h->t = t;
+  h->state = t == 0 ? kInitialised : kIterating;
+  return LRS_OK;
+}
+
+lrs_status lrs_get_progress(lrs_t h, double* eta, int32_t* t) {
+  if (!h) return fail(LRS_ERR_ARG, "lrs_get_progress: NULL handle");
+  if (eta) {
+    CUDA_TRY(cudaMemcpyAsync(eta, h->eta, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (h->t == 0) *eta = 0.0;
+  }
+  if (t) *t = h->t;
+  return LRS_OK;
+}
+
+lrs_status lrs_set_reference(lrs_t h, const void* Xref, int32_t mem_kind) {
+  if (!h || !Xref) return fail(LRS_ERR_ARG, "lrs_set_reference: NULL argument");
+  if (mem_kind != 0 && mem_kind != 1) return fail(LRS_ERR_ARG, "lrs_set_reference: bad mem_kind");
+  if (!h->Xref) CUDA_TRY(cudaMalloc(&h->Xref, sizeof(float) * h->n * h->q));
+  CUDA_TRY(cudaMemcpyAsync(h->Xref, Xref, sizeof(float) * h->n * h->q,
+                           mem_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return LRS_OK;
+}
+
+lrs_status lrs_phase_times(lrs_t h, double* out4) {
+  if (!h || !out4) return fail(LRS_ERR_ARG, "lrs_phase_times: NULL argument");
+  for (int i = 0; i < 3; ++i) out4[i] = h->phase_ms[i];
+  out4[3] = static_cast<double>(h->phase_iters);
+  h->phase_ms[0] = h->phase_ms[1] = h->phase_ms[2] = 0;
+  h->phase_iters = 0;
+  return LRS_OK;
+}
+
+lrs_status lrs_destroy(lrs_t h) {
+  if (!h) return LRS_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+  return LRS_OK;
+}
+
+}  // extern "C"

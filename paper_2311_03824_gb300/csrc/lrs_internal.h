@@ -1,0 +1,79 @@
+// Internal interfaces between the C ABI driver (lrs_api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace lrs {
+
+// Error codes written to the device error word {code, column} (first writer wins).
+enum : int { kErrNone = 0, kErrNotSPD = 1, kErrNaN = 2, kErrTimeout = 3 };
+
+// Sweep modes of the per-column kernel (Algorithm 1).
+enum SweepMode : int {
+  kModeInit = 0,  // IHT(y_k, A_k, rho, tau0, 0) then L0 column A_k^T(y_k - A_k s_k)
+  kModeLS = 1,    // b_k = (A_k U)^+ (y_k - A_k s_k) with the current s_k
+  kModeIter = 2   // one GDmin iteration's per-column work (lines z_k .. gradient term)
+};
+
+// Layout of the Gaussian operator inside the handle ("slab" layout): column k's
+// A_k is split by columns j into `cs` slabs of `ns` columns; slab c holds
+// columns [c*ns, min(n, (c+1)*ns)) as an m x ns_pad row-major block,
+// zero-padded, and slabs of one column are consecutive:
+//   A_int[((k*cs + c)*m + i)*ns_pad + jj] = A_k(i, c*ns + jj).
+struct GaussLayout {
+  int n, m, q, r, rho;
+  int cs;      // CTAs per column (thread-block cluster size)
+  int ns;      // slab width (multiple of 4)
+  int ns_pad;  // padded row length (>= ns, = 4 mod 32, multiple of 4)
+};
+
+struct SweepArgs {
+  GaussLayout L;
+  int mode;
+  int tau;
+  const float* A;   // slab layout
+  const float* y;   // q x m (y_k contiguous)
+  const float* U;   // n x r row-major
+  int* S_idx;       // q x rho (ascending per column), in/out
+  float* S_val;     // q x rho
+  float* B;         // q x r (b_k contiguous)
+  float* H;         // q x n: ITER: h_k = A_k^T(W b + A s - y); INIT: L0 column
+  int* err;         // device error word pair {code, column}
+  int resident;     // 1: slab staged in shared memory by TMA; 0: read from global
+};
+
+// Sweep kernel (sweep_gauss.cu).
+size_t sweep_smem_bytes(const GaussLayout& L, int resident, int nthreads);
+cudaError_t sweep_launch(const SweepArgs& a, int nthreads, cudaStream_t s);
+cudaError_t sweep_prepare(const GaussLayout& L, int nthreads);  // set attributes
+int sweep_max_active_clusters(const GaussLayout& L, int resident, int nthreads);
+cudaError_t repack_gauss(const GaussLayout& L, const float* A_rowmajor, int k0, int kc,
+                         float* A_int, cudaStream_t s);
+
+// Global (column-reduced) steps (global_ops.cu).
+struct GlobalWork {
+  int n, q, r;
+  float* grad;       // n x r row-major
+  double* part;      // partial r x r FP64 Grams: nblk x (r*r)
+  double* small;     // scratch: [0,r*r) Rinv1, [r*r,2r*r) Rinv2, [2r*r] eta, ...
+  float* Z;          // n x r scratch (U - eta grad, Q1)
+  int nblk;          // blocks of the row-parallel kernels
+};
+cudaError_t grad_reduce(const GlobalWork& g, const float* H, const float* Bk, cudaStream_t s);
+cudaError_t eta_from_grad(const GlobalWork& g, double c_eta, double* eta_dev, cudaStream_t s);
+cudaError_t qr_step(const GlobalWork& g, float* U, const double* eta_dev, int* err,
+                    cudaStream_t s);
+cudaError_t cholqr2(const GlobalWork& g, const float* Zin, float* Uout, int* err,
+                    cudaStream_t s);
+cudaError_t project_cols(const GlobalWork& g, const float* H, const float* U, float* P,
+                         cudaStream_t s);  // P(q x r) = H U  (H: q x n)
+// ||(I - Uold Uold^T) Unew||_F^2 (FP64) into *out, D = Uold^T Unew into D_rr.
+cudaError_t subspace_change(const GlobalWork& g, const float* Uold, const float* Unew,
+                            double* D_rr, double* out, cudaStream_t s);
+cudaError_t subspace_overlap(const GlobalWork& g, const float* Ua, const float* Ub,
+                             double* out_rr, cudaStream_t s);
+
+}  // namespace lrs

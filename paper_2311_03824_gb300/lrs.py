@@ -1,0 +1,233 @@
+"""Python binding of liblrs.so (include/lrs.h), by ctypes.
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  Host arrays are numpy arrays; device arrays are torch CUDA
+tensors (PyTorch supplies device memory and streams).  The functions carry
+the C names; `Solver` is a small convenience wrapper over them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblrs.so")
+
+LRS_OK, LRS_ERR_ARG, LRS_ERR_STATE, LRS_ERR_OOM, LRS_ERR_CUDA, LRS_ERR_NUMERICAL, \
+    LRS_ERR_TIMEOUT, LRS_ERR_UNSUPPORTED = range(8)
+STATUS_NAMES = ["LRS_OK", "LRS_ERR_ARG", "LRS_ERR_STATE", "LRS_ERR_OOM", "LRS_ERR_CUDA",
+                "LRS_ERR_NUMERICAL", "LRS_ERR_TIMEOUT", "LRS_ERR_UNSUPPORTED"]
+LRS_OP_GAUSSIAN, LRS_OP_DFT2D_MASK = 0, 1
+LRS_A_FP32, LRS_A_BF16, LRS_A_FP8_HI, LRS_A_FP8_HILO = 0, 1, 2, 3
+
+
+class LrsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class lrs_options(ctypes.Structure):
+    _fields_ = [("tau0", ctypes.c_int32), ("tau", ctypes.c_int32), ("T", ctypes.c_int32),
+                ("c_eta", ctypes.c_double), ("rho_max", ctypes.c_int32),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("a_dtype", ctypes.c_int32),
+                ("refine_every", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("power_iters", ctypes.c_int32), ("power_tol", ctypes.c_double),
+                ("use_graph", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("seed", ctypes.c_uint64), ("profile", ctypes.c_int32)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib():
+    """Load liblrs.so (fails loudly when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_2311_03824_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "lrs_create": [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                           ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(lrs_options),
+                           ctypes.POINTER(_P)],
+            "lrs_set_measurements": [_P, _P, _P, ctypes.c_int32],
+            "lrs_init": [_P],
+            "lrs_iterate": [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)],
+            "lrs_solve": [_P],
+            "lrs_get": [_P, _P, _P, _P, _P, ctypes.c_int32],
+            "lrs_set_state": [_P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_double,
+                              ctypes.c_int32],
+            "lrs_get_progress": [_P, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_int32)],
+            "lrs_set_reference": [_P, _P, ctypes.c_int32],
+            "lrs_phase_times": [_P, ctypes.POINTER(ctypes.c_double)],
+            "lrs_destroy": [_P],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.lrs_last_error.argtypes = []
+        L.lrs_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != LRS_OK:
+        raise LrsError(st, lib().lrs_last_error().decode())
+
+
+def _ptr(x):
+    """(pointer, mem_kind) of a numpy array (host, 0) or torch CUDA tensor (1)."""
+    if x is None:
+        return None, 0
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return x.ctypes.data_as(_P), 0
+    if hasattr(x, "data_ptr") and getattr(x, "is_cuda", False):
+        if not x.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return _P(x.data_ptr()), 1
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _same_kind(*bufs):
+    kinds = {_ptr(b)[1] for b in bufs if b is not None}
+    if len(kinds) > 1:
+        raise ValueError("mix of host and device buffers in one call")
+    return kinds.pop() if kinds else 0
+
+
+def make_options(**kw):
+    o = lrs_options()
+    for k, v in kw.items():
+        if k == "stream" and v is not None and not isinstance(v, int):
+            v = v.cuda_stream           # torch.cuda.Stream
+        setattr(o, k, v if v is not None else 0)
+    return o
+
+
+# ----------------------------------------------------------- C-name calls --
+
+def lrs_create(n, m, q, r, rho, kind=LRS_OP_GAUSSIAN, options=None):
+    h = _P()
+    _check(lib().lrs_create(n, m, q, r, rho, kind,
+                            ctypes.byref(options) if options is not None else None,
+                            ctypes.byref(h)))
+    return h
+
+
+def lrs_set_measurements(h, y, A_or_mask):
+    mk = _same_kind(y, A_or_mask)
+    _check(lib().lrs_set_measurements(h, _ptr(y)[0], _ptr(A_or_mask)[0], mk))
+
+
+def lrs_init(h):
+    _check(lib().lrs_init(h))
+
+
+def lrs_iterate(h, iters, err_log=None):
+    buf = None
+    if err_log is not None:
+        buf = (ctypes.c_double * iters)()
+    _check(lib().lrs_iterate(h, iters, buf))
+    if err_log is not None:
+        err_log[:] = list(buf)
+
+
+def lrs_solve(h):
+    _check(lib().lrs_solve(h))
+
+
+def lrs_get(h, U=None, B=None, S_idx=None, S_val=None):
+    mk = _same_kind(U, B, S_idx, S_val)
+    _check(lib().lrs_get(h, _ptr(U)[0], _ptr(B)[0], _ptr(S_idx)[0], _ptr(S_val)[0], mk))
+
+
+def lrs_set_state(h, U, B, S_idx, S_val, t, eta):
+    mk = _same_kind(U, B, S_idx, S_val)
+    _check(lib().lrs_set_state(h, _ptr(U)[0], _ptr(B)[0], _ptr(S_idx)[0], _ptr(S_val)[0],
+                               t, eta, mk))
+
+
+def lrs_get_progress(h):
+    eta = ctypes.c_double()
+    t = ctypes.c_int32()
+    _check(lib().lrs_get_progress(h, ctypes.byref(eta), ctypes.byref(t)))
+    return eta.value, t.value
+
+
+def lrs_set_reference(h, Xref):
+    _check(lib().lrs_set_reference(h, _ptr(Xref)[0], _ptr(Xref)[1]))
+
+
+def lrs_phase_times(h):
+    out = (ctypes.c_double * 4)()
+    _check(lib().lrs_phase_times(h, out))
+    return {"sweep_ms": out[0], "grad_ms": out[1], "qr_ms": out[2], "iters": int(out[3])}
+
+
+def lrs_destroy(h):
+    _check(lib().lrs_destroy(h))
+
+
+def lrs_last_error():
+    return lib().lrs_last_error().decode()
+
+
+# --------------------------------------------------------------- wrapper --
+
+class Solver:
+    """One problem: A (q, m, n) float32 and Y (q, m) float32 (rows = columns k)."""
+
+    def __init__(self, n, m, q, r, rho, kind=LRS_OP_GAUSSIAN, **opts):
+        self.n, self.m, self.q, self.r = n, m, q, r
+        self.opts = make_options(**opts)
+        self.rho = self.opts.rho_max or rho
+        self.h = lrs_create(n, m, q, r, rho, kind, self.opts)
+
+    def set_measurements(self, Y, A):
+        lrs_set_measurements(self.h, Y, A)
+
+    def init(self):
+        lrs_init(self.h)
+
+    def iterate(self, iters=1, err_log=None):
+        lrs_iterate(self.h, iters, err_log)
+
+    def get(self):
+        """Host copies: U (n, r), B (r, q), S_idx (q, rho), S_val (q, rho)."""
+        U = np.empty((self.r, self.n), np.float32)      # n x r column-major
+        B = np.empty((self.q, self.r), np.float32)      # r x q column-major
+        S_idx = np.empty((self.q, max(self.rho, 1)), np.int32)
+        S_val = np.empty((self.q, max(self.rho, 1)), np.float32)
+        lrs_get(self.h, U, B, S_idx if self.rho else None, S_val if self.rho else None)
+        return U.T.copy(), B.T.copy(), S_idx[:, :self.rho], S_val[:, :self.rho]
+
+    def X(self):
+        U, B, S_idx, S_val = self.get()
+        X = U.astype(np.float64) @ B.astype(np.float64)
+        for k in range(self.q):
+            X[S_idx[k], k] += S_val[k]
+        return X
+
+    def progress(self):
+        return lrs_get_progress(self.h)
+
+    def close(self):
+        if self.h:
+            lrs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
