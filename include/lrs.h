@@ -168,6 +168,11 @@ lrs_status lrs_set_reference(lrs_t h, const void* Xref, int32_t mem_kind);
  * LRS_ERR_CUDA. */
 lrs_status lrs_phase_times(lrs_t h, double* out4);
 
+/* Write a one-line description of the handle's launch shape (operator,
+ * CTAs per column, slab width, shared memory per CTA, resident clusters) into
+ * buf (NUL-terminated, truncated to len bytes).  Errors: LRS_ERR_ARG. */
+lrs_status lrs_describe(lrs_t h, char* buf, int32_t len);
+
 /* Release every resource of the handle (NULL is accepted). */
 lrs_status lrs_destroy(lrs_t h);
 

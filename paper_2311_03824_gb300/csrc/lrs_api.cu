@@ -597,6 +597,18 @@ lrs_status lrs_phase_times(lrs_t h, double* out4) {
   return LRS_OK;
 }
 
+lrs_status lrs_describe(lrs_t h, char* buf, int32_t len) {
+  if (!h || !buf || len <= 0) return fail(LRS_ERR_ARG, "lrs_describe: bad argument");
+  const size_t sm = sweep_smem_bytes(h->L, h->resident, kThreads);
+  const int nc = sweep_max_active_clusters(h->L, h->resident, kThreads);
+  snprintf(buf, static_cast<size_t>(len),
+           "{\"op\": \"%s\", \"cluster\": %d, \"ns\": %d, \"ns_pad\": %d, \"resident\": %d, "
+           "\"smem_per_cta\": %zu, \"max_active_clusters\": %d, \"threads\": %d}",
+           h->kind == LRS_OP_GAUSSIAN ? "gaussian" : "dft2d", h->L.cs, h->L.ns, h->L.ns_pad,
+           h->resident, sm, nc, kThreads);
+  return LRS_OK;
+}
+
 lrs_status lrs_destroy(lrs_t h) {
   if (!h) return LRS_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);

@@ -66,6 +66,7 @@ def lib():
                                  ctypes.POINTER(ctypes.c_int32)],
             "lrs_set_reference": [_P, _P, ctypes.c_int32],
             "lrs_phase_times": [_P, ctypes.POINTER(ctypes.c_double)],
+            "lrs_describe": [_P, ctypes.c_char_p, ctypes.c_int32],
             "lrs_destroy": [_P],
         }
         for name, args in sig.items():
@@ -172,6 +173,13 @@ def lrs_phase_times(h):
     out = (ctypes.c_double * 4)()
     _check(lib().lrs_phase_times(h, out))
     return {"sweep_ms": out[0], "grad_ms": out[1], "qr_ms": out[2], "iters": int(out[3])}
+
+
+def lrs_describe(h):
+    buf = ctypes.create_string_buffer(512)
+    _check(lib().lrs_describe(h, buf, 512))
+    import json
+    return json.loads(buf.value.decode())
 
 
 def lrs_destroy(h):
