@@ -80,6 +80,9 @@ typedef struct {
   void* stream;             /* cudaStream_t for every launch (NULL = default)  */
   uint64_t seed;            /* seed of the subspace-iteration start            */
   int32_t profile;          /* 1: time each phase of lrs_iterate with CUDA events */
+  int32_t slab_mode;        /* Gaussian sweep: 0 auto, 1 slab resident in shared
+                               memory, 2 slab streamed through a tile ring   */
+  int32_t stages;           /* tile stages of the streamed ring (0 -> auto)    */
 } lrs_options;
 
 /* Create a solver for one problem (Section I-A sizes).

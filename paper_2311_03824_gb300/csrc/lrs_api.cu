@@ -94,53 +94,64 @@ GlobalWork gw(lrs_ctx* h) {
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
-// Pick the cluster size (CTAs per column) and the slab shape.
-void choose_layout(lrs_ctx* h) {
+GaussLayout gauss_shape(const lrs_ctx* h, int cs, int stages) {
+  GaussLayout L{};
+  L.n = static_cast<int>(h->n);
+  L.m = static_cast<int>(h->m);
+  L.q = static_cast<int>(h->q);
+  L.r = h->r;
+  L.rho = h->rho;
+  L.cs = cs;
+  const int64_t w = (h->n + cs - 1) / cs;
+  L.ns = static_cast<int>((w + 31) / 32 * 32);
+  L.stages = stages;
+  return L;
+}
+
+bool shape_valid(const lrs_ctx* h, const GaussLayout& L) {
+  return static_cast<int64_t>(L.cs - 1) * L.ns < h->n;
+}
+
+int max_smem_optin() {
   int max_optin = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (max_optin <= 0) max_optin = 232448;
-  auto shape = [&](int cs) {
-    GaussLayout L{};
-    L.n = static_cast<int>(h->n);
-    L.m = static_cast<int>(h->m);
-    L.q = static_cast<int>(h->q);
-    L.r = h->r;
-    L.rho = h->rho;
-    L.cs = cs;
-    const int64_t w = (h->n + cs - 1) / cs;
-    L.ns = static_cast<int>((w + 3) / 4 * 4);
-    int pad = L.ns;
-    while (pad % 32 != 4) pad += 4;
-    L.ns_pad = pad;
-    return L;
-  };
-  auto valid = [&](const GaussLayout& L) {
-    return static_cast<int64_t>(L.cs - 1) * L.ns < h->n;
-  };
-  const int forced = h->opt.cluster;
+  return max_optin > 0 ? max_optin : 232448;
+}
+
+// Pick the cluster size (CTAs per column), the slab mode and the ring depth.
+// Preference: a slab resident in shared memory with two CTAs per SM, then a
+// streamed slab with the deepest ring that keeps two CTAs per SM, then any
+// shape that fits one CTA per SM.  Options can force each choice.
+void choose_layout(lrs_ctx* h) {
+  const size_t two_per_sm = 113 * 1024, one_per_sm = static_cast<size_t>(max_smem_optin());
   const int cands[5] = {1, 2, 4, 8, 16};
-  if (forced > 0) {
-    h->L = shape(forced);
-    h->resident = sweep_smem_bytes(h->L, 1, kThreads) <= static_cast<size_t>(max_optin);
-    return;
-  }
-  // prefer >= 2 resident CTAs per SM, then any resident shape, else stream
-  for (int pass = 0; pass < 2; ++pass) {
-    const size_t lim = pass == 0 ? 112 * 1024 : static_cast<size_t>(max_optin);
+  const int want_cs = h->opt.cluster, want_mode = h->opt.slab_mode, want_st = h->opt.stages;
+  for (size_t lim : {two_per_sm, one_per_sm}) {
     for (int cs : cands) {
-      GaussLayout L = shape(cs);
-      if (!valid(L)) continue;
-      if (sweep_smem_bytes(L, 1, kThreads) <= lim) {
-        h->L = L;
-        h->resident = 1;
-        return;
+      if (want_cs && cs != want_cs) continue;
+      if (want_mode != 2) {  // resident
+        GaussLayout L = gauss_shape(h, cs, 1);
+        if (shape_valid(h, L) && sweep_smem_bytes(L, 1, 0) <= lim) {
+          h->L = L;
+          h->resident = 1;
+          return;
+        }
+      }
+      if (want_mode != 1) {  // streamed
+        for (int st : {4, 3, 2}) {
+          if (want_st && st != want_st) continue;
+          GaussLayout L = gauss_shape(h, cs, st);
+          if (shape_valid(h, L) && sweep_smem_bytes(L, 0, 0) <= lim) {
+            h->L = L;
+            h->resident = 0;
+            return;
+          }
+        }
       }
     }
   }
-  GaussLayout L = shape(8);
-  if (!valid(L)) L = shape(1);
-  h->L = L;
+  h->L = gauss_shape(h, want_cs ? want_cs : 16, 2);
   h->resident = 0;
 }
 
@@ -321,6 +332,8 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
   if (o.cluster != 0 && o.cluster != 1 && o.cluster != 2 && o.cluster != 4 && o.cluster != 8 &&
       o.cluster != 16)
     return fail(LRS_ERR_ARG, "lrs_create: cluster must be 0, 1, 2, 4, 8 or 16");
+  if (o.slab_mode < 0 || o.slab_mode > 2 || o.stages < 0 || o.stages > 16)
+    return fail(LRS_ERR_ARG, "lrs_create: slab_mode in 0..2, stages in 0..16");
   if (o.a_dtype != LRS_A_FP32)
     return fail(LRS_ERR_UNSUPPORTED, "lrs_create: only float32 A_k storage is built in");
   if (o.tau0 == 0) o.tau0 = 10;
@@ -343,16 +356,20 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
   h->kind = kind;
   h->opt = o;
   h->stream = static_cast<cudaStream_t>(o.stream);
-  choose_layout(h);
-  if (o.cluster > 0 && (int64_t(h->L.cs) - 1) * h->L.ns >= n) {
+  if (m > 512) {
     delete h;
-    return fail(LRS_ERR_ARG, "lrs_create: cluster size too large for n");
+    return fail(LRS_ERR_UNSUPPORTED, "lrs_create: the Gaussian sweep handles m <= 512");
+  }
+  choose_layout(h);
+  if (!shape_valid(h, h->L) || sweep_smem_bytes(h->L, h->resident, 0) > static_cast<size_t>(max_smem_optin())) {
+    delete h;
+    return fail(LRS_ERR_ARG, "lrs_create: no sweep shape fits (cluster/slab options)");
   }
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   h->nblk = std::max(1, std::min<int>(nsm > 0 ? nsm : 148, static_cast<int>((n + 63) / 64)));
-  const size_t per_col = static_cast<size_t>(h->L.cs) * h->L.m * h->L.ns_pad;
+  const size_t per_col = static_cast<size_t>(h->L.cs) * h->L.m * h->L.ns;
   lrs_status st = LRS_OK;
   if ((st = dalloc(&h->A, per_col * q)) || (st = dalloc(&h->y, size_t(m) * q)) ||
       (st = dalloc(&h->U, size_t(n) * r)) || (st = dalloc(&h->Bk, size_t(q) * r)) ||
@@ -602,10 +619,10 @@ lrs_status lrs_describe(lrs_t h, char* buf, int32_t len) {
   const size_t sm = sweep_smem_bytes(h->L, h->resident, kThreads);
   const int nc = sweep_max_active_clusters(h->L, h->resident, kThreads);
   snprintf(buf, static_cast<size_t>(len),
-           "{\"op\": \"%s\", \"cluster\": %d, \"ns\": %d, \"ns_pad\": %d, \"resident\": %d, "
-           "\"smem_per_cta\": %zu, \"max_active_clusters\": %d, \"threads\": %d}",
-           h->kind == LRS_OP_GAUSSIAN ? "gaussian" : "dft2d", h->L.cs, h->L.ns, h->L.ns_pad,
-           h->resident, sm, nc, kThreads);
+           "{\"op\": \"%s\", \"cluster\": %d, \"ns\": %d, \"stages\": %d, \"resident\": %d, "
+           "\"smem_per_cta\": %zu, \"max_active_clusters\": %d}",
+           h->kind == LRS_OP_GAUSSIAN ? "gaussian" : "dft2d", h->L.cs, h->L.ns, h->L.stages,
+           h->resident, sm, nc);
   return LRS_OK;
 }
 

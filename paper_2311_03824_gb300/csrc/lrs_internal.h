@@ -19,15 +19,17 @@ enum SweepMode : int {
 };
 
 // Layout of the Gaussian operator inside the handle ("slab" layout): column k's
-// A_k is split by columns j into `cs` slabs of `ns` columns; slab c holds
-// columns [c*ns, min(n, (c+1)*ns)) as an m x ns_pad row-major block,
-// zero-padded, and slabs of one column are consecutive:
-//   A_int[((k*cs + c)*m + i)*ns_pad + jj] = A_k(i, c*ns + jj).
+// A_k is split by columns j into `cs` slabs of `ns` columns (ns a multiple of
+// 32); slab c holds columns [c*ns, min(n, (c+1)*ns)), zero-padded, as ns/32
+// consecutive tiles of m rows x 32 floats; inside a tile, row i is 32
+// consecutive floats whose 16-byte chunks are XOR-permuted by (i mod 8):
+//   A_k(i, c*ns + 32*b + 4*q + e) is at
+//   ((k*cs + c)*ns*m) + b*32*m + i*32 + 4*(q ^ (i & 7)) + e.
 struct GaussLayout {
   int n, m, q, r, rho;
   int cs;      // CTAs per column (thread-block cluster size)
-  int ns;      // slab width (multiple of 4)
-  int ns_pad;  // padded row length (>= ns, = 4 mod 32, multiple of 4)
+  int ns;      // slab width (multiple of 32)
+  int stages;  // tile stages of the streamed ring (ignored when resident)
 };
 
 struct SweepArgs {
@@ -42,7 +44,7 @@ struct SweepArgs {
   float* B;         // q x r (b_k contiguous)
   float* H;         // q x n: ITER: h_k = A_k^T(W b + A s - y); INIT: L0 column
   int* err;         // device error word pair {code, column}
-  int resident;     // 1: slab staged in shared memory by TMA; 0: read from global
+  int resident;     // 1: slab staged once in shared memory; 0: streamed per product
 };
 
 // Sweep kernel (sweep_gauss.cu).

@@ -1,10 +1,17 @@
 // Per-column sweep of AltGDmin-LR+S for the Gaussian operator (Algorithm 1
 // with Algorithm 2), one thread-block cluster of CS CTAs per column k.
 //
-// The cluster's CTAs split A_k by columns j into slabs (GaussLayout).  A slab
-// either stays in shared memory for the whole column (staged once by TMA bulk
-// copies) or, when it does not fit, is streamed from global memory (L2) for
-// each product.  The products of one column-iteration are
+// Storage.  The cluster's CTAs split A_k by columns j into slabs of `ns`
+// columns; a slab is a run of 32-column tiles, each tile m rows x 128 bytes
+// with the 16-byte chunks of row i XOR-permuted by (i mod 8), so that both a
+// thread-per-row read (row products) and a lane-per-column read (column
+// products) hit distinct shared-memory banks.  A slab either stays in shared
+// memory for the whole column (one TMA bulk copy) or streams through a ring
+// of S tile stages filled by TMA bulk copies from a producer warp, once per
+// product, while the consumer warps work on earlier tiles (the slab is hot in
+// L2 after the first product).
+//
+// Products of one column-iteration:
 //   W_k = A_k U                                 (row pass, r wide)
 //   u   = P_perp(A_k s - y_k)                   (sparse gather + r x r solve)
 //   g   = A_k^T u                               (column pass)
@@ -12,15 +19,18 @@
 //   s   = HardThreshold(s - mu g, rho)          (cluster-wide top-rho)
 //   b_k = G_k^{-1} W_k^T (y_k - A_k s)          (FP64 inverse Gram)
 //   h_k = A_k^T (W_k b_k + A_k s - y_k)         (column pass; gradient term)
-// with P_perp v = v - W_k G_k^{-1} W_k^T v and G_k = W_k^T W_k.  The r x r
-// Gram, its Cholesky factor and inverse are FP64; the m-space dot products of
-// the projections accumulate in FP64; the passes over A_k run in FP32.
+// with P_perp v = v - W_k G_k^{-1} W_k^T v, G_k = W_k^T W_k.  The r x r Gram,
+// its Cholesky factor and inverse are FP64, the m-space dot products of the
+// projections accumulate in FP64, and the passes over A_k run in FP32.
 //
-// Partial results of the slabs are combined through distributed shared
-// memory: each CTA writes its partial into one of two exchange slots of its
-// own shared memory, a cluster barrier publishes it, and every CTA sums all
-// partials in rank order, so every CTA holds bit-identical reduced values and
-// takes identical control-flow decisions.
+// Cluster exchanges.  Partial results of the slabs are combined through
+// distributed shared memory: each CTA writes its partial into one of two
+// exchange slots in its own shared memory and signals every peer's mbarrier
+// for that slot (release at cluster scope); each CTA waits on its own
+// mbarrier and sums the partials of all CTAs in rank order.  Every CTA holds
+// bit-identical reduced values and takes identical control-flow decisions.
+// A slot is rewritten two exchanges later, after every peer has signalled the
+// exchange in between, i.e. after it finished reading.
 #include "lrs_dev.cuh"
 #include "lrs_internal.h"
 
@@ -29,15 +39,20 @@ namespace {
 
 constexpr int kSelBlk = 128;  // block size of the local all-pairs ranking
 constexpr int kMaxR = 16;
-constexpr int kNT = 256;      // threads per CTA
+constexpr int kNT = 256;      // consumer threads per CTA
 constexpr int kNW = kNT / 32;
+constexpr int kThreadsAll = kNT + 32;  // + one producer warp
+constexpr int kTW = 32;       // tile width (columns)
+constexpr int kGE = 16;       // support entries per gather round
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct Carve {
-  size_t mbar, slab, Us, W, yv, dv, ev, gs, sl, vv, gpart, keys, bc, ck, cv, cn, Ginv, fsm,
-      flags, redd, sup, xch, xs, total;
+  size_t bars, slab, Us, W, yv, dv, ev, gs, sl, vv, gpart, keys, bc, ck, cv, cn, Gm, fsm, flags,
+      redd, sup, prod, xch, xs, total;
 };
+
+__host__ __device__ inline size_t tile_bytes(const GaussLayout& L) { return (size_t)L.m * kTW * 4; }
 
 __host__ __device__ inline Carve carve(const GaussLayout& L, int resident) {
   Carve c;
@@ -45,27 +60,29 @@ __host__ __device__ inline Carve carve(const GaussLayout& L, int resident) {
   const int RP = (L.r + 3) & ~3;
   const int rho = L.rho > 0 ? L.rho : 1;
   const int nb = (L.ns + kSelBlk - 1) / kSelBlk;
-  c.mbar = o;  o += 16;
-  c.slab = o;  if (resident) o += a16((size_t)L.m * L.ns_pad * 4);
-  c.Us = o;    o += a16((size_t)L.ns_pad * RP * 4);
+  const int ntile = L.ns / kTW;
+  c.bars = o;  o += a16(8 * (2 * 16 + 4));                   // ring full/empty, slab, exchange
+  c.slab = o;  o += a16(tile_bytes(L) * (resident ? ntile : L.stages));
+  c.Us = o;    o += a16((size_t)L.ns * RP * 4);
   c.W = o;     o += a16((size_t)L.m * RP * 4);
   c.yv = o;    o += a16((size_t)L.m * 4);
   c.dv = o;    o += a16((size_t)L.m * 4);
   c.ev = o;    o += a16((size_t)L.m * 4);
-  c.gs = o;    o += a16((size_t)L.ns_pad * 4);
-  c.sl = o;    o += a16((size_t)L.ns_pad * 4);
-  c.vv = o;    o += a16((size_t)L.ns_pad * 4);
-  c.gpart = o; o += a16((size_t)kNW * L.ns_pad * 4);
-  c.keys = o;  o += a16((size_t)L.ns_pad * 8);
+  c.gs = o;    o += a16((size_t)L.ns * 4);
+  c.sl = o;    o += a16((size_t)L.ns * 4);
+  c.vv = o;    o += a16((size_t)L.ns * 4);
+  c.gpart = o; o += a16((size_t)kNW * L.ns * 4);
+  c.keys = o;  o += a16((size_t)L.ns * 8);
   c.bc = o;    o += a16((size_t)nb * rho * 4);
   c.ck = o;    o += a16((size_t)L.cs * rho * 8);
   c.cv = o;    o += a16((size_t)L.cs * rho * 4);
   c.cn = o;    o += a16((size_t)L.cs * 4);
-  c.Ginv = o;  o += a16(3 * kMaxR * kMaxR * 8);       // G, L, Ginv (FP64)
-  c.fsm = o;   o += a16(4 * kMaxR * 8);               // FP64 r-vectors (c, x)
+  c.Gm = o;    o += a16(3 * kMaxR * kMaxR * 8);       // G (then L^-1), L, G^-1 (FP64)
+  c.fsm = o;   o += a16(4 * kMaxR * 8);               // FP64 r-vectors
   c.flags = o; o += a16((size_t)(rho + 4) * 4);
   c.redd = o;  o += a16((size_t)kNT * 8 + 64);
   c.sup = o;   o += a16((size_t)rho * 8 + 16);
+  c.prod = o;  if (!resident) o += a16((size_t)kGE * L.m * 4);
   const size_t xw = (size_t)L.m * RP * 4;                           // W partial
   const size_t xa = a16((size_t)L.m * 4) + kMaxR * kMaxR * 8 + 16;  // A s partial + Gram + count
   const size_t xg = a16((size_t)L.m * 4) + 16;                      // A g_G partial + ||g_G||^2
@@ -77,6 +94,11 @@ __host__ __device__ inline Carve carve(const GaussLayout& L, int resident) {
   c.xch = o;   o += 2 * c.xs;
   c.total = o;
   return c;
+}
+
+// offset of element (i, j) inside a slab (tiles of m x 32, swizzled chunks)
+__device__ __forceinline__ int elem_off(int m, int i, int j) {
+  return (j >> 5) * (m * kTW) + i * kTW + ((((j & 31) >> 2) ^ (i & 7)) << 2) + (j & 3);
 }
 
 __device__ __forceinline__ uint64_t ht_key(float v, int jglob) {
@@ -108,12 +130,46 @@ __device__ __forceinline__ double rsqrt_fp64(double s) {
   return y;
 }
 
+// barrier among the consumer warps only (the producer warp runs ahead)
+__device__ __forceinline__ void csync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kNT) : "memory");
+}
+
+// remote mbarrier arrive (release at cluster scope) on CTA `rank`'s copy
+__device__ __forceinline__ void mbar_arrive_remote(uint64_t* bar, unsigned rank) {
+  unsigned local = smem_u32(bar), remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Everything one CTA needs about its column and its shared memory.
 struct Ctx {
-  const float* Asl;  // slab: shared (resident) or global (streamed), m x ld row-major
-  int m, n, r, rho, ld, nsc, nq, j0, c, CS, k;
-  float* Us;         // ld x R (row j: U[j0 + j][0..R), zero padded)
-  float* W;          // m x R
+  const float* Asl;  // resident slab (shared) or nullptr
+  const float* Ag;   // this CTA's slab in global memory
+  const float* ring; // ring stages (streamed)
+  uint64_t* full;    // ring barriers
+  uint64_t* empty;
+  uint64_t* xbar;    // exchange barriers [2]
+  int stages, ntile;
+  int m, n, r, rho, nsc, j0, c, CS, k;
+  unsigned tile_seq; // consumer tile counter (uniform across consumer threads)
+  float* Us;
+  float* W;
   float* yv;
   float* dv;
   float* ev;
@@ -126,15 +182,16 @@ struct Ctx {
   uint64_t* ck;
   float* cvv;
   int* cn;
-  double* G;         // r x r (ld kMaxR)
+  double* G;
   double* Lc;
-  double* Gi;        // G^{-1}
-  double* fv;        // FP64 vectors: [0,16) c, [16,32) x
+  double* Gi;
+  double* fv;
   int* flags;
   double* redd;
   int* sup_j;
   float* sup_v;
   int* nloc;
+  float* prod;
   unsigned char* xch;
   size_t xs;
   int* err;
@@ -144,61 +201,158 @@ __device__ __forceinline__ unsigned char* xslot(const Ctx& C, int e) {
   return C.xch + (e & 1) * C.xs;
 }
 
+// Publish this CTA's slot of exchange e to the cluster and wait for all
+// peers' slots (consumer threads only).
+__device__ __forceinline__ void xchg_publish_wait(const Ctx& C, int e) {
+  csync();
+  if (C.CS > 1) {
+    if (threadIdx.x == 0) {
+      asm volatile("fence.acq_rel.cluster;" ::: "memory");
+      for (int p = 0; p < C.CS; ++p) mbar_arrive_remote(&C.xbar[e & 1], p);
+    }
+    const unsigned parity = (static_cast<unsigned>(e) >> 1) & 1u;
+    unsigned it = 0;
+    while (!mbar_try_wait_cluster(&C.xbar[e & 1], parity)) {
+      if (++it > (1u << 22)) {
+        if (threadIdx.x == 0) report_error(C.err, kErrTimeout, C.k);
+        break;
+      }
+    }
+  }
+}
+
+// ---- tile access --------------------------------------------------------
+// Returns tile b of the current product (waiting for it when streamed).
+__device__ __forceinline__ const float* acquire_tile(Ctx& C, int b) {
+  if (C.Asl) return C.Asl + static_cast<size_t>(b) * C.m * kTW;
+  const unsigned s = C.tile_seq % C.stages, use = C.tile_seq / C.stages;
+  unsigned it = 0;
+  while (!mbar_try_wait(&C.full[s], use & 1u)) {
+    if (++it > (1u << 22)) {
+      if (threadIdx.x == 0) report_error(C.err, kErrTimeout, C.k);
+      break;
+    }
+  }
+  return C.ring + static_cast<size_t>(s) * C.m * kTW;
+}
+__device__ __forceinline__ void release_tile(Ctx& C) {
+  if (C.Asl) return;
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive_local(&C.empty[C.tile_seq % C.stages]);
+  ++C.tile_seq;
+}
+// consume (without computing) the tiles of a product that is skipped
+__device__ __forceinline__ void drain_pass(Ctx& C) {
+  if (C.Asl) return;
+  for (int b = 0; b < C.ntile; ++b) {
+    acquire_tile(C, b);
+    release_tile(C);
+  }
+}
+
 // ---------------------------------------------------------------- passes --
-// g[0..nsc) = A_slab^T v: warps split rows, lanes take float4 column quads;
-// per-warp partials summed over warps in a fixed order.
-__device__ __forceinline__ void col_pass(const Ctx& C, const float* v, bool streamed) {
+// g[0..nsc) = A_slab^T v: per tile, warps split the rows and lanes take the
+// 32 columns; per-warp partials summed over warps in a fixed order.
+__device__ __forceinline__ void col_pass(Ctx& C, const float* v) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int RB = (C.m + kNW - 1) / kNW;
   const int rlo = wid * RB, rhi = min(C.m, rlo + RB);
-  for (int qd = lane; qd < C.nq; qd += 32) {
-    float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+  const int cq = lane >> 2, ce = lane & 3;
+  for (int b = 0; b < C.ntile; ++b) {
+    const float* t = acquire_tile(C, b);
+    float acc0 = 0.f, acc1 = 0.f;
     int i = rlo;
     for (; i + 1 < rhi; i += 2) {
-      const float4* p0 = reinterpret_cast<const float4*>(C.Asl + static_cast<size_t>(i) * C.ld) + qd;
-      const float4* p1 = reinterpret_cast<const float4*>(C.Asl + static_cast<size_t>(i + 1) * C.ld) + qd;
-      const float4 a0 = streamed ? __ldg(p0) : *p0;
-      const float4 a1 = streamed ? __ldg(p1) : *p1;
-      const float u0 = v[i], u1 = v[i + 1];
-      acc0.x = fmaf(a0.x, u0, acc0.x); acc0.y = fmaf(a0.y, u0, acc0.y);
-      acc0.z = fmaf(a0.z, u0, acc0.z); acc0.w = fmaf(a0.w, u0, acc0.w);
-      acc1.x = fmaf(a1.x, u1, acc1.x); acc1.y = fmaf(a1.y, u1, acc1.y);
-      acc1.z = fmaf(a1.z, u1, acc1.z); acc1.w = fmaf(a1.w, u1, acc1.w);
+      const float a0 = t[i * kTW + ((cq ^ (i & 7)) << 2) + ce];
+      const float a1 = t[(i + 1) * kTW + ((cq ^ ((i + 1) & 7)) << 2) + ce];
+      acc0 = fmaf(a0, v[i], acc0);
+      acc1 = fmaf(a1, v[i + 1], acc1);
     }
-    if (i < rhi) {
-      const float4* p0 = reinterpret_cast<const float4*>(C.Asl + static_cast<size_t>(i) * C.ld) + qd;
-      const float4 a0 = streamed ? __ldg(p0) : *p0;
-      const float u0 = v[i];
-      acc0.x = fmaf(a0.x, u0, acc0.x); acc0.y = fmaf(a0.y, u0, acc0.y);
-      acc0.z = fmaf(a0.z, u0, acc0.z); acc0.w = fmaf(a0.w, u0, acc0.w);
-    }
-    float4 s;
-    s.x = acc0.x + acc1.x; s.y = acc0.y + acc1.y; s.z = acc0.z + acc1.z; s.w = acc0.w + acc1.w;
-    reinterpret_cast<float4*>(C.gpart + static_cast<size_t>(wid) * C.ld)[qd] = s;
+    if (i < rhi) acc0 = fmaf(t[i * kTW + ((cq ^ (i & 7)) << 2) + ce], v[i], acc0);
+    C.gpart[wid * C.ntile * kTW + b * kTW + lane] = acc0 + acc1;
+    release_tile(C);
   }
-  __syncthreads();
+  csync();
   for (int j = threadIdx.x; j < C.nsc; j += kNT) {
     float s = 0.f;
 #pragma unroll
-    for (int w = 0; w < kNW; ++w) s += C.gpart[w * C.ld + j];
+    for (int w = 0; w < kNW; ++w) s += C.gpart[w * C.ntile * kTW + j];
     C.gs[j] = s;
   }
-  __syncthreads();
+  csync();
+}
+
+// W partial = A_slab U_slab (thread per row, up to 2 rows per thread), into
+// dst (m x R)
+template <int R>
+__device__ __forceinline__ void w_pass(Ctx& C, float* dst) {
+  const int m = C.m;
+  float acc[2][R];
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+#pragma unroll
+    for (int l = 0; l < R; ++l) acc[t][l] = 0.f;
+  for (int b = 0; b < C.ntile; ++b) {
+    const float* tl = acquire_tile(C, b);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int i = threadIdx.x + kNT * t;
+      if (i < m) {
+        const float* row = tl + i * kTW;
+#pragma unroll 2
+        for (int q4 = 0; q4 < 8; ++q4) {
+          const float4 av = *reinterpret_cast<const float4*>(row + ((q4 ^ (i & 7)) << 2));
+          const float* u0 = C.Us + (b * kTW + 4 * q4) * R;
+#pragma unroll
+          for (int l = 0; l < R; ++l) {
+            float s = acc[t][l];
+            s = fmaf(av.x, u0[l], s);
+            s = fmaf(av.y, u0[R + l], s);
+            s = fmaf(av.z, u0[2 * R + l], s);
+            s = fmaf(av.w, u0[3 * R + l], s);
+            acc[t][l] = s;
+          }
+        }
+      }
+    }
+    release_tile(C);
+  }
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int i = threadIdx.x + kNT * t;
+    if (i < m)
+#pragma unroll
+      for (int l = 0; l < R; ++l) dst[i * R + l] = acc[t][l];
+  }
 }
 
 // out[i] = sum_e coef[e] A(i, sup_j[e]) over the local support (partial of
-// the cluster sum).
-__device__ __forceinline__ void gather(const Ctx& C, const float* coef, float* out,
-                                       bool streamed) {
-  const int nl = *C.nloc;
-  for (int i = threadIdx.x; i < C.m; i += kNT) {
-    float s = 0.f;
-    const float* row = C.Asl + static_cast<size_t>(i) * C.ld;
-    for (int e = 0; e < nl; ++e) {
-      const float a = streamed ? __ldg(row + C.sup_j[e]) : row[C.sup_j[e]];
-      s = fmaf(a, coef[e], s);
+// the cluster sum).  Streamed slabs: products staged by entry so that the
+// global loads run in parallel, then summed per row in entry order.
+__device__ __forceinline__ void gather(const Ctx& C, const float* coef, float* out) {
+  const int nl = *C.nloc, m = C.m;
+  if (C.Asl) {
+    for (int i = threadIdx.x; i < m; i += kNT) {
+      float s = 0.f;
+      for (int e = 0; e < nl; ++e) s = fmaf(C.Asl[elem_off(m, i, C.sup_j[e])], coef[e], s);
+      out[i] = s;
     }
-    out[i] = s;
+    return;
+  }
+  for (int i = threadIdx.x; i < m; i += kNT) out[i] = 0.f;
+  for (int base = 0; base < nl; base += kGE) {
+    const int ne = min(kGE, nl - base);
+    for (int t = threadIdx.x; t < ne * m; t += kNT) {
+      const int e = t / m, i = t - e * m;
+      C.prod[e * m + i] = __ldg(C.Ag + elem_off(m, i, C.sup_j[base + e])) * coef[base + e];
+    }
+    csync();
+    for (int i = threadIdx.x; i < m; i += kNT) {
+      float s = out[i];
+      for (int e = 0; e < ne; ++e) s += C.prod[e * m + i];
+      out[i] = s;
+    }
+    csync();
   }
 }
 
@@ -211,7 +365,7 @@ __device__ __forceinline__ void reduce_m(const Ctx& C, const float* x, float* ou
   }
 }
 
-// FP64 sum over the CTA of nv per-thread values acc[0..nv) -> C.fv[0..nv)
+// FP64 sum over the consumers of nv per-thread values acc[0..nv) -> C.fv[0..nv)
 template <int R>
 __device__ __forceinline__ void block_sum_d(const Ctx& C, double (&acc)[R], int nv) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -222,17 +376,17 @@ __device__ __forceinline__ void block_sum_d(const Ctx& C, double (&acc)[R], int 
     for (int l = 0; l < R; ++l)
       if (l < nv) C.redd[w * kMaxR + l] = acc[l];
   }
-  __syncthreads();
+  csync();
   if (threadIdx.x < nv) {
     double s = 0.0;
 #pragma unroll
     for (int i = 0; i < kNW; ++i) s += C.redd[i * kMaxR + threadIdx.x];
     C.fv[threadIdx.x] = s;
   }
-  __syncthreads();
+  csync();
 }
 
-// x = G^{-1} W^T v  (FP64 dot products), x (FP64) in C.fv[16 + l]
+// x = G^{-1} W^T v (FP64 dot products); x in C.fv[16 + l]
 template <int R>
 __device__ __forceinline__ void ls_solve(const Ctx& C, const float* v) {
   double acc[R];
@@ -250,10 +404,10 @@ __device__ __forceinline__ void ls_solve(const Ctx& C, const float* v) {
       for (int b = 0; b < C.r; ++b) s = dfma(C.Gi[threadIdx.x * kMaxR + b], C.fv[b], s);
     C.fv[16 + threadIdx.x] = s;
   }
-  __syncthreads();
+  csync();
 }
 
-// v <- P_perp v = v - W G^{-1} W^T v   (in place; FP64 for the m-space sums)
+// v <- P_perp v = v - W G^{-1} W^T v (in place; FP64 for the m-space sums)
 template <int R>
 __device__ __forceinline__ void proj(const Ctx& C, float* v) {
   ls_solve<R>(C, v);
@@ -263,17 +417,17 @@ __device__ __forceinline__ void proj(const Ctx& C, float* v) {
     for (int l = 0; l < R; ++l) s = dfma(-static_cast<double>(C.W[i * R + l]), C.fv[16 + l], s);
     v[i] = static_cast<float>(s);
   }
-  __syncthreads();
+  csync();
 }
 
-// sum of squares of an m-vector in FP64 (returned to all threads)
+// sum of squares of an m-vector in FP64 (returned to every consumer thread)
 __device__ __forceinline__ double norm2_m(const Ctx& C, const float* v) {
   double acc = 0.0;
   for (int i = threadIdx.x; i < C.m; i += kNT) acc = dfma(static_cast<double>(v[i]), v[i], acc);
   acc = warp_sum(acc);
-  __syncthreads();
+  csync();
   if ((threadIdx.x & 31) == 0) C.redd[threadIdx.x >> 5] = acc;
-  __syncthreads();
+  csync();
   double s = 0.0;
 #pragma unroll
   for (int i = 0; i < kNW; ++i) s += C.redd[i];
@@ -287,7 +441,7 @@ __device__ __forceinline__ void factor_gram(const Ctx& C) {
   if (threadIdx.x >= 32) return;
   const int lane = threadIdx.x, r = C.r;
   double* L = C.Lc;
-  double* iL = C.fv + 32;  // inverse pivots
+  double* iL = C.fv + 32;
   if (lane == 0) {
     bool ok = true;
     for (int j = 0; j < r && ok; ++j) {
@@ -313,8 +467,7 @@ __device__ __forceinline__ void factor_gram(const Ctx& C) {
     }
   }
   __syncwarp();
-  // column `lane` of L^{-1} (lower triangular), stored in G's buffer
-  double* Li = C.G;
+  double* Li = C.G;  // L^{-1}, lower triangular (G no longer needed)
   if (lane < r) {
     const int cc = lane;
     for (int i = 0; i < r; ++i) {
@@ -334,22 +487,20 @@ __device__ __forceinline__ void factor_gram(const Ctx& C) {
 
 // ------------------------------------------------------------- exchanges --
 // A s over the cluster with the local support values; with_gram also carries
-// the FP64 partial Gram of this CTA's row range and factors it.  Result A s
-// in dv; the local support counts of every CTA in cn[].
+// the FP64 partial Gram of this CTA's row range and factors it.  A s -> dv;
+// every CTA's local support count -> cn[].
 template <int R>
-__device__ __forceinline__ void exchange_As(const Ctx& C, int& ex, bool with_gram, bool streamed) {
+__device__ __forceinline__ void exchange_As(Ctx& C, int& ex, bool with_gram) {
   unsigned char* x = xslot(C, ex);
   float* xa = reinterpret_cast<float*>(x);
   double* xgram = reinterpret_cast<double*>(x + a16(static_cast<size_t>(C.m) * 4));
   int* xcnt = reinterpret_cast<int*>(x + a16(static_cast<size_t>(C.m) * 4) + kMaxR * kMaxR * 8);
-  gather(C, C.sup_v, xa, streamed);
+  gather(C, C.sup_v, xa);
   if (with_gram) {
     const int mc = (C.m + C.CS - 1) / C.CS;
     const int ilo = C.c * mc, ihi = min(C.m, ilo + mc);
     const int r = C.r, E = r * r;
-    // thread t < E*P: entry t % E over rows ilo + t / E (step P); phases
-    // summed in order
-    const int P = max(1, kNT / E);
+    const int P = max(1, kNT / E);  // row phases, summed in order
     if (threadIdx.x < E * P) {
       const int e = threadIdx.x % E, ph = threadIdx.x / E;
       const int p = e / r, q2 = e - p * r;
@@ -359,7 +510,7 @@ __device__ __forceinline__ void exchange_As(const Ctx& C, int& ex, bool with_gra
           s = dfma(static_cast<double>(C.W[i * R + p]), static_cast<double>(C.W[i * R + q2]), s);
       C.redd[threadIdx.x] = s;
     }
-    __syncthreads();
+    csync();
     for (int e = threadIdx.x; e < E; e += kNT) {
       double s = 0.0;
       for (int ph = 0; ph < P; ++ph) s += C.redd[ph * E + e];
@@ -367,7 +518,7 @@ __device__ __forceinline__ void exchange_As(const Ctx& C, int& ex, bool with_gra
     }
   }
   if (threadIdx.x == 0) *xcnt = *C.nloc;
-  cluster_sync_all();
+  xchg_publish_wait(C, ex);
   reduce_m(C, xa, C.dv);
   if (threadIdx.x < C.CS) C.cn[threadIdx.x] = *peer_ptr(xcnt, threadIdx.x);
   if (with_gram) {
@@ -383,21 +534,20 @@ __device__ __forceinline__ void exchange_As(const Ctx& C, int& ex, bool with_gra
     }
   }
   ++ex;
-  __syncthreads();
+  csync();
   if (with_gram) {
     factor_gram(C);
-    __syncthreads();
+    csync();
   }
 }
 
 // HardThreshold over the cluster: values vv[0..nsc) -> new local support
 // (exactly rho entries cluster-wide, largest |v| first, ties to the lower
 // index).  keep_values = false keeps zero values (support of g at s = 0).
-__device__ __forceinline__ void hard_threshold(const Ctx& C, int& ex, bool keep_values) {
+__device__ __forceinline__ void hard_threshold(Ctx& C, int& ex, bool keep_values) {
   const int rho = C.rho, nsc = C.nsc;
   for (int j = threadIdx.x; j < nsc; j += kNT) C.keys[j] = ht_key(C.vv[j], C.j0 + j);
-  __syncthreads();
-  // rank inside blocks of kSelBlk; the first rho of each block are candidates
+  csync();
   for (int j = threadIdx.x; j < nsc; j += kNT) {
     const int blk = j / kSelBlk, lo = blk * kSelBlk, hi = min(nsc, lo + kSelBlk);
     const uint64_t kj = C.keys[j];
@@ -405,7 +555,7 @@ __device__ __forceinline__ void hard_threshold(const Ctx& C, int& ex, bool keep_
     for (int l = lo; l < hi; ++l) cnt += C.keys[l] > kj;
     if (cnt < rho) C.bc[blk * rho + cnt] = j;
   }
-  __syncthreads();
+  csync();
   unsigned char* x = xslot(C, ex);
   int* xcnt = reinterpret_cast<int*>(x);
   uint64_t* xkey = reinterpret_cast<uint64_t*>(x + 16);
@@ -440,7 +590,7 @@ __device__ __forceinline__ void hard_threshold(const Ctx& C, int& ex, bool keep_
     }
   }
   if (threadIdx.x == 0) *xcnt = min(rho, nsc);
-  if (C.CS > 1) cluster_sync_all(); else __syncthreads();
+  xchg_publish_wait(C, ex);
   for (int t = threadIdx.x; t < C.CS * rho; t += kNT) {
     const int p = t / rho, s = t - p * rho;
     const unsigned char* px = peer_ptr(x, p);
@@ -454,9 +604,7 @@ __device__ __forceinline__ void hard_threshold(const Ctx& C, int& ex, bool keep_
     if (s == 0) C.cn[p] = cp;
   }
   ++ex;
-  __syncthreads();
-  // own candidates: selected iff their cluster-wide rank is < rho; the
-  // selected ones are a prefix of the (descending) own list
+  csync();
   const int own = C.cn[C.c];
   for (int s = threadIdx.x; s < own; s += kNT) {
     const uint64_t kj = C.ck[C.c * rho + s];
@@ -464,16 +612,15 @@ __device__ __forceinline__ void hard_threshold(const Ctx& C, int& ex, bool keep_
     for (int p = 0; p < C.CS; ++p) g += count_greater(C.ck + p * rho, C.cn[p], kj);
     C.flags[1 + s] = (g < rho) ? 1 : 0;
   }
-  // clear the old support in the dense local s
   const int nl_old = *C.nloc;
   for (int e = threadIdx.x; e < nl_old; e += kNT) C.sl[C.sup_j[e]] = 0.f;
-  __syncthreads();
+  csync();
   if (threadIdx.x == 0) {
     int cnt = 0;
     while (cnt < own && C.flags[1 + cnt]) ++cnt;
     *C.nloc = cnt;
   }
-  __syncthreads();
+  csync();
   const int cnt = *C.nloc;
   for (int s = threadIdx.x; s < cnt; s += kNT) {
     const int j = key_index(C.ck[C.c * rho + s]) - C.j0;
@@ -482,14 +629,23 @@ __device__ __forceinline__ void hard_threshold(const Ctx& C, int& ex, bool keep_
     C.sup_v[s] = val;
     C.sl[j] = val;
   }
-  __syncthreads();
+  csync();
+}
+
+// number of products over A_k of one column in each mode (the producer
+// streams the slab once per product)
+__device__ __forceinline__ int passes_of(int mode, int tau, int rho) {
+  if (mode == kModeLS) return 1;
+  const int t = (rho == 0) ? 0 : tau;
+  return mode == kModeInit ? t + 1 : t + 2;
 }
 
 template <int R, bool RES>
-__global__ void __launch_bounds__(kNT, 2) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const GaussLayout& L = a.L;
   const int tid = threadIdx.x;
+  const bool producer = tid >= kNT;
   Ctx C;
   C.c = static_cast<int>(cluster_rank());
   C.CS = static_cast<int>(cluster_size());
@@ -498,15 +654,22 @@ __global__ void __launch_bounds__(kNT, 2) sweep_kernel(const SweepArgs a) {
   C.n = L.n;
   C.r = L.r;
   C.rho = L.rho;
-  C.ld = L.ns_pad;
   C.j0 = C.c * L.ns;
   C.nsc = max(0, min(L.ns, L.n - C.j0));
-  C.nq = (C.nsc + 3) >> 2;
+  C.ntile = L.ns / kTW;
+  C.stages = L.stages;
   C.err = a.err;
+  C.tile_seq = 0;
   const Carve cv = carve(L, RES ? 1 : 0);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + cv.mbar);
-  const float* gslab = a.A + (static_cast<size_t>(C.k) * C.CS + C.c) * static_cast<size_t>(C.m) * C.ld;
-  C.Asl = RES ? reinterpret_cast<const float*>(smem + cv.slab) : gslab;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + cv.bars);
+  C.full = bars;
+  C.empty = bars + 16;
+  uint64_t* slab_bar = bars + 32;
+  C.xbar = bars + 33;
+  const size_t slab_elems = static_cast<size_t>(C.ntile) * C.m * kTW;
+  C.Ag = a.A + (static_cast<size_t>(C.k) * C.CS + C.c) * slab_elems;
+  C.Asl = RES ? reinterpret_cast<const float*>(smem + cv.slab) : nullptr;
+  C.ring = reinterpret_cast<const float*>(smem + cv.slab);
   C.Us = reinterpret_cast<float*>(smem + cv.Us);
   C.W = reinterpret_cast<float*>(smem + cv.W);
   C.yv = reinterpret_cast<float*>(smem + cv.yv);
@@ -521,7 +684,7 @@ __global__ void __launch_bounds__(kNT, 2) sweep_kernel(const SweepArgs a) {
   C.ck = reinterpret_cast<uint64_t*>(smem + cv.ck);
   C.cvv = reinterpret_cast<float*>(smem + cv.cv);
   C.cn = reinterpret_cast<int*>(smem + cv.cn);
-  C.G = reinterpret_cast<double*>(smem + cv.Ginv);
+  C.G = reinterpret_cast<double*>(smem + cv.Gm);
   C.Lc = C.G + kMaxR * kMaxR;
   C.Gi = C.G + 2 * kMaxR * kMaxR;
   C.fv = reinterpret_cast<double*>(smem + cv.fsm);
@@ -531,31 +694,69 @@ __global__ void __launch_bounds__(kNT, 2) sweep_kernel(const SweepArgs a) {
   C.sup_j = reinterpret_cast<int*>(smem + cv.sup);
   C.sup_v = reinterpret_cast<float*>(smem + cv.sup + static_cast<size_t>(rho1) * 4);
   C.nloc = reinterpret_cast<int*>(smem + cv.sup + static_cast<size_t>(rho1) * 8);
+  C.prod = reinterpret_cast<float*>(smem + cv.prod);
   C.xch = smem + cv.xch;
   C.xs = cv.xs;
   int ex = 0;
   const int m = C.m, r = C.r, rho = C.rho, k = C.k;
-  const bool streamed = !RES;
+  const size_t tbytes = tile_bytes(L);
 
-  // ---- stage the slab (TMA bulk copies on one mbarrier) -------------------
-  if (RES && tid == 0) {
-    mbar_init(mbar, 1);
-    const size_t bytes = static_cast<size_t>(m) * C.ld * 4;
-    mbar_arrive_expect_tx(mbar, static_cast<unsigned>(bytes));
-    const char* src = reinterpret_cast<const char*>(gslab);
-    char* dst = reinterpret_cast<char*>(smem + cv.slab);
-    for (size_t off = 0; off < bytes; off += 32768) {
-      const size_t rem = bytes - off;
-      bulk_copy_g2s(dst + off, src + off, static_cast<unsigned>(rem < 32768 ? rem : 32768), mbar);
+  // ---- barriers -----------------------------------------------------------
+  if (tid == kNT) {
+    if (RES) {
+      mbar_init(slab_bar, 1);
+    } else {
+      for (int s = 0; s < C.stages; ++s) {
+        mbar_init(&C.full[s], 1);
+        mbar_init(&C.empty[s], kNW);
+      }
     }
+    mbar_init(&C.xbar[0], C.CS);
+    mbar_init(&C.xbar[1], C.CS);
   }
-  // ---- small operands --------------------------------------------------
-  for (int t = tid; t < C.ld * R; t += kNT) {
+  __syncthreads();
+  if (C.CS > 1) cluster_sync_all();  // peers' barriers initialised before any remote arrive
+
+  if (producer) {
+    // ---- producer warp: stream the slab's tiles for every product --------
+    if (tid == kNT) {
+      const char* src = reinterpret_cast<const char*>(C.Ag);
+      char* dst = reinterpret_cast<char*>(smem + cv.slab);
+      if (RES) {
+        const size_t bytes = slab_elems * 4;
+        mbar_arrive_expect_tx(slab_bar, static_cast<unsigned>(bytes));
+        for (size_t off = 0; off < bytes; off += 32768) {
+          const size_t rem = bytes - off;
+          bulk_copy_g2s(dst + off, src + off, static_cast<unsigned>(rem < 32768 ? rem : 32768),
+                        slab_bar);
+        }
+      } else {
+        const unsigned total = static_cast<unsigned>(passes_of(a.mode, a.tau, rho) * C.ntile);
+        for (unsigned t = 0; t < total; ++t) {
+          const unsigned s = t % C.stages, use = t / C.stages;
+          if (use > 0) {
+            unsigned it = 0;
+            while (!mbar_try_wait(&C.empty[s], (use - 1) & 1u))
+              if (++it > (1u << 22)) { report_error(a.err, kErrTimeout, k); break; }
+          }
+          mbar_arrive_expect_tx(&C.full[s], static_cast<unsigned>(tbytes));
+          bulk_copy_g2s(dst + s * tbytes, src + static_cast<size_t>(t % C.ntile) * tbytes,
+                        static_cast<unsigned>(tbytes), &C.full[s]);
+        }
+      }
+    }
+    __syncwarp();
+    if (C.CS > 1) cluster_sync_all();  // final cluster barrier (matches the consumers')
+    return;
+  }
+
+  // ---- consumers: small operands -------------------------------------------
+  for (int t = tid; t < L.ns * R; t += kNT) {
     const int j = t / R, l = t - j * R;
     C.Us[t] = (j < C.nsc && l < r) ? a.U[static_cast<size_t>(C.j0 + j) * r + l] : 0.f;
   }
   for (int i = tid; i < m; i += kNT) C.yv[i] = a.y[static_cast<size_t>(k) * m + i];
-  for (int j = tid; j < C.ld; j += kNT) C.sl[j] = 0.f;
+  for (int j = tid; j < L.ns; j += kNT) C.sl[j] = 0.f;
   if (tid == 0) {
     C.flags[0] = 0;
     int cnt = 0;
@@ -571,12 +772,12 @@ __global__ void __launch_bounds__(kNT, 2) sweep_kernel(const SweepArgs a) {
     }
     *C.nloc = cnt;
   }
-  __syncthreads();
+  csync();
   for (int e = tid; e < *C.nloc; e += kNT) C.sl[C.sup_j[e]] = C.sup_v[e];
   if (RES) {
-    if (!mbar_wait_bounded(mbar, 0) && (tid & 31) == 0) report_error(a.err, kErrTimeout, k);
+    if (!mbar_wait_bounded(slab_bar, 0) && (tid & 31) == 0) report_error(a.err, kErrTimeout, k);
   }
-  if (C.CS > 1) cluster_sync_all(); else __syncthreads();
+  csync();
 
   const bool project = (a.mode != kModeInit);
 
@@ -584,30 +785,9 @@ __global__ void __launch_bounds__(kNT, 2) sweep_kernel(const SweepArgs a) {
   bool need_gram = false;
   if (project) {
     float* xw = reinterpret_cast<float*>(xslot(C, ex));
-    for (int i = tid; i < m; i += kNT) {
-      float acc[R];
-#pragma unroll
-      for (int l = 0; l < R; ++l) acc[l] = 0.f;
-      const float4* arow = reinterpret_cast<const float4*>(C.Asl + static_cast<size_t>(i) * C.ld);
-      for (int jq = 0; jq < C.nq; ++jq) {
-        const float4 av = streamed ? __ldg(arow + jq) : arow[jq];
-        const float* u0 = C.Us + (4 * jq) * R;
-#pragma unroll
-        for (int l = 0; l < R; ++l) {
-          float t = acc[l];
-          t = fmaf(av.x, u0[l], t);
-          t = fmaf(av.y, u0[R + l], t);
-          t = fmaf(av.z, u0[2 * R + l], t);
-          t = fmaf(av.w, u0[3 * R + l], t);
-          acc[l] = t;
-        }
-      }
-      float* dst = (C.CS > 1) ? xw : C.W;
-#pragma unroll
-      for (int l = 0; l < R; ++l) dst[i * R + l] = acc[l];
-    }
+    w_pass<R>(C, C.CS > 1 ? xw : C.W);
     if (C.CS > 1) {
-      cluster_sync_all();
+      xchg_publish_wait(C, ex);
       for (int t = tid; t < m * R; t += kNT) {
         float s = 0.f;
         for (int p = 0; p < C.CS; ++p) s += peer_ptr(xw, p)[t];
@@ -615,77 +795,73 @@ __global__ void __launch_bounds__(kNT, 2) sweep_kernel(const SweepArgs a) {
       }
       ++ex;
     }
-    __syncthreads();
+    csync();
     need_gram = true;
   }
 
   // ----------------------------------------------------- IHT (Alg. 2) ----
   const int tau = (a.mode == kModeLS || rho == 0) ? 0 : a.tau;
-  for (int it = 0; it < tau; ++it) {
+  int it = 0;
+  for (; it < tau; ++it) {
     const bool zero_start = (a.mode == kModeInit && it == 0);
     // u = P_perp (A s - y)   (A s = 0 for the zero start)
     if (zero_start) {
       for (int i = tid; i < m; i += kNT) C.dv[i] = -C.yv[i];
-      __syncthreads();
+      csync();
     } else {
-      exchange_As<R>(C, ex, need_gram, streamed);
+      exchange_As<R>(C, ex, need_gram);
       need_gram = false;
       for (int i = tid; i < m; i += kNT) C.dv[i] -= C.yv[i];
-      __syncthreads();
+      csync();
       if (project) proj<R>(C, C.dv);
     }
-    col_pass(C, C.dv, streamed);  // g = A^T u  (= M^T (M s - z): P_perp is a projector)
+    col_pass(C, C.dv);  // g = A^T u  (= M^T (M s - z): P_perp is a projector)
     if (zero_start) {
-      // support G of the zero start: the rho largest |g_i|
       for (int j = tid; j < C.nsc; j += kNT) C.vv[j] = C.gs[j];
-      __syncthreads();
-      hard_threshold(C, ex, false);
+      csync();
+      hard_threshold(C, ex, false);  // support G of the zero start
     }
     // ||g_G||^2 and A g_G on the support, then mu
-    {
-      unsigned char* x = xslot(C, ex);
-      float* xg = reinterpret_cast<float*>(x);
-      double* xnum = reinterpret_cast<double*>(x + a16(static_cast<size_t>(m) * 4));
-      const int nl = *C.nloc;
-      for (int e = tid; e < nl; e += kNT) C.vv[e] = C.gs[C.sup_j[e]];
-      __syncthreads();
-      if (tid == 0) {
-        double s = 0.0;
-        for (int e = 0; e < nl; ++e) s = dfma(static_cast<double>(C.vv[e]), C.vv[e], s);
-        *xnum = s;
-      }
-      gather(C, C.vv, xg, streamed);
-      double num = 0.0;
-      if (C.CS > 1) {
-        cluster_sync_all();
-        reduce_m(C, xg, C.ev);
-        for (int p = 0; p < C.CS; ++p) num += *peer_ptr(xnum, p);
-        ++ex;
-      } else {
-        __syncthreads();
-        for (int i = tid; i < m; i += kNT) C.ev[i] = xg[i];
-        num = *xnum;
-      }
-      __syncthreads();
-      if (project) proj<R>(C, C.ev);
-      const double den = norm2_m(C, C.ev);
-      if (!(den > 0.0)) break;  // ||M g_G|| = 0: the column's IHT stops
-      double mu = num / den;
-      if (!isfinite(mu)) {
-        if (tid == 0) report_error(a.err, kErrNaN, k);
-        mu = 0.0;
-      }
-      const float muf = static_cast<float>(mu);
-      for (int j = tid; j < C.nsc; j += kNT) C.vv[j] = fmaf(-muf, C.gs[j], C.sl[j]);
-      __syncthreads();
+    unsigned char* x = xslot(C, ex);
+    float* xg = reinterpret_cast<float*>(x);
+    double* xnum = reinterpret_cast<double*>(x + a16(static_cast<size_t>(m) * 4));
+    const int nl = *C.nloc;
+    for (int e = tid; e < nl; e += kNT) C.vv[e] = C.gs[C.sup_j[e]];
+    csync();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int e = 0; e < nl; ++e) s = dfma(static_cast<double>(C.vv[e]), C.vv[e], s);
+      *xnum = s;
     }
+    gather(C, C.vv, xg);
+    xchg_publish_wait(C, ex);
+    reduce_m(C, xg, C.ev);
+    double num = 0.0;
+    for (int p = 0; p < C.CS; ++p) num += *peer_ptr(xnum, p);
+    ++ex;
+    csync();
+    if (project) proj<R>(C, C.ev);
+    const double den = norm2_m(C, C.ev);
+    if (!(den > 0.0)) {  // ||M g_G|| = 0: the column's IHT stops
+      ++it;
+      break;
+    }
+    double mu = num / den;
+    if (!isfinite(mu)) {
+      if (tid == 0) report_error(a.err, kErrNaN, k);
+      mu = 0.0;
+    }
+    const float muf = static_cast<float>(mu);
+    for (int j = tid; j < C.nsc; j += kNT) C.vv[j] = fmaf(-muf, C.gs[j], C.sl[j]);
+    csync();
     hard_threshold(C, ex, true);
   }
+  for (; it < tau; ++it) drain_pass(C);  // products the stopped IHT no longer needs
 
   // ------------------------------------------------------ final stage -----
-  exchange_As<R>(C, ex, need_gram, streamed);  // A s with the final support
+  exchange_As<R>(C, ex, need_gram);  // A s with the final support
   for (int i = tid; i < m; i += kNT) C.dv[i] = C.yv[i] - C.dv[i];  // y - A s
-  __syncthreads();
+  csync();
   if (a.mode != kModeInit) {
     ls_solve<R>(C, C.dv);  // b = G^{-1} W^T (y - A s)   (FP64)
     if (C.c == 0 && tid < r) a.B[static_cast<size_t>(k) * r + tid] = static_cast<float>(C.fv[16 + tid]);
@@ -696,11 +872,11 @@ __global__ void __launch_bounds__(kNT, 2) sweep_kernel(const SweepArgs a) {
         for (int l = 0; l < R; ++l) s = dfma(static_cast<double>(C.W[i * R + l]), C.fv[16 + l], s);
         C.ev[i] = static_cast<float>(s);
       }
-      __syncthreads();
+      csync();
     }
   }
   if (a.mode != kModeLS) {
-    col_pass(C, a.mode == kModeInit ? C.dv : C.ev, streamed);
+    col_pass(C, a.mode == kModeInit ? C.dv : C.ev);
     float* Hk = a.H + static_cast<size_t>(k) * C.n + C.j0;
     for (int j = tid; j < C.nsc; j += kNT) Hk[j] = C.gs[j];
     // S_k: this CTA's entries ascending by index, after those of lower ranks
@@ -735,23 +911,25 @@ void* pick_kernel(int r, int resident) {
   }
 }
 
-// repack columns [k0, k0 + kc) of row-major A_k into the slab layout
+// repack columns [k0, k0 + kc) of row-major A_k into the tiled slab layout
 __global__ void repack_kernel(GaussLayout L, const float* __restrict__ Ain, int k0, int kc,
                               float* __restrict__ Aout) {
-  const size_t per_col = static_cast<size_t>(L.cs) * L.m * L.ns_pad;
+  const size_t slab = static_cast<size_t>(L.ns) * L.m;   // elements per slab
+  const size_t per_col = slab * L.cs;
   const size_t total = per_col * kc;
   for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < total;
        t += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    // t enumerates source order: column kk, row i, column j (padded to cs*ns)
     const size_t kk = t / per_col;
     const size_t rem = t - kk * per_col;
-    const int c = static_cast<int>(rem / (static_cast<size_t>(L.m) * L.ns_pad));
-    const size_t rem2 = rem - static_cast<size_t>(c) * L.m * L.ns_pad;
-    const int i = static_cast<int>(rem2 / L.ns_pad);
-    const int jj = static_cast<int>(rem2 - static_cast<size_t>(i) * L.ns_pad);
-    const int j = c * L.ns + jj;
-    float v = 0.f;
-    if (jj < L.ns && j < L.n) v = Ain[(kk * L.m + i) * L.n + j];
-    Aout[(static_cast<size_t>(k0) + kk) * per_col + rem] = v;
+    const int i = static_cast<int>(rem / (static_cast<size_t>(L.cs) * L.ns));
+    const int j = static_cast<int>(rem - static_cast<size_t>(i) * L.cs * L.ns);
+    const int c = j / L.ns, jl = j - c * L.ns;
+    const float v = (j < L.n) ? Ain[(kk * L.m + i) * L.n + j] : 0.f;
+    const size_t dst = (static_cast<size_t>(k0) + kk) * per_col + static_cast<size_t>(c) * slab +
+                       static_cast<size_t>(jl >> 5) * L.m * kTW + static_cast<size_t>(i) * kTW +
+                       ((((jl & 31) >> 2) ^ (i & 7)) << 2) + (jl & 3);
+    Aout[dst] = v;
   }
 }
 
@@ -767,7 +945,6 @@ cudaError_t sweep_prepare(const GaussLayout& L, int nthreads) {
     const size_t sm = sweep_smem_bytes(L, res, nthreads);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(sm));
-    if (e != cudaSuccess && res == 0) return e;
     if (e != cudaSuccess) cudaGetLastError();
     e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) cudaGetLastError();
@@ -779,8 +956,8 @@ static void fill_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, cons
                         int resident, int ncols, cudaStream_t s) {
   cfg = cudaLaunchConfig_t{};
   cfg.gridDim = dim3(static_cast<unsigned>(ncols) * L.cs, 1, 1);
-  cfg.blockDim = dim3(kNT, 1, 1);
-  cfg.dynamicSmemBytes = sweep_smem_bytes(L, resident, kNT);
+  cfg.blockDim = dim3(kThreadsAll, 1, 1);
+  cfg.dynamicSmemBytes = sweep_smem_bytes(L, resident, kThreadsAll);
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = L.cs;

@@ -36,7 +36,8 @@ class lrs_options(ctypes.Structure):
                 ("refine_every", ctypes.c_int32), ("cluster", ctypes.c_int32),
                 ("power_iters", ctypes.c_int32), ("power_tol", ctypes.c_double),
                 ("use_graph", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("seed", ctypes.c_uint64), ("profile", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("profile", ctypes.c_int32),
+                ("slab_mode", ctypes.c_int32), ("stages", ctypes.c_int32)]
 
 
 _lib = None
