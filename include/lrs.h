@@ -79,7 +79,8 @@ typedef struct {
   int32_t use_graph;        /* 1: replay steady-state iterations as a CUDA graph */
   void* stream;             /* cudaStream_t for every launch (NULL = default)  */
   uint64_t seed;            /* seed of the subspace-iteration start            */
-  int32_t profile;          /* 1: time each phase of lrs_iterate with CUDA events */
+  int32_t profile;          /* 1: time each phase of lrs_iterate with CUDA events;
+                               2: also count SM cycles per sweep phase       */
   int32_t slab_mode;        /* Gaussian sweep: 0 auto, 1 slab resident in shared
                                memory, 2 slab streamed through a tile ring   */
   int32_t stages;           /* tile stages of the streamed ring (0 -> auto)    */
@@ -170,6 +171,16 @@ lrs_status lrs_set_reference(lrs_t h, const void* Xref, int32_t mem_kind);
  * The counters restart at zero after the call.  Errors: LRS_ERR_ARG,
  * LRS_ERR_CUDA. */
 lrs_status lrs_phase_times(lrs_t h, double* out4);
+
+/* Per-column SM cycle counts of the sweep phases accumulated by
+ * lrs_iterate since the previous call (handle created with profile = 2;
+ * tracing aid).  out receives q x 12 counters, column-major by column k:
+ * setup, W = A U, A s exchange, projection of u, column product (IHT),
+ * A g_G exchange, projection and norm of M g_G, HardThreshold, final A s,
+ * LS and residual, final column product, output writes.  len is the capacity
+ * of out in elements.  Counters restart at zero.  Errors: LRS_ERR_ARG,
+ * LRS_ERR_STATE (no trace buffer), LRS_ERR_CUDA. */
+lrs_status lrs_sweep_trace(lrs_t h, uint64_t* out, int64_t len);
 
 /* Write a one-line description of the handle's launch shape (operator,
  * CTAs per column, slab width, shared memory per CTA, resident clusters) into

@@ -67,6 +67,7 @@ struct lrs_ctx {
   int* err = nullptr;      // {code, column}
   float* Xref = nullptr;   // q x n (error log)
   double* errpart = nullptr;
+  unsigned long long* trace = nullptr;  // q x kTracePhases (profile = 2)
   int nblk = 0;
   // graph of one steady-state iteration
   cudaGraph_t graph = nullptr;
@@ -184,6 +185,7 @@ lrs_status launch_sweep(lrs_ctx* h, int mode, int tau) {
   a.H = h->H;
   a.err = h->err;
   a.resident = h->resident;
+  a.trace = (h->opt.profile == 2 && mode == kModeIter) ? h->trace : nullptr;
   CUDA_TRY(sweep_launch(a, kThreads, h->stream));
   return LRS_OK;
 }
@@ -295,7 +297,7 @@ void free_all(lrs_ctx* h) {
   h->gexec = nullptr;
   h->graph = nullptr;
   void* ps[] = {h->A, h->y, h->U, h->Bk, h->S_idx, h->S_val, h->H, h->grad, h->Z,
-                h->U2, h->P, h->part, h->small, h->eta, h->err, h->Xref, h->errpart};
+                h->U2, h->P, h->part, h->small, h->eta, h->err, h->Xref, h->errpart, h->trace};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -383,6 +385,14 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
     free_all(h);
     delete h;
     return fail(st, "lrs_create: " + msg);
+  }
+  if (o.profile == 2) {
+    if ((st = dalloc(&h->trace, size_t(q) * kTracePhases))) {
+      free_all(h);
+      delete h;
+      return st;
+    }
+    cudaMemset(h->trace, 0, sizeof(unsigned long long) * size_t(q) * kTracePhases);
   }
   cudaError_t e = sweep_prepare(h->L, kThreads);
   if (e == cudaSuccess) e = cudaMemset(h->err, 0, 2 * sizeof(int));
@@ -611,6 +621,16 @@ lrs_status lrs_phase_times(lrs_t h, double* out4) {
   out4[3] = static_cast<double>(h->phase_iters);
   h->phase_ms[0] = h->phase_ms[1] = h->phase_ms[2] = 0;
   h->phase_iters = 0;
+  return LRS_OK;
+}
+
+lrs_status lrs_sweep_trace(lrs_t h, uint64_t* out, int64_t len) {
+  if (!h || !out || len < 0) return fail(LRS_ERR_ARG, "lrs_sweep_trace: bad argument");
+  if (!h->trace) return fail(LRS_ERR_STATE, "lrs_sweep_trace: create the handle with profile = 2");
+  const int64_t n = std::min<int64_t>(len, h->q * kTracePhases);
+  CUDA_TRY(cudaMemcpyAsync(out, h->trace, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->trace, 0, sizeof(uint64_t) * h->q * kTracePhases, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
   return LRS_OK;
 }
 

@@ -45,7 +45,14 @@ struct SweepArgs {
   float* H;         // q x n: ITER: h_k = A_k^T(W b + A s - y); INIT: L0 column
   int* err;         // device error word pair {code, column}
   int resident;     // 1: slab staged once in shared memory; 0: streamed per product
+  unsigned long long* trace;  // optional: per-column cycle counts of the sweep phases
 };
+
+// Phases of the per-column sweep recorded by the trace (cycles, summed over
+// the IHT steps): setup, W pass, A s exchange, projection of u, column pass
+// (IHT), A g_G exchange, projection + norm of M g_G, HardThreshold, final
+// A s, LS + residual, final column pass, output writes.
+constexpr int kTracePhases = 12;
 
 // Sweep kernel (sweep_gauss.cu).
 size_t sweep_smem_bytes(const GaussLayout& L, int resident, int nthreads);

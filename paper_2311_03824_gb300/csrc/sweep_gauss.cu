@@ -157,6 +157,19 @@ __device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Per-phase cycle accounting (consumer thread 0 of cluster rank 0 only).
+struct Tracer {
+  unsigned long long* out;
+  long long t0;
+  __device__ __forceinline__ void mark(int phase) {
+    if (out) {
+      const long long t = clock64();
+      out[phase] += static_cast<unsigned long long>(t - t0);
+      t0 = t;
+    }
+  }
+};
+
 // Everything one CTA needs about its column and its shared memory.
 struct Ctx {
   const float* Asl;  // resident slab (shared) or nullptr
@@ -700,6 +713,9 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
   int ex = 0;
   const int m = C.m, r = C.r, rho = C.rho, k = C.k;
   const size_t tbytes = tile_bytes(L);
+  Tracer tr;
+  tr.out = (a.trace && tid == 0 && C.c == 0) ? a.trace + static_cast<size_t>(k) * kTracePhases : nullptr;
+  tr.t0 = clock64();
 
   // ---- barriers -----------------------------------------------------------
   if (tid == kNT) {
@@ -778,6 +794,7 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
     if (!mbar_wait_bounded(slab_bar, 0) && (tid & 31) == 0) report_error(a.err, kErrTimeout, k);
   }
   csync();
+  tr.mark(0);
 
   const bool project = (a.mode != kModeInit);
 
@@ -798,6 +815,7 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
     csync();
     need_gram = true;
   }
+  tr.mark(1);
 
   // ----------------------------------------------------- IHT (Alg. 2) ----
   const int tau = (a.mode == kModeLS || rho == 0) ? 0 : a.tau;
@@ -813,9 +831,12 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
       need_gram = false;
       for (int i = tid; i < m; i += kNT) C.dv[i] -= C.yv[i];
       csync();
+      tr.mark(2);
       if (project) proj<R>(C, C.dv);
+      tr.mark(3);
     }
     col_pass(C, C.dv);  // g = A^T u  (= M^T (M s - z): P_perp is a projector)
+    tr.mark(4);
     if (zero_start) {
       for (int j = tid; j < C.nsc; j += kNT) C.vv[j] = C.gs[j];
       csync();
@@ -840,8 +861,10 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
     for (int p = 0; p < C.CS; ++p) num += *peer_ptr(xnum, p);
     ++ex;
     csync();
+    tr.mark(5);
     if (project) proj<R>(C, C.ev);
     const double den = norm2_m(C, C.ev);
+    tr.mark(6);
     if (!(den > 0.0)) {  // ||M g_G|| = 0: the column's IHT stops
       ++it;
       break;
@@ -855,6 +878,7 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
     for (int j = tid; j < C.nsc; j += kNT) C.vv[j] = fmaf(-muf, C.gs[j], C.sl[j]);
     csync();
     hard_threshold(C, ex, true);
+    tr.mark(7);
   }
   for (; it < tau; ++it) drain_pass(C);  // products the stopped IHT no longer needs
 
@@ -862,6 +886,7 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
   exchange_As<R>(C, ex, need_gram);  // A s with the final support
   for (int i = tid; i < m; i += kNT) C.dv[i] = C.yv[i] - C.dv[i];  // y - A s
   csync();
+  tr.mark(8);
   if (a.mode != kModeInit) {
     ls_solve<R>(C, C.dv);  // b = G^{-1} W^T (y - A s)   (FP64)
     if (C.c == 0 && tid < r) a.B[static_cast<size_t>(k) * r + tid] = static_cast<float>(C.fv[16 + tid]);
@@ -875,8 +900,10 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
       csync();
     }
   }
+  tr.mark(9);
   if (a.mode != kModeLS) {
     col_pass(C, a.mode == kModeInit ? C.dv : C.ev);
+    tr.mark(10);
     float* Hk = a.H + static_cast<size_t>(k) * C.n + C.j0;
     for (int j = tid; j < C.nsc; j += kNT) Hk[j] = C.gs[j];
     // S_k: this CTA's entries ascending by index, after those of lower ranks
@@ -893,6 +920,8 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
       }
     }
   }
+  csync();
+  tr.mark(11);
   if (C.CS > 1) cluster_sync_all();  // no CTA leaves while a peer may still read its slots
 }
 

@@ -68,6 +68,7 @@ def lib():
             "lrs_set_reference": [_P, _P, ctypes.c_int32],
             "lrs_phase_times": [_P, ctypes.POINTER(ctypes.c_double)],
             "lrs_describe": [_P, ctypes.c_char_p, ctypes.c_int32],
+            "lrs_sweep_trace": [_P, _P, ctypes.c_int64],
             "lrs_destroy": [_P],
         }
         for name, args in sig.items():
@@ -174,6 +175,17 @@ def lrs_phase_times(h):
     out = (ctypes.c_double * 4)()
     _check(lib().lrs_phase_times(h, out))
     return {"sweep_ms": out[0], "grad_ms": out[1], "qr_ms": out[2], "iters": int(out[3])}
+
+
+TRACE_PHASES = ["setup", "w_pass", "As_exchange", "proj_u", "col_pass", "Ag_exchange",
+                "proj_norm", "hard_threshold", "final_As", "ls_residual", "final_col_pass",
+                "output"]
+
+
+def lrs_sweep_trace(h, q):
+    out = np.zeros(q * len(TRACE_PHASES), np.uint64)
+    _check(lib().lrs_sweep_trace(h, out.ctypes.data_as(_P), out.size))
+    return out.reshape(q, len(TRACE_PHASES))
 
 
 def lrs_describe(h):
