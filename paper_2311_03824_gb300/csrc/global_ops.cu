@@ -121,7 +121,9 @@ __global__ void chol_fin_kernel(int r, int nblk, const double* __restrict__ part
 __global__ void __launch_bounds__(256) apply_rinv_kernel(int n, int r, const float* __restrict__ X,
                                                          const double* __restrict__ Rinv,
                                                          float* __restrict__ Y,
-                                                         double* __restrict__ part) {
+                                                         double* __restrict__ part,
+                                                         float* __restrict__ Ypad = nullptr,
+                                                         int rpad = 0) {
   __shared__ float Rf[kMaxR * kMaxR];
   __shared__ float tile[256 * kMaxR];
   for (int t = threadIdx.x; t < r * r; t += blockDim.x) Rf[t] = static_cast<float>(Rinv[t]);
@@ -139,6 +141,7 @@ __global__ void __launch_bounds__(256) apply_rinv_kernel(int n, int r, const flo
       float s = 0.f;
       for (int p = 0; p <= l; ++p) s = fmaf(x[p], Rf[p * r + l], s);
       Y[static_cast<size_t>(base + i) * r + l] = s;
+      if (Ypad) Ypad[static_cast<size_t>(base + i) * rpad + l] = s;
       tile[u] = s;
     }
     __syncthreads();
@@ -306,7 +309,7 @@ cudaError_t cholqr2(const GlobalWork& g, const float* Zin, float* Uout, int* err
   chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R1, err);
   apply_rinv_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, Zin, R1, g.Z, g.part);
   chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R2, err);
-  apply_rinv_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, g.Z, R2, Uout, nullptr);
+  apply_rinv_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, g.Z, R2, Uout, nullptr, g.Upad, g.rpad);
   return cudaGetLastError();
 }
 
@@ -321,7 +324,7 @@ cudaError_t qr_step(const GlobalWork& g, float* U, const double* eta_dev, int* e
   // Q1 = Z R1^{-1} (into grad's buffer: grad is no longer needed), Gram(Q1)
   apply_rinv_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, g.Z, R1, g.grad, g.part);
   chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R2, err);
-  apply_rinv_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, g.grad, R2, U, nullptr);
+  apply_rinv_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, g.grad, R2, U, nullptr, g.Upad, g.rpad);
   return cudaGetLastError();
 }
 

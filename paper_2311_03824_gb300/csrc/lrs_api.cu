@@ -53,6 +53,7 @@ struct lrs_ctx {
   float* A = nullptr;      // slab layout
   float* y = nullptr;      // q x m
   float* U = nullptr;      // n x r row-major
+  float* Upad = nullptr;   // (cs*ns) x rpad row-major, zero padded (sweep input)
   float* Bk = nullptr;     // q x r
   int* S_idx = nullptr;    // q x rho
   float* S_val = nullptr;  // q x rho
@@ -90,6 +91,8 @@ GlobalWork gw(lrs_ctx* h) {
   g.small = h->small;
   g.Z = h->Z;
   g.nblk = h->nblk;
+  g.Upad = h->Upad;
+  g.rpad = sweep_rpad(h->r);
   return g;
 }
 
@@ -179,6 +182,7 @@ lrs_status launch_sweep(lrs_ctx* h, int mode, int tau) {
   a.A = h->A;
   a.y = h->y;
   a.U = h->U;
+  a.Upad = h->Upad;
   a.S_idx = h->S_idx;
   a.S_val = h->S_val;
   a.B = h->Bk;
@@ -253,6 +257,15 @@ lrs_status error_now(lrs_ctx* h, double* out) {
   return LRS_OK;
 }
 
+__global__ void pad_rows_kernel(const float* in, float* out, int rows, int cols, int ldo) {
+  // out[r*ldo + c] = in[r*cols + c]
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < rows * cols) {
+    const int rr = t / cols, cc = t - rr * cols;
+    out[static_cast<size_t>(rr) * ldo + cc] = in[t];
+  }
+}
+
 __global__ void transpose_kernel(const float* in, float* out, int rows, int cols) {
   // out[c*rows + r] = in[r*cols + c]
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -296,7 +309,7 @@ void free_all(lrs_ctx* h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   h->gexec = nullptr;
   h->graph = nullptr;
-  void* ps[] = {h->A, h->y, h->U, h->Bk, h->S_idx, h->S_val, h->H, h->grad, h->Z,
+  void* ps[] = {h->A, h->y, h->U, h->Upad, h->Bk, h->S_idx, h->S_val, h->H, h->grad, h->Z,
                 h->U2, h->P, h->part, h->small, h->eta, h->err, h->Xref, h->errpart, h->trace};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -373,7 +386,9 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
   h->nblk = std::max(1, std::min<int>(nsm > 0 ? nsm : 148, static_cast<int>((n + 63) / 64)));
   const size_t per_col = static_cast<size_t>(h->L.cs) * h->L.m * h->L.ns;
   lrs_status st = LRS_OK;
+  const size_t upad_n = static_cast<size_t>(h->L.cs) * h->L.ns * sweep_rpad(r);
   if ((st = dalloc(&h->A, per_col * q)) || (st = dalloc(&h->y, size_t(m) * q)) ||
+      (st = dalloc(&h->Upad, upad_n)) ||
       (st = dalloc(&h->U, size_t(n) * r)) || (st = dalloc(&h->Bk, size_t(q) * r)) ||
       (st = dalloc(&h->S_idx, size_t(q) * h->rho)) || (st = dalloc(&h->S_val, size_t(q) * h->rho)) ||
       (st = dalloc(&h->H, size_t(q) * n)) || (st = dalloc(&h->grad, size_t(n) * r)) ||
@@ -396,6 +411,7 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
   }
   cudaError_t e = sweep_prepare(h->L, kThreads);
   if (e == cudaSuccess) e = cudaMemset(h->err, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->Upad, 0, sizeof(float) * upad_n);
   if (e == cudaSuccess) e = cudaMemset(h->S_idx, 0, sizeof(int) * size_t(q) * std::max(1, h->rho));
   if (e == cudaSuccess) e = cudaMemset(h->S_val, 0, sizeof(float) * size_t(q) * std::max(1, h->rho));
   if (e != cudaSuccess) {
@@ -581,6 +597,9 @@ lrs_status lrs_set_state(lrs_t h, const void* U, const void* B, const int32_t* S
   const int tot = static_cast<int>(h->n) * h->r;
   CUDA_TRY(cudaMemcpyAsync(h->Z, U, sizeof(float) * tot, kin, h->stream));
   transpose_kernel<<<(tot + 255) / 256, 256, 0, h->stream>>>(h->Z, h->U, h->r, static_cast<int>(h->n));
+  CUDA_TRY(cudaGetLastError());
+  pad_rows_kernel<<<(tot + 255) / 256, 256, 0, h->stream>>>(h->U, h->Upad, static_cast<int>(h->n),
+                                                            h->r, sweep_rpad(h->r));
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(h->Bk, B, sizeof(float) * h->q * h->r, kin, h->stream));
   if (h->rho) {

@@ -39,6 +39,7 @@ struct SweepArgs {
   const float* A;   // slab layout
   const float* y;   // q x m (y_k contiguous)
   const float* U;   // n x r row-major
+  const float* Upad;  // (cs*ns) x sweep_rpad(r) row-major, zero padded
   int* S_idx;       // q x rho (ascending per column), in/out
   float* S_val;     // q x rho
   float* B;         // q x r (b_k contiguous)
@@ -63,8 +64,16 @@ cudaError_t repack_gauss(const GaussLayout& L, const float* A_rowmajor, int k0, 
                          float* A_int, cudaStream_t s);
 
 // Global (column-reduced) steps (global_ops.cu).
+// Row stride of the padded copy of U the sweep stages by TMA: r rounded up
+// to one of the compiled widths.
+__host__ __device__ inline int sweep_rpad(int r) {
+  return r <= 2 ? 2 : r <= 6 ? r : r <= 8 ? 8 : r <= 10 ? 10 : r <= 12 ? 12 : 16;
+}
+
 struct GlobalWork {
   int n, q, r;
+  float* Upad;       // (padded n) x rpad copy of U for the sweep (optional)
+  int rpad;
   float* grad;       // n x r row-major
   double* part;      // partial r x r FP64 Grams: nblk x (r*r)
   double* small;     // scratch: [0,r*r) Rinv1, [r*r,2r*r) Rinv2, [2r*r] eta, ...

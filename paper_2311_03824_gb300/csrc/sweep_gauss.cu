@@ -1,942 +1,34 @@
-// Per-column sweep of AltGDmin-LR+S for the Gaussian operator (Algorithm 1
-// with Algorithm 2), one thread-block cluster of CS CTAs per column k.
-//
-// Storage.  The cluster's CTAs split A_k by columns j into slabs of `ns`
-// columns; a slab is a run of 32-column tiles, each tile m rows x 128 bytes
-// with the 16-byte chunks of row i XOR-permuted by (i mod 8), so that both a
-// thread-per-row read (row products) and a lane-per-column read (column
-// products) hit distinct shared-memory banks.  A slab either stays in shared
-// memory for the whole column (one TMA bulk copy) or streams through a ring
-// of S tile stages filled by TMA bulk copies from a producer warp, once per
-// product, while the consumer warps work on earlier tiles (the slab is hot in
-// L2 after the first product).
-//
-// Products of one column-iteration:
-//   W_k = A_k U                                 (row pass, r wide)
-//   u   = P_perp(A_k s - y_k)                   (sparse gather + r x r solve)
-//   g   = A_k^T u                               (column pass)
-//   mu  = ||g_G||^2 / ||P_perp A_k g_G||^2      (gather on the support G)
-//   s   = HardThreshold(s - mu g, rho)          (cluster-wide top-rho)
-//   b_k = G_k^{-1} W_k^T (y_k - A_k s)          (FP64 inverse Gram)
-//   h_k = A_k^T (W_k b_k + A_k s - y_k)         (column pass; gradient term)
-// with P_perp v = v - W_k G_k^{-1} W_k^T v, G_k = W_k^T W_k.  The r x r Gram,
-// its Cholesky factor and inverse are FP64, the m-space dot products of the
-// projections accumulate in FP64, and the passes over A_k run in FP32.
-//
-// Cluster exchanges.  Partial results of the slabs are combined through
-// distributed shared memory: each CTA writes its partial into one of two
-// exchange slots in its own shared memory and signals every peer's mbarrier
-// for that slot (release at cluster scope); each CTA waits on its own
-// mbarrier and sums the partials of all CTAs in rank order.  Every CTA holds
-// bit-identical reduced values and takes identical control-flow decisions.
-// A slot is rewritten two exchanges later, after every peer has signalled the
-// exchange in between, i.e. after it finished reading.
-#include "lrs_dev.cuh"
-#include "lrs_internal.h"
+// Launch side of the per-column Gaussian sweep (kernel body in
+// sweep_gauss_impl.cuh, one translation unit per compiled rank width so the
+// build runs in parallel): shared-memory sizing, cluster launch, and the
+// repacking of row-major A_k into the tiled slab layout.
+#include "sweep_gauss_impl.cuh"
 
 namespace lrs {
+void* sweep_kernel_r2(int resident);
+void* sweep_kernel_r3(int resident);
+void* sweep_kernel_r4(int resident);
+void* sweep_kernel_r5(int resident);
+void* sweep_kernel_r6(int resident);
+void* sweep_kernel_r8(int resident);
+void* sweep_kernel_r10(int resident);
+void* sweep_kernel_r12(int resident);
+void* sweep_kernel_r16(int resident);
+
 namespace {
-
-constexpr int kSelBlk = 128;  // block size of the local all-pairs ranking
-constexpr int kMaxR = 16;
-constexpr int kNT = 256;      // consumer threads per CTA
-constexpr int kNW = kNT / 32;
-constexpr int kThreadsAll = kNT + 32;  // + one producer warp
-constexpr int kTW = 32;       // tile width (columns)
-constexpr int kGE = 16;       // support entries per gather round
-
-__host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
-
-struct Carve {
-  size_t bars, slab, Us, W, yv, dv, ev, gs, sl, vv, gpart, keys, bc, ck, cv, cn, Gm, fsm, flags,
-      redd, sup, prod, xch, xs, total;
-};
-
-__host__ __device__ inline size_t tile_bytes(const GaussLayout& L) { return (size_t)L.m * kTW * 4; }
-
-__host__ __device__ inline Carve carve(const GaussLayout& L, int resident) {
-  Carve c;
-  size_t o = 0;
-  const int RP = (L.r + 3) & ~3;
-  const int rho = L.rho > 0 ? L.rho : 1;
-  const int nb = (L.ns + kSelBlk - 1) / kSelBlk;
-  const int ntile = L.ns / kTW;
-  c.bars = o;  o += a16(8 * (2 * 16 + 4));                   // ring full/empty, slab, exchange
-  c.slab = o;  o += a16(tile_bytes(L) * (resident ? ntile : L.stages));
-  c.Us = o;    o += a16((size_t)L.ns * RP * 4);
-  c.W = o;     o += a16((size_t)L.m * RP * 4);
-  c.yv = o;    o += a16((size_t)L.m * 4);
-  c.dv = o;    o += a16((size_t)L.m * 4);
-  c.ev = o;    o += a16((size_t)L.m * 4);
-  c.gs = o;    o += a16((size_t)L.ns * 4);
-  c.sl = o;    o += a16((size_t)L.ns * 4);
-  c.vv = o;    o += a16((size_t)L.ns * 4);
-  c.gpart = o; o += a16((size_t)kNW * L.ns * 4);
-  c.keys = o;  o += a16((size_t)L.ns * 8);
-  c.bc = o;    o += a16((size_t)nb * rho * 4);
-  c.ck = o;    o += a16((size_t)L.cs * rho * 8);
-  c.cv = o;    o += a16((size_t)L.cs * rho * 4);
-  c.cn = o;    o += a16((size_t)L.cs * 4);
-  c.Gm = o;    o += a16(3 * kMaxR * kMaxR * 8);       // G (then L^-1), L, G^-1 (FP64)
-  c.fsm = o;   o += a16(4 * kMaxR * 8);               // FP64 r-vectors
-  c.flags = o; o += a16((size_t)(rho + 4) * 4);
-  c.redd = o;  o += a16((size_t)kNT * 8 + 64);
-  c.sup = o;   o += a16((size_t)rho * 8 + 16);
-  c.prod = o;  if (!resident) o += a16((size_t)kGE * L.m * 4);
-  const size_t xw = (size_t)L.m * RP * 4;                           // W partial
-  const size_t xa = a16((size_t)L.m * 4) + kMaxR * kMaxR * 8 + 16;  // A s partial + Gram + count
-  const size_t xg = a16((size_t)L.m * 4) + 16;                      // A g_G partial + ||g_G||^2
-  const size_t xc = 16 + (size_t)rho * 16;                          // candidates
-  size_t mx = xw > xa ? xw : xa;
-  mx = mx > xg ? mx : xg;
-  mx = mx > xc ? mx : xc;
-  c.xs = a16(mx);
-  c.xch = o;   o += 2 * c.xs;
-  c.total = o;
-  return c;
-}
-
-// offset of element (i, j) inside a slab (tiles of m x 32, swizzled chunks)
-__device__ __forceinline__ int elem_off(int m, int i, int j) {
-  return (j >> 5) * (m * kTW) + i * kTW + ((((j & 31) >> 2) ^ (i & 7)) << 2) + (j & 3);
-}
-
-__device__ __forceinline__ uint64_t ht_key(float v, int jglob) {
-  return (static_cast<uint64_t>(__float_as_uint(fabsf(v))) << 32) |
-         static_cast<uint64_t>(0xFFFFFFFFu - static_cast<unsigned>(jglob));
-}
-__device__ __forceinline__ int key_index(uint64_t key) {
-  return static_cast<int>(0xFFFFFFFFu - static_cast<unsigned>(key & 0xFFFFFFFFull));
-}
-// number of entries of the descending list l[0..len) that are > x
-__device__ __forceinline__ int count_greater(const uint64_t* l, int len, uint64_t x) {
-  int lo = 0, hi = len;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (l[mid] > x) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ double dfma(double a, double b, double c) { return __fma_rn(a, b, c); }
-
-// 1/sqrt(s) in FP64: float estimate refined by two Newton-Raphson steps
-// y <- y (3 - s y^2) / 2 (each step doubles the number of correct bits).
-__device__ __forceinline__ double rsqrt_fp64(double s) {
-  if (!(s > 1e-36 && s < 1e36)) return 1.0 / sqrt(s);
-  double y = static_cast<double>(rsqrtf(static_cast<float>(s)));
-  y = y * (1.5 - 0.5 * s * y * y);
-  y = y * (1.5 - 0.5 * s * y * y);
-  return y;
-}
-
-// barrier among the consumer warps only (the producer warp runs ahead)
-__device__ __forceinline__ void csync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kNT) : "memory");
-}
-
-// remote mbarrier arrive (release at cluster scope) on CTA `rank`'s copy
-__device__ __forceinline__ void mbar_arrive_remote(uint64_t* bar, unsigned rank) {
-  unsigned local = smem_u32(bar), remote;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Per-phase cycle accounting (consumer thread 0 of cluster rank 0 only).
-struct Tracer {
-  unsigned long long* out;
-  long long t0;
-  __device__ __forceinline__ void mark(int phase) {
-    if (out) {
-      const long long t = clock64();
-      out[phase] += static_cast<unsigned long long>(t - t0);
-      t0 = t;
-    }
-  }
-};
-
-// Everything one CTA needs about its column and its shared memory.
-struct Ctx {
-  const float* Asl;  // resident slab (shared) or nullptr
-  const float* Ag;   // this CTA's slab in global memory
-  const float* ring; // ring stages (streamed)
-  uint64_t* full;    // ring barriers
-  uint64_t* empty;
-  uint64_t* xbar;    // exchange barriers [2]
-  int stages, ntile;
-  int m, n, r, rho, nsc, j0, c, CS, k;
-  unsigned tile_seq; // consumer tile counter (uniform across consumer threads)
-  float* Us;
-  float* W;
-  float* yv;
-  float* dv;
-  float* ev;
-  float* gs;
-  float* sl;
-  float* vv;
-  float* gpart;
-  uint64_t* keys;
-  int* bc;
-  uint64_t* ck;
-  float* cvv;
-  int* cn;
-  double* G;
-  double* Lc;
-  double* Gi;
-  double* fv;
-  int* flags;
-  double* redd;
-  int* sup_j;
-  float* sup_v;
-  int* nloc;
-  float* prod;
-  unsigned char* xch;
-  size_t xs;
-  int* err;
-};
-
-__device__ __forceinline__ unsigned char* xslot(const Ctx& C, int e) {
-  return C.xch + (e & 1) * C.xs;
-}
-
-// Publish this CTA's slot of exchange e to the cluster and wait for all
-// peers' slots (consumer threads only).
-__device__ __forceinline__ void xchg_publish_wait(const Ctx& C, int e) {
-  csync();
-  if (C.CS > 1) {
-    if (threadIdx.x == 0) {
-      asm volatile("fence.acq_rel.cluster;" ::: "memory");
-      for (int p = 0; p < C.CS; ++p) mbar_arrive_remote(&C.xbar[e & 1], p);
-    }
-    const unsigned parity = (static_cast<unsigned>(e) >> 1) & 1u;
-    unsigned it = 0;
-    while (!mbar_try_wait_cluster(&C.xbar[e & 1], parity)) {
-      if (++it > (1u << 22)) {
-        if (threadIdx.x == 0) report_error(C.err, kErrTimeout, C.k);
-        break;
-      }
-    }
-  }
-}
-
-// ---- tile access --------------------------------------------------------
-// Returns tile b of the current product (waiting for it when streamed).
-__device__ __forceinline__ const float* acquire_tile(Ctx& C, int b) {
-  if (C.Asl) return C.Asl + static_cast<size_t>(b) * C.m * kTW;
-  const unsigned s = C.tile_seq % C.stages, use = C.tile_seq / C.stages;
-  unsigned it = 0;
-  while (!mbar_try_wait(&C.full[s], use & 1u)) {
-    if (++it > (1u << 22)) {
-      if (threadIdx.x == 0) report_error(C.err, kErrTimeout, C.k);
-      break;
-    }
-  }
-  return C.ring + static_cast<size_t>(s) * C.m * kTW;
-}
-__device__ __forceinline__ void release_tile(Ctx& C) {
-  if (C.Asl) return;
-  __syncwarp();
-  if ((threadIdx.x & 31) == 0) mbar_arrive_local(&C.empty[C.tile_seq % C.stages]);
-  ++C.tile_seq;
-}
-// consume (without computing) the tiles of a product that is skipped
-__device__ __forceinline__ void drain_pass(Ctx& C) {
-  if (C.Asl) return;
-  for (int b = 0; b < C.ntile; ++b) {
-    acquire_tile(C, b);
-    release_tile(C);
-  }
-}
-
-// ---------------------------------------------------------------- passes --
-// g[0..nsc) = A_slab^T v: per tile, warps split the rows and lanes take the
-// 32 columns; per-warp partials summed over warps in a fixed order.
-__device__ __forceinline__ void col_pass(Ctx& C, const float* v) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int RB = (C.m + kNW - 1) / kNW;
-  const int rlo = wid * RB, rhi = min(C.m, rlo + RB);
-  const int cq = lane >> 2, ce = lane & 3;
-  for (int b = 0; b < C.ntile; ++b) {
-    const float* t = acquire_tile(C, b);
-    float acc0 = 0.f, acc1 = 0.f;
-    int i = rlo;
-    for (; i + 1 < rhi; i += 2) {
-      const float a0 = t[i * kTW + ((cq ^ (i & 7)) << 2) + ce];
-      const float a1 = t[(i + 1) * kTW + ((cq ^ ((i + 1) & 7)) << 2) + ce];
-      acc0 = fmaf(a0, v[i], acc0);
-      acc1 = fmaf(a1, v[i + 1], acc1);
-    }
-    if (i < rhi) acc0 = fmaf(t[i * kTW + ((cq ^ (i & 7)) << 2) + ce], v[i], acc0);
-    C.gpart[wid * C.ntile * kTW + b * kTW + lane] = acc0 + acc1;
-    release_tile(C);
-  }
-  csync();
-  for (int j = threadIdx.x; j < C.nsc; j += kNT) {
-    float s = 0.f;
-#pragma unroll
-    for (int w = 0; w < kNW; ++w) s += C.gpart[w * C.ntile * kTW + j];
-    C.gs[j] = s;
-  }
-  csync();
-}
-
-// W partial = A_slab U_slab (thread per row, up to 2 rows per thread), into
-// dst (m x R)
-template <int R>
-__device__ __forceinline__ void w_pass(Ctx& C, float* dst) {
-  const int m = C.m;
-  float acc[2][R];
-#pragma unroll
-  for (int t = 0; t < 2; ++t)
-#pragma unroll
-    for (int l = 0; l < R; ++l) acc[t][l] = 0.f;
-  for (int b = 0; b < C.ntile; ++b) {
-    const float* tl = acquire_tile(C, b);
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int i = threadIdx.x + kNT * t;
-      if (i < m) {
-        const float* row = tl + i * kTW;
-#pragma unroll 2
-        for (int q4 = 0; q4 < 8; ++q4) {
-          const float4 av = *reinterpret_cast<const float4*>(row + ((q4 ^ (i & 7)) << 2));
-          const float* u0 = C.Us + (b * kTW + 4 * q4) * R;
-#pragma unroll
-          for (int l = 0; l < R; ++l) {
-            float s = acc[t][l];
-            s = fmaf(av.x, u0[l], s);
-            s = fmaf(av.y, u0[R + l], s);
-            s = fmaf(av.z, u0[2 * R + l], s);
-            s = fmaf(av.w, u0[3 * R + l], s);
-            acc[t][l] = s;
-          }
-        }
-      }
-    }
-    release_tile(C);
-  }
-#pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    const int i = threadIdx.x + kNT * t;
-    if (i < m)
-#pragma unroll
-      for (int l = 0; l < R; ++l) dst[i * R + l] = acc[t][l];
-  }
-}
-
-// out[i] = sum_e coef[e] A(i, sup_j[e]) over the local support (partial of
-// the cluster sum).  Streamed slabs: products staged by entry so that the
-// global loads run in parallel, then summed per row in entry order.
-__device__ __forceinline__ void gather(const Ctx& C, const float* coef, float* out) {
-  const int nl = *C.nloc, m = C.m;
-  if (C.Asl) {
-    for (int i = threadIdx.x; i < m; i += kNT) {
-      float s = 0.f;
-      for (int e = 0; e < nl; ++e) s = fmaf(C.Asl[elem_off(m, i, C.sup_j[e])], coef[e], s);
-      out[i] = s;
-    }
-    return;
-  }
-  for (int i = threadIdx.x; i < m; i += kNT) out[i] = 0.f;
-  for (int base = 0; base < nl; base += kGE) {
-    const int ne = min(kGE, nl - base);
-    for (int t = threadIdx.x; t < ne * m; t += kNT) {
-      const int e = t / m, i = t - e * m;
-      C.prod[e * m + i] = __ldg(C.Ag + elem_off(m, i, C.sup_j[base + e])) * coef[base + e];
-    }
-    csync();
-    for (int i = threadIdx.x; i < m; i += kNT) {
-      float s = out[i];
-      for (int e = 0; e < ne; ++e) s += C.prod[e * m + i];
-      out[i] = s;
-    }
-    csync();
-  }
-}
-
-// cluster-sum of an m-vector partial held in slot x -> out (rank order)
-__device__ __forceinline__ void reduce_m(const Ctx& C, const float* x, float* out) {
-  for (int i = threadIdx.x; i < C.m; i += kNT) {
-    float s = 0.f;
-    for (int p = 0; p < C.CS; ++p) s += peer_ptr(x, p)[i];
-    out[i] = s;
-  }
-}
-
-// FP64 sum over the consumers of nv per-thread values acc[0..nv) -> C.fv[0..nv)
-template <int R>
-__device__ __forceinline__ void block_sum_d(const Ctx& C, double (&acc)[R], int nv) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int l = 0; l < R; ++l) acc[l] = warp_sum(acc[l]);
-  if (lane == 0) {
-#pragma unroll
-    for (int l = 0; l < R; ++l)
-      if (l < nv) C.redd[w * kMaxR + l] = acc[l];
-  }
-  csync();
-  if (threadIdx.x < nv) {
-    double s = 0.0;
-#pragma unroll
-    for (int i = 0; i < kNW; ++i) s += C.redd[i * kMaxR + threadIdx.x];
-    C.fv[threadIdx.x] = s;
-  }
-  csync();
-}
-
-// x = G^{-1} W^T v (FP64 dot products); x in C.fv[16 + l]
-template <int R>
-__device__ __forceinline__ void ls_solve(const Ctx& C, const float* v) {
-  double acc[R];
-#pragma unroll
-  for (int l = 0; l < R; ++l) acc[l] = 0.0;
-  for (int i = threadIdx.x; i < C.m; i += kNT) {
-    const double vi = v[i];
-#pragma unroll
-    for (int l = 0; l < R; ++l) acc[l] = dfma(static_cast<double>(C.W[i * R + l]), vi, acc[l]);
-  }
-  block_sum_d<R>(C, acc, C.r);
-  if (threadIdx.x < R) {
-    double s = 0.0;
-    if (threadIdx.x < C.r)
-      for (int b = 0; b < C.r; ++b) s = dfma(C.Gi[threadIdx.x * kMaxR + b], C.fv[b], s);
-    C.fv[16 + threadIdx.x] = s;
-  }
-  csync();
-}
-
-// v <- P_perp v = v - W G^{-1} W^T v (in place; FP64 for the m-space sums)
-template <int R>
-__device__ __forceinline__ void proj(const Ctx& C, float* v) {
-  ls_solve<R>(C, v);
-  for (int i = threadIdx.x; i < C.m; i += kNT) {
-    double s = v[i];
-#pragma unroll
-    for (int l = 0; l < R; ++l) s = dfma(-static_cast<double>(C.W[i * R + l]), C.fv[16 + l], s);
-    v[i] = static_cast<float>(s);
-  }
-  csync();
-}
-
-// sum of squares of an m-vector in FP64 (returned to every consumer thread)
-__device__ __forceinline__ double norm2_m(const Ctx& C, const float* v) {
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < C.m; i += kNT) acc = dfma(static_cast<double>(v[i]), v[i], acc);
-  acc = warp_sum(acc);
-  csync();
-  if ((threadIdx.x & 31) == 0) C.redd[threadIdx.x >> 5] = acc;
-  csync();
-  double s = 0.0;
-#pragma unroll
-  for (int i = 0; i < kNW; ++i) s += C.redd[i];
-  return s;
-}
-
-// Cholesky of G (lane 0, FP64, no division: inverse pivots by rsqrt_fp64),
-// then G^{-1} = L^{-T} L^{-1} by warp 0.  A pivot that is not positive
-// marks the column as numerically failed (identity used to keep going).
-__device__ __forceinline__ void factor_gram(const Ctx& C) {
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x, r = C.r;
-  double* L = C.Lc;
-  double* iL = C.fv + 32;
-  if (lane == 0) {
-    bool ok = true;
-    for (int j = 0; j < r && ok; ++j) {
-      double s = C.G[j * kMaxR + j];
-      for (int p = 0; p < j; ++p) s -= L[j * kMaxR + p] * L[j * kMaxR + p];
-      if (!(s > 1e-13 * C.G[j * kMaxR + j]) || !(s < 1e300)) { ok = false; break; }
-      const double ij = rsqrt_fp64(s);
-      L[j * kMaxR + j] = s * ij;
-      iL[j] = ij;
-      for (int i = j + 1; i < r; ++i) {
-        double t = C.G[i * kMaxR + j];
-        for (int p = 0; p < j; ++p) t -= L[i * kMaxR + p] * L[j * kMaxR + p];
-        L[i * kMaxR + j] = t * ij;
-      }
-    }
-    if (!ok) {
-      C.flags[0] = 1;
-      report_error(C.err, kErrNotSPD, C.k);
-      for (int i = 0; i < r; ++i) {
-        for (int p = 0; p < r; ++p) L[i * kMaxR + p] = (i == p) ? 1.0 : 0.0;
-        iL[i] = 1.0;
-      }
-    }
-  }
-  __syncwarp();
-  double* Li = C.G;  // L^{-1}, lower triangular (G no longer needed)
-  if (lane < r) {
-    const int cc = lane;
-    for (int i = 0; i < r; ++i) {
-      double t = (i == cc) ? 1.0 : 0.0;
-      for (int p = cc; p < i; ++p) t -= L[i * kMaxR + p] * Li[p * kMaxR + cc];
-      Li[i * kMaxR + cc] = (i < cc) ? 0.0 : t * iL[i];
-    }
-  }
-  __syncwarp();
-  for (int t = lane; t < r * r; t += 32) {
-    const int a = t / r, b = t - a * r;
-    double s = 0.0;
-    for (int p = (a > b ? a : b); p < r; ++p) s = dfma(Li[p * kMaxR + a], Li[p * kMaxR + b], s);
-    C.Gi[a * kMaxR + b] = s;
-  }
-}
-
-// ------------------------------------------------------------- exchanges --
-// A s over the cluster with the local support values; with_gram also carries
-// the FP64 partial Gram of this CTA's row range and factors it.  A s -> dv;
-// every CTA's local support count -> cn[].
-template <int R>
-__device__ __forceinline__ void exchange_As(Ctx& C, int& ex, bool with_gram) {
-  unsigned char* x = xslot(C, ex);
-  float* xa = reinterpret_cast<float*>(x);
-  double* xgram = reinterpret_cast<double*>(x + a16(static_cast<size_t>(C.m) * 4));
-  int* xcnt = reinterpret_cast<int*>(x + a16(static_cast<size_t>(C.m) * 4) + kMaxR * kMaxR * 8);
-  gather(C, C.sup_v, xa);
-  if (with_gram) {
-    const int mc = (C.m + C.CS - 1) / C.CS;
-    const int ilo = C.c * mc, ihi = min(C.m, ilo + mc);
-    const int r = C.r, E = r * r;
-    const int P = max(1, kNT / E);  // row phases, summed in order
-    if (threadIdx.x < E * P) {
-      const int e = threadIdx.x % E, ph = threadIdx.x / E;
-      const int p = e / r, q2 = e - p * r;
-      double s = 0.0;
-      if (q2 <= p)
-        for (int i = ilo + ph; i < ihi; i += P)
-          s = dfma(static_cast<double>(C.W[i * R + p]), static_cast<double>(C.W[i * R + q2]), s);
-      C.redd[threadIdx.x] = s;
-    }
-    csync();
-    for (int e = threadIdx.x; e < E; e += kNT) {
-      double s = 0.0;
-      for (int ph = 0; ph < P; ++ph) s += C.redd[ph * E + e];
-      xgram[e] = s;
-    }
-  }
-  if (threadIdx.x == 0) *xcnt = *C.nloc;
-  xchg_publish_wait(C, ex);
-  reduce_m(C, xa, C.dv);
-  if (threadIdx.x < C.CS) C.cn[threadIdx.x] = *peer_ptr(xcnt, threadIdx.x);
-  if (with_gram) {
-    const int r = C.r;
-    for (int t = threadIdx.x; t < r * r; t += kNT) {
-      const int p = t / r, q2 = t - p * r;
-      if (q2 <= p) {
-        double s = 0.0;
-        for (int pp = 0; pp < C.CS; ++pp) s += peer_ptr(xgram, pp)[t];
-        C.G[p * kMaxR + q2] = s;
-        C.G[q2 * kMaxR + p] = s;
-      }
-    }
-  }
-  ++ex;
-  csync();
-  if (with_gram) {
-    factor_gram(C);
-    csync();
-  }
-}
-
-// HardThreshold over the cluster: values vv[0..nsc) -> new local support
-// (exactly rho entries cluster-wide, largest |v| first, ties to the lower
-// index).  keep_values = false keeps zero values (support of g at s = 0).
-__device__ __forceinline__ void hard_threshold(Ctx& C, int& ex, bool keep_values) {
-  const int rho = C.rho, nsc = C.nsc;
-  for (int j = threadIdx.x; j < nsc; j += kNT) C.keys[j] = ht_key(C.vv[j], C.j0 + j);
-  csync();
-  for (int j = threadIdx.x; j < nsc; j += kNT) {
-    const int blk = j / kSelBlk, lo = blk * kSelBlk, hi = min(nsc, lo + kSelBlk);
-    const uint64_t kj = C.keys[j];
-    int cnt = 0;
-    for (int l = lo; l < hi; ++l) cnt += C.keys[l] > kj;
-    if (cnt < rho) C.bc[blk * rho + cnt] = j;
-  }
-  csync();
-  unsigned char* x = xslot(C, ex);
-  int* xcnt = reinterpret_cast<int*>(x);
-  uint64_t* xkey = reinterpret_cast<uint64_t*>(x + 16);
-  float* xval = reinterpret_cast<float*>(x + 16 + static_cast<size_t>(rho) * 8);
-  const int nb = (nsc + kSelBlk - 1) / kSelBlk;
-  if (nb <= 1) {
-    for (int s = threadIdx.x; s < min(rho, nsc); s += kNT) {
-      const int j = C.bc[s];
-      xkey[s] = C.keys[j];
-      xval[s] = keep_values ? C.vv[j] : 0.f;
-    }
-  } else {
-    int ncb = 0;
-    for (int b = 0; b < nb; ++b) ncb += min(rho, min(nsc, (b + 1) * kSelBlk) - b * kSelBlk);
-    for (int t = threadIdx.x; t < ncb; t += kNT) {
-      int b = 0, s = t;
-      while (s >= min(rho, min(nsc, (b + 1) * kSelBlk) - b * kSelBlk)) {
-        s -= min(rho, min(nsc, (b + 1) * kSelBlk) - b * kSelBlk);
-        ++b;
-      }
-      const int j = C.bc[b * rho + s];
-      const uint64_t kj = C.keys[j];
-      int cnt = 0;
-      for (int b2 = 0; b2 < nb; ++b2) {
-        const int nb2 = min(rho, min(nsc, (b2 + 1) * kSelBlk) - b2 * kSelBlk);
-        for (int s2 = 0; s2 < nb2; ++s2) cnt += C.keys[C.bc[b2 * rho + s2]] > kj;
-      }
-      if (cnt < rho) {
-        xkey[cnt] = kj;
-        xval[cnt] = keep_values ? C.vv[j] : 0.f;
-      }
-    }
-  }
-  if (threadIdx.x == 0) *xcnt = min(rho, nsc);
-  xchg_publish_wait(C, ex);
-  for (int t = threadIdx.x; t < C.CS * rho; t += kNT) {
-    const int p = t / rho, s = t - p * rho;
-    const unsigned char* px = peer_ptr(x, p);
-    const int cp = *reinterpret_cast<const int*>(px);
-    if (s < cp) {
-      C.ck[t] = reinterpret_cast<const uint64_t*>(px + 16)[s];
-      C.cvv[t] = reinterpret_cast<const float*>(px + 16 + static_cast<size_t>(rho) * 8)[s];
-    } else {
-      C.ck[t] = 0ull;
-    }
-    if (s == 0) C.cn[p] = cp;
-  }
-  ++ex;
-  csync();
-  const int own = C.cn[C.c];
-  for (int s = threadIdx.x; s < own; s += kNT) {
-    const uint64_t kj = C.ck[C.c * rho + s];
-    int g = 0;
-    for (int p = 0; p < C.CS; ++p) g += count_greater(C.ck + p * rho, C.cn[p], kj);
-    C.flags[1 + s] = (g < rho) ? 1 : 0;
-  }
-  const int nl_old = *C.nloc;
-  for (int e = threadIdx.x; e < nl_old; e += kNT) C.sl[C.sup_j[e]] = 0.f;
-  csync();
-  if (threadIdx.x == 0) {
-    int cnt = 0;
-    while (cnt < own && C.flags[1 + cnt]) ++cnt;
-    *C.nloc = cnt;
-  }
-  csync();
-  const int cnt = *C.nloc;
-  for (int s = threadIdx.x; s < cnt; s += kNT) {
-    const int j = key_index(C.ck[C.c * rho + s]) - C.j0;
-    const float val = C.cvv[C.c * rho + s];
-    C.sup_j[s] = j;
-    C.sup_v[s] = val;
-    C.sl[j] = val;
-  }
-  csync();
-}
-
-// number of products over A_k of one column in each mode (the producer
-// streams the slab once per product)
-__device__ __forceinline__ int passes_of(int mode, int tau, int rho) {
-  if (mode == kModeLS) return 1;
-  const int t = (rho == 0) ? 0 : tau;
-  return mode == kModeInit ? t + 1 : t + 2;
-}
-
-template <int R, bool RES>
-__global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const GaussLayout& L = a.L;
-  const int tid = threadIdx.x;
-  const bool producer = tid >= kNT;
-  Ctx C;
-  C.c = static_cast<int>(cluster_rank());
-  C.CS = static_cast<int>(cluster_size());
-  C.k = static_cast<int>(cluster_id_x());
-  C.m = L.m;
-  C.n = L.n;
-  C.r = L.r;
-  C.rho = L.rho;
-  C.j0 = C.c * L.ns;
-  C.nsc = max(0, min(L.ns, L.n - C.j0));
-  C.ntile = L.ns / kTW;
-  C.stages = L.stages;
-  C.err = a.err;
-  C.tile_seq = 0;
-  const Carve cv = carve(L, RES ? 1 : 0);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + cv.bars);
-  C.full = bars;
-  C.empty = bars + 16;
-  uint64_t* slab_bar = bars + 32;
-  C.xbar = bars + 33;
-  const size_t slab_elems = static_cast<size_t>(C.ntile) * C.m * kTW;
-  C.Ag = a.A + (static_cast<size_t>(C.k) * C.CS + C.c) * slab_elems;
-  C.Asl = RES ? reinterpret_cast<const float*>(smem + cv.slab) : nullptr;
-  C.ring = reinterpret_cast<const float*>(smem + cv.slab);
-  C.Us = reinterpret_cast<float*>(smem + cv.Us);
-  C.W = reinterpret_cast<float*>(smem + cv.W);
-  C.yv = reinterpret_cast<float*>(smem + cv.yv);
-  C.dv = reinterpret_cast<float*>(smem + cv.dv);
-  C.ev = reinterpret_cast<float*>(smem + cv.ev);
-  C.gs = reinterpret_cast<float*>(smem + cv.gs);
-  C.sl = reinterpret_cast<float*>(smem + cv.sl);
-  C.vv = reinterpret_cast<float*>(smem + cv.vv);
-  C.gpart = reinterpret_cast<float*>(smem + cv.gpart);
-  C.keys = reinterpret_cast<uint64_t*>(smem + cv.keys);
-  C.bc = reinterpret_cast<int*>(smem + cv.bc);
-  C.ck = reinterpret_cast<uint64_t*>(smem + cv.ck);
-  C.cvv = reinterpret_cast<float*>(smem + cv.cv);
-  C.cn = reinterpret_cast<int*>(smem + cv.cn);
-  C.G = reinterpret_cast<double*>(smem + cv.Gm);
-  C.Lc = C.G + kMaxR * kMaxR;
-  C.Gi = C.G + 2 * kMaxR * kMaxR;
-  C.fv = reinterpret_cast<double*>(smem + cv.fsm);
-  C.flags = reinterpret_cast<int*>(smem + cv.flags);
-  C.redd = reinterpret_cast<double*>(smem + cv.redd);
-  const int rho1 = max(C.rho, 1);
-  C.sup_j = reinterpret_cast<int*>(smem + cv.sup);
-  C.sup_v = reinterpret_cast<float*>(smem + cv.sup + static_cast<size_t>(rho1) * 4);
-  C.nloc = reinterpret_cast<int*>(smem + cv.sup + static_cast<size_t>(rho1) * 8);
-  C.prod = reinterpret_cast<float*>(smem + cv.prod);
-  C.xch = smem + cv.xch;
-  C.xs = cv.xs;
-  int ex = 0;
-  const int m = C.m, r = C.r, rho = C.rho, k = C.k;
-  const size_t tbytes = tile_bytes(L);
-  Tracer tr;
-  tr.out = (a.trace && tid == 0 && C.c == 0) ? a.trace + static_cast<size_t>(k) * kTracePhases : nullptr;
-  tr.t0 = clock64();
-
-  // ---- barriers -----------------------------------------------------------
-  if (tid == kNT) {
-    if (RES) {
-      mbar_init(slab_bar, 1);
-    } else {
-      for (int s = 0; s < C.stages; ++s) {
-        mbar_init(&C.full[s], 1);
-        mbar_init(&C.empty[s], kNW);
-      }
-    }
-    mbar_init(&C.xbar[0], C.CS);
-    mbar_init(&C.xbar[1], C.CS);
-  }
-  __syncthreads();
-  if (C.CS > 1) cluster_sync_all();  // peers' barriers initialised before any remote arrive
-
-  if (producer) {
-    // ---- producer warp: stream the slab's tiles for every product --------
-    if (tid == kNT) {
-      const char* src = reinterpret_cast<const char*>(C.Ag);
-      char* dst = reinterpret_cast<char*>(smem + cv.slab);
-      if (RES) {
-        const size_t bytes = slab_elems * 4;
-        mbar_arrive_expect_tx(slab_bar, static_cast<unsigned>(bytes));
-        for (size_t off = 0; off < bytes; off += 32768) {
-          const size_t rem = bytes - off;
-          bulk_copy_g2s(dst + off, src + off, static_cast<unsigned>(rem < 32768 ? rem : 32768),
-                        slab_bar);
-        }
-      } else {
-        const unsigned total = static_cast<unsigned>(passes_of(a.mode, a.tau, rho) * C.ntile);
-        for (unsigned t = 0; t < total; ++t) {
-          const unsigned s = t % C.stages, use = t / C.stages;
-          if (use > 0) {
-            unsigned it = 0;
-            while (!mbar_try_wait(&C.empty[s], (use - 1) & 1u))
-              if (++it > (1u << 22)) { report_error(a.err, kErrTimeout, k); break; }
-          }
-          mbar_arrive_expect_tx(&C.full[s], static_cast<unsigned>(tbytes));
-          bulk_copy_g2s(dst + s * tbytes, src + static_cast<size_t>(t % C.ntile) * tbytes,
-                        static_cast<unsigned>(tbytes), &C.full[s]);
-        }
-      }
-    }
-    __syncwarp();
-    if (C.CS > 1) cluster_sync_all();  // final cluster barrier (matches the consumers')
-    return;
-  }
-
-  // ---- consumers: small operands -------------------------------------------
-  for (int t = tid; t < L.ns * R; t += kNT) {
-    const int j = t / R, l = t - j * R;
-    C.Us[t] = (j < C.nsc && l < r) ? a.U[static_cast<size_t>(C.j0 + j) * r + l] : 0.f;
-  }
-  for (int i = tid; i < m; i += kNT) C.yv[i] = a.y[static_cast<size_t>(k) * m + i];
-  for (int j = tid; j < L.ns; j += kNT) C.sl[j] = 0.f;
-  if (tid == 0) {
-    C.flags[0] = 0;
-    int cnt = 0;
-    if (a.mode != kModeInit) {
-      for (int e = 0; e < rho; ++e) {
-        const int jg = a.S_idx[static_cast<size_t>(k) * rho + e];
-        if (jg >= C.j0 && jg < C.j0 + C.nsc) {
-          C.sup_j[cnt] = jg - C.j0;
-          C.sup_v[cnt] = a.S_val[static_cast<size_t>(k) * rho + e];
-          ++cnt;
-        }
-      }
-    }
-    *C.nloc = cnt;
-  }
-  csync();
-  for (int e = tid; e < *C.nloc; e += kNT) C.sl[C.sup_j[e]] = C.sup_v[e];
-  if (RES) {
-    if (!mbar_wait_bounded(slab_bar, 0) && (tid & 31) == 0) report_error(a.err, kErrTimeout, k);
-  }
-  csync();
-  tr.mark(0);
-
-  const bool project = (a.mode != kModeInit);
-
-  // ---------------------------------------------------------- W pass -----
-  bool need_gram = false;
-  if (project) {
-    float* xw = reinterpret_cast<float*>(xslot(C, ex));
-    w_pass<R>(C, C.CS > 1 ? xw : C.W);
-    if (C.CS > 1) {
-      xchg_publish_wait(C, ex);
-      for (int t = tid; t < m * R; t += kNT) {
-        float s = 0.f;
-        for (int p = 0; p < C.CS; ++p) s += peer_ptr(xw, p)[t];
-        C.W[t] = s;
-      }
-      ++ex;
-    }
-    csync();
-    need_gram = true;
-  }
-  tr.mark(1);
-
-  // ----------------------------------------------------- IHT (Alg. 2) ----
-  const int tau = (a.mode == kModeLS || rho == 0) ? 0 : a.tau;
-  int it = 0;
-  for (; it < tau; ++it) {
-    const bool zero_start = (a.mode == kModeInit && it == 0);
-    // u = P_perp (A s - y)   (A s = 0 for the zero start)
-    if (zero_start) {
-      for (int i = tid; i < m; i += kNT) C.dv[i] = -C.yv[i];
-      csync();
-    } else {
-      exchange_As<R>(C, ex, need_gram);
-      need_gram = false;
-      for (int i = tid; i < m; i += kNT) C.dv[i] -= C.yv[i];
-      csync();
-      tr.mark(2);
-      if (project) proj<R>(C, C.dv);
-      tr.mark(3);
-    }
-    col_pass(C, C.dv);  // g = A^T u  (= M^T (M s - z): P_perp is a projector)
-    tr.mark(4);
-    if (zero_start) {
-      for (int j = tid; j < C.nsc; j += kNT) C.vv[j] = C.gs[j];
-      csync();
-      hard_threshold(C, ex, false);  // support G of the zero start
-    }
-    // ||g_G||^2 and A g_G on the support, then mu
-    unsigned char* x = xslot(C, ex);
-    float* xg = reinterpret_cast<float*>(x);
-    double* xnum = reinterpret_cast<double*>(x + a16(static_cast<size_t>(m) * 4));
-    const int nl = *C.nloc;
-    for (int e = tid; e < nl; e += kNT) C.vv[e] = C.gs[C.sup_j[e]];
-    csync();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int e = 0; e < nl; ++e) s = dfma(static_cast<double>(C.vv[e]), C.vv[e], s);
-      *xnum = s;
-    }
-    gather(C, C.vv, xg);
-    xchg_publish_wait(C, ex);
-    reduce_m(C, xg, C.ev);
-    double num = 0.0;
-    for (int p = 0; p < C.CS; ++p) num += *peer_ptr(xnum, p);
-    ++ex;
-    csync();
-    tr.mark(5);
-    if (project) proj<R>(C, C.ev);
-    const double den = norm2_m(C, C.ev);
-    tr.mark(6);
-    if (!(den > 0.0)) {  // ||M g_G|| = 0: the column's IHT stops
-      ++it;
-      break;
-    }
-    double mu = num / den;
-    if (!isfinite(mu)) {
-      if (tid == 0) report_error(a.err, kErrNaN, k);
-      mu = 0.0;
-    }
-    const float muf = static_cast<float>(mu);
-    for (int j = tid; j < C.nsc; j += kNT) C.vv[j] = fmaf(-muf, C.gs[j], C.sl[j]);
-    csync();
-    hard_threshold(C, ex, true);
-    tr.mark(7);
-  }
-  for (; it < tau; ++it) drain_pass(C);  // products the stopped IHT no longer needs
-
-  // ------------------------------------------------------ final stage -----
-  exchange_As<R>(C, ex, need_gram);  // A s with the final support
-  for (int i = tid; i < m; i += kNT) C.dv[i] = C.yv[i] - C.dv[i];  // y - A s
-  csync();
-  tr.mark(8);
-  if (a.mode != kModeInit) {
-    ls_solve<R>(C, C.dv);  // b = G^{-1} W^T (y - A s)   (FP64)
-    if (C.c == 0 && tid < r) a.B[static_cast<size_t>(k) * r + tid] = static_cast<float>(C.fv[16 + tid]);
-    if (a.mode == kModeIter) {
-      for (int i = tid; i < m; i += kNT) {  // W b + A s - y
-        double s = -static_cast<double>(C.dv[i]);
-#pragma unroll
-        for (int l = 0; l < R; ++l) s = dfma(static_cast<double>(C.W[i * R + l]), C.fv[16 + l], s);
-        C.ev[i] = static_cast<float>(s);
-      }
-      csync();
-    }
-  }
-  tr.mark(9);
-  if (a.mode != kModeLS) {
-    col_pass(C, a.mode == kModeInit ? C.dv : C.ev);
-    tr.mark(10);
-    float* Hk = a.H + static_cast<size_t>(k) * C.n + C.j0;
-    for (int j = tid; j < C.nsc; j += kNT) Hk[j] = C.gs[j];
-    // S_k: this CTA's entries ascending by index, after those of lower ranks
-    const int nl = *C.nloc;
-    int off = 0;
-    for (int p = 0; p < C.c; ++p) off += C.cn[p];
-    for (int e = tid; e < nl; e += kNT) {
-      const int je = C.sup_j[e];
-      int pos = 0;
-      for (int f = 0; f < nl; ++f) pos += C.sup_j[f] < je;
-      if (off + pos < rho) {
-        a.S_idx[static_cast<size_t>(k) * rho + off + pos] = C.j0 + je;
-        a.S_val[static_cast<size_t>(k) * rho + off + pos] = C.sup_v[e];
-      }
-    }
-  }
-  csync();
-  tr.mark(11);
-  if (C.CS > 1) cluster_sync_all();  // no CTA leaves while a peer may still read its slots
-}
-
-template <int R, bool RES>
-void* kernel_ptr() {
-  return reinterpret_cast<void*>(&sweep_kernel<R, RES>);
-}
+using namespace sweep;
 
 void* pick_kernel(int r, int resident) {
-  const int RP = (r + 3) & ~3;
-  switch (RP) {
-    case 4: return resident ? kernel_ptr<4, true>() : kernel_ptr<4, false>();
-    case 8: return resident ? kernel_ptr<8, true>() : kernel_ptr<8, false>();
-    case 12: return resident ? kernel_ptr<12, true>() : kernel_ptr<12, false>();
-    default: return resident ? kernel_ptr<16, true>() : kernel_ptr<16, false>();
+  switch (sweep_rpad(r)) {
+    case 2: return sweep_kernel_r2(resident);
+    case 3: return sweep_kernel_r3(resident);
+    case 4: return sweep_kernel_r4(resident);
+    case 5: return sweep_kernel_r5(resident);
+    case 6: return sweep_kernel_r6(resident);
+    case 8: return sweep_kernel_r8(resident);
+    case 10: return sweep_kernel_r10(resident);
+    case 12: return sweep_kernel_r12(resident);
+    default: return sweep_kernel_r16(resident);
   }
 }
 
