@@ -158,7 +158,9 @@ def iht(z, M, MH, rho, tau, s0, mu_rule="support", idx0=None):
     For t = 1..tau: g = M^H(M s - z) (the gradient of ||M s - z||^2 up to the
     factor 2, which cancels in mu g); mu = ||g_G||^2 / ||M g_G||^2 on the
     current support G; s <- HardThreshold(s - mu g, rho).
-    Returns (s (K, n), support (K, rho) ascending, margin (K,)).
+    Returns (s (K, n), support (K, rho) ascending, margin (K,)) where margin is
+    the smallest HardThreshold margin of the column over the sweeps (the gap
+    that any arithmetic must resolve to reproduce the supports).
     """
     s = np.array(s0, copy=True)
     K, n = s.shape
@@ -189,7 +191,7 @@ def iht(z, M, MH, rho, tau, s0, mu_rule="support", idx0=None):
         s_new = densify(idx, vals, n)
         s[active] = s_new[active]
         idx_cur[active] = idx[active]
-        margin[active] = mg[active]
+        margin[active] = np.minimum(margin[active], mg[active])
     if idx_cur is None:
         idx_cur = np.tile(np.arange(rho, dtype=np.int64), (K, 1))
     return s, idx_cur, margin
@@ -253,6 +255,7 @@ class OracleLog:
     U: list = field(default_factory=list)
     B: list = field(default_factory=list)
     S_idx: list = field(default_factory=list)
+    S_val: list = field(default_factory=list)
     margin: list = field(default_factory=list)
     eta: float = None
     init_sv: np.ndarray = None
@@ -348,6 +351,8 @@ def run_alg1(op, Y, r, rho, T, tau0=10, tau=3, c_eta=0.14, Xstar=None,
             log.U.append(st.U.copy())
             log.B.append(st.B.copy())
             log.S_idx.append(st.S_idx.copy())
+            log.S_val.append(np.take_along_axis(st.S, st.S_idx, axis=1) if st.S_idx.size
+                             else np.zeros((op.q, 0)))
             log.margin.append(margin.copy())
 
     record(0, m0)

@@ -70,6 +70,7 @@ struct lrs_ctx {
   double* errpart = nullptr;
   unsigned long long* trace = nullptr;  // q x kTracePhases (profile = 2)
   int nblk = 0;
+  int power_iters_done = 0;
   // graph of one steady-state iteration
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -357,8 +358,8 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
   if (o.c_eta == 0) o.c_eta = 0.14;
   if (o.rho_max == 0) o.rho_max = rho;
   if (o.rho_max > n) return fail(LRS_ERR_ARG, "lrs_create: rho_max > n");
-  if (o.power_iters == 0) o.power_iters = 300;
-  if (o.power_tol == 0) o.power_tol = 1e-6;
+  if (o.power_iters == 0) o.power_iters = 1000;
+  if (o.power_tol == 0) o.power_tol = 1e-11;
   if (o.refine_every == 0) o.refine_every = 1;
 
   lrs_ctx* h = new lrs_ctx();
@@ -390,7 +391,7 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
   if ((st = dalloc(&h->A, per_col * q)) || (st = dalloc(&h->y, size_t(m) * q)) ||
       (st = dalloc(&h->Upad, upad_n)) ||
       (st = dalloc(&h->U, size_t(n) * r)) || (st = dalloc(&h->Bk, size_t(q) * r)) ||
-      (st = dalloc(&h->S_idx, size_t(q) * h->rho)) || (st = dalloc(&h->S_val, size_t(q) * h->rho)) ||
+      (st = dalloc(&h->S_idx, size_t(q) * std::max(1, h->rho))) || (st = dalloc(&h->S_val, size_t(q) * std::max(1, h->rho))) ||
       (st = dalloc(&h->H, size_t(q) * n)) || (st = dalloc(&h->grad, size_t(n) * r)) ||
       (st = dalloc(&h->Z, size_t(n) * r)) || (st = dalloc(&h->U2, size_t(n) * r)) ||
       (st = dalloc(&h->P, size_t(q) * r)) || (st = dalloc(&h->part, size_t(h->nblk) * r * r)) ||
@@ -470,30 +471,52 @@ lrs_status lrs_init(lrs_t h) {
   // s_k = IHT(y_k, A_k, rho, tau0, 0); L0 column k = A_k^T (y_k - A_k s_k) -> H
   lrs_status st = launch_sweep(h, kModeInit, h->opt.tau0);
   if (st) return st;
-  // U0: top-r left singular subspace of L0 (= H^T) by subspace iteration
-  std::vector<float> U0 = start_block(h->n, h->r, h->opt.seed + 1);
-  CUDA_TRY(cudaMemcpyAsync(h->U2, U0.data(), sizeof(float) * U0.size(), cudaMemcpyHostToDevice,
-                           h->stream));
-  CUDA_TRY(cudaStreamSynchronize(h->stream));
-  CUDA_TRY(cholqr2(g, h->U2, h->U, h->err, h->stream));
-  double* D = h->small + 2 * 16 * 16;
+  // U0: top-r left singular subspace of L0 (= H^T) by subspace iteration in
+  // FP64 (U, L0^T U and L0 L0^T U held in FP64; L0 itself is the FP32 sweep
+  // output), Cholesky-QR2 after every product.
   const int r = h->r;
-  for (int it = 0; it < h->opt.power_iters; ++it) {
-    CUDA_TRY(project_cols(g, h->H, h->U, h->P, h->stream));      // P = L0^T U
-    CUDA_TRY(grad_reduce(g, h->H, h->P, h->stream));             // grad = L0 P
-    CUDA_TRY(cudaMemcpyAsync(h->U2, h->U, sizeof(float) * h->n * r, cudaMemcpyDeviceToDevice,
-                             h->stream));
-    CUDA_TRY(cholqr2(g, h->grad, h->U, h->err, h->stream));      // U = Q(L0 L0^T U)
-    if ((it % 5) == 4 || it + 1 == h->opt.power_iters) {
-      // subspace change ||(I - U_old U_old^T) U||_F
-      CUDA_TRY(subspace_change(g, h->U2, h->U, D, D + 16 * 16, h->stream));
+  const size_t nr = static_cast<size_t>(h->n) * r;
+  double *Ud = nullptr, *Uold = nullptr, *Zd = nullptr, *Pd = nullptr, *Td = nullptr;
+  auto free_d = [&]() {
+    if (Td) cudaFree(Td);
+    if (Ud) cudaFree(Ud);
+    if (Uold) cudaFree(Uold);
+    if (Zd) cudaFree(Zd);
+    if (Pd) cudaFree(Pd);
+  };
+  if (cudaMalloc(&Ud, nr * 8) != cudaSuccess || cudaMalloc(&Uold, nr * 8) != cudaSuccess ||
+      cudaMalloc(&Zd, nr * 8) != cudaSuccess || cudaMalloc(&Td, nr * 8) != cudaSuccess ||
+      cudaMalloc(&Pd, static_cast<size_t>(h->q) * r * 8) != cudaSuccess) {
+    free_d();
+    return fail(LRS_ERR_OOM, "lrs_init: no device memory for the subspace iteration");
+  }
+  std::vector<float> U0f = start_block(h->n, h->r, h->opt.seed + 1);
+  std::vector<double> U0(U0f.begin(), U0f.end());
+  cudaError_t e = cudaMemcpyAsync(Zd, U0.data(), nr * 8, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = dcholqr2(g, Zd, Td, Ud, nullptr, h->err, h->stream);
+  double* D = h->small + 2 * 16 * 16;
+  int it = 0;
+  for (; it < h->opt.power_iters && e == cudaSuccess; ++it) {
+    e = cudaMemcpyAsync(Uold, Ud, nr * 8, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = dsubspace_step(g, h->H, Uold, Pd, Zd, h->stream);
+    if (e == cudaSuccess) e = dcholqr2(g, Zd, Td, Ud, nullptr, h->err, h->stream);
+    if (e == cudaSuccess && ((it % 5) == 4 || it + 1 == h->opt.power_iters)) {
+      e = dsubspace_change(g, Uold, Ud, D, D + 16 * 16, h->stream);
       double chg2 = 0.0;
-      CUDA_TRY(cudaMemcpyAsync(&chg2, D + 16 * 16, sizeof(double), cudaMemcpyDeviceToHost,
-                               h->stream));
-      CUDA_TRY(cudaStreamSynchronize(h->stream));
-      if (std::sqrt(std::max(0.0, chg2)) < h->opt.power_tol) break;
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&chg2, D + 16 * 16, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (e == cudaSuccess && std::sqrt(std::max(0.0, chg2)) < h->opt.power_tol) break;
     }
   }
+  // final orthonormalisation writes the FP32 U and its padded copy
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Zd, Ud, nr * 8, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess) e = dcholqr2(g, Zd, Td, Ud, h->U, h->err, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  free_d();
+  if (e != cudaSuccess) return fail(LRS_ERR_CUDA, std::string("lrs_init: ") + cudaGetErrorString(e));
+  h->power_iters_done = it;
   // b_k = (A_k U0)^+ (y_k - A_k s_k)
   st = launch_sweep(h, kModeLS, 0);
   if (st) return st;

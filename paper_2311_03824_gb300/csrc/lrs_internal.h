@@ -91,6 +91,13 @@ cudaError_t project_cols(const GlobalWork& g, const float* H, const float* U, fl
 // ||(I - Uold Uold^T) Unew||_F^2 (FP64) into *out, D = Uold^T Unew into D_rr.
 cudaError_t subspace_change(const GlobalWork& g, const float* Uold, const float* Unew,
                             double* D_rr, double* out, cudaStream_t s);
+// FP64 pieces of the spectral initialisation (subspace iteration on L0 = H^T).
+cudaError_t dcholqr2(const GlobalWork& g, const double* Zin, double* Ztmp, double* Uout,
+                     float* Uf, int* err, cudaStream_t s);
+cudaError_t dsubspace_step(const GlobalWork& g, const float* H, const double* U, double* P,
+                           double* Z, cudaStream_t s);  // Z = H^T (H U)
+cudaError_t dsubspace_change(const GlobalWork& g, const double* Uold, const double* Unew,
+                             double* D_rr, double* out, cudaStream_t s);
 cudaError_t subspace_overlap(const GlobalWork& g, const float* Ua, const float* Ub,
                              double* out_rr, cudaStream_t s);
 

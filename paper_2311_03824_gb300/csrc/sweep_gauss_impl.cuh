@@ -330,54 +330,67 @@ __device__ __forceinline__ void col_pass(Ctx& C, const float* v, bool fill_cache
   csync();
 }
 
-// W partial = A_slab U_slab (thread per row, up to 2 rows per thread; U read
-// as 128-bit broadcasts), into dst (m x R)
+// Row iterations per lane of the W pass and the number of sub-passes over
+// the slab it needs (each sub-pass covers up to 8 row iterations per lane).
+__host__ __device__ inline int w_row_iters(int m) { return (((m + 7) / 8 + 3) / 4); }
+__host__ __device__ inline int w_chunks(int m) { return (w_row_iters(m) + 7) / 8; }
+
+// W partial = A_slab U_slab into dst (m x R).  Warps split the rows (RB per
+// warp); in a tile, lane (ro = lane / 8, q = lane % 8) holds U for the tile's
+// columns 4q..4q+3 in registers and accumulates rows w*RB + 4t + ro over all
+// tiles; the 8 lanes of a row are summed by shuffles at the end.
 template <int R>
 __device__ __forceinline__ void w_pass(Ctx& C, float* dst) {
-  const int m = C.m;
-  float acc[2][R];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int q = lane & 7, ro = lane >> 3;
+  const int nri = w_row_iters(C.m), RB = 4 * nri;
+  const int nch = (nri + 7) / 8;
+  for (int ch = 0; ch < nch; ++ch) {
+    float acc[8][R];
 #pragma unroll
-  for (int t = 0; t < 2; ++t)
+    for (int t = 0; t < 8; ++t)
 #pragma unroll
-    for (int l = 0; l < R; ++l) acc[t][l] = 0.f;
-  for (int b = 0; b < C.ntile; ++b) {
-    const float* tl = acquire_tile(C, b);
-    cache_fill_from_tile(C, tl, b);
+      for (int l = 0; l < R; ++l) acc[t][l] = 0.f;
+    for (int b = 0; b < C.ntile; ++b) {
+      const float* tl = acquire_tile(C, b);
+      if (ch == 0) cache_fill_from_tile(C, tl, b);
+      float u[4 * R];
+      const float4* u4 = reinterpret_cast<const float4*>(C.Us + (b * kTW + 4 * q) * R);
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int i = threadIdx.x + kNT * t;
-      if (i < m) {
-        const float* row = tl + i * kTW;
-#pragma unroll 2
-        for (int q4 = 0; q4 < 8; ++q4) {
-          const float4 av = *reinterpret_cast<const float4*>(row + ((q4 ^ (i & 7)) << 2));
-          const float4* u4 = reinterpret_cast<const float4*>(C.Us + (b * kTW + 4 * q4) * R);
-          float u[4 * R];
+      for (int z = 0; z < R; ++z) {
+        const float4 w = u4[z];
+        u[4 * z] = w.x; u[4 * z + 1] = w.y; u[4 * z + 2] = w.z; u[4 * z + 3] = w.w;
+      }
 #pragma unroll
-          for (int z = 0; z < R; ++z) {
-            const float4 w = u4[z];
-            u[4 * z] = w.x; u[4 * z + 1] = w.y; u[4 * z + 2] = w.z; u[4 * z + 3] = w.w;
-          }
+      for (int t = 0; t < 8; ++t) {
+        const int i = wid * RB + 4 * (ch * 8 + t) + ro;
+        if (ch * 8 + t < nri && i < C.m) {
+          const float4 a = *reinterpret_cast<const float4*>(tl + i * kTW + ((q ^ (i & 7)) << 2));
 #pragma unroll
           for (int l = 0; l < R; ++l) {
             float s = acc[t][l];
-            s = fmaf(av.x, u[l], s);
-            s = fmaf(av.y, u[R + l], s);
-            s = fmaf(av.z, u[2 * R + l], s);
-            s = fmaf(av.w, u[3 * R + l], s);
+            s = fmaf(a.x, u[l], s);
+            s = fmaf(a.y, u[R + l], s);
+            s = fmaf(a.z, u[2 * R + l], s);
+            s = fmaf(a.w, u[3 * R + l], s);
             acc[t][l] = s;
           }
         }
       }
+      release_tile(C);
     }
-    release_tile(C);
-  }
 #pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    const int i = threadIdx.x + kNT * t;
-    if (i < m)
+    for (int t = 0; t < 8; ++t) {
+      const int i = wid * RB + 4 * (ch * 8 + t) + ro;
 #pragma unroll
-      for (int l = 0; l < R; ++l) dst[i * R + l] = acc[t][l];
+      for (int l = 0; l < R; ++l) {
+        float v = acc[t][l];
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        if ((l & 7) == q && ch * 8 + t < nri && i < C.m) dst[i * R + l] = v;
+      }
+    }
   }
 }
 
@@ -635,9 +648,13 @@ __device__ __forceinline__ int local_topk(Ctx& C) {
   for (int shift = 24; shift >= 0; shift -= 8) {
     for (int t = threadIdx.x; t < 256; t += kNT) hist[t] = 0;
     csync();
-    for (int j = threadIdx.x; j < nsc; j += kNT) {
-      const unsigned key = __float_as_uint(fabsf(C.vv[j]));
-      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1);
+    for (int j0 = threadIdx.x - lane; j0 < nsc; j0 += kNT) {
+      const int j = j0 + lane;
+      const unsigned key = j < nsc ? __float_as_uint(fabsf(C.vv[j])) : 0u;
+      const bool in = j < nsc && (key & mask) == prefix;
+      const unsigned digit = in ? ((key >> shift) & 255u) : 256u;
+      const unsigned peers = __match_any_sync(0xffffffffu, digit);
+      if (in && (__ffs(peers) - 1) == lane) atomicAdd(&hist[digit], __popc(peers));
     }
     csync();
     if (threadIdx.x < 32) {
@@ -704,9 +721,52 @@ __device__ __forceinline__ int local_topk(Ctx& C) {
 // HardThreshold over the cluster: values vv[0..nsc) -> new local support
 // (exactly rho entries cluster-wide, largest |v| first, ties to the lower
 // index).  keep_values = false keeps zero values (support of g at s = 0).
+// Single-CTA fast path of the local top-K: when this CTA holds the whole
+// current support (rho entries), every element of the new top-rho has |v| at
+// least the smallest |v| on the current support, so the candidates are the
+// elements at or above it; they are ranked exactly by the full key.  Returns
+// the number of candidates in key order in C.tie[0..K), or -1 when the
+// candidate set is too large (the caller then uses the radix select).
+__device__ __forceinline__ int local_topk_support(Ctx& C) {
+  const int nl = *C.nloc, K = min(C.rho, C.nsc);
+  if (C.CS != 1 || nl != C.rho || K == 0) return -1;
+  int* info = C.hist + 256;
+  int* cand = C.tie + C.ntile * kTW;   // up to 2*rho + 8 entries
+  const int cap = 2 * C.rho + 8;
+  float* tmin = reinterpret_cast<float*>(C.hist);
+  if (threadIdx.x < 32) {
+    float t = INFINITY;
+    for (int e = threadIdx.x; e < nl; e += 32) t = fminf(t, fabsf(C.vv[C.sup_j[e]]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fminf(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (threadIdx.x == 0) { tmin[0] = t; info[3] = 0; }
+  }
+  csync();
+  const float t0 = tmin[0];
+  for (int j = threadIdx.x; j < C.nsc; j += kNT) {
+    if (fabsf(C.vv[j]) >= t0) {
+      const int slot = atomicAdd(&info[3], 1);
+      if (slot < cap) cand[slot] = j;
+    }
+  }
+  csync();
+  const int c = info[3];
+  if (c > cap) return -1;
+  for (int t = threadIdx.x; t < c; t += kNT) {
+    const int j = cand[t];
+    const uint64_t kj = ht_key(C.vv[j], C.j0 + j);
+    int rank = 0;
+    for (int u = 0; u < c; ++u) rank += ht_key(C.vv[cand[u]], C.j0 + cand[u]) > kj;
+    if (rank < K) C.tie[rank] = j;
+  }
+  csync();
+  return K;
+}
+
 __device__ __forceinline__ void hard_threshold(Ctx& C, int& ex, bool keep_values) {
   const int rho = C.rho;
-  const int K = local_topk(C);  // local candidates in key order in C.tie[0..K)
+  int K = local_topk_support(C);
+  if (K < 0) K = local_topk(C);  // local candidates in key order in C.tie[0..K)
   unsigned char* x = xslot(C, ex);
   int* xcnt = reinterpret_cast<int*>(x);
   uint64_t* xkey = reinterpret_cast<uint64_t*>(x + 16);
@@ -762,14 +822,15 @@ __device__ __forceinline__ void hard_threshold(Ctx& C, int& ex, bool keep_values
 
 // number of products over A_k of one column in each mode (the producer
 // streams the slab once per product)
-__device__ __forceinline__ int passes_of(int mode, int tau, int rho) {
-  if (mode == kModeLS) return 1;
+__device__ __forceinline__ int passes_of(int mode, int tau, int rho, int m) {
+  const int wp = w_chunks(m);
+  if (mode == kModeLS) return wp;
   const int t = (rho == 0) ? 0 : tau;
-  return mode == kModeInit ? t + 1 : t + 2;
+  return mode == kModeInit ? t + 1 : t + 1 + wp;
 }
 
 template <int R, bool RES>
-__global__ void __launch_bounds__(kThreadsAll, 1) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const GaussLayout& L = a.L;
   const int tid = threadIdx.x;
@@ -870,7 +931,7 @@ __global__ void __launch_bounds__(kThreadsAll, 1) sweep_kernel(const SweepArgs a
                         slab_bar);
         }
       } else {
-        const unsigned total = static_cast<unsigned>(passes_of(a.mode, a.tau, rho) * C.ntile);
+        const unsigned total = static_cast<unsigned>(passes_of(a.mode, a.tau, rho, m) * C.ntile);
         for (unsigned t = 0; t < total; ++t) {
           const unsigned s = t % C.stages, use = t / C.stages;
           if (use > 0) {
