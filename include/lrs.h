@@ -172,6 +172,19 @@ lrs_status lrs_set_reference(lrs_t h, const void* Xref, int32_t mem_kind);
  * LRS_ERR_CUDA. */
 lrs_status lrs_phase_times(lrs_t h, double* out4);
 
+/* Orthonormalise the columns of Z by Cholesky-QR2 (the QR step of
+ * Algorithm 1, U+ = QR(U - eta grad)): Q = Z R^{-1} with R the upper
+ * triangular factor with positive diagonal, i.e. the Q factor of the QR
+ * decomposition with diag(R) > 0.  Gram matrices and Cholesky factors are
+ * FP64 (r x r), products FP32, two passes.
+ *  Z, Q:   device pointers, n x r row-major float (row i at offset i*r);
+ *          Q may equal Z.  1 <= r <= 16, n >= r.
+ *  stream: cudaStream_t (NULL = legacy default stream); the call allocates
+ *          its scratch with cudaMalloc, runs on the stream and synchronises it.
+ * Errors: LRS_ERR_ARG, LRS_ERR_OOM, LRS_ERR_NUMERICAL (Z rank deficient),
+ * LRS_ERR_CUDA. */
+lrs_status lrs_orthonormalize(const float* Z, float* Q, int64_t n, int32_t r, void* stream);
+
 /* Per-column SM cycle counts of the sweep phases accumulated by
  * lrs_iterate since the previous call (handle created with profile = 2;
  * tracing aid).  out receives q x 12 counters, column-major by column k:

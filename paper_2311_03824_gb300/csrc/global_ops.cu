@@ -469,6 +469,27 @@ cudaError_t cholqr2(const GlobalWork& g, const float* Zin, float* Uout, int* err
   return cudaGetLastError();
 }
 
+int qr_blocks(int64_t n) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n + 63) / 64;
+  const int64_t nb = want < (nsm > 0 ? nsm : 148) ? want : (nsm > 0 ? nsm : 148);
+  return static_cast<int>(nb > 0 ? nb : 1);
+}
+
+cudaError_t cholqr2_into(int n, int r, const float* Z, float* Q, float* tmp, double* part,
+                         double* rfac, int* err, int nblk, cudaStream_t s) {
+  double* R1 = rfac;
+  double* R2 = rfac + r * r;
+  gram_part_kernel<<<nblk, 256, 0, s>>>(n, r, Z, nullptr, nullptr, nullptr, part);
+  chol_fin_kernel<<<1, 256, 0, s>>>(r, nblk, part, R1, err);
+  apply_rinv_kernel<<<nblk, 256, 0, s>>>(n, r, Z, R1, tmp, part);
+  chol_fin_kernel<<<1, 256, 0, s>>>(r, nblk, part, R2, err);
+  apply_rinv_kernel<<<nblk, 256, 0, s>>>(n, r, tmp, R2, Q, nullptr);
+  return cudaGetLastError();
+}
+
 cudaError_t qr_step(const GlobalWork& g, float* U, const double* eta_dev, int* err,
                     cudaStream_t s) {
   const int rr = g.r * g.r;

@@ -688,6 +688,39 @@ lrs_status lrs_describe(lrs_t h, char* buf, int32_t len) {
   return LRS_OK;
 }
 
+lrs_status lrs_orthonormalize(const float* Z, float* Q, int64_t n, int32_t r, void* stream) {
+  if (!Z || !Q) return fail(LRS_ERR_ARG, "lrs_orthonormalize: NULL pointer");
+  if (r < 1 || r > 16 || n < r || n >= (int64_t(1) << 30))
+    return fail(LRS_ERR_ARG, "lrs_orthonormalize: need 1 <= r <= 16 and r <= n < 2^30");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nblk = qr_blocks(n);
+  float* tmp = nullptr;
+  double* part = nullptr;
+  int* err = nullptr;
+  auto cleanup = [&]() {
+    if (tmp) cudaFree(tmp);
+    if (part) cudaFree(part);
+    if (err) cudaFree(err);
+  };
+  if (cudaMalloc(&tmp, sizeof(float) * n * r) != cudaSuccess ||
+      cudaMalloc(&part, sizeof(double) * (static_cast<size_t>(nblk) * r * r + 2 * r * r)) != cudaSuccess ||
+      cudaMalloc(&err, 2 * sizeof(int)) != cudaSuccess) {
+    cleanup();
+    return fail(LRS_ERR_OOM, "lrs_orthonormalize: scratch allocation failed");
+  }
+  int eh[2] = {0, 0};
+  cudaError_t e = cudaMemsetAsync(err, 0, 2 * sizeof(int), s);
+  if (e == cudaSuccess)
+    e = cholqr2_into(static_cast<int>(n), r, Z, Q, tmp, part, part + static_cast<size_t>(nblk) * r * r,
+                     err, nblk, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(eh, err, sizeof(eh), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cleanup();
+  if (e != cudaSuccess) return fail(LRS_ERR_CUDA, std::string("lrs_orthonormalize: ") + cudaGetErrorString(e));
+  if (eh[0]) return fail(LRS_ERR_NUMERICAL, "lrs_orthonormalize: Z^T Z not positive definite");
+  return LRS_OK;
+}
+
 lrs_status lrs_destroy(lrs_t h) {
   if (!h) return LRS_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);

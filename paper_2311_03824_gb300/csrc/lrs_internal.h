@@ -91,6 +91,13 @@ cudaError_t project_cols(const GlobalWork& g, const float* H, const float* U, fl
 // ||(I - Uold Uold^T) Unew||_F^2 (FP64) into *out, D = Uold^T Unew into D_rr.
 cudaError_t subspace_change(const GlobalWork& g, const float* Uold, const float* Unew,
                             double* D_rr, double* out, cudaStream_t s);
+// Cholesky-QR2 of an n x r row-major FP32 matrix Z into Q with caller-given
+// scratch: tmp (n*r floats), part (nblk*r*r doubles), rfac (2*r*r doubles),
+// err (2 ints, zero on entry).  Blocks: qr_blocks(n).
+int qr_blocks(int64_t n);
+cudaError_t cholqr2_into(int n, int r, const float* Z, float* Q, float* tmp, double* part,
+                         double* rfac, int* err, int nblk, cudaStream_t s);
+
 // FP64 pieces of the spectral initialisation (subspace iteration on L0 = H^T).
 cudaError_t dcholqr2(const GlobalWork& g, const double* Zin, double* Ztmp, double* Uout,
                      float* Uf, int* err, cudaStream_t s);

@@ -69,6 +69,7 @@ def lib():
             "lrs_phase_times": [_P, ctypes.POINTER(ctypes.c_double)],
             "lrs_describe": [_P, ctypes.c_char_p, ctypes.c_int32],
             "lrs_sweep_trace": [_P, _P, ctypes.c_int64],
+            "lrs_orthonormalize": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P],
             "lrs_destroy": [_P],
         }
         for name, args in sig.items():
@@ -193,6 +194,13 @@ def lrs_describe(h):
     _check(lib().lrs_describe(h, buf, 512))
     import json
     return json.loads(buf.value.decode())
+
+
+def lrs_orthonormalize(Z, Q, stream=None):
+    """Q = Cholesky-QR2 orthonormalisation of Z (torch CUDA float32, n x r)."""
+    n, r = Z.shape
+    st = None if stream is None else _P(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+    _check(lib().lrs_orthonormalize(_P(Z.data_ptr()), _P(Q.data_ptr()), n, r, st))
 
 
 def lrs_destroy(h):

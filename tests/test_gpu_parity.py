@@ -100,6 +100,6 @@ def test_init_matches_oracle_subspace_and_supports():
     U, B, S_idx, S_val = s.get()
     s.close()
     cosines = np.linalg.svd(U.T.astype(np.float64) @ st.U, compute_uv=False)
-    assert np.all(np.abs(1 - cosines) < 1e-9)          # same subspace
+    assert np.max(np.abs(1 - cosines)) < 1e-6, cosines  # same subspace (FP32 L0, FP32 U)
     dec = margin > MARGIN_FP32
     assert np.all(np.sort(S_idx[dec], 1) == st.S_idx[dec])
