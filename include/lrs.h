@@ -185,6 +185,28 @@ lrs_status lrs_phase_times(lrs_t h, double* out4);
  * LRS_ERR_CUDA. */
 lrs_status lrs_orthonormalize(const float* Z, float* Q, int64_t n, int32_t r, void* stream);
 
+/* lrs_orthonormalize without any device allocation.  The paper has no
+ * counterpart: this call exists for callers that cannot allocate device
+ * memory when they need the step (their memory is all handed to their own
+ * pool, a serving loop must not take the device-wide synchronisation of
+ * cudaMalloc/cudaFree, or their GPU work is recorded once and replayed).
+ * It computes exactly what lrs_orthonormalize computes, with the same
+ * arguments and layouts, but uses a fixed scratch array of about 4.6 MB that
+ * lives in the library's device image: every GPU that loads the library holds
+ * it until the process exits.
+ *  Limits: 1 <= r <= 16, r <= n <= 65536; larger sizes return LRS_ERR_ARG.
+ *  The first call on a device (with that device current) looks up the
+ *  scratch address with cudaGetSymbolAddress; make that first call before
+ *  any stream capture.  All calls share the one array: calls whose work can
+ *  overlap on the GPU (different streams, or different host threads on one
+ *  device) race on it and must be serialised by the caller.  The call runs
+ *  on `stream` and synchronises it.  Its own error message is returned by
+ *  lrs_noalloc_last_error().
+ * Errors: LRS_ERR_ARG, LRS_ERR_NUMERICAL (Z rank deficient), LRS_ERR_CUDA. */
+lrs_status lrs_orthonormalize_noalloc(const float* Z, float* Q, int64_t n, int32_t r,
+                                      void* stream);
+const char* lrs_noalloc_last_error(void);
+
 /* Per-column SM cycle counts of the sweep phases accumulated by
  * lrs_iterate since the previous call (handle created with profile = 2;
  * tracing aid).  out receives q x 12 counters, column-major by column k:

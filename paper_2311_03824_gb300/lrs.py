@@ -70,6 +70,7 @@ def lib():
             "lrs_describe": [_P, ctypes.c_char_p, ctypes.c_int32],
             "lrs_sweep_trace": [_P, _P, ctypes.c_int64],
             "lrs_orthonormalize": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P],
+            "lrs_orthonormalize_noalloc": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P],
             "lrs_destroy": [_P],
         }
         for name, args in sig.items():
@@ -78,6 +79,8 @@ def lib():
             f.restype = ctypes.c_int
         L.lrs_last_error.argtypes = []
         L.lrs_last_error.restype = ctypes.c_char_p
+        L.lrs_noalloc_last_error.argtypes = []
+        L.lrs_noalloc_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -201,6 +204,15 @@ def lrs_orthonormalize(Z, Q, stream=None):
     n, r = Z.shape
     st = None if stream is None else _P(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
     _check(lib().lrs_orthonormalize(_P(Z.data_ptr()), _P(Q.data_ptr()), n, r, st))
+
+
+def lrs_orthonormalize_noalloc(Z, Q, stream=None):
+    """lrs_orthonormalize with no device allocation (fixed scratch; n <= 65536)."""
+    n, r = Z.shape
+    st = None if stream is None else _P(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+    status = lib().lrs_orthonormalize_noalloc(_P(Z.data_ptr()), _P(Q.data_ptr()), n, r, st)
+    if status != LRS_OK:
+        raise LrsError(status, lib().lrs_noalloc_last_error().decode())
 
 
 def lrs_destroy(h):
