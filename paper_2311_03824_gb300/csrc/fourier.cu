@@ -1,0 +1,1312 @@
+// AltGDmin-LR+S for the row-masked 2D DFT operator (the Fourier / dynamic-MRI
+// case of Section I-A): A_k x = (F2 x)[Omega_k], A_k^H v = F2^H(zero-fill_k v),
+// F2 the unitary 2D DFT of an nx x ny frame, rows indexed kx*ny + ky in natural
+// order.  Complex throughout: transposes become conjugate transposes and
+// HardThreshold ranks by the modulus.
+//
+// Per GDmin iteration (Algorithm 1):
+//   FU = F2 U                      r forward 2D FFTs (shared by all frames),
+//                                  so W_k = A_k U = FU[Omega_k, :]
+//   sweep (one CTA per frame k)    G_k = W_k^H W_k and its inverse (FP64),
+//                                  IHT: A s and A g_G as sparse DFTs, g = A^H u
+//                                  as one inverse 2D FFT of the frame held in
+//                                  shared memory, HardThreshold by radix select,
+//                                  then b_k and res_k = W_k b_k + A_k s_k - y_k
+//   K = sum_k zero-fill_k(res_k) b_k^H   k-space accumulation through the
+//                                  inverse index of the masks (fixed order)
+//   grad = F2^H K                  r inverse 2D FFTs (linearity of F2)
+//   eta at t = 1, U <- Q(U - eta grad) by complex Cholesky-QR2 (FP64 r x r).
+// The initialisation forms L0 = [A_k^H (y_k - A_k s_k)] and its top-r left
+// singular subspace by FP64 complex subspace iteration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lrs_dev.cuh"
+#include "lrs_internal.h"
+
+namespace lrs {
+namespace fourier {
+
+constexpr int kFT = 512;   // threads of the frame kernels
+constexpr int kFW = kFT / 32;
+constexpr int kMaxR = 16;
+
+// ------------------------------------------------------------ complex --
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// acc += a * b
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
+  acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+  acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+  return acc;
+}
+// acc += conj(a) * b
+__device__ __forceinline__ float2 ccfma(float2 a, float2 b, float2 acc) {
+  acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
+  acc.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y));
+  return acc;
+}
+__device__ __forceinline__ double2 dcmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 dccmul(double2 a, double2 b) {  // conj(a) * b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------ 2D FFT --
+// In-place unitary 2D FFT of the frame X (nx rows x ny columns, row stride
+// ny + 1 complex) in shared memory by radix-2 decimation in time along the
+// rows, then along the columns.  tx[k] = exp(-2 pi i k / nx), k < nx (same for
+// ty); inverse uses the conjugate twiddles.  All threads of the CTA call it.
+__device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const float2* tx,
+                          const float2* ty, bool inverse) {
+  const int ld = ny + 1, n = nx * ny;
+  // rows: bit reversal, then lny stages
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int row = e / ny, j = e - row * ny;
+    const int p = static_cast<int>(__brev(static_cast<unsigned>(j)) >> (32 - lny));
+    if (lny > 0 && p > j) {
+      const float2 t = X[row * ld + j];
+      X[row * ld + j] = X[row * ld + p];
+      X[row * ld + p] = t;
+    }
+  }
+  __syncthreads();
+  for (int s = 0; s < lny; ++s) {
+    const int half = 1 << s, step = ny >> (s + 1);
+    for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
+      const int row = b / (ny / 2), t = b - row * (ny / 2);
+      const int j = t & (half - 1), i1 = ((t >> s) << (s + 1)) + j, i2 = i1 + half;
+      float2 w = ty[j * step];
+      if (inverse) w.y = -w.y;
+      const float2 a = X[row * ld + i1], c = cmul(X[row * ld + i2], w);
+      X[row * ld + i1] = cadd(a, c);
+      X[row * ld + i2] = csub(a, c);
+    }
+    __syncthreads();
+  }
+  // columns: bit reversal, then lnx stages
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int i = e / ny, col = e - i * ny;
+    const int p = static_cast<int>(__brev(static_cast<unsigned>(i)) >> (32 - lnx));
+    if (lnx > 0 && p > i) {
+      const float2 t = X[i * ld + col];
+      X[i * ld + col] = X[p * ld + col];
+      X[p * ld + col] = t;
+    }
+  }
+  __syncthreads();
+  for (int s = 0; s < lnx; ++s) {
+    const int half = 1 << s, step = nx >> (s + 1);
+    for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
+      const int col = b % ny, t = b / ny;
+      const int j = t & (half - 1), i1 = ((t >> s) << (s + 1)) + j, i2 = i1 + half;
+      float2 w = tx[j * step];
+      if (inverse) w.y = -w.y;
+      const float2 a = X[i1 * ld + col], c = cmul(X[i2 * ld + col], w);
+      X[i1 * ld + col] = cadd(a, c);
+      X[i2 * ld + col] = csub(a, c);
+    }
+    __syncthreads();
+  }
+  const float sc = rsqrtf(static_cast<float>(n));
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int row = e / ny, j = e - row * ny;
+    X[row * ld + j].x *= sc;
+    X[row * ld + j].y *= sc;
+  }
+  __syncthreads();
+}
+
+struct Geo {
+  int nx, ny, lnx, lny, n;
+};
+
+// out[f] = F2(in[f]) (or F2^H) for frames f; frames are n-vectors in natural
+// row-major order (pixel kx*ny + ky), frame f at in + f*n.
+__global__ void __launch_bounds__(kFT) fft_frames_kernel(Geo g, const float2* __restrict__ in,
+                                                         float2* __restrict__ out, int inverse,
+                                                         const float2* __restrict__ twx,
+                                                         const float2* __restrict__ twy) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  float2* X = reinterpret_cast<float2*>(sm);
+  float2* tx = X + static_cast<size_t>(g.nx) * (g.ny + 1);
+  float2* ty = tx + g.nx;
+  const size_t f = blockIdx.x;
+  for (int k = threadIdx.x; k < g.nx; k += blockDim.x) tx[k] = twx[k];
+  for (int k = threadIdx.x; k < g.ny; k += blockDim.x) ty[k] = twy[k];
+  for (int e = threadIdx.x; e < g.n; e += blockDim.x) {
+    const int row = e / g.ny, j = e - row * g.ny;
+    X[row * (g.ny + 1) + j] = in[f * g.n + e];
+  }
+  __syncthreads();
+  fft2_smem(X, g.nx, g.ny, g.lnx, g.lny, tx, ty, inverse != 0);
+  for (int e = threadIdx.x; e < g.n; e += blockDim.x) {
+    const int row = e / g.ny, j = e - row * g.ny;
+    out[f * g.n + e] = X[row * (g.ny + 1) + j];
+  }
+}
+
+// ----------------------------------------------------------- the sweep --
+struct FArgs {
+  Geo g;
+  int m, q, r, rho, tau, mode;
+  const float2* y;      // q x m
+  const int* mask;      // q x m
+  const float2* FU;     // r x n (column l = F2 u_l)
+  int* S_idx;           // q x rho
+  float2* S_val;        // q x rho
+  float2* B;            // q x r
+  float2* RES;          // q x m: W b + A s - y (iteration)
+  float2* H;            // q x n: L0 columns A^H (y - A s) (initialisation)
+  const float2* twx;
+  const float2* twy;
+  int* err;
+};
+
+struct FCarve {
+  size_t X, tx, ty, yv, dv, ev, msk, sp, sv, gv, G, Gi, vec, red, hist, cand, total;
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline FCarve fcarve(const Geo& g, int m, int rho) {
+  FCarve c;
+  size_t o = 0;
+  const int rh = rho > 0 ? rho : 1;
+  c.X = o;    o += al16(static_cast<size_t>(g.nx) * (g.ny + 1) * 8);
+  c.tx = o;   o += al16(static_cast<size_t>(g.nx) * 8);
+  c.ty = o;   o += al16(static_cast<size_t>(g.ny) * 8);
+  c.yv = o;   o += al16(static_cast<size_t>(m) * 8);
+  c.dv = o;   o += al16(static_cast<size_t>(m) * 8);
+  c.ev = o;   o += al16(static_cast<size_t>(m) * 8);
+  c.msk = o;  o += al16(static_cast<size_t>(m) * 4);
+  c.sp = o;   o += al16(static_cast<size_t>(rh) * 4 + 16);
+  c.sv = o;   o += al16(static_cast<size_t>(rh) * 8);
+  c.gv = o;   o += al16(static_cast<size_t>(rh) * 8);
+  c.G = o;    o += al16(4 * kMaxR * kMaxR * 16);     // G, L, Linv, Ginv (complex FP64)
+  c.vec = o;  o += al16(4 * kMaxR * 16);
+  c.red = o;  o += al16(static_cast<size_t>(kFW) * 2 * kMaxR * 4 + 64);
+  c.hist = o; o += al16(256 * 4 + 64);
+  c.cand = o; o += al16(static_cast<size_t>(2 * rh + 64) * 4);
+  c.total = o;
+  return c;
+}
+
+struct FCtx {
+  Geo g;
+  int m, r, rho, k;
+  float2* X;
+  float2* tx;      // full-period twiddles exp(-2 pi i k / nx), k < nx
+  float2* ty;
+  float2* yv;
+  float2* dv;
+  float2* ev;
+  int* msk;
+  int* sp;         // support pixels
+  float2* sv;      // support values
+  float2* gv;      // g on the support
+  double2* G;      // r x r (ld kMaxR): G, then scratch
+  double2* Lc;
+  double2* Li;
+  double2* Gi;
+  double2* vec;    // [0,16) c, [16,32) x
+  float* red;
+  int* hist;
+  int* cand;
+  const float2* FU;
+  int* err;
+};
+
+__device__ __forceinline__ float2 W_at(const FCtx& C, int i, int l) {
+  return __ldg(C.FU + static_cast<size_t>(l) * C.g.n + C.msk[i]);
+}
+
+// out[i] = (A x)[i] for the sparse frame x with pixels p[e], values v[e]
+// (direct DFT of the nonzeros at the sampled frequencies).
+__device__ void sparse_dft(const FCtx& C, const int* p, const float2* v, int nnz, float2* out) {
+  const float sc = rsqrtf(static_cast<float>(C.g.n));
+  for (int i = threadIdx.x; i < C.m; i += blockDim.x) {
+    const int om = C.msk[i];
+    const int kx = om >> C.g.lny, ky = om & (C.g.ny - 1);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int e = 0; e < nnz; ++e) {
+      const int pe = p[e];
+      const int px = pe >> C.g.lny, py = pe & (C.g.ny - 1);
+      const float2 w = cmul(C.tx[(kx * px) & (C.g.nx - 1)], C.ty[(ky * py) & (C.g.ny - 1)]);
+      acc = cfma(w, v[e], acc);
+    }
+    out[i] = make_float2(acc.x * sc, acc.y * sc);
+  }
+}
+
+// x = G^{-1} W^H v (W^H v in FP32, block-summed in fixed order; solve FP64);
+// x in C.vec[16 + l] (double2)
+__device__ void fls_solve(const FCtx& C, const float2* v) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, r = C.r;
+  float2 acc[kMaxR];
+#pragma unroll
+  for (int l = 0; l < kMaxR; ++l) acc[l] = make_float2(0.f, 0.f);
+  for (int i = threadIdx.x; i < C.m; i += blockDim.x) {
+    const float2 vi = v[i];
+#pragma unroll
+    for (int l = 0; l < kMaxR; ++l)
+      if (l < r) acc[l] = ccfma(W_at(C, i, l), vi, acc[l]);
+  }
+#pragma unroll
+  for (int l = 0; l < kMaxR; ++l) {
+    if (l >= r) break;
+    const float sx = warp_sumf(acc[l].x), sy = warp_sumf(acc[l].y);
+    if (lane == 0) {
+      C.red[(w * kMaxR + l) * 2] = sx;
+      C.red[(w * kMaxR + l) * 2 + 1] = sy;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < r) {
+    double sx = 0, sy = 0;
+    for (int ww = 0; ww < kFW; ++ww) {
+      sx += C.red[(ww * kMaxR + threadIdx.x) * 2];
+      sy += C.red[(ww * kMaxR + threadIdx.x) * 2 + 1];
+    }
+    C.vec[threadIdx.x] = make_double2(sx, sy);
+  }
+  __syncthreads();
+  if (threadIdx.x < r) {
+    double2 x = make_double2(0, 0);
+    for (int b = 0; b < r; ++b) {
+      const double2 t = dcmul(C.Gi[threadIdx.x * kMaxR + b], C.vec[b]);
+      x.x += t.x;
+      x.y += t.y;
+    }
+    C.vec[16 + threadIdx.x] = x;
+  }
+  __syncthreads();
+}
+
+// v <- v - W x with x from fls_solve (float arithmetic)
+__device__ void fapply_Wx(const FCtx& C, float2* v, float sign) {
+  for (int i = threadIdx.x; i < C.m; i += blockDim.x) {
+    float2 s = v[i];
+    for (int l = 0; l < C.r; ++l) {
+      const double2 xd = C.vec[16 + l];
+      const float2 x = make_float2(sign * static_cast<float>(xd.x), sign * static_cast<float>(xd.y));
+      s = cfma(W_at(C, i, l), x, s);
+    }
+    v[i] = s;
+  }
+  __syncthreads();
+}
+
+__device__ void fproj(const FCtx& C, float2* v) {
+  fls_solve(C, v);
+  fapply_Wx(C, v, -1.f);
+}
+
+__device__ double fnorm2(const FCtx& C, const float2* v) {
+  float acc = 0.f;
+  for (int i = threadIdx.x; i < C.m; i += blockDim.x) acc += cabs2(v[i]);
+  acc = warp_sumf(acc);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) C.red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < kFW; ++i) s += C.red[i];
+  __syncthreads();
+  return s;
+}
+
+// Hermitian Gram G = W^H W (FP64), complex Cholesky G = L L^H (lane 0, inverse
+// pivots by Newton rsqrt), L^{-1} per lane, G^{-1} = L^{-H} L^{-1}.
+__device__ void fgram_factor(const FCtx& C) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, r = C.r;
+  for (int t = w; t < r * r; t += kFW) {
+    const int a = t / r, b = t - a * r;
+    if (b > a) continue;
+    double sx = 0, sy = 0;
+    for (int i = lane; i < C.m; i += 32) {
+      const float2 wa = W_at(C, i, a), wb = W_at(C, i, b);
+      const double2 p = dccmul(make_double2(wb.x, wb.y), make_double2(wa.x, wa.y));  // conj(W_ib) W_ia
+      sx += p.x;
+      sy += p.y;
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) {
+      C.G[a * kMaxR + b] = make_double2(sx, sy);             // G[a][b] = sum conj(W_b) W_a ... (lower)
+      C.G[b * kMaxR + a] = make_double2(sx, -sy);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double* iL = reinterpret_cast<double*>(C.vec + 32);
+    int ok = 1;
+    if (lane == 0) {
+      // G here holds G[a][b] = sum_i conj(W_ib) W_ia = (W^H W)[b][a]; factor
+      // the Hermitian matrix M = W^H W with M[a][b] = conj(G[a][b]).
+      for (int j = 0; j < r && ok; ++j) {
+        double s = C.G[j * kMaxR + j].x;
+        for (int p = 0; p < j; ++p) {
+          const double2 l = C.Lc[j * kMaxR + p];
+          s -= l.x * l.x + l.y * l.y;
+        }
+        if (!(s > 1e-13 * C.G[j * kMaxR + j].x) || !(s < 1e300)) { ok = 0; break; }
+        const double ij = rsqrt_newton(s);
+        C.Lc[j * kMaxR + j] = make_double2(s * ij, 0.0);
+        iL[j] = ij;
+        for (int i = j + 1; i < r; ++i) {
+          // M[i][j] = conj(G[i][j])
+          double2 t = make_double2(C.G[i * kMaxR + j].x, -C.G[i * kMaxR + j].y);
+          for (int p = 0; p < j; ++p) {
+            const double2 a = C.Lc[i * kMaxR + p], b = C.Lc[j * kMaxR + p];
+            // t -= L[i][p] * conj(L[j][p])
+            t.x -= a.x * b.x + a.y * b.y;
+            t.y -= a.y * b.x - a.x * b.y;
+          }
+          C.Lc[i * kMaxR + j] = make_double2(t.x * ij, t.y * ij);
+        }
+      }
+      if (!ok) {
+        report_error(C.err, kErrNotSPD, C.k);
+        for (int i = 0; i < r; ++i) {
+          for (int p = 0; p < r; ++p) C.Lc[i * kMaxR + p] = make_double2(i == p ? 1.0 : 0.0, 0.0);
+          iL[i] = 1.0;
+        }
+      }
+    }
+    __syncwarp();
+    if (lane < r) {  // column lane of L^{-1}
+      const int cc = lane;
+      for (int i = 0; i < r; ++i) {
+        double2 t = make_double2(i == cc ? 1.0 : 0.0, 0.0);
+        for (int p = cc; p < i; ++p) {
+          const double2 q = dcmul(C.Lc[i * kMaxR + p], C.Li[p * kMaxR + cc]);
+          t.x -= q.x;
+          t.y -= q.y;
+        }
+        C.Li[i * kMaxR + cc] = (i < cc) ? make_double2(0, 0) : make_double2(t.x * iL[i], t.y * iL[i]);
+      }
+    }
+    __syncwarp();
+    // G^{-1} = L^{-H} L^{-1}: Gi[a][b] = sum_p conj(Li[p][a]) Li[p][b]
+    for (int t = lane; t < r * r; t += 32) {
+      const int a = t / r, b = t - a * r;
+      double2 s = make_double2(0, 0);
+      for (int p = (a > b ? a : b); p < r; ++p) {
+        const double2 q = dccmul(C.Li[p * kMaxR + a], C.Li[p * kMaxR + b]);
+        s.x += q.x;
+        s.y += q.y;
+      }
+      C.Gi[a * kMaxR + b] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// HardThreshold of the frame values X (modulus; ties to the lower pixel
+// index) -> the rho kept pixels and values (support order: by key).
+__device__ void fhard_threshold(const FCtx& C, bool keep_values) {
+  const int n = C.g.n, ld = C.g.ny + 1, rho = C.rho, lane = threadIdx.x & 31;
+  int* info = C.hist + 256;
+  unsigned prefix = 0, mask = 0;
+  if (threadIdx.x == 0) info[1] = rho;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) C.hist[t] = 0;
+    __syncthreads();
+    for (int e0 = threadIdx.x - lane; e0 < n; e0 += blockDim.x) {
+      const int e = e0 + lane;
+      unsigned key = 0u;
+      if (e < n) {
+        const int row = e >> C.g.lny, col = e & (C.g.ny - 1);
+        key = __float_as_uint(cabs2(C.X[row * ld + col]));
+      }
+      const bool in = e < n && (key & mask) == prefix;
+      const unsigned digit = in ? ((key >> shift) & 255u) : 256u;
+      const unsigned peers = __match_any_sync(0xffffffffu, digit);
+      if (in && (__ffs(peers) - 1) == lane) atomicAdd(&C.hist[digit], __popc(peers));
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int need = info[1];
+      int own[8], tot = 0;
+#pragma unroll
+      for (int z = 0; z < 8; ++z) { own[z] = C.hist[255 - 8 * lane - z]; tot += own[z]; }
+      int incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int excl = incl - tot;
+      if (excl < need && incl >= need) {
+        int acc = excl;
+        for (int z = 0; z < 8; ++z) {
+          if (acc + own[z] >= need) {
+            info[0] = 255 - 8 * lane - z;
+            info[1] = need - acc;
+            break;
+          }
+          acc += own[z];
+        }
+      }
+    }
+    __syncthreads();
+    prefix |= static_cast<unsigned>(info[0]) << shift;
+    mask |= 255u << shift;
+  }
+  const unsigned T = prefix;
+  const int need = info[1];
+  int* sel = C.cand;            // rho entries
+  int* ties = C.cand + rho + 8; // tie candidates (bounded below)
+  const int tie_cap = 56;
+  if (threadIdx.x == 0) { info[2] = 0; info[3] = 0; }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int row = e >> C.g.lny, col = e & (C.g.ny - 1);
+    const unsigned key = __float_as_uint(cabs2(C.X[row * ld + col]));
+    if (key > T) sel[atomicAdd(&info[3], 1)] = e;
+    else if (key == T) {
+      const int s = atomicAdd(&info[2], 1);
+      if (s < tie_cap) ties[s] = e;
+    }
+  }
+  __syncthreads();
+  const int nt = min(info[2], tie_cap), ngt = info[3];
+  if (info[2] > tie_cap && threadIdx.x == 0) report_error(C.err, kErrNaN, C.k);
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    const int e = ties[t];
+    int rank = 0;
+    for (int u = 0; u < nt; ++u) rank += ties[u] < e;
+    if (rank < need) sel[ngt + rank] = e;
+  }
+  __syncthreads();
+  // store ascending by pixel (fixed order for every later sum over the support)
+  for (int t = threadIdx.x; t < rho; t += blockDim.x) {
+    const int e = sel[t];
+    int pos = 0;
+    for (int u = 0; u < rho; ++u) pos += sel[u] < e;
+    const int row = e >> C.g.lny, col = e & (C.g.ny - 1);
+    C.sp[pos] = e;
+    C.sv[pos] = keep_values ? C.X[row * ld + col] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const FCarve cv = fcarve(a.g, a.m, a.rho);
+  FCtx C;
+  C.g = a.g;
+  C.m = a.m;
+  C.r = a.r;
+  C.rho = a.rho;
+  C.k = blockIdx.x;
+  C.X = reinterpret_cast<float2*>(sm + cv.X);
+  C.tx = reinterpret_cast<float2*>(sm + cv.tx);
+  C.ty = reinterpret_cast<float2*>(sm + cv.ty);
+  C.yv = reinterpret_cast<float2*>(sm + cv.yv);
+  C.dv = reinterpret_cast<float2*>(sm + cv.dv);
+  C.ev = reinterpret_cast<float2*>(sm + cv.ev);
+  C.msk = reinterpret_cast<int*>(sm + cv.msk);
+  C.sp = reinterpret_cast<int*>(sm + cv.sp);
+  C.sv = reinterpret_cast<float2*>(sm + cv.sv);
+  C.gv = reinterpret_cast<float2*>(sm + cv.gv);
+  C.G = reinterpret_cast<double2*>(sm + cv.G);
+  C.Lc = C.G + kMaxR * kMaxR;
+  C.Li = C.G + 2 * kMaxR * kMaxR;
+  C.Gi = C.G + 3 * kMaxR * kMaxR;
+  C.vec = reinterpret_cast<double2*>(sm + cv.vec);
+  C.red = reinterpret_cast<float*>(sm + cv.red);
+  C.hist = reinterpret_cast<int*>(sm + cv.hist);
+  C.cand = reinterpret_cast<int*>(sm + cv.cand);
+  C.FU = a.FU;
+  C.err = a.err;
+  const int k = C.k, m = C.m, r = C.r, rho = C.rho, n = C.g.n, ld = C.g.ny + 1;
+  for (int t = threadIdx.x; t < C.g.nx; t += blockDim.x) C.tx[t] = a.twx[t];
+  for (int t = threadIdx.x; t < C.g.ny; t += blockDim.x) C.ty[t] = a.twy[t];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    C.yv[i] = a.y[static_cast<size_t>(k) * m + i];
+    C.msk[i] = a.mask[static_cast<size_t>(k) * m + i];
+  }
+  for (int e = threadIdx.x; e < rho; e += blockDim.x) {
+    if (a.mode != kModeInit) {
+      C.sp[e] = a.S_idx[static_cast<size_t>(k) * rho + e];
+      C.sv[e] = a.S_val[static_cast<size_t>(k) * rho + e];
+    } else {
+      C.sp[e] = 0;
+      C.sv[e] = make_float2(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  const bool project = (a.mode != kModeInit);
+  if (project) fgram_factor(C);
+  const int tau = (a.mode == kModeLS || rho == 0) ? 0 : a.tau;
+  for (int it = 0; it < tau; ++it) {
+    const bool zero_start = (a.mode == kModeInit && it == 0);
+    // u = P_perp (A s - y)
+    if (zero_start) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) C.dv[i] = make_float2(-C.yv[i].x, -C.yv[i].y);
+      __syncthreads();
+    } else {
+      sparse_dft(C, C.sp, C.sv, rho, C.dv);
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += blockDim.x) C.dv[i] = csub(C.dv[i], C.yv[i]);
+      __syncthreads();
+      if (project) fproj(C, C.dv);
+    }
+    // g = A^H u: zero-filled frame, inverse 2D FFT
+    for (int e = threadIdx.x; e < C.g.nx * ld; e += blockDim.x) C.X[e] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const int om = C.msk[i];
+      C.X[(om >> C.g.lny) * ld + (om & (C.g.ny - 1))] = C.dv[i];
+    }
+    __syncthreads();
+    fft2_smem(C.X, C.g.nx, C.g.ny, C.g.lnx, C.g.lny, C.tx, C.ty, true);
+    if (zero_start) {
+      fhard_threshold(C, false);  // support of the zero start: the rho largest |g|
+    }
+    // g on the support, ||g_G||^2, A g_G
+    __syncthreads();
+    for (int e = threadIdx.x; e < rho; e += blockDim.x) {
+      const int p = C.sp[e];
+      C.gv[e] = C.X[(p >> C.g.lny) * ld + (p & (C.g.ny - 1))];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int e = 0; e < rho; ++e)
+        s += static_cast<double>(C.gv[e].x) * C.gv[e].x + static_cast<double>(C.gv[e].y) * C.gv[e].y;
+      C.vec[48] = make_double2(s, 0.0);
+    }
+    __syncthreads();
+    sparse_dft(C, C.sp, C.gv, rho, C.ev);
+    __syncthreads();
+    if (project) fproj(C, C.ev);
+    const double num = C.vec[48].x;
+    const double den = fnorm2(C, C.ev);
+    if (!(den > 0.0)) break;
+    double mu = num / den;
+    if (!isfinite(mu)) {
+      if (threadIdx.x == 0) report_error(a.err, kErrNaN, k);
+      mu = 0.0;
+    }
+    const float muf = static_cast<float>(mu);
+    // v = s - mu g in the frame
+    for (int e = threadIdx.x; e < C.g.nx * ld; e += blockDim.x) {
+      C.X[e].x *= -muf;
+      C.X[e].y *= -muf;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rho; e += blockDim.x) {
+      const int p = C.sp[e];
+      float2& x = C.X[(p >> C.g.lny) * ld + (p & (C.g.ny - 1))];
+      x = cadd(x, C.sv[e]);
+    }
+    __syncthreads();
+    fhard_threshold(C, true);
+  }
+  // ---- final stage ----
+  sparse_dft(C, C.sp, C.sv, rho, C.dv);  // A s
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) C.dv[i] = csub(C.yv[i], C.dv[i]);  // y - A s
+  __syncthreads();
+  if (a.mode == kModeInit) {
+    for (int e = threadIdx.x; e < C.g.nx * ld; e += blockDim.x) C.X[e] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const int om = C.msk[i];
+      C.X[(om >> C.g.lny) * ld + (om & (C.g.ny - 1))] = C.dv[i];
+    }
+    __syncthreads();
+    fft2_smem(C.X, C.g.nx, C.g.ny, C.g.lnx, C.g.lny, C.tx, C.ty, true);
+    float2* Hk = a.H + static_cast<size_t>(k) * n;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) Hk[e] = C.X[(e >> C.g.lny) * ld + (e & (C.g.ny - 1))];
+  } else {
+    fls_solve(C, C.dv);  // b = G^{-1} W^H (y - A s)
+    if (threadIdx.x < r) {
+      const double2 b = C.vec[16 + threadIdx.x];
+      a.B[static_cast<size_t>(k) * r + threadIdx.x] = make_float2(static_cast<float>(b.x), static_cast<float>(b.y));
+    }
+    if (a.mode == kModeIter) {
+      // res = W b - (y - A s)
+      for (int i = threadIdx.x; i < m; i += blockDim.x) C.ev[i] = make_float2(-C.dv[i].x, -C.dv[i].y);
+      __syncthreads();
+      fapply_Wx(C, C.ev, 1.f);
+      for (int i = threadIdx.x; i < m; i += blockDim.x) a.RES[static_cast<size_t>(k) * m + i] = C.ev[i];
+    }
+  }
+  if (a.mode != kModeLS) {
+    // S_k ascending by pixel
+    for (int e = threadIdx.x; e < rho; e += blockDim.x) {
+      const int p = C.sp[e];
+      int pos = 0;
+      for (int f = 0; f < rho; ++f) pos += C.sp[f] < p;
+      a.S_idx[static_cast<size_t>(k) * rho + pos] = p;
+      a.S_val[static_cast<size_t>(k) * rho + pos] = C.sv[e];
+    }
+  }
+}
+
+// K[l][w] = sum over the (k, i) with mask_k[i] = w (fixed order) of
+// res_k[i] conj(b_k[l])
+__global__ void kspace_kernel(int n, int m, int r, const int* __restrict__ ptr,
+                              const int* __restrict__ list, const float2* __restrict__ RES,
+                              const float2* __restrict__ B, float2* __restrict__ K) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n) return;
+  float2 acc[kMaxR];
+  for (int l = 0; l < kMaxR; ++l) acc[l] = make_float2(0.f, 0.f);
+  for (int t = ptr[w]; t < ptr[w + 1]; ++t) {
+    const int ki = list[t];
+    const int k = ki / m;
+    const float2 rv = RES[ki];
+    for (int l = 0; l < r; ++l) acc[l] = cfma(rv, cconj(B[static_cast<size_t>(k) * r + l]), acc[l]);
+  }
+  for (int l = 0; l < r; ++l) K[static_cast<size_t>(l) * n + w] = acc[l];
+}
+
+// ---- complex column-reduced ops on r x n column-major matrices (l-major) ----
+// partial Hermitian Grams: part[blk][a][b] = sum_j conj(X_ja) X_jb (a >= b)
+__global__ void cgram_part_kernel(int n, int r, const float2* __restrict__ X,
+                                  const float2* __restrict__ G2, const double* __restrict__ eta,
+                                  float2* __restrict__ Xout, double2* __restrict__ part) {
+  const int rows = (n + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * rows, hi = min(n, lo + rows);
+  const float e = eta ? static_cast<float>(*eta) : 0.f;
+  if (Xout) {
+    for (int j = lo + threadIdx.x; j < hi; j += blockDim.x)
+      for (int l = 0; l < r; ++l) {
+        float2 v = X[static_cast<size_t>(l) * n + j];
+        if (G2) {
+          const float2 g = G2[static_cast<size_t>(l) * n + j];
+          v = make_float2(fmaf(-e, g.x, v.x), fmaf(-e, g.y, v.y));
+        }
+        Xout[static_cast<size_t>(l) * n + j] = v;
+      }
+    __syncthreads();
+  }
+  const float2* Y = Xout ? Xout : X;
+  const int t = threadIdx.x, a = t / kMaxR, b = t - (t / kMaxR) * kMaxR;
+  if (a >= r || b > a) return;
+  double sx = 0, sy = 0;
+  for (int j = lo; j < hi; ++j) {
+    const float2 xa = Y[static_cast<size_t>(a) * n + j], xb = Y[static_cast<size_t>(b) * n + j];
+    sx += static_cast<double>(xa.x) * xb.x + static_cast<double>(xa.y) * xb.y;   // conj(x_a) x_b
+    sy += static_cast<double>(xa.x) * xb.y - static_cast<double>(xa.y) * xb.x;
+  }
+  part[static_cast<size_t>(blockIdx.x) * r * r + a * r + b] = make_double2(sx, sy);
+}
+// M = sum of partials (M[a][b] for a >= b = sum conj(x_a) x_b), Hermitian;
+// M = R^H R with R = L^H (L lower from the Cholesky of M^T... we factor the
+// matrix N[i][j] = sum conj(x_i) x_j directly: N = L L^H), Rinv = L^{-H}.
+__global__ void cchol_fin_kernel(int r, int nblk, const double2* __restrict__ part,
+                                 double2* __restrict__ Rinv, int* err) {
+  __shared__ double2 N[kMaxR * kMaxR], Lw[kMaxR * kMaxR], Li[kMaxR * kMaxR];
+  __shared__ double iL[kMaxR];
+  __shared__ int okf;
+  const int lane = threadIdx.x;
+  for (int t = lane; t < r * r; t += 32) {
+    const int a = t / r, b = t - a * r;
+    if (b <= a) {
+      double sx = 0, sy = 0;
+      for (int k = 0; k < nblk; ++k) {
+        const double2 v = part[static_cast<size_t>(k) * r * r + a * r + b];
+        sx += v.x;
+        sy += v.y;
+      }
+      // N[a][b] = sum conj(x_a) x_b ; N[b][a] = conj(N[a][b])
+      N[a * kMaxR + b] = make_double2(sx, sy);
+      N[b * kMaxR + a] = make_double2(sx, -sy);
+    }
+  }
+  __syncwarp();
+  // X^H X = N^T?  (X^H X)[i][j] = sum conj(x_i) x_j = N[i][j]: factor N = L L^H
+  if (lane == 0) {
+    int ok = 1;
+    for (int j = 0; j < r && ok; ++j) {
+      double s = N[j * kMaxR + j].x;
+      for (int p = 0; p < j; ++p) s -= Lw[j * kMaxR + p].x * Lw[j * kMaxR + p].x + Lw[j * kMaxR + p].y * Lw[j * kMaxR + p].y;
+      if (!(s > 1e-13 * N[j * kMaxR + j].x) || !(s < 1e300)) { ok = 0; break; }
+      const double ij = rsqrt_newton(s);
+      Lw[j * kMaxR + j] = make_double2(s * ij, 0);
+      iL[j] = ij;
+      for (int i = j + 1; i < r; ++i) {
+        double2 t = N[i * kMaxR + j];
+        for (int p = 0; p < j; ++p) {
+          const double2 a = Lw[i * kMaxR + p], b = Lw[j * kMaxR + p];
+          t.x -= a.x * b.x + a.y * b.y;
+          t.y -= a.y * b.x - a.x * b.y;
+        }
+        Lw[i * kMaxR + j] = make_double2(t.x * ij, t.y * ij);
+      }
+    }
+    if (!ok) {
+      report_error(err, kErrNotSPD, -1);
+      for (int i = 0; i < r; ++i) {
+        for (int p = 0; p < r; ++p) Lw[i * kMaxR + p] = make_double2(i == p ? 1.0 : 0.0, 0);
+        iL[i] = 1.0;
+      }
+    }
+    okf = ok;
+  }
+  __syncwarp();
+  if (lane < r) {
+    const int cc = lane;
+    for (int i = 0; i < r; ++i) {
+      double2 t = make_double2(i == cc ? 1.0 : 0.0, 0.0);
+      for (int p = cc; p < i; ++p) {
+        const double2 q = dcmul(Lw[i * kMaxR + p], Li[p * kMaxR + cc]);
+        t.x -= q.x;
+        t.y -= q.y;
+      }
+      Li[i * kMaxR + cc] = (i < cc) ? make_double2(0, 0) : make_double2(t.x * iL[i], t.y * iL[i]);
+    }
+  }
+  __syncwarp();
+  // X^H X = L L^H  ->  with R = L^H (upper), Q = X R^{-1} = X L^{-H}:
+  // Rinv[a][b] = (L^{-H})[a][b] = conj(Li[b][a])
+  for (int t = lane; t < r * r; t += 32) {
+    const int a = t / r, b = t - a * r;
+    const double2 v = Li[b * kMaxR + a];
+    Rinv[a * r + b] = make_double2(v.x, -v.y);
+  }
+}
+// Y = X Rinv (column-major complex, FP64 accumulation); optional float out
+__global__ void capply_kernel(int n, int r, const float2* __restrict__ X,
+                              const double2* __restrict__ Rinv, float2* __restrict__ Y) {
+  const size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (t >= static_cast<size_t>(n) * r) return;
+  const int l = static_cast<int>(t / n), j = static_cast<int>(t - static_cast<size_t>(l) * n);
+  double sx = 0, sy = 0;
+  for (int p = 0; p <= l; ++p) {
+    const float2 x = X[static_cast<size_t>(p) * n + j];
+    const double2 q = Rinv[p * r + l];
+    sx += x.x * q.x - x.y * q.y;
+    sy += x.x * q.y + x.y * q.x;
+  }
+  Y[t] = make_float2(static_cast<float>(sx), static_cast<float>(sy));
+}
+// eta = c / sqrt(lambda_max(grad^H grad)) via the real 2r x 2r symmetric
+// embedding [[Re, -Im], [Im, Re]] of the Hermitian Gram (cyclic Jacobi).
+__global__ void ceta_kernel(int r, int nblk, const double2* __restrict__ part, double c_eta,
+                            double* __restrict__ eta) {
+  if (threadIdx.x != 0) return;
+  double A[2 * kMaxR][2 * kMaxR];
+  const int R2 = 2 * r;
+  for (int a = 0; a < r; ++a)
+    for (int b = 0; b <= a; ++b) {
+      double sx = 0, sy = 0;
+      for (int k = 0; k < nblk; ++k) {
+        const double2 v = part[static_cast<size_t>(k) * r * r + a * r + b];
+        sx += v.x;
+        sy += v.y;
+      }
+      // N[a][b] = sx + i sy, N[b][a] = sx - i sy
+      A[a][b] = sx; A[b][a] = sx; A[a + r][b + r] = sx; A[b + r][a + r] = sx;
+      A[a + r][b] = sy; A[b][a + r] = sy; A[a][b + r] = -sy; A[b + r][a] = -sy;
+    }
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int a = 0; a < R2; ++a)
+      for (int b = 0; b < R2; ++b) (a == b ? diag : off) += A[a][b] * A[a][b];
+    if (off <= 1e-30 * diag) break;
+    for (int p = 0; p < R2 - 1; ++p)
+      for (int q2 = p + 1; q2 < R2; ++q2) {
+        if (A[p][q2] == 0.0) continue;
+        const double th = (A[q2][q2] - A[p][p]) / (2.0 * A[p][q2]);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+        for (int kk = 0; kk < R2; ++kk) {
+          const double akp = A[kk][p], akq = A[kk][q2];
+          A[kk][p] = cs * akp - sn * akq;
+          A[kk][q2] = sn * akp + cs * akq;
+        }
+        for (int kk = 0; kk < R2; ++kk) {
+          const double apk = A[p][kk], aqk = A[q2][kk];
+          A[p][kk] = cs * apk - sn * aqk;
+          A[q2][kk] = sn * apk + cs * aqk;
+        }
+      }
+  }
+  double lmax = 0.0;
+  for (int a = 0; a < R2; ++a) lmax = fmax(lmax, A[a][a]);
+  const double nrm = sqrt(lmax);
+  *eta = (nrm > 0.0) ? c_eta / nrm : 0.0;
+}
+
+// ---- FP64 complex subspace iteration on L0 (rows of H are its columns) ----
+// P[k][l] = sum_j conj(H[k][j]) U[j][l]   (U FP64 complex, column-major l-major)
+__global__ void cdproject_kernel(int n, int q, int r, const float2* __restrict__ H,
+                                 const double2* __restrict__ U, double2* __restrict__ P) {
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (k >= q) return;
+  for (int l = 0; l < r; ++l) {
+    double sx = 0, sy = 0;
+    for (int j = lane; j < n; j += 32) {
+      const float2 h = H[static_cast<size_t>(k) * n + j];
+      const double2 u = U[static_cast<size_t>(l) * n + j];
+      sx += h.x * u.x + h.y * u.y;
+      sy += h.x * u.y - h.y * u.x;
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) P[static_cast<size_t>(k) * r + l] = make_double2(sx, sy);
+  }
+}
+// Z[j][l] = sum_k H[k][j] P[k][l]
+__global__ void cdgrad_kernel(int n, int q, int r, const float2* __restrict__ H,
+                              const double2* __restrict__ P, double2* __restrict__ Z) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double2 acc[kMaxR];
+  for (int l = 0; l < kMaxR; ++l) acc[l] = make_double2(0, 0);
+  for (int k = 0; k < q; ++k) {
+    const float2 h = H[static_cast<size_t>(k) * n + j];
+    for (int l = 0; l < r; ++l) {
+      const double2 p = P[static_cast<size_t>(k) * r + l];
+      acc[l].x += h.x * p.x - h.y * p.y;
+      acc[l].y += h.x * p.y + h.y * p.x;
+    }
+  }
+  for (int l = 0; l < r; ++l) Z[static_cast<size_t>(l) * n + j] = acc[l];
+}
+__global__ void cdgram_part_kernel(int n, int r, const double2* __restrict__ X,
+                                   double2* __restrict__ part) {
+  const int rows = (n + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * rows, hi = min(n, lo + rows);
+  const int t = threadIdx.x, a = t / kMaxR, b = t - (t / kMaxR) * kMaxR;
+  if (a >= r || b > a) return;
+  double sx = 0, sy = 0;
+  for (int j = lo; j < hi; ++j) {
+    const double2 xa = X[static_cast<size_t>(a) * n + j], xb = X[static_cast<size_t>(b) * n + j];
+    sx += xa.x * xb.x + xa.y * xb.y;
+    sy += xa.x * xb.y - xa.y * xb.x;
+  }
+  part[static_cast<size_t>(blockIdx.x) * r * r + a * r + b] = make_double2(sx, sy);
+}
+__global__ void cdapply_kernel(int n, int r, const double2* __restrict__ X,
+                               const double2* __restrict__ Rinv, double2* __restrict__ Y,
+                               float2* __restrict__ Yf) {
+  const size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (t >= static_cast<size_t>(n) * r) return;
+  const int l = static_cast<int>(t / n), j = static_cast<int>(t - static_cast<size_t>(l) * n);
+  double sx = 0, sy = 0;
+  for (int p = 0; p <= l; ++p) {
+    const double2 x = X[static_cast<size_t>(p) * n + j];
+    const double2 q = Rinv[p * r + l];
+    sx += x.x * q.x - x.y * q.y;
+    sy += x.x * q.y + x.y * q.x;
+  }
+  Y[t] = make_double2(sx, sy);
+  if (Yf) Yf[t] = make_float2(static_cast<float>(sx), static_cast<float>(sy));
+}
+// ||Unew - Uold (Uold^H Unew)||_F^2 (FP64)
+__global__ void cdchange_kernel(int n, int r, const double2* __restrict__ Uo,
+                                const double2* __restrict__ Un, double* __restrict__ out) {
+  __shared__ double2 D[kMaxR * kMaxR];
+  __shared__ double red[32];
+  // D = Uo^H Un by one block (n small enough for this one-off check)
+  for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+    const int a = t / r, b = t - a * r;
+    double sx = 0, sy = 0;
+    for (int j = 0; j < n; ++j) {
+      const double2 x = Uo[static_cast<size_t>(a) * n + j], y = Un[static_cast<size_t>(b) * n + j];
+      sx += x.x * y.x + x.y * y.y;
+      sy += x.x * y.y - x.y * y.x;
+    }
+    D[t] = make_double2(sx, sy);
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (size_t t = threadIdx.x; t < static_cast<size_t>(n) * r; t += blockDim.x) {
+    const int l = static_cast<int>(t / n), j = static_cast<int>(t - static_cast<size_t>(l) * n);
+    double2 s = Un[t];
+    for (int p = 0; p < r; ++p) {
+      const double2 u = Uo[static_cast<size_t>(p) * n + j], d = D[p * r + l];
+      s.x -= u.x * d.x - u.y * d.y;
+      s.y -= u.x * d.y + u.y * d.x;
+    }
+    acc += s.x * s.x + s.y * s.y;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s += red[w];
+    *out = s;
+  }
+}
+
+}  // namespace fourier
+
+using namespace fourier;
+
+// --------------------------------------------------------------- driver --
+struct FourierSolver {
+  Geo g{};
+  int m = 0, q = 0, r = 0, rho = 0;
+  int tau0 = 10, tau = 3;
+  double c_eta = 0.14;
+  int power_iters = 1000;
+  double power_tol = 1e-11;
+  uint64_t seed = 0;
+  cudaStream_t s = nullptr;
+  int nblk = 1;
+  int t = 0;
+  bool have_eta = false;
+  // device
+  float2 *y = nullptr, *U = nullptr, *FU = nullptr, *B = nullptr, *S_val = nullptr, *RES = nullptr,
+         *H = nullptr, *K = nullptr, *grad = nullptr, *Z = nullptr, *Z2 = nullptr, *twx = nullptr,
+         *twy = nullptr;
+  int *mask = nullptr, *S_idx = nullptr, *iptr = nullptr, *ilist = nullptr, *err = nullptr;
+  double2* part = nullptr;
+  double2* rfac = nullptr;
+  double* eta = nullptr;
+  double* scal = nullptr;
+  size_t smem = 0;
+};
+
+static size_t fft_smem(const Geo& g) {
+  return al16(static_cast<size_t>(g.nx) * (g.ny + 1) * 8) + static_cast<size_t>(g.nx + g.ny) * 8;
+}
+
+static cudaError_t fft_frames(FourierSolver* F, const float2* in, float2* out, int nframes,
+                              bool inverse) {
+  fft_frames_kernel<<<nframes, kFT, fft_smem(F->g), F->s>>>(F->g, in, out, inverse ? 1 : 0, F->twx,
+                                                             F->twy);
+  return cudaGetLastError();
+}
+
+static int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int tau0, int tau,
+                              double c_eta, int power_iters, double power_tol, uint64_t seed,
+                              cudaStream_t s, std::string* msg) {
+  FourierSolver* F = new FourierSolver();
+  F->g.nx = nx;
+  F->g.ny = ny;
+  F->g.lnx = ilog2(nx);
+  F->g.lny = ilog2(ny);
+  F->g.n = nx * ny;
+  F->m = m;
+  F->q = q;
+  F->r = r;
+  F->rho = rho;
+  F->tau0 = tau0;
+  F->tau = tau;
+  F->c_eta = c_eta;
+  F->power_iters = power_iters;
+  F->power_tol = power_tol;
+  F->seed = seed;
+  F->s = s;
+  const int n = F->g.n;
+  F->nblk = std::max(1, std::min(152, (n + 63) / 64));
+  F->smem = fcarve(F->g, m, rho).total;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (F->smem > static_cast<size_t>(optin) || fft_smem(F->g) > static_cast<size_t>(optin)) {
+    *msg = "frame too large for one CTA's shared memory (n <= 16384 with m <= 2048 fits)";
+    delete F;
+    return nullptr;
+  }
+  cudaFuncSetAttribute(fsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(F->smem));
+  cudaFuncSetAttribute(fft_frames_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(fft_smem(F->g)));
+  const size_t rr = static_cast<size_t>(r) * r;
+  bool ok = cudaMalloc(&F->y, sizeof(float2) * m * q) == cudaSuccess &&
+            cudaMalloc(&F->mask, sizeof(int) * m * q) == cudaSuccess &&
+            cudaMalloc(&F->U, sizeof(float2) * n * r) == cudaSuccess &&
+            cudaMalloc(&F->FU, sizeof(float2) * n * r) == cudaSuccess &&
+            cudaMalloc(&F->B, sizeof(float2) * q * r) == cudaSuccess &&
+            cudaMalloc(&F->S_idx, sizeof(int) * q * std::max(1, rho)) == cudaSuccess &&
+            cudaMalloc(&F->S_val, sizeof(float2) * q * std::max(1, rho)) == cudaSuccess &&
+            cudaMalloc(&F->RES, sizeof(float2) * m * q) == cudaSuccess &&
+            cudaMalloc(&F->H, sizeof(float2) * static_cast<size_t>(n) * q) == cudaSuccess &&
+            cudaMalloc(&F->K, sizeof(float2) * n * r) == cudaSuccess &&
+            cudaMalloc(&F->grad, sizeof(float2) * n * r) == cudaSuccess &&
+            cudaMalloc(&F->Z, sizeof(float2) * n * r) == cudaSuccess &&
+            cudaMalloc(&F->Z2, sizeof(float2) * n * r) == cudaSuccess &&
+            cudaMalloc(&F->twx, sizeof(float2) * nx) == cudaSuccess &&
+            cudaMalloc(&F->twy, sizeof(float2) * ny) == cudaSuccess &&
+            cudaMalloc(&F->iptr, sizeof(int) * (n + 1)) == cudaSuccess &&
+            cudaMalloc(&F->ilist, sizeof(int) * m * q) == cudaSuccess &&
+            cudaMalloc(&F->err, sizeof(int) * 2) == cudaSuccess &&
+            cudaMalloc(&F->part, sizeof(double2) * F->nblk * rr) == cudaSuccess &&
+            cudaMalloc(&F->rfac, sizeof(double2) * 2 * rr) == cudaSuccess &&
+            cudaMalloc(&F->eta, sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&F->scal, sizeof(double) * 4) == cudaSuccess;
+  if (!ok) {
+    *msg = "device allocation failed";
+    return F;  // caller frees
+  }
+  std::vector<float2> tw(std::max(nx, ny));
+  for (int k = 0; k < nx; ++k) {
+    const double a = -2.0 * M_PI * k / nx;
+    tw[k] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+  }
+  cudaMemcpy(F->twx, tw.data(), sizeof(float2) * nx, cudaMemcpyHostToDevice);
+  for (int k = 0; k < ny; ++k) {
+    const double a = -2.0 * M_PI * k / ny;
+    tw[k] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+  }
+  cudaMemcpy(F->twy, tw.data(), sizeof(float2) * ny, cudaMemcpyHostToDevice);
+  cudaMemset(F->err, 0, 8);
+  cudaMemset(F->S_idx, 0, sizeof(int) * q * std::max(1, rho));
+  cudaMemset(F->S_val, 0, sizeof(float2) * q * std::max(1, rho));
+  return F;
+}
+
+void fourier_destroy(FourierSolver* F) {
+  if (!F) return;
+  void* ps[] = {F->y, F->mask, F->U, F->FU, F->B, F->S_idx, F->S_val, F->RES, F->H, F->K, F->grad,
+                F->Z, F->Z2, F->twx, F->twy, F->iptr, F->ilist, F->err, F->part, F->rfac, F->eta, F->scal};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  delete F;
+}
+
+// masks: host int32 q x m (each column ascending, in [0, n)); y host or device
+int fourier_set_measurements(FourierSolver* F, const void* y, const void* mask, int mem_kind,
+                             std::string* msg) {
+  const int n = F->g.n, m = F->m, q = F->q;
+  std::vector<int> hm(static_cast<size_t>(m) * q);
+  if (mem_kind) {
+    if (cudaMemcpy(hm.data(), mask, sizeof(int) * hm.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      *msg = "mask copy failed";
+      return 4;
+    }
+  } else {
+    std::memcpy(hm.data(), mask, sizeof(int) * hm.size());
+  }
+  for (int k = 0; k < q; ++k)
+    for (int i = 0; i < m; ++i) {
+      const int v = hm[static_cast<size_t>(k) * m + i];
+      if (v < 0 || v >= n || (i > 0 && v <= hm[static_cast<size_t>(k) * m + i - 1])) {
+        *msg = "mask row indices must be strictly ascending in [0, n)";
+        return 1;
+      }
+    }
+  // inverse index: for each frequency the (k, i) that sample it, k ascending
+  std::vector<int> ptr(n + 1, 0), list(static_cast<size_t>(m) * q);
+  for (int v : hm) ptr[v + 1]++;
+  for (int w = 0; w < n; ++w) ptr[w + 1] += ptr[w];
+  std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+  for (int k = 0; k < q; ++k)
+    for (int i = 0; i < m; ++i) list[fill[hm[static_cast<size_t>(k) * m + i]]++] = k * m + i;
+  cudaError_t e = cudaMemcpyAsync(F->mask, hm.data(), sizeof(int) * hm.size(), cudaMemcpyHostToDevice, F->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(F->iptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, F->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(F->ilist, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, F->s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(F->y, y, sizeof(float2) * m * q,
+                        mem_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, F->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(F->s);
+  if (e != cudaSuccess) {
+    *msg = cudaGetErrorString(e);
+    return 4;
+  }
+  F->t = 0;
+  F->have_eta = false;
+  return 0;
+}
+
+static cudaError_t launch_fsweep(FourierSolver* F, int mode, int tau) {
+  FArgs a{};
+  a.g = F->g;
+  a.m = F->m;
+  a.q = F->q;
+  a.r = F->r;
+  a.rho = F->rho;
+  a.tau = tau;
+  a.mode = mode;
+  a.y = F->y;
+  a.mask = F->mask;
+  a.FU = F->FU;
+  a.S_idx = F->S_idx;
+  a.S_val = F->S_val;
+  a.B = F->B;
+  a.RES = F->RES;
+  a.H = F->H;
+  a.twx = F->twx;
+  a.twy = F->twy;
+  a.err = F->err;
+  fsweep_kernel<<<F->q, kFT, F->smem, F->s>>>(a);
+  return cudaGetLastError();
+}
+
+// complex Cholesky-QR2 of Zin (r x n column-major) into Uout
+static cudaError_t ccholqr2(FourierSolver* F, const float2* Zin, float2* Uout) {
+  const int n = F->g.n, r = F->r;
+  const unsigned nb = static_cast<unsigned>((static_cast<size_t>(n) * r + 255) / 256);
+  cgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, Zin, nullptr, nullptr, nullptr, F->part);
+  cchol_fin_kernel<<<1, 32, 0, F->s>>>(r, F->nblk, F->part, F->rfac, F->err);
+  capply_kernel<<<nb, 256, 0, F->s>>>(n, r, Zin, F->rfac, F->Z2);
+  cgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, F->Z2, nullptr, nullptr, nullptr, F->part);
+  cchol_fin_kernel<<<1, 32, 0, F->s>>>(r, F->nblk, F->part, F->rfac + r * r, F->err);
+  capply_kernel<<<nb, 256, 0, F->s>>>(n, r, F->Z2, F->rfac + r * r, Uout);
+  return cudaGetLastError();
+}
+
+int fourier_check_error(FourierSolver* F, std::string* msg) {
+  int e[2] = {0, 0};
+  cudaMemcpyAsync(e, F->err, sizeof(e), cudaMemcpyDeviceToHost, F->s);
+  if (cudaStreamSynchronize(F->s) != cudaSuccess) {
+    *msg = "CUDA error";
+    return 4;
+  }
+  if (e[0]) {
+    cudaMemsetAsync(F->err, 0, 8, F->s);
+    *msg = e[0] == kErrNotSPD ? "r x r Gram matrix not positive definite" : "NaN/Inf in the iteration";
+    if (e[1] >= 0) *msg += " (frame " + std::to_string(e[1]) + ")";
+    return 5;
+  }
+  return 0;
+}
+
+int fourier_init(FourierSolver* F, std::string* msg) {
+  const int n = F->g.n, q = F->q, r = F->r;
+  cudaError_t e = launch_fsweep(F, kModeInit, F->tau0);  // s_k and the L0 columns in H
+  // FP64 complex subspace iteration for the top-r left singular vectors of L0
+  const size_t nr = static_cast<size_t>(n) * r;
+  double2 *Ud = nullptr, *Uo = nullptr, *Zd = nullptr, *Td = nullptr, *Pd = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&Ud, nr * 16);
+  if (e == cudaSuccess) e = cudaMalloc(&Uo, nr * 16);
+  if (e == cudaSuccess) e = cudaMalloc(&Zd, nr * 16);
+  if (e == cudaSuccess) e = cudaMalloc(&Td, nr * 16);
+  if (e == cudaSuccess) e = cudaMalloc(&Pd, static_cast<size_t>(q) * r * 16);
+  // start: deterministic complex Gaussian block
+  std::vector<double2> st(nr);
+  uint64_t sd = F->seed * 0x9E3779B97F4A7C15ull + 0x2545F4914F6CDD1Dull;
+  auto nxt = [&]() {
+    uint64_t z = (sd += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  for (auto& v : st) {
+    const double u1 = ((nxt() >> 11) + 1.0) * 0x1.0p-53, u2 = (nxt() >> 11) * 0x1.0p-53;
+    const double rad = std::sqrt(-2.0 * std::log(u1));
+    v = make_double2(rad * std::cos(6.283185307179586 * u2), rad * std::sin(6.283185307179586 * u2));
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Zd, st.data(), nr * 16, cudaMemcpyHostToDevice, F->s);
+  const unsigned nb = static_cast<unsigned>((nr + 255) / 256);
+  auto dqr = [&](const double2* Zin, double2* Uout, float2* Uf) {
+    cdgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, Zin, F->part);
+    cchol_fin_kernel<<<1, 32, 0, F->s>>>(r, F->nblk, F->part, F->rfac, F->err);
+    cdapply_kernel<<<nb, 256, 0, F->s>>>(n, r, Zin, F->rfac, Td, nullptr);
+    cdgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, Td, F->part);
+    cchol_fin_kernel<<<1, 32, 0, F->s>>>(r, F->nblk, F->part, F->rfac + r * r, F->err);
+    cdapply_kernel<<<nb, 256, 0, F->s>>>(n, r, Td, F->rfac + r * r, Uout, Uf);
+  };
+  if (e == cudaSuccess) dqr(Zd, Ud, nullptr);
+  for (int it = 0; it < F->power_iters && e == cudaSuccess; ++it) {
+    e = cudaMemcpyAsync(Uo, Ud, nr * 16, cudaMemcpyDeviceToDevice, F->s);
+    cdproject_kernel<<<(q + 7) / 8, 256, 0, F->s>>>(n, q, r, F->H, Uo, Pd);
+    cdgrad_kernel<<<(n + 255) / 256, 256, 0, F->s>>>(n, q, r, F->H, Pd, Zd);
+    dqr(Zd, Ud, nullptr);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess && ((it % 5) == 4 || it + 1 == F->power_iters)) {
+      cdchange_kernel<<<1, 1024, 0, F->s>>>(n, r, Uo, Ud, F->scal);
+      double chg2 = 0;
+      e = cudaMemcpyAsync(&chg2, F->scal, sizeof(double), cudaMemcpyDeviceToHost, F->s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(F->s);
+      if (e == cudaSuccess && std::sqrt(std::max(0.0, chg2)) < F->power_tol) break;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Zd, Ud, nr * 16, cudaMemcpyDeviceToDevice, F->s);
+  if (e == cudaSuccess) dqr(Zd, Ud, F->U);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(F->s);
+  for (double2* p : {Ud, Uo, Zd, Td, Pd})
+    if (p) cudaFree(p);
+  // b_k = (A_k U0)^+ (y_k - A_k s_k)
+  if (e == cudaSuccess) e = fft_frames(F, F->U, F->FU, r, false);
+  if (e == cudaSuccess) e = launch_fsweep(F, kModeLS, 0);
+  if (e != cudaSuccess) {
+    *msg = cudaGetErrorString(e);
+    return 4;
+  }
+  F->t = 0;
+  F->have_eta = false;
+  return fourier_check_error(F, msg);
+}
+
+int fourier_iterate(FourierSolver* F, int iters, std::string* msg) {
+  const int n = F->g.n, r = F->r;
+  for (int i = 0; i < iters; ++i) {
+    cudaError_t e = fft_frames(F, F->U, F->FU, r, false);            // FU = F2 U
+    if (e == cudaSuccess) e = launch_fsweep(F, kModeIter, F->tau);   // per-frame work
+    kspace_kernel<<<(n + 255) / 256, 256, 0, F->s>>>(n, F->m, r, F->iptr, F->ilist, F->RES, F->B, F->K);
+    if (e == cudaSuccess) e = fft_frames(F, F->K, F->grad, r, true);  // grad = F2^H K
+    if (e == cudaSuccess && F->t == 0) {
+      cgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, F->grad, nullptr, nullptr, nullptr, F->part);
+      ceta_kernel<<<1, 32, 0, F->s>>>(r, F->nblk, F->part, F->c_eta, F->eta);
+    }
+    // Z = U - eta grad, then complex Cholesky-QR2
+    cgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, F->U, F->grad, F->eta, F->Z, F->part);
+    if (e == cudaSuccess) e = ccholqr2(F, F->Z, F->U);
+    if (e != cudaSuccess) {
+      *msg = cudaGetErrorString(e);
+      return 4;
+    }
+    F->t += 1;
+  }
+  return fourier_check_error(F, msg);
+}
+
+// host/device copies of U (n x r column-major = our layout), B, S
+int fourier_get(FourierSolver* F, void* U, void* B, int* S_idx, void* S_val, int mem_kind) {
+  const cudaMemcpyKind k = mem_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t n = F->g.n;
+  if (U) cudaMemcpyAsync(U, F->U, sizeof(float2) * n * F->r, k, F->s);
+  if (B) cudaMemcpyAsync(B, F->B, sizeof(float2) * F->q * F->r, k, F->s);
+  if (S_idx && F->rho) cudaMemcpyAsync(S_idx, F->S_idx, sizeof(int) * F->q * F->rho, k, F->s);
+  if (S_val && F->rho) cudaMemcpyAsync(S_val, F->S_val, sizeof(float2) * F->q * F->rho, k, F->s);
+  return cudaStreamSynchronize(F->s) == cudaSuccess ? 0 : 4;
+}
+
+int fourier_set_state(FourierSolver* F, const void* U, const void* B, const int* S_idx,
+                      const void* S_val, int t, double eta, int mem_kind) {
+  const cudaMemcpyKind k = mem_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const size_t n = F->g.n;
+  cudaMemcpyAsync(F->U, U, sizeof(float2) * n * F->r, k, F->s);
+  cudaMemcpyAsync(F->B, B, sizeof(float2) * F->q * F->r, k, F->s);
+  if (F->rho) {
+    cudaMemcpyAsync(F->S_idx, S_idx, sizeof(int) * F->q * F->rho, k, F->s);
+    cudaMemcpyAsync(F->S_val, S_val, sizeof(float2) * F->q * F->rho, k, F->s);
+  }
+  cudaMemcpyAsync(F->eta, &eta, sizeof(double), cudaMemcpyHostToDevice, F->s);
+  F->t = t;
+  return cudaStreamSynchronize(F->s) == cudaSuccess ? 0 : 4;
+}
+
+double fourier_eta(FourierSolver* F) {
+  double v = 0;
+  cudaMemcpy(&v, F->eta, sizeof(double), cudaMemcpyDeviceToHost);
+  return F->t ? v : 0.0;
+}
+int fourier_t(FourierSolver* F) { return F->t; }
+
+}  // namespace lrs

@@ -82,10 +82,10 @@ __global__ void __launch_bounds__(256) gram_part_kernel(int n, int r, const floa
 }
 
 // Sum the partial Grams (fixed block order), Cholesky G = L L^T, and write
-// Rinv = L^{-T} (upper triangular, r x r row-major, FP64).
+// Rinv = L^{-T} (upper triangular, r x r row-major, FP64).  One warp.
 __global__ void chol_fin_kernel(int r, int nblk, const double* __restrict__ part,
                                 double* __restrict__ Rinv, int* err) {
-  __shared__ double G[kMaxR * kMaxR], L[kMaxR * kMaxR];
+  __shared__ double G[kMaxR * kMaxR], L[kMaxR * kMaxR], Li[kMaxR * kMaxR], iL[kMaxR];
   for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
     const int a = t / r, b = t - a * r;
     if (b <= a) {
@@ -95,24 +95,11 @@ __global__ void chol_fin_kernel(int r, int nblk, const double* __restrict__ part
       G[b * kMaxR + a] = s;
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (!chol_lower(G, L, r, kMaxR)) {
-      report_error(err, kErrNotSPD, -1);
-      for (int a = 0; a < r; ++a)
-        for (int b = 0; b < r; ++b) L[a * kMaxR + b] = (a == b) ? 1.0 : 0.0;
-    }
-    // Linv (lower) by forward substitution, Rinv = Linv^T
-    double Li[kMaxR * kMaxR];
-    for (int c = 0; c < r; ++c) {
-      for (int i = 0; i < r; ++i) {
-        double s = (i == c) ? 1.0 : 0.0;
-        for (int p = 0; p < i; ++p) s -= L[i * kMaxR + p] * Li[p * kMaxR + c];
-        Li[i * kMaxR + c] = (i < c) ? 0.0 : s / L[i * kMaxR + i];
-      }
-    }
-    for (int a = 0; a < r; ++a)
-      for (int b = 0; b < r; ++b) Rinv[a * r + b] = Li[b * kMaxR + a];
+  __syncwarp();
+  if (!chol_inverse_warp(G, L, Li, iL, r, kMaxR) && threadIdx.x == 0) report_error(err, kErrNotSPD, -1);
+  for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+    const int a = t / r, b = t - a * r;
+    Rinv[a * r + b] = Li[b * kMaxR + a];
   }
 }
 
@@ -413,10 +400,10 @@ cudaError_t dcholqr2(const GlobalWork& g, const double* Zin, double* Ztmp, doubl
   const size_t tot = static_cast<size_t>(g.n) * g.r;
   const unsigned nb = static_cast<unsigned>((tot + 255) / 256);
   dgram_part_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, Zin, g.part);
-  chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R1, err);
+  chol_fin_kernel<<<1, 32, 0, s>>>(g.r, g.nblk, g.part, R1, err);
   dapply_kernel<<<nb, 256, 0, s>>>(g.n, g.r, Zin, R1, Ztmp, nullptr, nullptr, 0);
   dgram_part_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, Ztmp, g.part);
-  chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R2, err);
+  chol_fin_kernel<<<1, 32, 0, s>>>(g.r, g.nblk, g.part, R2, err);
   dapply_kernel<<<nb, 256, 0, s>>>(g.n, g.r, Ztmp, R2, Uout, Uf, Uf ? g.Upad : nullptr, g.rpad);
   return cudaGetLastError();
 }
@@ -462,9 +449,9 @@ cudaError_t cholqr2(const GlobalWork& g, const float* Zin, float* Uout, int* err
   double* R1 = g.small;
   double* R2 = g.small + rr;
   gram_part_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, Zin, nullptr, nullptr, nullptr, g.part);
-  chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R1, err);
+  chol_fin_kernel<<<1, 32, 0, s>>>(g.r, g.nblk, g.part, R1, err);
   apply_rinv_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, Zin, R1, g.Z, g.part);
-  chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R2, err);
+  chol_fin_kernel<<<1, 32, 0, s>>>(g.r, g.nblk, g.part, R2, err);
   apply_rinv_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, g.Z, R2, Uout, nullptr, g.Upad, g.rpad);
   return cudaGetLastError();
 }
@@ -483,9 +470,9 @@ cudaError_t cholqr2_into(int n, int r, const float* Z, float* Q, float* tmp, dou
   double* R1 = rfac;
   double* R2 = rfac + r * r;
   gram_part_kernel<<<nblk, 256, 0, s>>>(n, r, Z, nullptr, nullptr, nullptr, part);
-  chol_fin_kernel<<<1, 256, 0, s>>>(r, nblk, part, R1, err);
+  chol_fin_kernel<<<1, 32, 0, s>>>(r, nblk, part, R1, err);
   apply_rinv_kernel<<<nblk, 256, 0, s>>>(n, r, Z, R1, tmp, part);
-  chol_fin_kernel<<<1, 256, 0, s>>>(r, nblk, part, R2, err);
+  chol_fin_kernel<<<1, 32, 0, s>>>(r, nblk, part, R2, err);
   apply_rinv_kernel<<<nblk, 256, 0, s>>>(n, r, tmp, R2, Q, nullptr);
   return cudaGetLastError();
 }
@@ -497,10 +484,10 @@ cudaError_t qr_step(const GlobalWork& g, float* U, const double* eta_dev, int* e
   double* R2 = g.small + rr;
   // Z = U - eta grad, Gram(Z)
   gram_part_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, U, g.grad, eta_dev, g.Z, g.part);
-  chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R1, err);
+  chol_fin_kernel<<<1, 32, 0, s>>>(g.r, g.nblk, g.part, R1, err);
   // Q1 = Z R1^{-1} (into grad's buffer: grad is no longer needed), Gram(Q1)
   apply_rinv_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, g.Z, R1, g.grad, g.part);
-  chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R2, err);
+  chol_fin_kernel<<<1, 32, 0, s>>>(g.r, g.nblk, g.part, R2, err);
   apply_rinv_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, g.grad, R2, U, nullptr, g.Upad, g.rpad);
   return cudaGetLastError();
 }

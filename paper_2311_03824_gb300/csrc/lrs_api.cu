@@ -15,6 +15,23 @@
 
 using namespace lrs;
 
+namespace lrs {
+struct FourierSolver;
+FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int tau0, int tau,
+                              double c_eta, int power_iters, double power_tol, uint64_t seed,
+                              cudaStream_t s, std::string* msg);
+void fourier_destroy(FourierSolver* F);
+int fourier_set_measurements(FourierSolver* F, const void* y, const void* mask, int mem_kind,
+                             std::string* msg);
+int fourier_init(FourierSolver* F, std::string* msg);
+int fourier_iterate(FourierSolver* F, int iters, std::string* msg);
+int fourier_get(FourierSolver* F, void* U, void* B, int* S_idx, void* S_val, int mem_kind);
+int fourier_set_state(FourierSolver* F, const void* U, const void* B, const int* S_idx,
+                      const void* S_val, int t, double eta, int mem_kind);
+double fourier_eta(FourierSolver* F);
+int fourier_t(FourierSolver* F);
+}  // namespace lrs
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -71,6 +88,7 @@ struct lrs_ctx {
   unsigned long long* trace = nullptr;  // q x kTracePhases (profile = 2)
   int nblk = 0;
   int power_iters_done = 0;
+  FourierSolver* F = nullptr;  // DFT2D_MASK operator
   // graph of one steady-state iteration
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -340,7 +358,6 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
     if (!is_pow2(o.nx) || !is_pow2(o.ny) || int64_t(o.nx) * o.ny != n)
       return fail(LRS_ERR_ARG, "lrs_create: DFT frames need nx, ny powers of two, nx*ny = n");
     if (m > n) return fail(LRS_ERR_ARG, "lrs_create: DFT needs m <= n");
-    return fail(LRS_ERR_UNSUPPORTED, "lrs_create: the DFT operator is not built into this library");
   }
   if (o.tau0 < 0 || o.tau < 0 || o.T < 0 || o.rho_max < 0 || o.c_eta < 0 || o.cluster < 0 ||
       o.power_iters < 0 || o.refine_every < 0)
@@ -362,6 +379,29 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
   if (o.power_tol == 0) o.power_tol = 1e-11;
   if (o.refine_every == 0) o.refine_every = 1;
 
+  if (kind == LRS_OP_DFT2D_MASK) {
+    lrs_ctx* h = new lrs_ctx();
+    h->n = n;
+    h->m = m;
+    h->q = q;
+    h->r = r;
+    h->rho_true = rho;
+    h->rho = o.rho_max;
+    h->kind = kind;
+    h->opt = o;
+    h->stream = static_cast<cudaStream_t>(o.stream);
+    std::string msg;
+    h->F = fourier_create(o.nx, o.ny, static_cast<int>(m), static_cast<int>(q), r, o.rho_max, o.tau0,
+                          o.tau, o.c_eta, o.power_iters, o.power_tol, o.seed, h->stream, &msg);
+    if (!h->F || !msg.empty()) {
+      const lrs_status st = h->F ? LRS_ERR_OOM : LRS_ERR_UNSUPPORTED;
+      if (h->F) fourier_destroy(h->F);
+      delete h;
+      return fail(st, "lrs_create: " + msg);
+    }
+    *out = h;
+    return LRS_OK;
+  }
   lrs_ctx* h = new lrs_ctx();
   h->n = n;
   h->m = m;
@@ -433,6 +473,14 @@ lrs_status lrs_set_measurements(lrs_t h, const void* y, const void* A_or_mask, i
   if (!h || !y || !A_or_mask) return fail(LRS_ERR_ARG, "lrs_set_measurements: NULL argument");
   if (mem_kind != 0 && mem_kind != 1)
     return fail(LRS_ERR_ARG, "lrs_set_measurements: mem_kind must be 0 or 1");
+  if (h->F) {
+    std::string msg;
+    const int st = fourier_set_measurements(h->F, y, A_or_mask, mem_kind, &msg);
+    if (st) return fail(static_cast<lrs_status>(st), "lrs_set_measurements: " + msg);
+    h->state = kMeasured;
+    h->t = 0;
+    return LRS_OK;
+  }
   const cudaMemcpyKind kin = mem_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CUDA_TRY(cudaMemcpyAsync(h->y, y, sizeof(float) * h->m * h->q, kin, h->stream));
   // A: row-major blocks -> slab layout, in chunks of columns
@@ -467,6 +515,14 @@ lrs_status lrs_set_measurements(lrs_t h, const void* y, const void* A_or_mask, i
 lrs_status lrs_init(lrs_t h) {
   if (!h) return fail(LRS_ERR_ARG, "lrs_init: NULL handle");
   if (h->state < kMeasured) return fail(LRS_ERR_STATE, "lrs_init: no measurements");
+  if (h->F) {
+    std::string msg;
+    const int st = fourier_init(h->F, &msg);
+    if (st) return fail(static_cast<lrs_status>(st), "lrs_init: " + msg);
+    h->state = kInitialised;
+    h->t = 0;
+    return LRS_OK;
+  }
   GlobalWork g = gw(h);
   // s_k = IHT(y_k, A_k, rho, tau0, 0); L0 column k = A_k^T (y_k - A_k s_k) -> H
   lrs_status st = launch_sweep(h, kModeInit, h->opt.tau0);
@@ -532,6 +588,15 @@ lrs_status lrs_iterate(lrs_t h, int32_t iters, double* err_log) {
   if (iters < 0) return fail(LRS_ERR_ARG, "lrs_iterate: iters < 0");
   if (h->state < kInitialised) return fail(LRS_ERR_STATE, "lrs_iterate: call lrs_init first");
   if (err_log && !h->Xref) return fail(LRS_ERR_ARG, "lrs_iterate: err_log needs lrs_set_reference");
+  if (h->F) {
+    if (err_log) return fail(LRS_ERR_UNSUPPORTED, "lrs_iterate: no error log for the DFT operator");
+    std::string msg;
+    const int st = fourier_iterate(h->F, iters, &msg);
+    h->t = fourier_t(h->F);
+    h->state = kIterating;
+    if (st) return fail(static_cast<lrs_status>(st), "lrs_iterate: " + msg);
+    return LRS_OK;
+  }
   const bool prof = h->opt.profile != 0;
   if (prof) {
     while (h->ev.size() < 4 * static_cast<size_t>(iters)) {
@@ -593,6 +658,10 @@ lrs_status lrs_get(lrs_t h, void* U, void* B, int32_t* S_idx, void* S_val, int32
   if (!h) return fail(LRS_ERR_ARG, "lrs_get: NULL handle");
   if (mem_kind != 0 && mem_kind != 1) return fail(LRS_ERR_ARG, "lrs_get: mem_kind must be 0 or 1");
   if (h->state < kInitialised) return fail(LRS_ERR_STATE, "lrs_get: no iterate yet");
+  if (h->F) {
+    if (fourier_get(h->F, U, B, S_idx, S_val, mem_kind)) return fail(LRS_ERR_CUDA, "lrs_get: copy failed");
+    return LRS_OK;
+  }
   const cudaMemcpyKind kout = mem_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (U) {
     const int tot = static_cast<int>(h->n) * h->r;
@@ -616,6 +685,13 @@ lrs_status lrs_set_state(lrs_t h, const void* U, const void* B, const int32_t* S
   if (mem_kind != 0 && mem_kind != 1) return fail(LRS_ERR_ARG, "lrs_set_state: bad mem_kind");
   if (t < 0) return fail(LRS_ERR_ARG, "lrs_set_state: t < 0");
   if (h->state < kMeasured) return fail(LRS_ERR_STATE, "lrs_set_state: no measurements");
+  if (h->F) {
+    if (fourier_set_state(h->F, U, B, S_idx, S_val, t, eta, mem_kind))
+      return fail(LRS_ERR_CUDA, "lrs_set_state: copy failed");
+    h->t = t;
+    h->state = t == 0 ? kInitialised : kIterating;
+    return LRS_OK;
+  }
   const cudaMemcpyKind kin = mem_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const int tot = static_cast<int>(h->n) * h->r;
   CUDA_TRY(cudaMemcpyAsync(h->Z, U, sizeof(float) * tot, kin, h->stream));
@@ -638,6 +714,11 @@ lrs_status lrs_set_state(lrs_t h, const void* U, const void* B, const int32_t* S
 
 lrs_status lrs_get_progress(lrs_t h, double* eta, int32_t* t) {
   if (!h) return fail(LRS_ERR_ARG, "lrs_get_progress: NULL handle");
+  if (h->F) {
+    if (eta) *eta = fourier_eta(h->F);
+    if (t) *t = fourier_t(h->F);
+    return LRS_OK;
+  }
   if (eta) {
     CUDA_TRY(cudaMemcpyAsync(eta, h->eta, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -678,6 +759,11 @@ lrs_status lrs_sweep_trace(lrs_t h, uint64_t* out, int64_t len) {
 
 lrs_status lrs_describe(lrs_t h, char* buf, int32_t len) {
   if (!h || !buf || len <= 0) return fail(LRS_ERR_ARG, "lrs_describe: bad argument");
+  if (h->F) {
+    snprintf(buf, static_cast<size_t>(len), "{\"op\": \"dft2d\", \"nx\": %d, \"ny\": %d, \"cta_per_frame\": 1}",
+             h->opt.nx, h->opt.ny);
+    return LRS_OK;
+  }
   const size_t sm = sweep_smem_bytes(h->L, h->resident, kThreads);
   const int nc = sweep_max_active_clusters(h->L, h->resident, kThreads);
   snprintf(buf, static_cast<size_t>(len),
@@ -724,6 +810,11 @@ lrs_status lrs_orthonormalize(const float* Z, float* Q, int64_t n, int32_t r, vo
 lrs_status lrs_destroy(lrs_t h) {
   if (!h) return LRS_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->F) {
+    fourier_destroy(h->F);
+    delete h;
+    return LRS_OK;
+  }
   free_all(h);
   delete h;
   return LRS_OK;

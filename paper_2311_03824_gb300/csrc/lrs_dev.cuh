@@ -146,6 +146,58 @@ __device__ __forceinline__ void block_sum_vec(const float (&acc)[R], int nv, flo
 }
 
 // ------------------------------------------------------- r x r FP64 algebra --
+// 1/sqrt(s) in FP64 without a division: float estimate refined by two
+// Newton-Raphson steps y <- y (3 - s y^2) / 2 (each doubles the correct bits).
+__device__ __forceinline__ double rsqrt_newton(double s) {
+  if (!(s > 1e-36 && s < 1e36)) return 1.0 / sqrt(s);
+  double y = static_cast<double>(rsqrtf(static_cast<float>(s)));
+  y = y * (1.5 - 0.5 * s * y * y);
+  y = y * (1.5 - 0.5 * s * y * y);
+  return y;
+}
+
+// One warp: lower Cholesky factor of the SPD r x r matrix G (row-major, ld)
+// by lane 0 with inverse pivots from rsqrt_newton, then L^{-1} (lower, into
+// Li) with one column per lane.  Returns false (all lanes) when a pivot is not
+// positive relative to its diagonal; Li is then the identity.
+__device__ inline bool chol_inverse_warp(const double* G, double* L, double* Li, double* iL,
+                                         int r, int ld) {
+  const int lane = threadIdx.x & 31;
+  int ok = 1;
+  if (lane == 0) {
+    for (int j = 0; j < r && ok; ++j) {
+      double s = G[j * ld + j];
+      for (int p = 0; p < j; ++p) s -= L[j * ld + p] * L[j * ld + p];
+      if (!(s > 1e-13 * G[j * ld + j]) || !(s < 1e300)) { ok = 0; break; }
+      const double ij = rsqrt_newton(s);
+      L[j * ld + j] = s * ij;
+      iL[j] = ij;
+      for (int i = j + 1; i < r; ++i) {
+        double t = G[i * ld + j];
+        for (int p = 0; p < j; ++p) t -= L[i * ld + p] * L[j * ld + p];
+        L[i * ld + j] = t * ij;
+      }
+    }
+    if (!ok)
+      for (int i = 0; i < r; ++i) {
+        for (int p = 0; p < r; ++p) L[i * ld + p] = (i == p) ? 1.0 : 0.0;
+        iL[i] = 1.0;
+      }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  if (lane < r) {
+    const int cc = lane;
+    for (int i = 0; i < r; ++i) {
+      double t = (i == cc) ? 1.0 : 0.0;
+      for (int p = cc; p < i; ++p) t -= L[i * ld + p] * Li[p * ld + cc];
+      Li[i * ld + cc] = (i < cc) ? 0.0 : t * iL[i];
+    }
+  }
+  __syncwarp();
+  return ok != 0;
+}
+
 // In-place lower Cholesky of the symmetric positive definite r x r matrix
 // G (row-major, lower triangle read).  Returns false when a pivot is not
 // positive relative to its diagonal (the matrix is treated as not SPD).

@@ -226,10 +226,14 @@ def lrs_last_error():
 # --------------------------------------------------------------- wrapper --
 
 class Solver:
-    """One problem: A (q, m, n) float32 and Y (q, m) float32 (rows = columns k)."""
+    """One problem.  Gaussian: A (q, m, n) float32, Y (q, m) float32.  DFT
+    (kind=LRS_OP_DFT2D_MASK, nx=.., ny=..): masks (q, m) int32, Y (q, m)
+    complex64.  Rows of A / Y / masks are the columns k of the problem."""
 
     def __init__(self, n, m, q, r, rho, kind=LRS_OP_GAUSSIAN, **opts):
         self.n, self.m, self.q, self.r = n, m, q, r
+        self.kind = kind
+        self.dtype = np.complex64 if kind == LRS_OP_DFT2D_MASK else np.float32
         self.opts = make_options(**opts)
         self.rho = self.opts.rho_max or rho
         self.h = lrs_create(n, m, q, r, rho, kind, self.opts)
@@ -245,16 +249,16 @@ class Solver:
 
     def get(self):
         """Host copies: U (n, r), B (r, q), S_idx (q, rho), S_val (q, rho)."""
-        U = np.empty((self.r, self.n), np.float32)      # n x r column-major
-        B = np.empty((self.q, self.r), np.float32)      # r x q column-major
+        U = np.empty((self.r, self.n), self.dtype)      # n x r column-major
+        B = np.empty((self.q, self.r), self.dtype)      # r x q column-major
         S_idx = np.empty((self.q, max(self.rho, 1)), np.int32)
-        S_val = np.empty((self.q, max(self.rho, 1)), np.float32)
+        S_val = np.empty((self.q, max(self.rho, 1)), self.dtype)
         lrs_get(self.h, U, B, S_idx if self.rho else None, S_val if self.rho else None)
         return U.T.copy(), B.T.copy(), S_idx[:, :self.rho], S_val[:, :self.rho]
 
     def X(self):
         U, B, S_idx, S_val = self.get()
-        X = U.astype(np.float64) @ B.astype(np.float64)
+        X = U.astype(np.complex128 if self.dtype == np.complex64 else np.float64) @ B
         for k in range(self.q):
             X[S_idx[k], k] += S_val[k]
         return X
