@@ -71,11 +71,12 @@ typedef struct {
   int32_t rho_max;          /* entries HardThreshold keeps (0 -> rho)          */
   int32_t nx, ny;           /* DFT frame: n = nx*ny, both powers of two        */
   lrs_a_dtype a_dtype;      /* storage of A_k for the sweeps                   */
-  int32_t refine_every;     /* low-precision A_k: exact-operator refinement of
-                               the residual every this many iterations (0 -> 1) */
+  int32_t refine_every;     /* low-precision A_k: defect correction of y_k with
+                               the exact FP32 operator every this many
+                               iterations (0 -> 8); see lrs_iterate          */
   int32_t cluster;          /* Gaussian sweep: CTAs per column (0 -> autotune) */
-  int32_t power_iters;      /* cap on subspace iterations in lrs_init (0 -> 300) */
-  double power_tol;         /* stop when ||(I - U_old U_old^T) U||_F < tol (0 -> 1e-6) */
+  int32_t power_iters;      /* cap on subspace iterations in lrs_init (0 -> 1000) */
+  double power_tol;         /* stop when ||(I - U_old U_old^T) U||_F < tol (0 -> 1e-11) */
   int32_t use_graph;        /* 1: replay steady-state iterations as a CUDA graph */
   void* stream;             /* cudaStream_t for every launch (NULL = default)  */
   uint64_t seed;            /* seed of the subspace-iteration start            */
@@ -105,6 +106,11 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho,
  *             [0, n) and strictly ascending.
  *  mem_kind:  0 = host pointers, 1 = device pointers.  Either way the data is
  *             copied (and re-laid-out) before the call returns.
+ * With a_dtype BF16 / FP8_HI / FP8_HILO the handle keeps the FP32 blocks as
+ * given (the exact operator, used by the defect correction) plus the sweep's
+ * encoded copy: BF16 by round-to-nearest; FP8_HI as e4m3(A(i,j)/s1_i) with
+ * s1_i = max_j |A(i,j)| / 448; FP8_HILO adds a second e4m3 plane of the
+ * remainder A - s1_i hi with its own row scale s2_i.
  * State: CREATED or later (re-measuring resets the handle to MEASURED).
  * Errors: LRS_ERR_ARG (NULL pointer, bad mem_kind, mask out of range or not
  * ascending), LRS_ERR_STATE, LRS_ERR_OOM, LRS_ERR_CUDA. */
@@ -124,7 +130,14 @@ lrs_status lrs_init(lrs_t h);
  * gradient (spectral norm), U <- Q(U - eta grad) by Cholesky-QR2.
  * err_log: NULL, or a host array of `iters` doubles that receives
  * ||X_t - X_ref||_F / ||X_ref||_F after each iteration (needs
- * lrs_set_reference).  State: INITIALISED or ITERATING -> ITERATING.
+ * lrs_set_reference).
+ * Low-precision A_k (a_dtype != FP32): the sweep runs on the encoded copy
+ * Ã_k against corrected measurements ỹ_k = y_k - (A_k - Ã_k)(U b_k + s_k),
+ * refreshed with the exact operator before the first iteration after
+ * lrs_init / lrs_set_state and then every refine_every iterations, so that
+ * an exact solution of y_k = A_k x_k is a fixed point of the iteration
+ * (defect correction; the paper computes in one precision throughout).
+ * State: INITIALISED or ITERATING -> ITERATING.
  * Errors: LRS_ERR_ARG (iters < 0, err_log without reference), LRS_ERR_STATE,
  * LRS_ERR_NUMERICAL (column id in lrs_last_error), LRS_ERR_CUDA. */
 lrs_status lrs_iterate(lrs_t h, int32_t iters, double* err_log);

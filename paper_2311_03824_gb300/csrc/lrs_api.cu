@@ -67,8 +67,12 @@ struct lrs_ctx {
   GaussLayout L{};
   int resident = 1;
   // device buffers
-  float* A = nullptr;      // slab layout
+  void* A = nullptr;       // slab layout, element type L.et
   float* y = nullptr;      // q x m
+  float* Aex = nullptr;    // low-precision forms: exact FP32 A_k, row-major q x m x n
+  float* rscale = nullptr; // FP8 forms: q x m x (1 or 2) row scales
+  float* ycorr = nullptr;  // low-precision forms: defect-corrected y (q x m)
+  int last_refine = -1;    // iteration count t at the last refinement (-1: none since set-up)
   float* U = nullptr;      // n x r row-major
   float* Upad = nullptr;   // (cs*ns) x rpad row-major, zero padded (sweep input)
   float* Bk = nullptr;     // q x r
@@ -128,6 +132,7 @@ GaussLayout gauss_shape(const lrs_ctx* h, int cs, int stages) {
   const int64_t w = (h->n + cs - 1) / cs;
   L.ns = static_cast<int>((w + 31) / 32 * 32);
   L.stages = stages;
+  L.et = static_cast<int>(h->opt.a_dtype);
   return L;
 }
 
@@ -199,7 +204,8 @@ lrs_status launch_sweep(lrs_ctx* h, int mode, int tau) {
   a.mode = mode;
   a.tau = tau;
   a.A = h->A;
-  a.y = h->y;
+  a.y = (mode == kModeIter && h->L.et != 0) ? h->ycorr : h->y;
+  a.rscale = h->rscale;
   a.U = h->U;
   a.Upad = h->Upad;
   a.S_idx = h->S_idx;
@@ -215,8 +221,14 @@ lrs_status launch_sweep(lrs_ctx* h, int mode, int tau) {
 
 // One GDmin iteration (Algorithm 1): sweep, gradient, eta at t = 1, QR.
 // With `evs` (4 events) the phase boundaries are recorded on the stream.
-lrs_status enqueue_iteration(lrs_ctx* h, bool first, cudaEvent_t* evs = nullptr) {
+// Low-precision forms of A_k first refresh the defect-corrected measurements
+// when `refine` is set (counted in the sweep phase).
+lrs_status enqueue_iteration(lrs_ctx* h, bool first, cudaEvent_t* evs = nullptr,
+                             bool refine = false) {
   if (evs) CUDA_TRY(cudaEventRecord(evs[0], h->stream));
+  if (refine)
+    CUDA_TRY(refine_residual(h->L, h->Aex, h->A, h->rscale, h->U, h->Bk, h->S_idx, h->S_val,
+                             h->y, h->ycorr, h->H, h->stream));
   lrs_status st = launch_sweep(h, kModeIter, h->opt.tau);
   if (st != LRS_OK) return st;
   if (evs) CUDA_TRY(cudaEventRecord(evs[1], h->stream));
@@ -328,7 +340,7 @@ void free_all(lrs_ctx* h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   h->gexec = nullptr;
   h->graph = nullptr;
-  void* ps[] = {h->A, h->y, h->U, h->Upad, h->Bk, h->S_idx, h->S_val, h->H, h->grad, h->Z,
+  void* ps[] = {h->A, h->y, h->Aex, h->rscale, h->ycorr, h->U, h->Upad, h->Bk, h->S_idx, h->S_val, h->H, h->grad, h->Z,
                 h->U2, h->P, h->part, h->small, h->eta, h->err, h->Xref, h->errpart, h->trace};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -367,8 +379,10 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
     return fail(LRS_ERR_ARG, "lrs_create: cluster must be 0, 1, 2, 4, 8 or 16");
   if (o.slab_mode < 0 || o.slab_mode > 2 || o.stages < 0 || o.stages > 16)
     return fail(LRS_ERR_ARG, "lrs_create: slab_mode in 0..2, stages in 0..16");
-  if (o.a_dtype != LRS_A_FP32)
-    return fail(LRS_ERR_UNSUPPORTED, "lrs_create: only float32 A_k storage is built in");
+  if (o.a_dtype < LRS_A_FP32 || o.a_dtype > LRS_A_FP8_HILO)
+    return fail(LRS_ERR_ARG, "lrs_create: unknown a_dtype");
+  if (kind == LRS_OP_DFT2D_MASK && o.a_dtype != LRS_A_FP32)
+    return fail(LRS_ERR_ARG, "lrs_create: a_dtype applies to the Gaussian operator only");
   if (o.tau0 == 0) o.tau0 = 10;
   if (o.tau == 0) o.tau = 3;
   if (o.T == 0) o.T = 200;
@@ -377,7 +391,7 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
   if (o.rho_max > n) return fail(LRS_ERR_ARG, "lrs_create: rho_max > n");
   if (o.power_iters == 0) o.power_iters = 1000;
   if (o.power_tol == 0) o.power_tol = 1e-11;
-  if (o.refine_every == 0) o.refine_every = 1;
+  if (o.refine_every == 0) o.refine_every = 8;
 
   if (kind == LRS_OP_DFT2D_MASK) {
     lrs_ctx* h = new lrs_ctx();
@@ -425,10 +439,15 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   h->nblk = std::max(1, std::min<int>(nsm > 0 ? nsm : 148, static_cast<int>((n + 63) / 64)));
-  const size_t per_col = static_cast<size_t>(h->L.cs) * h->L.m * h->L.ns;
+  const size_t per_col = static_cast<size_t>(h->L.cs) * h->L.m * h->L.ns * elem_bytes(h->L.et);
   lrs_status st = LRS_OK;
   const size_t upad_n = static_cast<size_t>(h->L.cs) * h->L.ns * sweep_rpad(r);
-  if ((st = dalloc(&h->A, per_col * q)) || (st = dalloc(&h->y, size_t(m) * q)) ||
+  const int lowp = h->L.et != 0, per_row = h->L.et == 3 ? 2 : 1;
+  if ((st = dalloc(reinterpret_cast<unsigned char**>(&h->A), per_col * q)) ||
+      (st = dalloc(&h->y, size_t(m) * q)) ||
+      (lowp && (st = dalloc(&h->Aex, size_t(m) * n * q))) ||
+      (lowp && (st = dalloc(&h->ycorr, size_t(m) * q))) ||
+      (h->L.et >= 2 && (st = dalloc(&h->rscale, size_t(m) * q * per_row))) ||
       (st = dalloc(&h->Upad, upad_n)) ||
       (st = dalloc(&h->U, size_t(n) * r)) || (st = dalloc(&h->Bk, size_t(q) * r)) ||
       (st = dalloc(&h->S_idx, size_t(q) * std::max(1, h->rho))) || (st = dalloc(&h->S_val, size_t(q) * std::max(1, h->rho))) ||
@@ -483,8 +502,23 @@ lrs_status lrs_set_measurements(lrs_t h, const void* y, const void* A_or_mask, i
   }
   const cudaMemcpyKind kin = mem_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CUDA_TRY(cudaMemcpyAsync(h->y, y, sizeof(float) * h->m * h->q, kin, h->stream));
-  // A: row-major blocks -> slab layout, in chunks of columns
   const size_t col_elems = static_cast<size_t>(h->m) * h->n;
+  h->last_refine = -1;
+  if (h->L.et != 0) {
+    // low-precision forms: keep the exact FP32 operator, encode the sweep's copy from it
+    CUDA_TRY(cudaMemcpyAsync(h->Aex, A_or_mask, sizeof(float) * col_elems * h->q, kin, h->stream));
+    const int64_t chunk = std::max<int64_t>(1, (int64_t(1) << 30) / (int64_t)(col_elems * 4));
+    for (int64_t k0 = 0; k0 < h->q; k0 += chunk) {
+      const int64_t kc = std::min(chunk, h->q - k0);
+      CUDA_TRY(repack_gauss(h->L, h->Aex + k0 * col_elems, static_cast<int>(k0),
+                            static_cast<int>(kc), h->A, h->rscale, h->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->state = kMeasured;
+    h->t = 0;
+    return LRS_OK;
+  }
+  // A: row-major blocks -> slab layout, in chunks of columns
   int64_t chunk = std::max<int64_t>(1, (int64_t(256) << 20) / (int64_t)(col_elems * 4));
   chunk = std::min<int64_t>(chunk, h->q);
   float* tmp = nullptr;
@@ -495,14 +529,14 @@ lrs_status lrs_set_measurements(lrs_t h, const void* y, const void* A_or_mask, i
     if (mem_kind == 0) {
       cudaError_t e = cudaMemcpyAsync(tmp, src, sizeof(float) * col_elems * kc,
                                       cudaMemcpyHostToDevice, h->stream);
-      if (e == cudaSuccess) e = repack_gauss(h->L, tmp, static_cast<int>(k0), static_cast<int>(kc), h->A, h->stream);
+      if (e == cudaSuccess) e = repack_gauss(h->L, tmp, static_cast<int>(k0), static_cast<int>(kc), h->A, nullptr, h->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
       if (e != cudaSuccess) {
         cudaFree(tmp);
         return fail(LRS_ERR_CUDA, std::string("lrs_set_measurements: ") + cudaGetErrorString(e));
       }
     } else {
-      CUDA_TRY(repack_gauss(h->L, src, static_cast<int>(k0), static_cast<int>(kc), h->A, h->stream));
+      CUDA_TRY(repack_gauss(h->L, src, static_cast<int>(k0), static_cast<int>(kc), h->A, nullptr, h->stream));
     }
   }
   if (tmp) cudaFree(tmp);
@@ -580,6 +614,7 @@ lrs_status lrs_init(lrs_t h) {
   if (st) return st;
   h->state = kInitialised;
   h->t = 0;
+  h->last_refine = -1;
   return LRS_OK;
 }
 
@@ -608,7 +643,10 @@ lrs_status lrs_iterate(lrs_t h, int32_t iters, double* err_log) {
   for (int i = 0; i < iters; ++i) {
     const bool first = (h->t == 0);
     cudaEvent_t* evs = prof ? &h->ev[4 * static_cast<size_t>(i)] : nullptr;
-    if (!first && h->opt.use_graph && h->stream && !prof) {
+    const bool refine = h->L.et != 0 &&
+                        (h->last_refine < 0 || h->t - h->last_refine >= h->opt.refine_every);
+    if (refine) h->last_refine = h->t;
+    if (!first && h->opt.use_graph && h->stream && !prof && h->L.et == 0) {
       if (!h->gexec) {
         CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         lrs_status st = enqueue_iteration(h, false);
@@ -621,7 +659,7 @@ lrs_status lrs_iterate(lrs_t h, int32_t iters, double* err_log) {
       }
       CUDA_TRY(cudaGraphLaunch(h->gexec, h->stream));
     } else {
-      lrs_status st = enqueue_iteration(h, first, evs);
+      lrs_status st = enqueue_iteration(h, first, evs, refine);
       if (st) return st;
     }
     h->t += 1;
@@ -708,6 +746,7 @@ lrs_status lrs_set_state(lrs_t h, const void* U, const void* B, const int32_t* S
   CUDA_TRY(cudaMemcpyAsync(h->eta, &eta, sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   h->t = t;
+  h->last_refine = -1;
   h->state = t == 0 ? kInitialised : kIterating;
   return LRS_OK;
 }
@@ -768,9 +807,10 @@ lrs_status lrs_describe(lrs_t h, char* buf, int32_t len) {
   const int nc = sweep_max_active_clusters(h->L, h->resident, kThreads);
   snprintf(buf, static_cast<size_t>(len),
            "{\"op\": \"%s\", \"cluster\": %d, \"ns\": %d, \"stages\": %d, \"resident\": %d, "
-           "\"smem_per_cta\": %zu, \"max_active_clusters\": %d}",
+           "\"smem_per_cta\": %zu, \"max_active_clusters\": %d, \"a_dtype\": %d, "
+           "\"refine_every\": %d}",
            h->kind == LRS_OP_GAUSSIAN ? "gaussian" : "dft2d", h->L.cs, h->L.ns, h->L.stages,
-           h->resident, sm, nc);
+           h->resident, sm, nc, h->L.et, h->opt.refine_every);
   return LRS_OK;
 }
 

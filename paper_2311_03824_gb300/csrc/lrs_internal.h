@@ -21,25 +21,34 @@ enum SweepMode : int {
 // Layout of the Gaussian operator inside the handle ("slab" layout): column k's
 // A_k is split by columns j into `cs` slabs of `ns` columns (ns a multiple of
 // 32); slab c holds columns [c*ns, min(n, (c+1)*ns)), zero-padded, as ns/32
-// consecutive tiles of m rows x 32 floats; inside a tile, row i is 32
-// consecutive floats whose 16-byte chunks are XOR-permuted by (i mod 8):
-//   A_k(i, c*ns + 32*b + 4*q + e) is at
-//   ((k*cs + c)*ns*m) + b*32*m + i*32 + 4*(q ^ (i & 7)) + e.
+// consecutive tiles of m rows x 32 elements; inside a tile, row i is 32
+// consecutive elements whose 4-element chunks are XOR-permuted by (i mod 8):
+//   A_k(i, c*ns + 32*b + 4*q + e) is element
+//   ((k*cs + c)*ns*m) + b*32*m + i*32 + 4*(q ^ (i & 7)) + e
+// counted in elements of the stored type.  The FP8 hi/lo form stores each
+// tile as its hi plane (m x 32 bytes) followed by its lo plane, so a tile is
+// 64*m bytes and element offsets inside a plane are as above.
 struct GaussLayout {
   int n, m, q, r, rho;
   int cs;      // CTAs per column (thread-block cluster size)
   int ns;      // slab width (multiple of 32)
   int stages;  // tile stages of the streamed ring (ignored when resident)
+  int et;      // element type of the stored A_k: 0 fp32, 1 bf16, 2 fp8 e4m3 (row scale),
+               // 3 fp8 e4m3 hi + lo planes (two row scales)
 };
+
+// bytes per element of a tile (both planes for the hi/lo form)
+__host__ __device__ inline int elem_bytes(int et) { return et == 0 ? 4 : (et == 1 || et == 3) ? 2 : 1; }
 
 struct SweepArgs {
   GaussLayout L;
   int mode;
   int tau;
-  const float* A;   // slab layout
+  const void* A;    // slab layout, element type L.et
   const float* y;   // q x m (y_k contiguous)
   const float* U;   // n x r row-major
   const float* Upad;  // (cs*ns) x sweep_rpad(r) row-major, zero padded
+  const float* rscale;  // FP8 forms: q x m x (1 or 2) per-row scales (hi, lo)
   int* S_idx;       // q x rho (ascending per column), in/out
   float* S_val;     // q x rho
   float* B;         // q x r (b_k contiguous)
@@ -61,7 +70,14 @@ cudaError_t sweep_launch(const SweepArgs& a, int nthreads, cudaStream_t s);
 cudaError_t sweep_prepare(const GaussLayout& L, int nthreads);  // set attributes
 int sweep_max_active_clusters(const GaussLayout& L, int resident, int nthreads);
 cudaError_t repack_gauss(const GaussLayout& L, const float* A_rowmajor, int k0, int kc,
-                         float* A_int, cudaStream_t s);
+                         void* A_int, float* rscale, cudaStream_t s);
+// ycorr_k = y_k - (A_k - Atilde_k)(U b_k + s_k) for every column (exact FP32
+// operator A row-major q x m x n, Atilde in the slab layout of element type
+// L.et != 0); xbuf: q x n scratch that receives x_k = U b_k + s_k.
+cudaError_t refine_residual(const GaussLayout& L, const float* A_exact, const void* A_int,
+                            const float* rscale, const float* U, const float* Bk,
+                            const int* S_idx, const float* S_val, const float* y, float* ycorr,
+                            float* xbuf, cudaStream_t s);
 
 // Global (column-reduced) steps (global_ops.cu).
 // Row stride of the padded copy of U the sweep stages by TMA: r rounded up

@@ -34,6 +34,9 @@
 // decisions.  A slot is rewritten two exchanges later, after every peer has
 // signalled the exchange in between, i.e. after it finished reading.
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
 #include "lrs_dev.cuh"
 #include "lrs_internal.h"
 
@@ -57,10 +60,12 @@ __host__ __device__ inline int cache_slots(const GaussLayout& L, int resident) {
 
 struct Carve {
   size_t bars, slab, Us, W, yv, dv, ev, gs, sl, vv, gpart, hist, tie, ck, cv, cn, Gm, fsm, flags,
-      redf, sup, cache, xch, xs, total;
+      redf, sup, cache, rsc, xch, xs, total;
 };
 
-__host__ __device__ inline size_t tile_bytes(const GaussLayout& L) { return (size_t)L.m * kTW * 4; }
+__host__ __device__ inline size_t tile_bytes(const GaussLayout& L) {
+  return (size_t)L.m * kTW * elem_bytes(L.et);
+}
 
 __host__ __device__ inline Carve carve(const GaussLayout& L, int resident) {
   Carve c;
@@ -91,6 +96,7 @@ __host__ __device__ inline Carve carve(const GaussLayout& L, int resident) {
   c.redf = o;  o += a16((size_t)kNW * kMaxR * 4 + 256);
   c.sup = o;   o += a16((size_t)rho * 12 + 16);        // sup_j, sup_v, slot
   c.cache = o; o += a16((size_t)nc * L.m * 4 + (size_t)(nc + 1) * 4);
+  c.rsc = o;   o += a16((size_t)2 * L.m * 4);                  // row scales (FP8 forms)
   const size_t xw = (size_t)L.m * R * 4;                            // W partial
   const size_t xa = a16((size_t)L.m * 4) + kMaxR * kMaxR * 8 + 16;  // A s partial + Gram + count
   const size_t xg = a16((size_t)L.m * 4) + 16;                      // A g_G partial + ||g_G||^2
@@ -107,6 +113,65 @@ __host__ __device__ inline Carve carve(const GaussLayout& L, int resident) {
 // offset of element (i, j) inside a slab (tiles of m x 32, swizzled chunks)
 __device__ __forceinline__ int elem_off(int m, int i, int j) {
   return (j >> 5) * (m * kTW) + i * kTW + ((((j & 31) >> 2) ^ (i & 7)) << 2) + (j & 3);
+}
+
+// ---- element access for the stored forms of A_k -----------------------------
+// 4 consecutive columns 4q..4q+3 of row i of a tile (chunk q), dequantised
+// (sc1/sc2: per-row scales of the FP8 forms, in shared memory).
+template <int ET>
+__device__ __forceinline__ float4 load4(const unsigned char* tile, int m, int i, int q,
+                                        const float* sc1, const float* sc2) {
+  const int off = i * kTW + ((q ^ (i & 7)) << 2);  // element offset of the chunk
+  if constexpr (ET == 0) {
+    return *reinterpret_cast<const float4*>(tile + static_cast<size_t>(off) * 4);
+  } else if constexpr (ET == 1) {
+    const uint2 raw = *reinterpret_cast<const uint2*>(tile + static_cast<size_t>(off) * 2);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    const __nv_fp8x4_e4m3 h = *reinterpret_cast<const __nv_fp8x4_e4m3*>(tile + off);
+    const float4 fh = static_cast<float4>(h);
+    const float s1 = sc1[i];
+    float4 v = make_float4(fh.x * s1, fh.y * s1, fh.z * s1, fh.w * s1);
+    if constexpr (ET == 3) {
+      const __nv_fp8x4_e4m3 lo = *reinterpret_cast<const __nv_fp8x4_e4m3*>(tile + static_cast<size_t>(m) * kTW + off);
+      const float4 fl = static_cast<float4>(lo);
+      const float s2 = sc2[i];
+      v.x = fmaf(fl.x, s2, v.x);
+      v.y = fmaf(fl.y, s2, v.y);
+      v.z = fmaf(fl.z, s2, v.z);
+      v.w = fmaf(fl.w, s2, v.w);
+    }
+    return v;
+  }
+}
+// element (i, j) of a slab (any tile), dequantised with the row's scales s1, s2
+template <int ET>
+__device__ __forceinline__ float elem1s(const unsigned char* slab, int m, int i, int j, float s1,
+                                        float s2) {
+  const size_t tb = static_cast<size_t>(m) * kTW * elem_bytes(ET);
+  const unsigned char* tile = slab + static_cast<size_t>(j >> 5) * tb;
+  const int off = i * kTW + ((((j & 31) >> 2) ^ (i & 7)) << 2) + (j & 3);
+  if constexpr (ET == 0) {
+    return *reinterpret_cast<const float*>(tile + static_cast<size_t>(off) * 4);
+  } else if constexpr (ET == 1) {
+    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(tile + static_cast<size_t>(off) * 2));
+  } else {
+    float v = static_cast<float>(*reinterpret_cast<const __nv_fp8_e4m3*>(tile + off)) * s1;
+    if constexpr (ET == 3)
+      v = fmaf(static_cast<float>(*reinterpret_cast<const __nv_fp8_e4m3*>(tile + static_cast<size_t>(m) * kTW + off)),
+               s2, v);
+    return v;
+  }
+}
+template <int ET>
+__device__ __forceinline__ float elem1(const unsigned char* slab, int m, int i, int j,
+                                       const float* sc1, const float* sc2) {
+  if constexpr (ET >= 2)
+    return elem1s<ET>(slab, m, i, j, sc1[i], ET == 3 ? sc2[i] : 0.f);
+  else
+    return elem1s<ET>(slab, m, i, j, 0.f, 0.f);
 }
 
 // HardThreshold order: larger |v| first, then the lower index.
@@ -181,9 +246,12 @@ struct Tracer {
 
 // Everything one CTA needs about its column and its shared memory.
 struct Ctx {
-  const float* Asl;  // resident slab (shared) or nullptr
-  const float* Ag;   // this CTA's slab in global memory
-  const float* ring; // ring stages (streamed)
+  const unsigned char* Asl;   // resident slab (shared) or nullptr
+  const unsigned char* Ag;    // this CTA's slab in global memory
+  const unsigned char* ring;  // ring stages (streamed)
+  size_t tbytes;              // bytes of one tile
+  const float* sc1;           // per-row scales of the FP8 forms (shared)
+  const float* sc2;
   uint64_t* full;    // ring barriers
   uint64_t* empty;
   uint64_t* xbar;    // exchange barriers [2]
@@ -248,8 +316,8 @@ __device__ __forceinline__ void xchg_publish_wait(const Ctx& C, int e) {
 
 // ---- tile access --------------------------------------------------------
 // Returns tile b of the current product (waiting for it when streamed).
-__device__ __forceinline__ const float* acquire_tile(Ctx& C, int b) {
-  if (C.Asl) return C.Asl + static_cast<size_t>(b) * C.m * kTW;
+__device__ __forceinline__ const unsigned char* acquire_tile(Ctx& C, int b) {
+  if (C.Asl) return C.Asl + static_cast<size_t>(b) * C.tbytes;
   const unsigned s = C.tile_seq % C.stages, use = C.tile_seq / C.stages;
   unsigned it = 0;
   while (!mbar_try_wait(&C.full[s], use & 1u)) {
@@ -258,7 +326,7 @@ __device__ __forceinline__ const float* acquire_tile(Ctx& C, int b) {
       break;
     }
   }
-  return C.ring + static_cast<size_t>(s) * C.m * kTW;
+  return C.ring + static_cast<size_t>(s) * C.tbytes;
 }
 __device__ __forceinline__ void release_tile(Ctx& C) {
   if (C.Asl) return;
@@ -276,13 +344,14 @@ __device__ __forceinline__ void drain_pass(Ctx& C) {
 }
 // While the slots are pending (flag in cache_col[nc]), warp 0 copies the
 // cached support columns that lie in tile b out of the tile.
-__device__ __forceinline__ void cache_fill_from_tile(const Ctx& C, const float* t, int b) {
+template <int ET>
+__device__ __forceinline__ void cache_fill_from_tile(const Ctx& C, const unsigned char* t, int b) {
   if ((threadIdx.x >> 5) != 0 || C.nc == 0 || !C.cache_col[C.nc]) return;
   for (int s = 0; s < C.nc; ++s) {
     const int j = C.cache_col[s];
     if (j >= b * kTW && j < (b + 1) * kTW)
       for (int i = threadIdx.x & 31; i < C.m; i += 32)
-        C.cache[s * C.m + i] = t[i * kTW + ((((j & 31) >> 2) ^ (i & 7)) << 2) + (j & 3)];
+        C.cache[s * C.m + i] = elem1<ET>(t, C.m, i, j & 31, C.sc1, C.sc2);
   }
 }
 
@@ -291,18 +360,19 @@ __device__ __forceinline__ void cache_fill_from_tile(const Ctx& C, const float* 
 // consecutive columns (chunk q = lane % 8) of rows i = 4t + lane / 8, summed
 // over the lanes of a chunk by shuffles; per-warp partials then summed over
 // warps in a fixed order.
+template <int ET>
 __device__ __forceinline__ void col_pass(Ctx& C, const float* v, bool fill_cache) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int RB = ((C.m + kNW - 1) / kNW + 3) & ~3;
   const int rlo = wid * RB, rhi = min(C.m, rlo + RB);
   const int q = lane & 7, ro = lane >> 3;
   for (int b = 0; b < C.ntile; ++b) {
-    const float* t = acquire_tile(C, b);
-    if (fill_cache) cache_fill_from_tile(C, t, b);
+    const unsigned char* t = acquire_tile(C, b);
+    if (fill_cache) cache_fill_from_tile<ET>(C, t, b);
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
     for (int i = rlo + ro; i < rhi; i += 4) {
-      const float4 a = *reinterpret_cast<const float4*>(t + i * kTW + ((q ^ (i & 7)) << 2));
+      const float4 a = load4<ET>(t, C.m, i, q, C.sc1, C.sc2);
       const float u = v[i];
       acc.x = fmaf(a.x, u, acc.x);
       acc.y = fmaf(a.y, u, acc.y);
@@ -339,7 +409,7 @@ __host__ __device__ inline int w_chunks(int m) { return (w_row_iters(m) + 7) / 8
 // warp); in a tile, lane (ro = lane / 8, q = lane % 8) holds U for the tile's
 // columns 4q..4q+3 in registers and accumulates rows w*RB + 4t + ro over all
 // tiles; the 8 lanes of a row are summed by shuffles at the end.
-template <int R>
+template <int R, int ET>
 __device__ __forceinline__ void w_pass(Ctx& C, float* dst) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int q = lane & 7, ro = lane >> 3;
@@ -352,8 +422,8 @@ __device__ __forceinline__ void w_pass(Ctx& C, float* dst) {
 #pragma unroll
       for (int l = 0; l < R; ++l) acc[t][l] = 0.f;
     for (int b = 0; b < C.ntile; ++b) {
-      const float* tl = acquire_tile(C, b);
-      if (ch == 0) cache_fill_from_tile(C, tl, b);
+      const unsigned char* tl = acquire_tile(C, b);
+      if (ch == 0) cache_fill_from_tile<ET>(C, tl, b);
       float u[4 * R];
       const float4* u4 = reinterpret_cast<const float4*>(C.Us + (b * kTW + 4 * q) * R);
 #pragma unroll
@@ -365,7 +435,7 @@ __device__ __forceinline__ void w_pass(Ctx& C, float* dst) {
       for (int t = 0; t < 8; ++t) {
         const int i = wid * RB + 4 * (ch * 8 + t) + ro;
         if (ch * 8 + t < nri && i < C.m) {
-          const float4 a = *reinterpret_cast<const float4*>(tl + i * kTW + ((q ^ (i & 7)) << 2));
+          const float4 a = load4<ET>(tl, C.m, i, q, C.sc1, C.sc2);
 #pragma unroll
           for (int l = 0; l < R; ++l) {
             float s = acc[t][l];
@@ -395,20 +465,22 @@ __device__ __forceinline__ void w_pass(Ctx& C, float* dst) {
 }
 
 // column e of the local support: A(i, sup_j[e])
+template <int ET>
 __device__ __forceinline__ float support_elem(const Ctx& C, int e, int i) {
-  if (C.Asl) return C.Asl[elem_off(C.m, i, C.sup_j[e])];
+  if (C.Asl) return elem1<ET>(C.Asl, C.m, i, C.sup_j[e], C.sc1, C.sc2);
   const int s = C.sup_slot[e];
   if (s >= 0) return C.cache[s * C.m + i];
-  return __ldg(C.Ag + elem_off(C.m, i, C.sup_j[e]));
+  return elem1<ET>(C.Ag, C.m, i, C.sup_j[e], C.sc1, C.sc2);
 }
 
 // out[i] = sum_e coef[e] A(i, sup_j[e]) over the local support (partial of
 // the cluster sum), in entry order.
+template <int ET>
 __device__ __forceinline__ void gather(const Ctx& C, const float* coef, float* out) {
   const int nl = *C.nloc;
   for (int i = threadIdx.x; i < C.m; i += kNT) {
     float s = 0.f;
-    for (int e = 0; e < nl; ++e) s = fmaf(support_elem(C, e, i), coef[e], s);
+    for (int e = 0; e < nl; ++e) s = fmaf(support_elem<ET>(C, e, i), coef[e], s);
     out[i] = s;
   }
 }
@@ -416,6 +488,7 @@ __device__ __forceinline__ void gather(const Ctx& C, const float* coef, float* o
 // Give every local support entry a cache slot: entries whose column is
 // already cached keep it; the others take free slots and are loaded from the
 // slab in global memory (slots run out -> entry read from global when used).
+template <int ET>
 __device__ __forceinline__ void cache_assign_load(const Ctx& C) {
   if (C.Asl || C.nc == 0) return;
   const int nl = *C.nloc;
@@ -442,7 +515,7 @@ __device__ __forceinline__ void cache_assign_load(const Ctx& C) {
   for (int t = threadIdx.x; t < C.nc * C.m; t += kNT) {
     const int s = t / C.m, i = t - s * C.m;
     const int cc = C.cache_col[s];
-    if (cc <= -2) C.cache[s * C.m + i] = __ldg(C.Ag + elem_off(C.m, i, -2 - cc));
+    if (cc <= -2) C.cache[s * C.m + i] = elem1<ET>(C.Ag, C.m, i, -2 - cc, C.sc1, C.sc2);
   }
   csync();
   if (threadIdx.x == 0)
@@ -585,13 +658,13 @@ __device__ __forceinline__ void factor_gram(const Ctx& C) {
 // A s over the cluster with the local support values; with_gram also carries
 // the FP64 partial Gram of this CTA's row range and factors it.  A s -> dv;
 // every CTA's local support count -> cn[].
-template <int R>
+template <int R, int ET>
 __device__ __forceinline__ void exchange_As(Ctx& C, int& ex, bool with_gram) {
   unsigned char* x = xslot(C, ex);
   float* xa = reinterpret_cast<float*>(x);
   double* xgram = reinterpret_cast<double*>(x + a16(static_cast<size_t>(C.m) * 4));
   int* xcnt = reinterpret_cast<int*>(x + a16(static_cast<size_t>(C.m) * 4) + kMaxR * kMaxR * 8);
-  gather(C, C.sup_v, xa);
+  gather<ET>(C, C.sup_v, xa);
   if (with_gram) {
     // FP64 Gram of this CTA's row range: warp w takes entries t = w, w+8, ...
     // of the lower triangle; lanes stride the rows; fixed-order warp sum.
@@ -763,6 +836,7 @@ __device__ __forceinline__ int local_topk_support(Ctx& C) {
   return K;
 }
 
+template <int ET>
 __device__ __forceinline__ void hard_threshold(Ctx& C, int& ex, bool keep_values) {
   const int rho = C.rho;
   int K = local_topk_support(C);
@@ -817,7 +891,7 @@ __device__ __forceinline__ void hard_threshold(Ctx& C, int& ex, bool keep_values
     C.sl[j] = val;
   }
   csync();
-  cache_assign_load(C);
+  cache_assign_load<ET>(C);
 }
 
 // number of products over A_k of one column in each mode (the producer
@@ -829,7 +903,7 @@ __device__ __forceinline__ int passes_of(int mode, int tau, int rho, int m) {
   return mode == kModeInit ? t + 1 : t + 1 + wp;
 }
 
-template <int R, bool RES>
+template <int R, bool RES, int ET>
 __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const GaussLayout& L = a.L;
@@ -856,10 +930,13 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
   uint64_t* slab_bar = bars + 32;
   C.xbar = bars + 33;
   uint64_t* u_bar = bars + 35;
-  const size_t slab_elems = static_cast<size_t>(C.ntile) * C.m * kTW;
-  C.Ag = a.A + (static_cast<size_t>(C.k) * C.CS + C.c) * slab_elems;
-  C.Asl = RES ? reinterpret_cast<const float*>(smem + cv.slab) : nullptr;
-  C.ring = reinterpret_cast<const float*>(smem + cv.slab);
+  C.tbytes = tile_bytes(L);
+  const size_t slab_bytes = static_cast<size_t>(C.ntile) * C.tbytes;
+  C.Ag = reinterpret_cast<const unsigned char*>(a.A) + (static_cast<size_t>(C.k) * C.CS + C.c) * slab_bytes;
+  C.Asl = RES ? reinterpret_cast<const unsigned char*>(smem + cv.slab) : nullptr;
+  C.ring = reinterpret_cast<const unsigned char*>(smem + cv.slab);
+  C.sc1 = reinterpret_cast<const float*>(smem + cv.rsc);
+  C.sc2 = C.sc1 + L.m;
   C.Us = reinterpret_cast<float*>(smem + cv.Us);
   C.W = reinterpret_cast<float*>(smem + cv.W);
   C.yv = reinterpret_cast<float*>(smem + cv.yv);
@@ -923,7 +1000,7 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
       const char* src = reinterpret_cast<const char*>(C.Ag);
       char* dst = reinterpret_cast<char*>(smem + cv.slab);
       if (RES) {
-        const size_t bytes = slab_elems * 4;
+        const size_t bytes = slab_bytes;
         mbar_arrive_expect_tx(slab_bar, static_cast<unsigned>(bytes));
         for (size_t off = 0; off < bytes; off += 32768) {
           const size_t rem = bytes - off;
@@ -952,6 +1029,14 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
 
   // ---- consumers: small operands -------------------------------------------
   for (int i = tid; i < m; i += kNT) C.yv[i] = a.y[static_cast<size_t>(k) * m + i];
+  if (ET >= 2) {
+    float* scw = reinterpret_cast<float*>(smem + cv.rsc);
+    const int per = (ET == 3) ? 2 : 1;
+    for (int i = tid; i < m; i += kNT) {
+      scw[i] = a.rscale[(static_cast<size_t>(k) * m + i) * per];
+      scw[m + i] = (ET == 3) ? a.rscale[(static_cast<size_t>(k) * m + i) * per + 1] : 0.f;
+    }
+  }
   for (int j = tid; j < L.ns; j += kNT) C.sl[j] = 0.f;
   for (int s = tid; s <= C.nc; s += kNT) C.cache_col[s] = -1;
   if (tid == 0) {
@@ -987,7 +1072,7 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
   bool need_gram = false;
   if (project) {
     float* xw = reinterpret_cast<float*>(xslot(C, ex));
-    w_pass<R>(C, C.CS > 1 ? xw : C.W);
+    w_pass<R, ET>(C, C.CS > 1 ? xw : C.W);
     if (C.CS > 1) {
       xchg_publish_wait(C, ex);
       for (int t = tid; t < m * R; t += kNT) {
@@ -1001,7 +1086,7 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
   }
   if (tid == 0) C.cache_col[C.nc] = 0;  // W pass filled the slots (no-op if no W pass)
   csync();
-  if (!project) cache_assign_load(C);  // no W pass streamed: load the slots directly
+  if (!project) cache_assign_load<ET>(C);  // no W pass streamed: load the slots directly
   tr.mark(1);
 
   // ----------------------------------------------------- IHT (Alg. 2) ----
@@ -1014,7 +1099,7 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
       for (int i = tid; i < m; i += kNT) C.dv[i] = -C.yv[i];
       csync();
     } else {
-      exchange_As<R>(C, ex, need_gram);
+      exchange_As<R, ET>(C, ex, need_gram);
       need_gram = false;
       for (int i = tid; i < m; i += kNT) C.dv[i] -= C.yv[i];
       csync();
@@ -1022,12 +1107,12 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
       if (project) proj<R>(C, C.dv);
       tr.mark(3);
     }
-    col_pass(C, C.dv, false);  // g = A^T u  (= M^T (M s - z): P_perp is a projector)
+    col_pass<ET>(C, C.dv, false);  // g = A^T u  (= M^T (M s - z): P_perp is a projector)
     tr.mark(4);
     if (zero_start) {
       for (int j = tid; j < C.nsc; j += kNT) C.vv[j] = C.gs[j];
       csync();
-      hard_threshold(C, ex, false);  // support G of the zero start
+      hard_threshold<ET>(C, ex, false);  // support G of the zero start
     }
     // ||g_G||^2 and A g_G on the support, then mu
     unsigned char* x = xslot(C, ex);
@@ -1041,7 +1126,7 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
       for (int e = 0; e < nl; ++e) s = dfma(static_cast<double>(C.vv[e]), C.vv[e], s);
       *xnum = s;
     }
-    gather(C, C.vv, xg);
+    gather<ET>(C, C.vv, xg);
     xchg_publish_wait(C, ex);
     reduce_m(C, xg, C.ev);
     double num = 0.0;
@@ -1064,13 +1149,13 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
     const float muf = static_cast<float>(mu);
     for (int j = tid; j < C.nsc; j += kNT) C.vv[j] = fmaf(-muf, C.gs[j], C.sl[j]);
     csync();
-    hard_threshold(C, ex, true);
+    hard_threshold<ET>(C, ex, true);
     tr.mark(7);
   }
   for (; it < tau; ++it) drain_pass(C);  // products the stopped IHT no longer needs
 
   // ------------------------------------------------------ final stage -----
-  exchange_As<R>(C, ex, need_gram);  // A s with the final support
+  exchange_As<R, ET>(C, ex, need_gram);  // A s with the final support
   for (int i = tid; i < m; i += kNT) C.dv[i] = C.yv[i] - C.dv[i];  // y - A s
   csync();
   tr.mark(8);
@@ -1090,7 +1175,7 @@ __global__ void __launch_bounds__(kThreadsAll, 2) sweep_kernel(const SweepArgs a
   }
   tr.mark(9);
   if (a.mode != kModeLS) {
-    col_pass(C, a.mode == kModeInit ? C.dv : C.ev, false);
+    col_pass<ET>(C, a.mode == kModeInit ? C.dv : C.ev, false);
     tr.mark(10);
     float* Hk = a.H + static_cast<size_t>(k) * C.n + C.j0;
     for (int j = tid; j < C.nsc; j += kNT) Hk[j] = C.gs[j];
