@@ -85,6 +85,14 @@ typedef struct {
   int32_t slab_mode;        /* Gaussian sweep: 0 auto, 1 slab resident in shared
                                memory, 2 slab streamed through a tile ring   */
   int32_t stages;           /* tile stages of the streamed ring (0 -> auto)    */
+  int32_t engine;           /* Gaussian sweep engine: 0 auto, 1 one thread-block
+                               cluster per column, 2 persistent task engine
+                               (passes over A_k split into tasks, columns
+                               in flight share the GPU)                      */
+  int32_t inflight;         /* task engine: columns in flight (0 -> all q)    */
+  int32_t task_kib;         /* task engine: A_k bytes per task in KiB (0 -> 256) */
+  int32_t ctas_per_sm;      /* task engine: resident CTAs per SM (0 -> 2, or 1
+                               when two do not fit; 3 allowed for r <= 6)    */
 } lrs_options;
 
 /* Create a solver for one problem (Section I-A sizes).
@@ -225,9 +233,14 @@ const char* lrs_noalloc_last_error(void);
  * tracing aid).  out receives q x 12 counters, column-major by column k:
  * setup, W = A U, A s exchange, projection of u, column product (IHT),
  * A g_G exchange, projection and norm of M g_G, HardThreshold, final A s,
- * LS and residual, final column product, output writes.  len is the capacity
- * of out in elements.  Counters restart at zero.  Errors: LRS_ERR_ARG,
- * LRS_ERR_STATE (no trace buffer), LRS_ERR_CUDA. */
+ * LS and residual, final column product, output writes.  With the task
+ * engine (engine = 2) out receives 15 launch-wide counters instead (cycles
+ * summed over CTAs): waiting for a task, in W tasks, in A^T tasks, waiting
+ * for pieces inside tasks, in the small steps after W / IHT / final passes,
+ * producer waiting for a ticket, the numbers of tasks and small steps, then
+ * the IHT step's parts: loads, mu, HardThreshold, next residual, publish.
+ * len is the capacity of out in elements.  Counters restart at zero.
+ * Errors: LRS_ERR_ARG, LRS_ERR_STATE (no trace buffer), LRS_ERR_CUDA. */
 lrs_status lrs_sweep_trace(lrs_t h, uint64_t* out, int64_t len);
 
 /* Write a one-line description of the handle's launch shape (operator,

@@ -150,7 +150,7 @@ def densify(idx, vals, n):
     return S
 
 
-def iht(z, M, MH, rho, tau, s0, mu_rule="support", idx0=None):
+def iht(z, M, MH, rho, tau, s0, mu_rule="support", idx0=None, perturb=None):
     """Algorithm 2 (IHT), batched over columns.
 
     z: (K, m); M(s) -> (K, m) and MH(u) -> (K, n) apply M_k and M_k^H;
@@ -161,6 +161,10 @@ def iht(z, M, MH, rho, tau, s0, mu_rule="support", idx0=None):
     Returns (s (K, n), support (K, rho) ascending, margin (K,)) where margin is
     the smallest HardThreshold margin of the column over the sweeps (the gap
     that any arithmetic must resolve to reproduce the supports).
+    perturb: None, or a function applied to v = s - mu g before each
+    HardThreshold.  It is a test aid only (a relative perturbation of
+    rounding size shows whether a column's sweeps amplify rounding); every
+    plain run leaves it None.
     """
     s = np.array(s0, copy=True)
     K, n = s.shape
@@ -187,6 +191,8 @@ def iht(z, M, MH, rho, tau, s0, mu_rule="support", idx0=None):
         else:
             mu[active] = num[active] / den[active]
         v = s - mu[:, None] * g
+        if perturb is not None:
+            v = perturb(v)
         idx, vals, mg = hard_threshold(v, rho)
         s_new = densify(idx, vals, n)
         s[active] = s_new[active]
@@ -261,12 +267,14 @@ class OracleLog:
     init_sv: np.ndarray = None
 
 
-def init_alg1(op, Y, r, rho, tau0=10, mu_rule="support"):
-    """Algorithm 1, Initialization: IHT(y_k, A_k, rho, tau0, 0); L0; U0; b_k."""
+def init_alg1(op, Y, r, rho, tau0=10, mu_rule="support", perturb=None):
+    """Algorithm 1, Initialization: IHT(y_k, A_k, rho, tau0, 0); L0; U0; b_k.
+    perturb: see `iht` (test aid, None in plain runs)."""
     q, n = op.q, op.n
     dt = np.complex128 if op.complex else np.float64
     Y = np.asarray(Y, dtype=dt)
-    S, S_idx, margin = iht(Y, op.A, op.AH, rho, tau0, np.zeros((q, n), dtype=dt), mu_rule)
+    S, S_idx, margin = iht(Y, op.A, op.AH, rho, tau0, np.zeros((q, n), dtype=dt), mu_rule,
+                           perturb=perturb)
     L0 = op.AH(Y - op.A(S)).T               # n x q, column k = A_k^H (y_k - A_k s_k)
     U0, sv = top_r_left(L0, r)
     W = op.AU(U0)
@@ -274,7 +282,8 @@ def init_alg1(op, Y, r, rho, tau0=10, mu_rule="support"):
     return OracleState(U=U0, B=B, S=S, S_idx=S_idx), L0, sv, margin
 
 
-def iterate_alg1(op, Y, st, rho, tau=3, c_eta=0.14, mu_rule="support", chunk=None):
+def iterate_alg1(op, Y, st, rho, tau=3, c_eta=0.14, mu_rule="support", chunk=None,
+                 perturb=None):
     """One GDmin iteration of Algorithm 1 (t = st.t + 1), in place on `st`.
 
     z_k = P_perp y_k, M_k = P_perp A_k (explicit matrices for the Gaussian
@@ -282,6 +291,7 @@ def iterate_alg1(op, Y, st, rho, tau=3, c_eta=0.14, mu_rule="support", chunk=Non
     s_k = IHT(z_k, M_k, rho, tau, s_k); b_k = (A_k U)^dagger (y_k - A_k s_k);
     grad = sum_k A_k^H (A_k(U b_k + s_k) - y_k) b_k^H; eta at t = 1;
     U <- QR(U - eta grad).  Returns the per-column margins of the last HT.
+    perturb: see `iht` (test aid, None in plain runs).
     """
     q, n = op.q, op.n
     dt = np.complex128 if op.complex else np.float64
@@ -309,7 +319,7 @@ def iterate_alg1(op, Y, st, rho, tau=3, c_eta=0.14, mu_rule="support", chunk=Non
             def MH(u, opc=opc, W=W, Wp=Wp):
                 Pu = u - np.einsum("kmr,kr->km", W, np.einsum("krm,km->kr", Wp, u))
                 return opc.AH(Pu)
-        S_c, I_c, mg = iht(z, M, MH, rho, tau, st.S[ks], mu_rule, st.S_idx[ks])
+        S_c, I_c, mg = iht(z, M, MH, rho, tau, st.S[ks], mu_rule, st.S_idx[ks], perturb)
         st.S[ks] = S_c
         st.S_idx[ks] = I_c
         margins[ks] = mg

@@ -103,13 +103,14 @@ def corrected_measurements(A, At, Y, X):
 
 
 def run_defect_corrected(A, At, Y, r, rho, T, refine_every, Xstar=None, keep=(), tau0=10,
-                         tau=3, c_eta=0.14):
+                         tau=3, c_eta=0.14, perturb=None):
     """Algorithm 1 on the stored form Ã with defect correction: the
     initialisation runs on (Ã, y); iteration t + 1 runs on (Ã, ỹ) with ỹ
     recomputed from the iterate X_t when t is 0 or a multiple of
-    refine_every.  Logs as `run_alg1` (err against Xstar every t)."""
+    refine_every.  Logs as `run_alg1` (err against Xstar every t).
+    perturb: see altgdmin_lrs.iht (test aid, None in plain runs)."""
     opt = O.GaussianOperator(At)
-    st, _, sv, m0 = O.init_alg1(opt, Y, r, rho, tau0)
+    st, _, sv, m0 = O.init_alg1(opt, Y, r, rho, tau0, perturb=perturb)
     log = O.OracleLog()
     log.init_sv = sv
 
@@ -132,7 +133,7 @@ def run_defect_corrected(A, At, Y, r, rho, T, refine_every, Xstar=None, keep=(),
     for t in range(T):
         if t % refine_every == 0:
             Yc = corrected_measurements(A, At, Y, st.U @ st.B + st.S.T)
-        mg, _ = O.iterate_alg1(opt, Yc, st, rho, tau, c_eta)
+        mg, _ = O.iterate_alg1(opt, Yc, st, rho, tau, c_eta, perturb=perturb)
         record(st.t, mg)
     log.eta = st.eta
     return st, log

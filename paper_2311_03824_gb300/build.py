@@ -51,7 +51,7 @@ def build(force=False, verbose=False):
             print(res.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(os.cpu_count() or 8, len(srcs)))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp"
     cmd = [nv, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]

@@ -93,6 +93,23 @@ struct lrs_ctx {
   int nblk = 0;
   int power_iters_done = 0;
   FourierSolver* F = nullptr;  // DFT2D_MASK operator
+  // persistent task engine (engine == 2)
+  int engine = 1;
+  TaskShape tshape{};
+  TaskProblem tp[3]{};               // per sweep mode (INIT, LS, ITER)
+  TaskProblem* dtp = nullptr;        // device copies [3]
+  unsigned long long* dseed = nullptr;  // [3][F * first-pass tasks]
+  int n_seed[3] = {0, 0, 0};
+  size_t seed_stride = 0;
+  int total[3] = {0, 0, 0};
+  int tF = 0;                        // columns in flight
+  int trp = 0;                       // rows per A^T piece
+  float *tWk = nullptr, *tWp = nullptr, *tu = nullptr, *tg = nullptr, *tsupv = nullptr;
+  double* tGi = nullptr;
+  int *tsupj = nullptr, *tnsup = nullptr, *tcnt = nullptr, *tstop = nullptr, *tseq = nullptr,
+      *tctr = nullptr;
+  unsigned long long* ttasks = nullptr;
+  unsigned long long* tprof = nullptr;  // kTaskProf counters (profile = 2)
   // graph of one steady-state iteration
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -199,6 +216,23 @@ lrs_status check_device_error(lrs_ctx* h, const char* where) {
 }
 
 lrs_status launch_sweep(lrs_ctx* h, int mode, int tau) {
+  if (h->engine == 2) {
+    TaskQueue Q{};
+    Q.tasks = h->ttasks;
+    Q.seq = h->tseq;
+    Q.ctr = h->tctr;
+    Q.total = h->total[mode];
+    Q.ncols = static_cast<int>(h->q);
+    Q.F = h->tF;
+    Q.nprob = 1;
+    Q.probs = h->dtp + mode;
+    Q.prof = (h->opt.profile == 2 && mode == kModeIter) ? h->tprof : nullptr;
+    CUDA_TRY(task_launch_seeded(Q, h->dseed + static_cast<size_t>(mode) * h->seed_stride,
+                                h->n_seed[mode], h->tcnt, sweep_rpad(h->r), h->L.et, h->tshape,
+                                h->L.m, h->L.ns, h->rho, h->stream));
+    (void)tau;
+    return LRS_OK;
+  }
   SweepArgs a{};
   a.L = h->L;
   a.mode = mode;
@@ -340,10 +374,131 @@ void free_all(lrs_ctx* h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   h->gexec = nullptr;
   h->graph = nullptr;
+  void* ps2[] = {h->dtp, h->dseed, h->tWk, h->tWp, h->tu, h->tg, h->tsupv, h->tGi, h->tsupj,
+                 h->tnsup, h->tcnt, h->tstop, h->tseq, h->tctr, h->ttasks, h->tprof};
+  for (void* p : ps2)
+    if (p) cudaFree(p);
   void* ps[] = {h->A, h->y, h->Aex, h->rscale, h->ycorr, h->U, h->Upad, h->Bk, h->S_idx, h->S_val, h->H, h->grad, h->Z,
                 h->U2, h->P, h->part, h->small, h->eta, h->err, h->Xref, h->errpart, h->trace};
   for (void* p : ps)
     if (p) cudaFree(p);
+}
+
+// Task engine shapes: task sizes, ring stages (two CTAs per SM when they
+// fit), columns in flight.  False when no shape fits shared memory.
+bool plan_task_engine(lrs_ctx* h, int nsm) {
+  const int R = sweep_rpad(h->r), et = h->L.et;
+  const size_t task_bytes = static_cast<size_t>(h->opt.task_kib > 0 ? h->opt.task_kib : 256) * 1024;
+  // piece height from the shared-memory budget: two CTAs per SM if 8 rows fit
+  const size_t fixed = task_smem_bytes(R, et, h->L.m, h->L.ns, h->rho, 0, 0);
+  // two CTAs per SM by default (three, which the registers allow for r <= 6,
+  // only on request: their pieces get too short), else one
+  const size_t optin = static_cast<size_t>(max_smem_optin());
+  const int cps_max = (R <= 6 && h->opt.ctas_per_sm == 3) ? 3 : 2;
+  int rp = 0, cps = 0;
+  for (int c = cps_max; c >= 1 && !rp; --c) {
+    if (h->opt.ctas_per_sm > 0 && c != h->opt.ctas_per_sm) continue;
+    const size_t budget = c == 1 ? optin : (228 * 1024) / c - 1024;
+    if (budget <= fixed + 64) continue;
+    const size_t per_stage = (budget - fixed) / kTaskStages;
+    const long cap = static_cast<long>(per_stage) - static_cast<long>(kTileCols) * R * 4 - 16;
+    if (cap <= 0) continue;
+    rp = task_rows_per_piece(et, h->L.m, static_cast<int>(cap));
+    cps = c;
+  }
+  if (!rp) return false;
+  TaskProblem P{};
+  P.L = h->L;
+  P.mode = kModeIter;
+  P.tau_eff = h->rho > 0 ? h->opt.tau : 0;
+  task_plan(P, R, task_bytes, rp);
+  if (P.nrc > kMaxTaskPieces) return false;  // rows too tall for one A^T task
+  const int pbytes = rp * kTileCols * elem_bytes(et);
+  h->tshape.stages = kTaskStages;
+  h->tshape.piece_bytes = pbytes;
+  h->tshape.smem = task_smem_bytes(R, et, h->L.m, h->L.ns, h->rho, kTaskStages, pbytes);
+  h->trp = rp;
+  const int grid = cps * nsm;
+  // columns in flight: all of them unless asked otherwise (the small steps
+  // of a column are latency-bound, so the more columns advance at once the
+  // better the grid stays busy; measured on the n=1000, q=1000, m=150 case)
+  (void)grid;
+  const int F = h->opt.inflight > 0 ? h->opt.inflight : static_cast<int>(h->q);
+  h->tF = static_cast<int>(std::min<int64_t>(F, h->q));
+  return true;
+}
+
+// Scratch, queue, problem tables (one per sweep mode) and seeds.
+lrs_status alloc_task_engine(lrs_ctx* h) {
+  const int R = sweep_rpad(h->r), m = static_cast<int>(h->m);
+  const size_t q = static_cast<size_t>(h->q), ns = h->L.ns, rho1 = std::max(1, h->rho);
+  const size_t task_bytes = static_cast<size_t>(h->opt.task_kib > 0 ? h->opt.task_kib : 256) * 1024;
+  TaskProblem base{};
+  base.L = h->L;
+  task_plan(base, R, task_bytes, h->trp);
+  lrs_status st = LRS_OK;
+  if ((st = dalloc(&h->tWk, q * m * R)) || (st = dalloc(&h->tWp, q * base.ncw * m * R)) ||
+      (st = dalloc(&h->tGi, q * 16 * 16)) || (st = dalloc(&h->tu, q * m)) ||
+      (st = dalloc(&h->tg, q * ns)) || (st = dalloc(&h->tsupj, q * rho1)) ||
+      (st = dalloc(&h->tsupv, q * rho1)) || (st = dalloc(&h->tnsup, q)) ||
+      (st = dalloc(&h->tcnt, q)) || (st = dalloc(&h->tstop, q)) || (st = dalloc(&h->tctr, 4)) ||
+      (st = dalloc(&h->dtp, 3)) || (st = dalloc(&h->tprof, 16)))
+    return st;
+  CUDA_TRY(cudaMemset(h->tprof, 0, 16 * sizeof(unsigned long long)));
+  int max_total = 0, max_seed = 0;
+  for (int mode = 0; mode < 3; ++mode) {
+    TaskProblem& P = h->tp[mode];
+    P = base;
+    P.mode = mode;
+    P.tau_eff = h->rho == 0 ? 0 : (mode == kModeInit ? h->opt.tau0 : mode == kModeIter ? h->opt.tau : 0);
+    task_plan(P, R, task_bytes, h->trp);
+    P.A = h->A;
+    P.rscale = h->rscale;
+    P.y = (mode == kModeIter && h->L.et != 0) ? h->ycorr : h->y;
+    P.Upad = h->Upad;
+    P.S_idx = h->S_idx;
+    P.S_val = h->S_val;
+    P.B = h->Bk;
+    P.H = h->H;
+    P.err = h->err;
+    P.Wk = h->tWk;
+    P.Wp = h->tWp;
+    P.Gi = h->tGi;
+    P.uvec = h->tu;
+    P.g = h->tg;
+    P.supj = h->tsupj;
+    P.supv = h->tsupv;
+    P.nsup = h->tnsup;
+    P.cnt = h->tcnt;
+    P.stop = h->tstop;
+    P.col0 = 0;
+    const int64_t tot = static_cast<int64_t>(P.tasks_per_col) * h->q;
+    if (tot >= (int64_t(1) << 31)) return fail(LRS_ERR_UNSUPPORTED, "task engine: too many tasks");
+    h->total[mode] = static_cast<int>(tot);
+    h->n_seed[mode] = h->tF * phase_tasks(P, 0);
+    max_total = std::max(max_total, h->total[mode]);
+    max_seed = std::max(max_seed, h->n_seed[mode]);
+  }
+  h->seed_stride = static_cast<size_t>(max_seed);
+  if ((st = dalloc(&h->ttasks, static_cast<size_t>(max_total))) ||
+      (st = dalloc(&h->tseq, static_cast<size_t>(max_total))) ||
+      (st = dalloc(&h->dseed, 3 * h->seed_stride)))
+    return st;
+  std::vector<unsigned long long> seed(3 * h->seed_stride, 0ull);
+  for (int mode = 0; mode < 3; ++mode) {
+    const TaskProblem& P = h->tp[mode];
+    const int n0 = phase_tasks(P, 0);
+    for (int c = 0; c < h->tF; ++c)
+      for (int i = 0; i < n0; ++i)
+        seed[mode * h->seed_stride + static_cast<size_t>(c) * n0 + i] =
+            tdesc(c, 0, phase_type(P, 0), 0, i);
+  }
+  CUDA_TRY(cudaMemcpy(h->dseed, seed.data(), seed.size() * 8, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(h->dtp, h->tp, sizeof(h->tp), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemset(h->tcnt, 0, q * sizeof(int)));
+  CUDA_TRY(cudaMemset(h->tnsup, 0, q * sizeof(int)));
+  CUDA_TRY(cudaMemset(h->tstop, 0, q * sizeof(int)));
+  return LRS_OK;
 }
 
 }  // namespace
@@ -426,19 +581,36 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
   h->kind = kind;
   h->opt = o;
   h->stream = static_cast<cudaStream_t>(o.stream);
-  if (m > 512) {
-    delete h;
-    return fail(LRS_ERR_UNSUPPORTED, "lrs_create: the Gaussian sweep handles m <= 512");
-  }
-  choose_layout(h);
-  if (!shape_valid(h, h->L) || sweep_smem_bytes(h->L, h->resident, 0) > static_cast<size_t>(max_smem_optin())) {
-    delete h;
-    return fail(LRS_ERR_ARG, "lrs_create: no sweep shape fits (cluster/slab options)");
-  }
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  h->nblk = std::max(1, std::min<int>(nsm > 0 ? nsm : 148, static_cast<int>((n + 63) / 64)));
+  if (nsm <= 0) nsm = 148;
+  // engine: the task engine unless the cluster sweep is asked for (or the
+  // task engine has no shape and the cluster sweep has one)
+  h->engine = o.engine == 1 ? 1 : 2;
+  if (h->engine == 2) {
+    h->L = gauss_shape(h, 1, 0);
+    if (!plan_task_engine(h, nsm)) {
+      if (o.engine == 2 || m > 512) {
+        delete h;
+        return fail(LRS_ERR_UNSUPPORTED, "lrs_create: no task-engine shape fits shared memory");
+      }
+      h->engine = 1;
+    }
+  }
+  if (h->engine == 1) {
+    if (m > 512) {
+      delete h;
+      return fail(LRS_ERR_UNSUPPORTED, "lrs_create: the cluster sweep handles m <= 512");
+    }
+    choose_layout(h);
+    if (!shape_valid(h, h->L) ||
+        sweep_smem_bytes(h->L, h->resident, 0) > static_cast<size_t>(max_smem_optin())) {
+      delete h;
+      return fail(LRS_ERR_ARG, "lrs_create: no sweep shape fits (cluster/slab options)");
+    }
+  }
+  h->nblk = std::max(1, std::min<int>(nsm, static_cast<int>((n + 63) / 64)));
   const size_t per_col = static_cast<size_t>(h->L.cs) * h->L.m * h->L.ns * elem_bytes(h->L.et);
   lrs_status st = LRS_OK;
   const size_t upad_n = static_cast<size_t>(h->L.cs) * h->L.ns * sweep_rpad(r);
@@ -455,7 +627,8 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
       (st = dalloc(&h->Z, size_t(n) * r)) || (st = dalloc(&h->U2, size_t(n) * r)) ||
       (st = dalloc(&h->P, size_t(q) * r)) || (st = dalloc(&h->part, size_t(h->nblk) * r * r)) ||
       (st = dalloc(&h->small, 4 * 16 * 16 + 64)) || (st = dalloc(&h->eta, 1)) ||
-      (st = dalloc(&h->err, 2)) || (st = dalloc(&h->errpart, 2 * size_t(q)))) {
+      (st = dalloc(&h->err, 2)) || (st = dalloc(&h->errpart, 2 * size_t(q))) ||
+      (h->engine == 2 && (st = alloc_task_engine(h)))) {
     std::string msg = g_last_error;
     free_all(h);
     delete h;
@@ -469,7 +642,8 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
     }
     cudaMemset(h->trace, 0, sizeof(unsigned long long) * size_t(q) * kTracePhases);
   }
-  cudaError_t e = sweep_prepare(h->L, kThreads);
+  cudaError_t e = h->engine == 1 ? sweep_prepare(h->L, kThreads)
+                                 : task_prepare(sweep_rpad(r), h->L.et, h->tshape.smem);
   if (e == cudaSuccess) e = cudaMemset(h->err, 0, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->Upad, 0, sizeof(float) * upad_n);
   if (e == cudaSuccess) e = cudaMemset(h->S_idx, 0, sizeof(int) * size_t(q) * std::max(1, h->rho));
@@ -479,10 +653,20 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
     delete h;
     return fail(LRS_ERR_CUDA, std::string("lrs_create: ") + cudaGetErrorString(e));
   }
-  if (sweep_max_active_clusters(h->L, h->resident, kThreads) <= 0) {
+  if (h->engine == 1 && sweep_max_active_clusters(h->L, h->resident, kThreads) <= 0) {
     free_all(h);
     delete h;
     return fail(LRS_ERR_UNSUPPORTED, "lrs_create: sweep kernel shape cannot be scheduled");
+  }
+  if (h->engine == 2) {
+    const int cps = task_ctas_per_sm(sweep_rpad(r), h->L.et, h->tshape.smem);
+    if (cps <= 0) {
+      free_all(h);
+      delete h;
+      return fail(LRS_ERR_UNSUPPORTED, "lrs_create: task engine cannot be scheduled");
+    }
+    h->tshape.ctas_per_sm = cps;
+    h->tshape.grid = cps * nsm;
   }
   *out = h;
   return LRS_OK;
@@ -788,6 +972,13 @@ lrs_status lrs_phase_times(lrs_t h, double* out4) {
 
 lrs_status lrs_sweep_trace(lrs_t h, uint64_t* out, int64_t len) {
   if (!h || !out || len < 0) return fail(LRS_ERR_ARG, "lrs_sweep_trace: bad argument");
+  if (h->engine == 2 && h->opt.profile == 2) {
+    const int64_t n = std::min<int64_t>(len, kTaskProf);
+    CUDA_TRY(cudaMemcpyAsync(out, h->tprof, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemsetAsync(h->tprof, 0, sizeof(uint64_t) * kTaskProf, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return LRS_OK;
+  }
   if (!h->trace) return fail(LRS_ERR_STATE, "lrs_sweep_trace: create the handle with profile = 2");
   const int64_t n = std::min<int64_t>(len, h->q * kTracePhases);
   CUDA_TRY(cudaMemcpyAsync(out, h->trace, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, h->stream));
@@ -803,10 +994,21 @@ lrs_status lrs_describe(lrs_t h, char* buf, int32_t len) {
              h->opt.nx, h->opt.ny);
     return LRS_OK;
   }
+  if (h->engine == 2) {
+    const TaskProblem& P = h->tp[kModeIter];
+    snprintf(buf, static_cast<size_t>(len),
+             "{\"op\": \"gaussian\", \"engine\": \"task\", \"grid\": %d, \"ctas_per_sm\": %d, "
+             "\"stages\": %d, \"piece_bytes\": %d, \"smem_per_cta\": %zu, \"inflight\": %d, "
+             "\"w_tasks\": %d, \"g_tasks\": %d, \"rows_per_piece\": %d, \"tiles_per_task\": %d, "
+             "\"a_dtype\": %d, \"refine_every\": %d}",
+             h->tshape.grid, h->tshape.ctas_per_sm, h->tshape.stages, h->tshape.piece_bytes,
+             h->tshape.smem, h->tF, P.nrb * P.ncw, P.ngb, P.rp, P.TB, h->L.et, h->opt.refine_every);
+    return LRS_OK;
+  }
   const size_t sm = sweep_smem_bytes(h->L, h->resident, kThreads);
   const int nc = sweep_max_active_clusters(h->L, h->resident, kThreads);
   snprintf(buf, static_cast<size_t>(len),
-           "{\"op\": \"%s\", \"cluster\": %d, \"ns\": %d, \"stages\": %d, \"resident\": %d, "
+           "{\"op\": \"%s\", \"engine\": \"cluster\", \"cluster\": %d, \"ns\": %d, \"stages\": %d, \"resident\": %d, "
            "\"smem_per_cta\": %zu, \"max_active_clusters\": %d, \"a_dtype\": %d, "
            "\"refine_every\": %d}",
            h->kind == LRS_OP_GAUSSIAN ? "gaussian" : "dft2d", h->L.cs, h->L.ns, h->L.stages,

