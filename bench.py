@@ -3,11 +3,16 @@
 A step is one GDmin iteration of Algorithm 1 over every column of one
 problem: the per-column sweep (A_k U, P_perp-projected IHT, LS for b_k,
 gradient terms), the column reduction of the gradient and the Cholesky-QR2
-of U.  The workload is the float32 Gaussian problem n=1000, q=1000, r=5,
-m=150, rho=10 (A_k resident in HBM, 600 MB > L2).  Inputs are synthetic and
-seeded (lrsgen).  One JSON line is printed by rank 0.
+of U.  The default workload is the float32 Gaussian problem n=1000, q=1000,
+r=5, m=150, rho=10 (A_k resident in HBM, 600 MB > L2).  Inputs are synthetic
+and seeded (lrsgen).  One JSON line is printed by rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c1|c2] [--a-dtype fp32|bf16|fp8_hi|fp8_hilo]
+
+--workload c2 measures the precision forms on the Gaussian problem n=4096,
+q=2048, r=10, m=512, rho=40 (A_k drawn on the device, 17.2 GB in float32):
+device-timed column-iterations/s and the final relative error against X*.
 """
 import argparse
 import json
@@ -23,13 +28,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(n=1000, q=1000, r=5, m=150, rho=10, seed=2)
+WORKLOAD_C2 = dict(n=4096, q=2048, r=10, m=512, rho=40, seed=3)
 METRIC = "column-iters/s"
+A_DTYPES = {"fp32": 0, "bf16": 1, "fp8_hi": 2, "fp8_hilo": 3}
+A_BYTES = {"fp32": 4.0, "bf16": 2.0, "fp8_hi": 1.0, "fp8_hilo": 2.0}
 
 
-def b_alg_per_col_iter(n, m, r, rho, a_bytes=4):
-    """Algorithmic HBM bytes of one column-iteration: A_k once, y_k, h_k write,
-    s_k (index + value) and b_k."""
-    return m * n * a_bytes + 4 * m + 4 * n + 8 * rho + 4 * r
+def b_alg_per_col_iter(n, m, r, rho, a_bytes=4, scales=0):
+    """Algorithmic HBM bytes of one column-iteration: A_k once (plus its row
+    scales for the FP8 forms), y_k, h_k write, s_k (index + value) and b_k."""
+    return m * n * a_bytes + 4 * m * scales + 4 * m + 4 * n + 8 * rho + 4 * r
 
 
 def load_peaks():
@@ -170,6 +178,7 @@ def run_ours(args):
     n, q, r, m, rho = cfg["n"], cfg["q"], cfg["r"], cfg["m"], cfg["rho"]
     stream = torch.cuda.Stream()
     s = L.Solver(n, m, q, r, rho, stream=stream, profile=1)
+    desc = L.lrs_describe(s.h)
     s.set_measurements(Y, A)
     s.init()
     s.iterate(args.warmup)
@@ -189,6 +198,8 @@ def run_ours(args):
         barrier()
     ms = e0.elapsed_time(e1)
     ph = L.lrs_phase_times(s.h)
+    X = s.X()
+    rel_err = float(np.linalg.norm(X - inst.Xstar) / np.linalg.norm(inst.Xstar))
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -229,22 +240,81 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": "gaussian n=1000 q=1000 r=5 m=150 rho=10 (float32 A_k, 600 MB)",
                        "l2": "inputs larger than L2 (A 600 MB)", "iterations_per_step": 1,
-                       "cluster": s.opts.cluster or "auto"},
+                       "engine": desc.get("engine"),
+                       "rel_err_after": {"iterations": args.warmup + args.steps, "rel_err": rel_err}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "sweep_kernel", "kernel_ms": sweep_ms,
-                         "bytes_per_launch": bytes_launch},
+                         "kernel": "task_kernel" if desc.get("engine") == "task" else "sweep_kernel",
+                         "kernel_ms": sweep_ms, "bytes_per_launch": bytes_launch},
             "phases_ms_per_step": {k: ph[k] / max(1, ph["iters"]) for k in ("sweep_ms", "grad_ms", "qr_ms")},
             "e2e": {"value": e2e_value, "unit": "column-iters/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "iterations": T_e2e,
                     "includes": "lrs_set_measurements(host) + lrs_init + lrs_iterate + lrs_get(host)"},
-            "gpu_launches": 7 * args.steps,
+            "gpu_launches": (8 if desc.get("engine") == "task" else 7) * args.steps,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_c2(args):
+    """Precision forms on the n=4096, q=2048, r=10, m=512, rho=40 problem."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2311_03824_gb300 import build
+    build.build()
+    from paper_2311_03824_gb300 import lrs as L
+    from lrsgen.device import DeviceGaussianInstance
+    cfg = dict(WORKLOAD_C2)
+    inst = DeviceGaussianInstance(**cfg)
+    n, q, r, m, rho = cfg["n"], cfg["q"], cfg["r"], cfg["m"], cfg["rho"]
+    stream = torch.cuda.Stream()
+    s = L.Solver(n, m, q, r, rho, stream=stream, profile=1, a_dtype=A_DTYPES[args.a_dtype])
+    desc = L.lrs_describe(s.h)
+    s.set_measurements(inst.Y, inst.A)
+    inst.free()
+    torch.cuda.empty_cache()
+    s.init()
+    s.iterate(args.warmup)
+    L.lrs_phase_times(s.h)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.iterate(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ph = L.lrs_phase_times(s.h)
+    X = s.X()
+    rel_err = float(np.linalg.norm(X - inst.Xstar) / np.linalg.norm(inst.Xstar))
+    s.close()
+    peak, peak_kind = load_peaks()
+    sweep_ms = ph["sweep_ms"] / max(1, ph["iters"])
+    bytes_launch = q * b_alg_per_col_iter(n, m, r, rho, A_BYTES[args.a_dtype],
+                                          {"fp8_hi": 1, "fp8_hilo": 2}.get(args.a_dtype, 0))
+    achieved = bytes_launch / (sweep_ms / 1000.0) / 1e9
+    line = {
+        "metric": METRIC, "value": q * args.steps / (ms / 1000.0), "unit": "column-iters/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16 storage, f32 compute", "fp8_hi": "e4m3 storage, f32 compute",
+                  "fp8_hilo": "e4m3 hi+lo storage, f32 compute"}[args.a_dtype],
+        "data": "synthetic (A_k drawn on the device by a seeded generator)",
+        "config": {"workload": "gaussian n=4096 q=2048 r=10 m=512 rho=40 (precision forms)",
+                   "a_dtype": args.a_dtype, "refine_every": 8, "engine": desc.get("engine"),
+                   "l2": "inputs larger than L2",
+                   "rel_err_after": {"iterations": args.warmup + args.steps, "rel_err": rel_err}},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "task_kernel", "kernel_ms": sweep_ms, "bytes_per_launch": bytes_launch},
+        "phases_ms_per_step": {k: ph[k] / max(1, ph["iters"]) for k in ("sweep_ms", "grad_ms", "qr_ms")},
+        "e2e": None, "gpu_launches": None, "clocks": clk.summary(), "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -256,11 +326,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-iters", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c1", choices=["c1", "c2"])
+    ap.add_argument("--a-dtype", default="fp32", choices=list(A_DTYPES))
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c2":
+        return run_c2(args)
     return run_ours(args)
 
 

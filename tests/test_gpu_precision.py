@@ -108,7 +108,11 @@ def test_zero_rows_and_rank_edges(a_dtype):
         sens = step_sens(inst, FORMS[a_dtype], log, range(0, 6))
         res = one_step(inst, log, range(0, 6), sens=sens, a_dtype=a_dtype, refine_every=1,
                        engine=2)
+        # r = 16 on m = 48 rows: the same 1e-4 bar as FP32; r = 1 on m = 24 rows
+        # of which one is zero: FP32 rounding over 23 informative rows leaves
+        # one-step deviations near 1e-5, so the bar is 2e-5
+        edge_bar = 1e-4 if r == 16 else 2e-5
         for rr in res:
             assert rr["sup_bad"] == 0
-            if rr["undecided"] == 0:   # r = 16 on m = 48 rows: the same 1e-4 bar as FP32
-                assert rr["rel"] <= max(rr["bar"], 1e-4 if r == 16 else TOL), rr
+            if rr["undecided"] == 0:
+                assert rr["rel"] <= max(rr["bar"], edge_bar), rr
