@@ -48,6 +48,51 @@ __global__ void __launch_bounds__(256) grad_kernel(int n, int q, int r,
   }
 }
 
+// Split form of the two column reductions above for many SMs: block (jb, ks)
+// sums rows k of its k-range (warps k = w mod 8) into out[ks][j][l]; the
+// finishing kernel adds the ks partials in index order (fixed order).
+template <typename T>
+__global__ void __launch_bounds__(256) kred_part_kernel(int n, int q, int r, int qc,
+                                                        const float* __restrict__ H,
+                                                        const T* __restrict__ Bk,
+                                                        T* __restrict__ out) {
+  __shared__ T part[8][kMaxR][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  const int k0 = blockIdx.y * qc, k1 = min(q, k0 + qc);
+  T acc[kMaxR];
+#pragma unroll
+  for (int l = 0; l < kMaxR; ++l) acc[l] = T(0);
+  if (j < n) {
+    for (int k = k0 + w; k < k1; k += 8) {
+      const T h = static_cast<T>(H[static_cast<size_t>(k) * n + j]);
+      const T* b = Bk + static_cast<size_t>(k) * r;
+#pragma unroll
+      for (int l = 0; l < kMaxR; ++l)
+        if (l < r) acc[l] = fma(h, b[l], acc[l]);
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < kMaxR; ++l) part[w][l][lane] = acc[l];
+  __syncthreads();
+  for (int t = threadIdx.x; t < 32 * r; t += blockDim.x) {
+    const int l = t / 32, jj = t - l * 32;
+    T sum = T(0);
+    for (int ww = 0; ww < 8; ++ww) sum += part[ww][l][jj];
+    const int jg = blockIdx.x * 32 + jj;
+    if (jg < n) out[(static_cast<size_t>(blockIdx.y) * n + jg) * r + l] = sum;
+  }
+}
+template <typename T>
+__global__ void kred_fin_kernel(int nr, int ks, const T* __restrict__ part, T* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nr) {
+    T sum = T(0);
+    for (int s = 0; s < ks; ++s) sum += part[static_cast<size_t>(s) * nr + t];
+    out[t] = sum;
+  }
+}
+
 // Partial FP64 Gram X^T X of the row range handled by this block (X n x r
 // row-major); optionally X is first formed as U - eta*G and stored.
 // part[blk][a*r+b] (a >= b filled).
@@ -411,7 +456,15 @@ cudaError_t dcholqr2(const GlobalWork& g, const double* Zin, double* Ztmp, doubl
 cudaError_t dsubspace_step(const GlobalWork& g, const float* H, const double* U, double* P,
                            double* Z, cudaStream_t s) {
   dproject_kernel<<<(g.q + 7) / 8, 256, 0, s>>>(g.n, g.q, g.r, H, U, P);
-  dgrad_kernel<<<(g.n + 31) / 32, 256, 0, s>>>(g.n, g.q, g.r, H, P, Z);
+  if (g.ks > 1 && g.dsplit) {
+    const int qc = (g.q + g.ks - 1) / g.ks;
+    kred_part_kernel<double><<<dim3((g.n + 31) / 32, g.ks), 256, 0, s>>>(g.n, g.q, g.r, qc, H, P,
+                                                                         g.dsplit);
+    const int nr = g.n * g.r;
+    kred_fin_kernel<double><<<(nr + 255) / 256, 256, 0, s>>>(nr, g.ks, g.dsplit, Z);
+  } else {
+    dgrad_kernel<<<(g.n + 31) / 32, 256, 0, s>>>(g.n, g.q, g.r, H, P, Z);
+  }
   return cudaGetLastError();
 }
 
@@ -434,7 +487,15 @@ cudaError_t subspace_change(const GlobalWork& g, const float* Uold, const float*
 }
 
 cudaError_t grad_reduce(const GlobalWork& g, const float* H, const float* Bk, cudaStream_t s) {
-  grad_kernel<<<(g.n + 31) / 32, 256, 0, s>>>(g.n, g.q, g.r, H, Bk, g.grad);
+  if (g.ks > 1 && g.gsplit) {
+    const int qc = (g.q + g.ks - 1) / g.ks;
+    kred_part_kernel<float><<<dim3((g.n + 31) / 32, g.ks), 256, 0, s>>>(g.n, g.q, g.r, qc, H, Bk,
+                                                                        g.gsplit);
+    const int nr = g.n * g.r;
+    kred_fin_kernel<float><<<(nr + 255) / 256, 256, 0, s>>>(nr, g.ks, g.gsplit, g.grad);
+  } else {
+    grad_kernel<<<(g.n + 31) / 32, 256, 0, s>>>(g.n, g.q, g.r, H, Bk, g.grad);
+  }
   return cudaGetLastError();
 }
 

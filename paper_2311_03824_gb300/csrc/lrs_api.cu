@@ -89,6 +89,9 @@ struct lrs_ctx {
   int* err = nullptr;      // {code, column}
   float* Xref = nullptr;   // q x n (error log)
   double* errpart = nullptr;
+  int ks = 1;                // k-splits of the column reductions
+  float* gsplit = nullptr;   // ks x n x r
+  double* dsplit = nullptr;  // ks x n x r
   unsigned long long* trace = nullptr;  // q x kTracePhases (profile = 2)
   int nblk = 0;
   int power_iters_done = 0;
@@ -133,6 +136,9 @@ GlobalWork gw(lrs_ctx* h) {
   g.nblk = h->nblk;
   g.Upad = h->Upad;
   g.rpad = sweep_rpad(h->r);
+  g.ks = h->ks;
+  g.gsplit = h->gsplit;
+  g.dsplit = h->dsplit;
   return g;
 }
 
@@ -378,7 +384,7 @@ void free_all(lrs_ctx* h) {
                  h->tnsup, h->tcnt, h->tstop, h->tseq, h->tctr, h->ttasks, h->tprof};
   for (void* p : ps2)
     if (p) cudaFree(p);
-  void* ps[] = {h->A, h->y, h->Aex, h->rscale, h->ycorr, h->U, h->Upad, h->Bk, h->S_idx, h->S_val, h->H, h->grad, h->Z,
+  void* ps[] = {h->gsplit, h->dsplit, h->A, h->y, h->Aex, h->rscale, h->ycorr, h->U, h->Upad, h->Bk, h->S_idx, h->S_val, h->H, h->grad, h->Z,
                 h->U2, h->P, h->part, h->small, h->eta, h->err, h->Xref, h->errpart, h->trace};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -426,6 +432,21 @@ bool plan_task_engine(lrs_ctx* h, int nsm) {
   const int F = h->opt.inflight > 0 ? h->opt.inflight : static_cast<int>(h->q);
   h->tF = static_cast<int>(std::min<int64_t>(F, h->q));
   return true;
+}
+
+// Column reductions (gradient, subspace step) split over k so that about
+// four blocks per SM work on them; FP32 and FP64 partial buffers.
+lrs_status alloc_split(lrs_ctx* h, int nsm) {
+  const int64_t jb = (h->n + 31) / 32;
+  int ks = static_cast<int>(std::max<int64_t>(1, (4 * nsm + jb - 1) / jb));
+  ks = std::min<int>(ks, 32);
+  ks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ks, h->q / 8)));
+  h->ks = ks;
+  if (ks <= 1) return LRS_OK;
+  lrs_status st = LRS_OK;
+  const size_t cnt = static_cast<size_t>(ks) * h->n * h->r;
+  if ((st = dalloc(&h->gsplit, cnt)) || (st = dalloc(&h->dsplit, cnt))) return st;
+  return LRS_OK;
 }
 
 // Scratch, queue, problem tables (one per sweep mode) and seeds.
@@ -628,7 +649,7 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
       (st = dalloc(&h->P, size_t(q) * r)) || (st = dalloc(&h->part, size_t(h->nblk) * r * r)) ||
       (st = dalloc(&h->small, 4 * 16 * 16 + 64)) || (st = dalloc(&h->eta, 1)) ||
       (st = dalloc(&h->err, 2)) || (st = dalloc(&h->errpart, 2 * size_t(q))) ||
-      (h->engine == 2 && (st = alloc_task_engine(h)))) {
+      (h->engine == 2 && (st = alloc_task_engine(h))) || (st = alloc_split(h, nsm))) {
     std::string msg = g_last_error;
     free_all(h);
     delete h;

@@ -212,6 +212,9 @@ struct GlobalWork {
   double* small;     // scratch: [0,r*r) Rinv1, [r*r,2r*r) Rinv2, [2r*r] eta, ...
   float* Z;          // n x r scratch (U - eta grad, Q1)
   int nblk;          // blocks of the row-parallel kernels
+  int ks = 1;        // k-splits of the column reductions (grad, subspace step)
+  float* gsplit = nullptr;   // ks x n x r FP32 partial sums (ks > 1)
+  double* dsplit = nullptr;  // ks x n x r FP64 partial sums (ks > 1)
 };
 cudaError_t grad_reduce(const GlobalWork& g, const float* H, const float* Bk, cudaStream_t s);
 cudaError_t eta_from_grad(const GlobalWork& g, double c_eta, double* eta_dev, cudaStream_t s);
