@@ -93,6 +93,9 @@ typedef struct {
   int32_t task_kib;         /* task engine: A_k bytes per task in KiB (0 -> 256) */
   int32_t ctas_per_sm;      /* task engine: resident CTAs per SM (0 -> 2, or 1
                                when two do not fit; 3 allowed for r <= 6)    */
+  int32_t autotune;         /* task engine: 1 = run lrs_autotune (2 trial
+                               iterations per shape) before the first
+                               iteration unless this shape is cached         */
 } lrs_options;
 
 /* Create a solver for one problem (Section I-A sizes).
@@ -192,6 +195,19 @@ lrs_status lrs_set_reference(lrs_t h, const void* Xref, int32_t mem_kind);
  * The counters restart at zero after the call.  Errors: LRS_ERR_ARG,
  * LRS_ERR_CUDA. */
 lrs_status lrs_phase_times(lrs_t h, double* out4);
+
+/* Autotuner of the task engine (the paper has no counterpart): from the
+ * current iterate, run trial_iters GDmin iterations
+ * with each candidate task shape (128 / 256 / 512 KiB of A_k per task x
+ * q, q/2 or 2 x grid columns in flight), restoring the iterate (U, B, S,
+ * eta, t and the corrected measurements) after each, keep the fastest and
+ * cache it for the process, keyed by (n, m, q, r, rho_max, a_dtype, grid):
+ * later handles of the same shape start with it.  report: NULL or a buffer
+ * of len bytes receiving a JSON summary of the trials.  State: INITIALISED
+ * or later (unchanged on return).  Errors: LRS_ERR_ARG, LRS_ERR_STATE,
+ * LRS_ERR_UNSUPPORTED (cluster engine or DFT operator), LRS_ERR_OOM,
+ * LRS_ERR_CUDA, LRS_ERR_NUMERICAL. */
+lrs_status lrs_autotune(lrs_t h, int32_t trial_iters, char* report, int32_t len);
 
 /* Orthonormalise the columns of Z by Cholesky-QR2 (the QR step of
  * Algorithm 1, U+ = QR(U - eta grad)): Q = Z R^{-1} with R the upper

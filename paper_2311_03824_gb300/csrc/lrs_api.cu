@@ -4,10 +4,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/lrs.h"
@@ -106,6 +110,10 @@ struct lrs_ctx {
   size_t seed_stride = 0;
   int total[3] = {0, 0, 0};
   int tF = 0;                        // columns in flight
+  int t_kib = 256;                   // KiB of A_k per task
+  int t_ncw_max = 1;                 // W chunks the scratch holds
+  int64_t t_total_max = 0;           // tasks the queue holds
+  int tuned = 0;                     // autotuner ran (or its cache was used)
   int trp = 0;                       // rows per A^T piece
   float *tWk = nullptr, *tWp = nullptr, *tu = nullptr, *tg = nullptr, *tsupv = nullptr;
   double* tGi = nullptr;
@@ -113,9 +121,10 @@ struct lrs_ctx {
       *tctr = nullptr;
   unsigned long long* ttasks = nullptr;
   unsigned long long* tprof = nullptr;  // kTaskProf counters (profile = 2)
-  // graph of one steady-state iteration
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
+  // graphs of one steady-state iteration: [0] plain, [1] with the refinement
+  // of the measurements (low-precision forms)
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   // phase timing (profile = 1): 4 events per iteration
   std::vector<cudaEvent_t> ev;
   double phase_ms[3] = {0, 0, 0};
@@ -376,10 +385,12 @@ lrs_status dalloc(T** p, size_t count) {
 void free_all(lrs_ctx* h) {
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   h->ev.clear();
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  if (h->graph) cudaGraphDestroy(h->graph);
-  h->gexec = nullptr;
-  h->graph = nullptr;
+  for (int g = 0; g < 2; ++g) {
+    if (h->gexec[g]) cudaGraphExecDestroy(h->gexec[g]);
+    if (h->graph[g]) cudaGraphDestroy(h->graph[g]);
+    h->gexec[g] = nullptr;
+    h->graph[g] = nullptr;
+  }
   void* ps2[] = {h->dtp, h->dseed, h->tWk, h->tWp, h->tu, h->tg, h->tsupv, h->tGi, h->tsupj,
                  h->tnsup, h->tcnt, h->tstop, h->tseq, h->tctr, h->ttasks, h->tprof};
   for (void* p : ps2)
@@ -388,6 +399,21 @@ void free_all(lrs_ctx* h) {
                 h->U2, h->P, h->part, h->small, h->eta, h->err, h->Xref, h->errpart, h->trace};
   for (void* p : ps)
     if (p) cudaFree(p);
+}
+
+// ---- autotuner: shapes per problem, cached for the process -----------------------
+struct TuneKey {
+  int64_t n, m, q;
+  int r, rho, et, grid;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(n, m, q, r, rho, et, grid) < std::tie(o.n, o.m, o.q, o.r, o.rho, o.et, o.grid);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;  // -> (KiB per task, columns in flight)
+
+TuneKey tune_key(const lrs_ctx* h) {
+  return TuneKey{h->n, h->m, h->q, h->r, h->rho, h->L.et, h->tshape.grid};
 }
 
 // Task engine shapes: task sizes, ring stages (two CTAs per SM when they
@@ -428,9 +454,19 @@ bool plan_task_engine(lrs_ctx* h, int nsm) {
   // columns in flight: all of them unless asked otherwise (the small steps
   // of a column are latency-bound, so the more columns advance at once the
   // better the grid stays busy; measured on the n=1000, q=1000, m=150 case)
-  (void)grid;
+  h->tshape.grid = grid;
   const int F = h->opt.inflight > 0 ? h->opt.inflight : static_cast<int>(h->q);
   h->tF = static_cast<int>(std::min<int64_t>(F, h->q));
+  h->t_kib = h->opt.task_kib > 0 ? h->opt.task_kib : 256;
+  if (h->opt.task_kib <= 0 && h->opt.inflight <= 0) {  // a shape the autotuner chose before
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(tune_key(h));
+    if (it != g_tune_cache.end()) {
+      h->t_kib = it->second.first;
+      h->tF = it->second.second;
+      h->tuned = 1;
+    }
+  }
   return true;
 }
 
@@ -449,30 +485,23 @@ lrs_status alloc_split(lrs_ctx* h, int nsm) {
   return LRS_OK;
 }
 
-// Scratch, queue, problem tables (one per sweep mode) and seeds.
-lrs_status alloc_task_engine(lrs_ctx* h) {
-  const int R = sweep_rpad(h->r), m = static_cast<int>(h->m);
-  const size_t q = static_cast<size_t>(h->q), ns = h->L.ns, rho1 = std::max(1, h->rho);
-  const size_t task_bytes = static_cast<size_t>(h->opt.task_kib > 0 ? h->opt.task_kib : 256) * 1024;
-  TaskProblem base{};
-  base.L = h->L;
-  task_plan(base, R, task_bytes, h->trp);
-  lrs_status st = LRS_OK;
-  if ((st = dalloc(&h->tWk, q * m * R)) || (st = dalloc(&h->tWp, q * base.ncw * m * R)) ||
-      (st = dalloc(&h->tGi, q * 16 * 16)) || (st = dalloc(&h->tu, q * m)) ||
-      (st = dalloc(&h->tg, q * ns)) || (st = dalloc(&h->tsupj, q * rho1)) ||
-      (st = dalloc(&h->tsupv, q * rho1)) || (st = dalloc(&h->tnsup, q)) ||
-      (st = dalloc(&h->tcnt, q)) || (st = dalloc(&h->tstop, q)) || (st = dalloc(&h->tctr, 4)) ||
-      (st = dalloc(&h->dtp, 3)) || (st = dalloc(&h->tprof, 16)))
-    return st;
-  CUDA_TRY(cudaMemset(h->tprof, 0, 16 * sizeof(unsigned long long)));
-  int max_total = 0, max_seed = 0;
+// Task sizes the autotuner tries (KiB of A_k per task).
+constexpr int kTuneKib[3] = {128, 256, 512};
+
+// Problem tables (one per sweep mode) and seeds for `task_kib` KiB per task
+// and F columns in flight, uploaded to the device.
+lrs_status plan_tables(lrs_ctx* h, int task_kib, int F) {
+  const int R = sweep_rpad(h->r);
+  const size_t task_bytes = static_cast<size_t>(task_kib) * 1024;
+  F = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(F, h->q)));
   for (int mode = 0; mode < 3; ++mode) {
     TaskProblem& P = h->tp[mode];
-    P = base;
+    P = TaskProblem{};
+    P.L = h->L;
     P.mode = mode;
     P.tau_eff = h->rho == 0 ? 0 : (mode == kModeInit ? h->opt.tau0 : mode == kModeIter ? h->opt.tau : 0);
     task_plan(P, R, task_bytes, h->trp);
+    if (P.ncw > h->t_ncw_max) return fail(LRS_ERR_STATE, "task engine: W chunks exceed the scratch");
     P.A = h->A;
     P.rscale = h->rscale;
     P.y = (mode == kModeIter && h->L.et != 0) ? h->ycorr : h->y;
@@ -494,32 +523,67 @@ lrs_status alloc_task_engine(lrs_ctx* h) {
     P.stop = h->tstop;
     P.col0 = 0;
     const int64_t tot = static_cast<int64_t>(P.tasks_per_col) * h->q;
-    if (tot >= (int64_t(1) << 31)) return fail(LRS_ERR_UNSUPPORTED, "task engine: too many tasks");
+    if (tot > h->t_total_max) return fail(LRS_ERR_STATE, "task engine: tasks exceed the queue");
     h->total[mode] = static_cast<int>(tot);
-    h->n_seed[mode] = h->tF * phase_tasks(P, 0);
-    max_total = std::max(max_total, h->total[mode]);
-    max_seed = std::max(max_seed, h->n_seed[mode]);
+    h->n_seed[mode] = F * phase_tasks(P, 0);
+    if (static_cast<size_t>(h->n_seed[mode]) > h->seed_stride)
+      return fail(LRS_ERR_STATE, "task engine: seed exceeds its buffer");
   }
-  h->seed_stride = static_cast<size_t>(max_seed);
-  if ((st = dalloc(&h->ttasks, static_cast<size_t>(max_total))) ||
-      (st = dalloc(&h->tseq, static_cast<size_t>(max_total))) ||
-      (st = dalloc(&h->dseed, 3 * h->seed_stride)))
-    return st;
   std::vector<unsigned long long> seed(3 * h->seed_stride, 0ull);
   for (int mode = 0; mode < 3; ++mode) {
     const TaskProblem& P = h->tp[mode];
     const int n0 = phase_tasks(P, 0);
-    for (int c = 0; c < h->tF; ++c)
+    for (int c = 0; c < F; ++c)
       for (int i = 0; i < n0; ++i)
         seed[mode * h->seed_stride + static_cast<size_t>(c) * n0 + i] =
             tdesc(c, 0, phase_type(P, 0), 0, i);
   }
   CUDA_TRY(cudaMemcpy(h->dseed, seed.data(), seed.size() * 8, cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(h->dtp, h->tp, sizeof(h->tp), cudaMemcpyHostToDevice));
+  h->tF = F;
+  h->t_kib = task_kib;
+  return LRS_OK;
+}
+
+// Scratch, queue and seeds sized for every shape the autotuner may pick
+// (the smallest tasks and all q columns in flight), then the tables.
+lrs_status alloc_task_engine(lrs_ctx* h) {
+  const int R = sweep_rpad(h->r), m = static_cast<int>(h->m);
+  const size_t q = static_cast<size_t>(h->q), ns = h->L.ns, rho1 = std::max(1, h->rho);
+  const int kib = h->t_kib;
+  const int kib_min = std::min(kib, kTuneKib[0]);
+  int ncw_max = 1, n0_max = 1;
+  int64_t total_max = 0;
+  for (int mode = 0; mode < 3; ++mode) {
+    TaskProblem P{};
+    P.L = h->L;
+    P.mode = mode;
+    P.tau_eff = h->rho == 0 ? 0 : (mode == kModeInit ? h->opt.tau0 : mode == kModeIter ? h->opt.tau : 0);
+    task_plan(P, R, static_cast<size_t>(kib_min) * 1024, h->trp);
+    ncw_max = std::max(ncw_max, P.ncw);
+    n0_max = std::max(n0_max, phase_tasks(P, 0));
+    total_max = std::max<int64_t>(total_max, static_cast<int64_t>(P.tasks_per_col) * h->q);
+  }
+  if (total_max >= (int64_t(1) << 31)) return fail(LRS_ERR_UNSUPPORTED, "task engine: too many tasks");
+  h->t_ncw_max = ncw_max;
+  h->t_total_max = total_max;
+  h->seed_stride = q * static_cast<size_t>(n0_max);
+  lrs_status st = LRS_OK;
+  if ((st = dalloc(&h->tWk, q * m * R)) || (st = dalloc(&h->tWp, q * ncw_max * m * R)) ||
+      (st = dalloc(&h->tGi, q * 16 * 16)) || (st = dalloc(&h->tu, q * m)) ||
+      (st = dalloc(&h->tg, q * ns)) || (st = dalloc(&h->tsupj, q * rho1)) ||
+      (st = dalloc(&h->tsupv, q * rho1)) || (st = dalloc(&h->tnsup, q)) ||
+      (st = dalloc(&h->tcnt, q)) || (st = dalloc(&h->tstop, q)) || (st = dalloc(&h->tctr, 4)) ||
+      (st = dalloc(&h->dtp, 3)) || (st = dalloc(&h->tprof, 16)) ||
+      (st = dalloc(&h->ttasks, static_cast<size_t>(total_max))) ||
+      (st = dalloc(&h->tseq, static_cast<size_t>(total_max))) ||
+      (st = dalloc(&h->dseed, 3 * h->seed_stride)))
+    return st;
+  CUDA_TRY(cudaMemset(h->tprof, 0, 16 * sizeof(unsigned long long)));
   CUDA_TRY(cudaMemset(h->tcnt, 0, q * sizeof(int)));
   CUDA_TRY(cudaMemset(h->tnsup, 0, q * sizeof(int)));
   CUDA_TRY(cudaMemset(h->tstop, 0, q * sizeof(int)));
-  return LRS_OK;
+  return plan_tables(h, kib, h->tF);
 }
 
 }  // namespace
@@ -837,6 +901,10 @@ lrs_status lrs_iterate(lrs_t h, int32_t iters, double* err_log) {
     if (st) return fail(static_cast<lrs_status>(st), "lrs_iterate: " + msg);
     return LRS_OK;
   }
+  if (h->opt.autotune && h->engine == 2 && !h->tuned && iters > 0) {
+    lrs_status st = lrs_autotune(h, 2, nullptr, 0);
+    if (st) return st;
+  }
   const bool prof = h->opt.profile != 0;
   if (prof) {
     while (h->ev.size() < 4 * static_cast<size_t>(iters)) {
@@ -851,18 +919,21 @@ lrs_status lrs_iterate(lrs_t h, int32_t iters, double* err_log) {
     const bool refine = h->L.et != 0 &&
                         (h->last_refine < 0 || h->t - h->last_refine >= h->opt.refine_every);
     if (refine) h->last_refine = h->t;
-    if (!first && h->opt.use_graph && h->stream && !prof && h->L.et == 0) {
-      if (!h->gexec) {
+    if (!first && h->opt.use_graph && h->stream && !prof) {
+      // replay the captured iteration (captured on first use; every launch of
+      // it reads only device state, so one capture serves all later iterations)
+      const int gi = refine ? 1 : 0;
+      if (!h->gexec[gi]) {
         CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        lrs_status st = enqueue_iteration(h, false);
+        lrs_status st = enqueue_iteration(h, false, nullptr, refine);
         cudaGraph_t gph = nullptr;
         cudaError_t e = cudaStreamEndCapture(h->stream, &gph);
         if (st) return st;
         CUDA_TRY(e);
-        h->graph = gph;
-        CUDA_TRY(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+        h->graph[gi] = gph;
+        CUDA_TRY(cudaGraphInstantiate(&h->gexec[gi], h->graph[gi], 0));
       }
-      CUDA_TRY(cudaGraphLaunch(h->gexec, h->stream));
+      CUDA_TRY(cudaGraphLaunch(h->gexec[gi], h->stream));
     } else {
       lrs_status st = enqueue_iteration(h, first, evs, refine);
       if (st) return st;
@@ -1035,6 +1106,129 @@ lrs_status lrs_describe(lrs_t h, char* buf, int32_t len) {
            h->kind == LRS_OP_GAUSSIAN ? "gaussian" : "dft2d", h->L.cs, h->L.ns, h->L.stages,
            h->resident, sm, nc, h->L.et, h->opt.refine_every);
   return LRS_OK;
+}
+
+lrs_status lrs_autotune(lrs_t h, int32_t trial_iters, char* report, int32_t len) {
+  if (!h) return fail(LRS_ERR_ARG, "lrs_autotune: NULL handle");
+  if (trial_iters < 1) return fail(LRS_ERR_ARG, "lrs_autotune: trial_iters < 1");
+  if (h->F || h->engine != 2) return fail(LRS_ERR_UNSUPPORTED, "lrs_autotune: task engine only");
+  if (h->state < kInitialised) return fail(LRS_ERR_STATE, "lrs_autotune: call lrs_init first");
+  const size_t nr = static_cast<size_t>(h->n) * h->r, qr = static_cast<size_t>(h->q) * h->r;
+  const size_t qs = static_cast<size_t>(h->q) * std::max(1, h->rho);
+  const size_t upad_n = static_cast<size_t>(h->L.ns) * sweep_rpad(h->r);
+  const size_t qm = h->L.et != 0 ? static_cast<size_t>(h->q) * h->m : 0;
+  // the state the trials start from, restored after each of them
+  float *U = nullptr, *Up = nullptr, *B = nullptr, *Sv = nullptr, *Yc = nullptr;
+  int* Si = nullptr;
+  double* eta = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    for (void* p : {static_cast<void*>(U), static_cast<void*>(Up), static_cast<void*>(B),
+                    static_cast<void*>(Sv), static_cast<void*>(Yc), static_cast<void*>(Si),
+                    static_cast<void*>(eta)})
+      if (p) cudaFree(p);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&U, nr * 4) != cudaSuccess || cudaMalloc(&Up, upad_n * 4) != cudaSuccess ||
+      cudaMalloc(&B, qr * 4) != cudaSuccess || cudaMalloc(&Sv, qs * 4) != cudaSuccess ||
+      cudaMalloc(&Si, qs * 4) != cudaSuccess || cudaMalloc(&eta, 8) != cudaSuccess ||
+      (qm && cudaMalloc(&Yc, qm * 4) != cudaSuccess) || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    cleanup();
+    return fail(LRS_ERR_OOM, "lrs_autotune: no memory for the saved state");
+  }
+  const int t_saved = h->t, lr_saved = h->last_refine;
+  auto copy_state = [&](bool save) -> cudaError_t {
+    auto cp = [&](void* keep, void* live, size_t bytes) {
+      return save ? cudaMemcpyAsync(keep, live, bytes, cudaMemcpyDeviceToDevice, h->stream)
+                  : cudaMemcpyAsync(live, keep, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    };
+    cudaError_t e = cp(U, h->U, nr * 4);
+    if (e == cudaSuccess) e = cp(Up, h->Upad, upad_n * 4);
+    if (e == cudaSuccess) e = cp(B, h->Bk, qr * 4);
+    if (e == cudaSuccess) e = cp(Si, h->S_idx, qs * 4);
+    if (e == cudaSuccess) e = cp(Sv, h->S_val, qs * 4);
+    if (e == cudaSuccess) e = cp(eta, h->eta, 8);
+    if (e == cudaSuccess && qm) e = cp(Yc, h->ycorr, qm * 4);
+    if (!save) {
+      h->t = t_saved;
+      h->last_refine = lr_saved;
+    }
+    return e;
+  };
+  cudaError_t e = copy_state(true);
+  const int q = static_cast<int>(h->q);
+  std::vector<std::pair<int, int>> cands;
+  for (int kib : kTuneKib)
+    for (int F : {q, std::max(1, q / 2), std::min(q, 2 * h->tshape.grid)}) {
+      std::pair<int, int> c{kib, F};
+      if (std::find(cands.begin(), cands.end(), c) == cands.end()) cands.push_back(c);
+    }
+  const int kib0 = h->t_kib, F0 = h->tF;
+  std::pair<int, int> best{kib0, F0};
+  float best_ms = 1e30f;
+  std::string rep = "{\"trials\": [";
+  for (size_t ci = 0; ci < cands.size() && e == cudaSuccess; ++ci) {
+    lrs_status st = plan_tables(h, cands[ci].first, cands[ci].second);
+    if (st) {
+      cleanup();
+      return st;
+    }
+    e = copy_state(false);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int i = 0; i < trial_iters && e == cudaSuccess; ++i) {
+      const bool refine = h->L.et != 0 &&
+                          (h->last_refine < 0 || h->t - h->last_refine >= h->opt.refine_every);
+      if (refine) h->last_refine = h->t;
+      st = enqueue_iteration(h, h->t == 0, nullptr, refine);
+      if (st) {
+        cleanup();
+        return st;
+      }
+      h->t += 1;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    ms /= static_cast<float>(trial_iters);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cands[ci];
+    }
+    char buf[96];
+    snprintf(buf, sizeof(buf), "%s{\"task_kib\": %d, \"inflight\": %d, \"ms\": %.4f}",
+             ci ? ", " : "", cands[ci].first, cands[ci].second, ms);
+    rep += buf;
+  }
+  lrs_status st = LRS_OK;
+  if (e == cudaSuccess) st = plan_tables(h, best.first, best.second);
+  if (e == cudaSuccess && st == LRS_OK) e = copy_state(false);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cleanup();
+  if (e != cudaSuccess) return fail(LRS_ERR_CUDA, std::string("lrs_autotune: ") + cudaGetErrorString(e));
+  if (st) return st;
+  for (int g = 0; g < 2; ++g) {  // captured iterations carry the old task shapes
+    if (h->gexec[g]) cudaGraphExecDestroy(h->gexec[g]);
+    if (h->graph[g]) cudaGraphDestroy(h->graph[g]);
+    h->gexec[g] = nullptr;
+    h->graph[g] = nullptr;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[tune_key(h)] = best;
+  }
+  h->tuned = 1;
+  lrs_status stc = check_device_error(h, "lrs_autotune");
+  if (report && len > 0) {
+    char buf[128];
+    snprintf(buf, sizeof(buf), "], \"chosen\": {\"task_kib\": %d, \"inflight\": %d, \"ms\": %.4f}}",
+             best.first, best.second, best_ms);
+    rep += buf;
+    snprintf(report, static_cast<size_t>(len), "%s", rep.c_str());
+  }
+  return stc;
 }
 
 lrs_status lrs_orthonormalize(const float* Z, float* Q, int64_t n, int32_t r, void* stream) {

@@ -39,7 +39,8 @@ class lrs_options(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("profile", ctypes.c_int32),
                 ("slab_mode", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("engine", ctypes.c_int32), ("inflight", ctypes.c_int32),
-                ("task_kib", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("task_kib", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("autotune", ctypes.c_int32)]
 
 
 _lib = None
@@ -72,6 +73,7 @@ def lib():
             "lrs_describe": [_P, ctypes.c_char_p, ctypes.c_int32],
             "lrs_sweep_trace": [_P, _P, ctypes.c_int64],
             "lrs_orthonormalize": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P],
+            "lrs_autotune": [_P, ctypes.c_int32, ctypes.c_char_p, ctypes.c_int32],
             "lrs_orthonormalize_noalloc": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P],
             "lrs_destroy": [_P],
         }
@@ -209,6 +211,15 @@ def lrs_task_profile(h):
 def lrs_describe(h):
     buf = ctypes.create_string_buffer(512)
     _check(lib().lrs_describe(h, buf, 512))
+    import json
+    return json.loads(buf.value.decode())
+
+
+def lrs_autotune(h, trial_iters=2):
+    """Time candidate task-engine shapes from the current iterate; returns the
+    trials and the chosen shape (cached for later handles of this shape)."""
+    buf = ctypes.create_string_buffer(4096)
+    _check(lib().lrs_autotune(h, trial_iters, buf, 4096))
     import json
     return json.loads(buf.value.decode())
 
