@@ -13,6 +13,10 @@ and seeded (lrsgen).  One JSON line is printed by rank 0.
 --workload c2 measures the precision forms on the Gaussian problem n=4096,
 q=2048, r=10, m=512, rho=40 (A_k drawn on the device, 17.2 GB in float32):
 device-timed column-iterations/s and the final relative error against X*.
+--workload c4 runs the serving mix (--requests problems, 70 % Gaussian with
+BF16-stored A_k, 30 % DFT, T=100 each): first all at once to measure the
+saturation throughput, then with Poisson arrivals at 0.8 x that rate; p50 /
+p99 latency (arrival to completion, input generation included).
 """
 import argparse
 import json
@@ -318,6 +322,39 @@ def run_c2(args):
     return 0
 
 
+def run_c4(args):
+    """Serving mix: saturation throughput, then Poisson arrivals at 0.8 x."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2311_03824_gb300 import build
+    build.build()
+    from paper_2311_03824_gb300 import serve as S
+    budget = int(0.8 * torch.cuda.mem_get_info()[0])
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    reqs = S.c4_requests(args.requests, seed=5, T=100)
+    srv = S.Server(budget, slots=args.slots, sms=nsm)
+    res = srv.run(reqs)                     # every request at t = 0: saturation
+    sat = S.summarize(res, srv.makespan, reqs)
+    rate = 0.8 * sat["throughput_req_s"]
+    reqs = S.poisson_arrivals(S.c4_requests(args.requests, seed=5, T=100), rate, seed=6)
+    srv2 = S.Server(budget, slots=args.slots, sms=nsm)
+    with ClockSampler(0) as clk:
+        res2 = srv2.run(reqs)
+    lat = S.summarize(res2, srv2.makespan, reqs)
+    line = {
+        "metric": "serving p99 latency", "value": lat["p99_latency_s"], "unit": "s",
+        "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+        "dtype": "bf16 storage (Gaussian), f32 compute",
+        "config": {"workload": f"serving mix, {args.requests} requests, 70% Gaussian BF16 / 30% DFT, T=100",
+                   "slots": args.slots, "hbm_budget_gb": budget / 1e9,
+                   "arrival_rate_req_s": rate},
+        "saturation": sat, "poisson_0.8": lat, "clocks": clk.summary(),
+        "peak_concurrent": srv2.peak_running,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,7 +363,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-iters", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c1", choices=["c1", "c2"])
+    ap.add_argument("--workload", default="c1", choices=["c1", "c2", "c4"])
+    ap.add_argument("--requests", type=int, default=100)
+    ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--a-dtype", default="fp32", choices=list(A_DTYPES))
     args = ap.parse_args()
     if args.warmup < 3:
@@ -335,6 +374,8 @@ def main():
         return run_reference(args)
     if args.workload == "c2":
         return run_c2(args)
+    if args.workload == "c4":
+        return run_c4(args)
     return run_ours(args)
 
 

@@ -96,6 +96,9 @@ typedef struct {
   int32_t autotune;         /* task engine: 1 = run lrs_autotune (2 trial
                                iterations per shape) before the first
                                iteration unless this shape is cached         */
+  int32_t grid;             /* task engine: CTAs of the persistent launch (0 ->
+                               all that fit; fewer let concurrent handles on
+                               other streams share the GPU)                  */
 } lrs_options;
 
 /* Create a solver for one problem (Section I-A sizes).

@@ -32,7 +32,7 @@ class DeviceGaussianInstance:
                                         dtype=torch.float32)
             y = torch.bmm(self.A[k0:k1].double(), X[k0:k1, :, None])[:, :, 0]
             self.Y[k0:k1] = y.float()
-        torch.cuda.synchronize()
+        torch.cuda.current_stream().synchronize()  # this stream only: others keep running
 
     def free(self):
         self.A = None

@@ -1033,32 +1033,32 @@ FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int 
     delete F;
     return nullptr;
   }
-  cudaFuncSetAttribute(fsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(F->smem));
+  cudaFuncSetAttribute(fsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_limit());
   cudaFuncSetAttribute(fft_frames_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       static_cast<int>(fft_smem(F->g)));
+                       smem_optin_limit());
   const size_t rr = static_cast<size_t>(r) * r;
-  bool ok = cudaMalloc(&F->y, sizeof(float2) * m * q) == cudaSuccess &&
-            cudaMalloc(&F->mask, sizeof(int) * m * q) == cudaSuccess &&
-            cudaMalloc(&F->U, sizeof(float2) * n * r) == cudaSuccess &&
-            cudaMalloc(&F->FU, sizeof(float2) * n * r) == cudaSuccess &&
-            cudaMalloc(&F->B, sizeof(float2) * q * r) == cudaSuccess &&
-            cudaMalloc(&F->S_idx, sizeof(int) * q * std::max(1, rho)) == cudaSuccess &&
-            cudaMalloc(&F->S_val, sizeof(float2) * q * std::max(1, rho)) == cudaSuccess &&
-            cudaMalloc(&F->RES, sizeof(float2) * m * q) == cudaSuccess &&
-            cudaMalloc(&F->H, sizeof(float2) * static_cast<size_t>(n) * q) == cudaSuccess &&
-            cudaMalloc(&F->K, sizeof(float2) * n * r) == cudaSuccess &&
-            cudaMalloc(&F->grad, sizeof(float2) * n * r) == cudaSuccess &&
-            cudaMalloc(&F->Z, sizeof(float2) * n * r) == cudaSuccess &&
-            cudaMalloc(&F->Z2, sizeof(float2) * n * r) == cudaSuccess &&
-            cudaMalloc(&F->twx, sizeof(float2) * nx) == cudaSuccess &&
-            cudaMalloc(&F->twy, sizeof(float2) * ny) == cudaSuccess &&
-            cudaMalloc(&F->iptr, sizeof(int) * (n + 1)) == cudaSuccess &&
-            cudaMalloc(&F->ilist, sizeof(int) * m * q) == cudaSuccess &&
-            cudaMalloc(&F->err, sizeof(int) * 2) == cudaSuccess &&
-            cudaMalloc(&F->part, sizeof(double2) * F->nblk * rr) == cudaSuccess &&
-            cudaMalloc(&F->rfac, sizeof(double2) * 2 * rr) == cudaSuccess &&
-            cudaMalloc(&F->eta, sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&F->scal, sizeof(double) * 4) == cudaSuccess;
+  bool ok = cudaMallocAsync(reinterpret_cast<void**>(&F->y), sizeof(float2) * m * q, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->mask), sizeof(int) * m * q, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->U), sizeof(float2) * n * r, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->FU), sizeof(float2) * n * r, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->B), sizeof(float2) * q * r, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->S_idx), sizeof(int) * q * std::max(1, rho), F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->S_val), sizeof(float2) * q * std::max(1, rho), F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->RES), sizeof(float2) * m * q, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->H), sizeof(float2) * static_cast<size_t>(n) * q, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->K), sizeof(float2) * n * r, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->grad), sizeof(float2) * n * r, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->Z), sizeof(float2) * n * r, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->Z2), sizeof(float2) * n * r, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->twx), sizeof(float2) * nx, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->twy), sizeof(float2) * ny, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->iptr), sizeof(int) * (n + 1), F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->ilist), sizeof(int) * m * q, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->err), sizeof(int) * 2, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->part), sizeof(double2) * F->nblk * rr, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->rfac), sizeof(double2) * 2 * rr, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->eta), sizeof(double), F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->scal), sizeof(double) * 4, F->s) == cudaSuccess;
   if (!ok) {
     *msg = "device allocation failed";
     return F;  // caller frees
@@ -1068,15 +1068,16 @@ FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int 
     const double a = -2.0 * M_PI * k / nx;
     tw[k] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
   }
-  cudaMemcpy(F->twx, tw.data(), sizeof(float2) * nx, cudaMemcpyHostToDevice);
+  cudaMemcpyAsync(F->twx, tw.data(), sizeof(float2) * nx, cudaMemcpyHostToDevice, F->s);
   for (int k = 0; k < ny; ++k) {
     const double a = -2.0 * M_PI * k / ny;
     tw[k] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
   }
-  cudaMemcpy(F->twy, tw.data(), sizeof(float2) * ny, cudaMemcpyHostToDevice);
-  cudaMemset(F->err, 0, 8);
-  cudaMemset(F->S_idx, 0, sizeof(int) * q * std::max(1, rho));
-  cudaMemset(F->S_val, 0, sizeof(float2) * q * std::max(1, rho));
+  cudaMemcpyAsync(F->twy, tw.data(), sizeof(float2) * ny, cudaMemcpyHostToDevice, F->s);
+  cudaMemsetAsync(F->err, 0, 8, F->s);
+  cudaMemsetAsync(F->S_idx, 0, sizeof(int) * q * std::max(1, rho), F->s);
+  cudaMemsetAsync(F->S_val, 0, sizeof(float2) * q * std::max(1, rho), F->s);
+  cudaStreamSynchronize(F->s);  // the twiddle tables' host staging ends here
   return F;
 }
 
@@ -1085,7 +1086,8 @@ void fourier_destroy(FourierSolver* F) {
   void* ps[] = {F->y, F->mask, F->U, F->FU, F->B, F->S_idx, F->S_val, F->RES, F->H, F->K, F->grad,
                 F->Z, F->Z2, F->twx, F->twy, F->iptr, F->ilist, F->err, F->part, F->rfac, F->eta, F->scal};
   for (void* p : ps)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, F->s);
+  cudaStreamSynchronize(F->s);
   delete F;
 }
 
@@ -1095,7 +1097,9 @@ int fourier_set_measurements(FourierSolver* F, const void* y, const void* mask, 
   const int n = F->g.n, m = F->m, q = F->q;
   std::vector<int> hm(static_cast<size_t>(m) * q);
   if (mem_kind) {
-    if (cudaMemcpy(hm.data(), mask, sizeof(int) * hm.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    if (cudaMemcpyAsync(hm.data(), mask, sizeof(int) * hm.size(), cudaMemcpyDeviceToHost, F->s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(F->s) != cudaSuccess) {
       *msg = "mask copy failed";
       return 4;
     }
@@ -1192,11 +1196,11 @@ int fourier_init(FourierSolver* F, std::string* msg) {
   // FP64 complex subspace iteration for the top-r left singular vectors of L0
   const size_t nr = static_cast<size_t>(n) * r;
   double2 *Ud = nullptr, *Uo = nullptr, *Zd = nullptr, *Td = nullptr, *Pd = nullptr;
-  if (e == cudaSuccess) e = cudaMalloc(&Ud, nr * 16);
-  if (e == cudaSuccess) e = cudaMalloc(&Uo, nr * 16);
-  if (e == cudaSuccess) e = cudaMalloc(&Zd, nr * 16);
-  if (e == cudaSuccess) e = cudaMalloc(&Td, nr * 16);
-  if (e == cudaSuccess) e = cudaMalloc(&Pd, static_cast<size_t>(q) * r * 16);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Ud), nr * 16, F->s);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Uo), nr * 16, F->s);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Zd), nr * 16, F->s);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Td), nr * 16, F->s);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Pd), static_cast<size_t>(q) * r * 16, F->s);
   // start: deterministic complex Gaussian block
   std::vector<double2> st(nr);
   uint64_t sd = F->seed * 0x9E3779B97F4A7C15ull + 0x2545F4914F6CDD1Dull;
@@ -1240,7 +1244,7 @@ int fourier_init(FourierSolver* F, std::string* msg) {
   if (e == cudaSuccess) dqr(Zd, Ud, F->U);
   if (e == cudaSuccess) e = cudaStreamSynchronize(F->s);
   for (double2* p : {Ud, Uo, Zd, Td, Pd})
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, F->s);
   // b_k = (A_k U0)^+ (y_k - A_k s_k)
   if (e == cudaSuccess) e = fft_frames(F, F->U, F->FU, r, false);
   if (e == cudaSuccess) e = launch_fsweep(F, kModeLS, 0);
@@ -1304,7 +1308,8 @@ int fourier_set_state(FourierSolver* F, const void* U, const void* B, const int*
 
 double fourier_eta(FourierSolver* F) {
   double v = 0;
-  cudaMemcpy(&v, F->eta, sizeof(double), cudaMemcpyDeviceToHost);
+  cudaMemcpyAsync(&v, F->eta, sizeof(double), cudaMemcpyDeviceToHost, F->s);
+  cudaStreamSynchronize(F->s);
   return F->t ? v : 0.0;
 }
 int fourier_t(FourierSolver* F) { return F->t; }

@@ -375,10 +375,13 @@ std::vector<float> start_block(int64_t n, int r, uint64_t seed) {
   return v;
 }
 
+// Device memory of a handle: stream-ordered (cudaMallocAsync / cudaFreeAsync on
+// the handle's stream), so that creating or destroying one handle never waits
+// for work that other handles run on other streams.
 template <typename T>
-lrs_status dalloc(T** p, size_t count) {
+lrs_status dalloc(T** p, size_t count, cudaStream_t s) {
   if (count == 0) count = 1;
-  CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)));
+  CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(p), count * sizeof(T), s));
   return LRS_OK;
 }
 
@@ -394,11 +397,11 @@ void free_all(lrs_ctx* h) {
   void* ps2[] = {h->dtp, h->dseed, h->tWk, h->tWp, h->tu, h->tg, h->tsupv, h->tGi, h->tsupj,
                  h->tnsup, h->tcnt, h->tstop, h->tseq, h->tctr, h->ttasks, h->tprof};
   for (void* p : ps2)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, h->stream);
   void* ps[] = {h->gsplit, h->dsplit, h->A, h->y, h->Aex, h->rscale, h->ycorr, h->U, h->Upad, h->Bk, h->S_idx, h->S_val, h->H, h->grad, h->Z,
                 h->U2, h->P, h->part, h->small, h->eta, h->err, h->Xref, h->errpart, h->trace};
   for (void* p : ps)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, h->stream);
 }
 
 // ---- autotuner: shapes per problem, cached for the process -----------------------
@@ -481,7 +484,7 @@ lrs_status alloc_split(lrs_ctx* h, int nsm) {
   if (ks <= 1) return LRS_OK;
   lrs_status st = LRS_OK;
   const size_t cnt = static_cast<size_t>(ks) * h->n * h->r;
-  if ((st = dalloc(&h->gsplit, cnt)) || (st = dalloc(&h->dsplit, cnt))) return st;
+  if ((st = dalloc(&h->gsplit, cnt, h->stream)) || (st = dalloc(&h->dsplit, cnt, h->stream))) return st;
   return LRS_OK;
 }
 
@@ -538,8 +541,9 @@ lrs_status plan_tables(lrs_ctx* h, int task_kib, int F) {
         seed[mode * h->seed_stride + static_cast<size_t>(c) * n0 + i] =
             tdesc(c, 0, phase_type(P, 0), 0, i);
   }
-  CUDA_TRY(cudaMemcpy(h->dseed, seed.data(), seed.size() * 8, cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(h->dtp, h->tp, sizeof(h->tp), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpyAsync(h->dseed, seed.data(), seed.size() * 8, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->dtp, h->tp, sizeof(h->tp), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));  // the host tables may go once this returns
   h->tF = F;
   h->t_kib = task_kib;
   return LRS_OK;
@@ -569,20 +573,20 @@ lrs_status alloc_task_engine(lrs_ctx* h) {
   h->t_total_max = total_max;
   h->seed_stride = q * static_cast<size_t>(n0_max);
   lrs_status st = LRS_OK;
-  if ((st = dalloc(&h->tWk, q * m * R)) || (st = dalloc(&h->tWp, q * ncw_max * m * R)) ||
-      (st = dalloc(&h->tGi, q * 16 * 16)) || (st = dalloc(&h->tu, q * m)) ||
-      (st = dalloc(&h->tg, q * ns)) || (st = dalloc(&h->tsupj, q * rho1)) ||
-      (st = dalloc(&h->tsupv, q * rho1)) || (st = dalloc(&h->tnsup, q)) ||
-      (st = dalloc(&h->tcnt, q)) || (st = dalloc(&h->tstop, q)) || (st = dalloc(&h->tctr, 4)) ||
-      (st = dalloc(&h->dtp, 3)) || (st = dalloc(&h->tprof, 16)) ||
-      (st = dalloc(&h->ttasks, static_cast<size_t>(total_max))) ||
-      (st = dalloc(&h->tseq, static_cast<size_t>(total_max))) ||
-      (st = dalloc(&h->dseed, 3 * h->seed_stride)))
+  if ((st = dalloc(&h->tWk, q * m * R, h->stream)) || (st = dalloc(&h->tWp, q * ncw_max * m * R, h->stream)) ||
+      (st = dalloc(&h->tGi, q * 16 * 16, h->stream)) || (st = dalloc(&h->tu, q * m, h->stream)) ||
+      (st = dalloc(&h->tg, q * ns, h->stream)) || (st = dalloc(&h->tsupj, q * rho1, h->stream)) ||
+      (st = dalloc(&h->tsupv, q * rho1, h->stream)) || (st = dalloc(&h->tnsup, q, h->stream)) ||
+      (st = dalloc(&h->tcnt, q, h->stream)) || (st = dalloc(&h->tstop, q, h->stream)) || (st = dalloc(&h->tctr, 4, h->stream)) ||
+      (st = dalloc(&h->dtp, 3, h->stream)) || (st = dalloc(&h->tprof, 16, h->stream)) ||
+      (st = dalloc(&h->ttasks, static_cast<size_t>(total_max), h->stream)) ||
+      (st = dalloc(&h->tseq, static_cast<size_t>(total_max), h->stream)) ||
+      (st = dalloc(&h->dseed, 3 * h->seed_stride, h->stream)))
     return st;
-  CUDA_TRY(cudaMemset(h->tprof, 0, 16 * sizeof(unsigned long long)));
-  CUDA_TRY(cudaMemset(h->tcnt, 0, q * sizeof(int)));
-  CUDA_TRY(cudaMemset(h->tnsup, 0, q * sizeof(int)));
-  CUDA_TRY(cudaMemset(h->tstop, 0, q * sizeof(int)));
+  CUDA_TRY(cudaMemsetAsync(h->tprof, 0, 16 * sizeof(unsigned long long), h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->tcnt, 0, q * sizeof(int), h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->tnsup, 0, q * sizeof(int), h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->tstop, 0, q * sizeof(int), h->stream));
   return plan_tables(h, kib, h->tF);
 }
 
@@ -612,7 +616,7 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
     if (m > n) return fail(LRS_ERR_ARG, "lrs_create: DFT needs m <= n");
   }
   if (o.tau0 < 0 || o.tau < 0 || o.T < 0 || o.rho_max < 0 || o.c_eta < 0 || o.cluster < 0 ||
-      o.power_iters < 0 || o.refine_every < 0)
+      o.power_iters < 0 || o.refine_every < 0 || o.grid < 0)
     return fail(LRS_ERR_ARG, "lrs_create: negative option");
   if (o.cluster != 0 && o.cluster != 1 && o.cluster != 2 && o.cluster != 4 && o.cluster != 8 &&
       o.cluster != 16)
@@ -700,19 +704,19 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
   lrs_status st = LRS_OK;
   const size_t upad_n = static_cast<size_t>(h->L.cs) * h->L.ns * sweep_rpad(r);
   const int lowp = h->L.et != 0, per_row = h->L.et == 3 ? 2 : 1;
-  if ((st = dalloc(reinterpret_cast<unsigned char**>(&h->A), per_col * q)) ||
-      (st = dalloc(&h->y, size_t(m) * q)) ||
-      (lowp && (st = dalloc(&h->Aex, size_t(m) * n * q))) ||
-      (lowp && (st = dalloc(&h->ycorr, size_t(m) * q))) ||
-      (h->L.et >= 2 && (st = dalloc(&h->rscale, size_t(m) * q * per_row))) ||
-      (st = dalloc(&h->Upad, upad_n)) ||
-      (st = dalloc(&h->U, size_t(n) * r)) || (st = dalloc(&h->Bk, size_t(q) * r)) ||
-      (st = dalloc(&h->S_idx, size_t(q) * std::max(1, h->rho))) || (st = dalloc(&h->S_val, size_t(q) * std::max(1, h->rho))) ||
-      (st = dalloc(&h->H, size_t(q) * n)) || (st = dalloc(&h->grad, size_t(n) * r)) ||
-      (st = dalloc(&h->Z, size_t(n) * r)) || (st = dalloc(&h->U2, size_t(n) * r)) ||
-      (st = dalloc(&h->P, size_t(q) * r)) || (st = dalloc(&h->part, size_t(h->nblk) * r * r)) ||
-      (st = dalloc(&h->small, 4 * 16 * 16 + 64)) || (st = dalloc(&h->eta, 1)) ||
-      (st = dalloc(&h->err, 2)) || (st = dalloc(&h->errpart, 2 * size_t(q))) ||
+  if ((st = dalloc(reinterpret_cast<unsigned char**>(&h->A), per_col * q, h->stream)) ||
+      (st = dalloc(&h->y, size_t(m) * q, h->stream)) ||
+      (lowp && (st = dalloc(&h->Aex, size_t(m) * n * q, h->stream))) ||
+      (lowp && (st = dalloc(&h->ycorr, size_t(m) * q, h->stream))) ||
+      (h->L.et >= 2 && (st = dalloc(&h->rscale, size_t(m) * q * per_row, h->stream))) ||
+      (st = dalloc(&h->Upad, upad_n, h->stream)) ||
+      (st = dalloc(&h->U, size_t(n) * r, h->stream)) || (st = dalloc(&h->Bk, size_t(q) * r, h->stream)) ||
+      (st = dalloc(&h->S_idx, size_t(q) * std::max(1, h->rho), h->stream)) || (st = dalloc(&h->S_val, size_t(q) * std::max(1, h->rho), h->stream)) ||
+      (st = dalloc(&h->H, size_t(q) * n, h->stream)) || (st = dalloc(&h->grad, size_t(n) * r, h->stream)) ||
+      (st = dalloc(&h->Z, size_t(n) * r, h->stream)) || (st = dalloc(&h->U2, size_t(n) * r, h->stream)) ||
+      (st = dalloc(&h->P, size_t(q) * r, h->stream)) || (st = dalloc(&h->part, size_t(h->nblk) * r * r, h->stream)) ||
+      (st = dalloc(&h->small, 4 * 16 * 16 + 64, h->stream)) || (st = dalloc(&h->eta, 1, h->stream)) ||
+      (st = dalloc(&h->err, 2, h->stream)) || (st = dalloc(&h->errpart, 2 * size_t(q), h->stream)) ||
       (h->engine == 2 && (st = alloc_task_engine(h))) || (st = alloc_split(h, nsm))) {
     std::string msg = g_last_error;
     free_all(h);
@@ -720,19 +724,21 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
     return fail(st, "lrs_create: " + msg);
   }
   if (o.profile == 2) {
-    if ((st = dalloc(&h->trace, size_t(q) * kTracePhases))) {
+    if ((st = dalloc(&h->trace, size_t(q) * kTracePhases, h->stream))) {
       free_all(h);
       delete h;
       return st;
     }
-    cudaMemset(h->trace, 0, sizeof(unsigned long long) * size_t(q) * kTracePhases);
+    cudaMemsetAsync(h->trace, 0, sizeof(unsigned long long) * size_t(q) * kTracePhases, h->stream);
   }
   cudaError_t e = h->engine == 1 ? sweep_prepare(h->L, kThreads)
                                  : task_prepare(sweep_rpad(r), h->L.et, h->tshape.smem);
-  if (e == cudaSuccess) e = cudaMemset(h->err, 0, 2 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(h->Upad, 0, sizeof(float) * upad_n);
-  if (e == cudaSuccess) e = cudaMemset(h->S_idx, 0, sizeof(int) * size_t(q) * std::max(1, h->rho));
-  if (e == cudaSuccess) e = cudaMemset(h->S_val, 0, sizeof(float) * size_t(q) * std::max(1, h->rho));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, 2 * sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Upad, 0, sizeof(float) * upad_n, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->S_idx, 0, sizeof(int) * size_t(q) * std::max(1, h->rho), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->S_val, 0, sizeof(float) * size_t(q) * std::max(1, h->rho), h->stream);
+  // the handle's memory is ready for any stream once its own stream gets here
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     free_all(h);
     delete h;
@@ -752,6 +758,7 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
     }
     h->tshape.ctas_per_sm = cps;
     h->tshape.grid = cps * nsm;
+    if (o.grid > 0) h->tshape.grid = std::min(o.grid, h->tshape.grid);
   }
   *out = h;
   return LRS_OK;
@@ -791,7 +798,7 @@ lrs_status lrs_set_measurements(lrs_t h, const void* y, const void* A_or_mask, i
   int64_t chunk = std::max<int64_t>(1, (int64_t(256) << 20) / (int64_t)(col_elems * 4));
   chunk = std::min<int64_t>(chunk, h->q);
   float* tmp = nullptr;
-  if (mem_kind == 0) CUDA_TRY(cudaMalloc(&tmp, sizeof(float) * col_elems * chunk));
+  if (mem_kind == 0) CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(float) * col_elems * chunk, h->stream));
   for (int64_t k0 = 0; k0 < h->q; k0 += chunk) {
     const int64_t kc = std::min(chunk, h->q - k0);
     const float* src = static_cast<const float*>(A_or_mask) + k0 * col_elems;
@@ -801,14 +808,14 @@ lrs_status lrs_set_measurements(lrs_t h, const void* y, const void* A_or_mask, i
       if (e == cudaSuccess) e = repack_gauss(h->L, tmp, static_cast<int>(k0), static_cast<int>(kc), h->A, nullptr, h->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
       if (e != cudaSuccess) {
-        cudaFree(tmp);
+        cudaFreeAsync(tmp, h->stream);
         return fail(LRS_ERR_CUDA, std::string("lrs_set_measurements: ") + cudaGetErrorString(e));
       }
     } else {
       CUDA_TRY(repack_gauss(h->L, src, static_cast<int>(k0), static_cast<int>(kc), h->A, nullptr, h->stream));
     }
   }
-  if (tmp) cudaFree(tmp);
+  if (tmp) cudaFreeAsync(tmp, h->stream);
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   h->state = kMeasured;
   h->t = 0;
@@ -837,15 +844,14 @@ lrs_status lrs_init(lrs_t h) {
   const size_t nr = static_cast<size_t>(h->n) * r;
   double *Ud = nullptr, *Uold = nullptr, *Zd = nullptr, *Pd = nullptr, *Td = nullptr;
   auto free_d = [&]() {
-    if (Td) cudaFree(Td);
-    if (Ud) cudaFree(Ud);
-    if (Uold) cudaFree(Uold);
-    if (Zd) cudaFree(Zd);
-    if (Pd) cudaFree(Pd);
+    for (double* p : {Td, Ud, Uold, Zd, Pd})
+      if (p) cudaFreeAsync(p, h->stream);
   };
-  if (cudaMalloc(&Ud, nr * 8) != cudaSuccess || cudaMalloc(&Uold, nr * 8) != cudaSuccess ||
-      cudaMalloc(&Zd, nr * 8) != cudaSuccess || cudaMalloc(&Td, nr * 8) != cudaSuccess ||
-      cudaMalloc(&Pd, static_cast<size_t>(h->q) * r * 8) != cudaSuccess) {
+  auto am = [&](double** p, size_t bytes) {
+    return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, h->stream) == cudaSuccess;
+  };
+  if (!am(&Ud, nr * 8) || !am(&Uold, nr * 8) || !am(&Zd, nr * 8) || !am(&Td, nr * 8) ||
+      !am(&Pd, static_cast<size_t>(h->q) * r * 8)) {
     free_d();
     return fail(LRS_ERR_OOM, "lrs_init: no device memory for the subspace iteration");
   }
@@ -1046,7 +1052,7 @@ lrs_status lrs_get_progress(lrs_t h, double* eta, int32_t* t) {
 lrs_status lrs_set_reference(lrs_t h, const void* Xref, int32_t mem_kind) {
   if (!h || !Xref) return fail(LRS_ERR_ARG, "lrs_set_reference: NULL argument");
   if (mem_kind != 0 && mem_kind != 1) return fail(LRS_ERR_ARG, "lrs_set_reference: bad mem_kind");
-  if (!h->Xref) CUDA_TRY(cudaMalloc(&h->Xref, sizeof(float) * h->n * h->q));
+  if (!h->Xref) CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&h->Xref), sizeof(float) * h->n * h->q, h->stream));
   CUDA_TRY(cudaMemcpyAsync(h->Xref, Xref, sizeof(float) * h->n * h->q,
                            mem_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -1126,14 +1132,16 @@ lrs_status lrs_autotune(lrs_t h, int32_t trial_iters, char* report, int32_t len)
     for (void* p : {static_cast<void*>(U), static_cast<void*>(Up), static_cast<void*>(B),
                     static_cast<void*>(Sv), static_cast<void*>(Yc), static_cast<void*>(Si),
                     static_cast<void*>(eta)})
-      if (p) cudaFree(p);
+      if (p) cudaFreeAsync(p, h->stream);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
   };
-  if (cudaMalloc(&U, nr * 4) != cudaSuccess || cudaMalloc(&Up, upad_n * 4) != cudaSuccess ||
-      cudaMalloc(&B, qr * 4) != cudaSuccess || cudaMalloc(&Sv, qs * 4) != cudaSuccess ||
-      cudaMalloc(&Si, qs * 4) != cudaSuccess || cudaMalloc(&eta, 8) != cudaSuccess ||
-      (qm && cudaMalloc(&Yc, qm * 4) != cudaSuccess) || cudaEventCreate(&e0) != cudaSuccess ||
+  auto am = [&](auto** p, size_t bytes) {
+    return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, h->stream) == cudaSuccess;
+  };
+  if (!am(&U, nr * 4) || !am(&Up, upad_n * 4) || !am(&B, qr * 4) || !am(&Sv, qs * 4) ||
+      !am(&Si, qs * 4) || !am(&eta, 8) || (qm && !am(&Yc, qm * 4)) ||
+      cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess) {
     cleanup();
     return fail(LRS_ERR_OOM, "lrs_autotune: no memory for the saved state");
@@ -1241,13 +1249,14 @@ lrs_status lrs_orthonormalize(const float* Z, float* Q, int64_t n, int32_t r, vo
   double* part = nullptr;
   int* err = nullptr;
   auto cleanup = [&]() {
-    if (tmp) cudaFree(tmp);
-    if (part) cudaFree(part);
-    if (err) cudaFree(err);
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (part) cudaFreeAsync(part, s);
+    if (err) cudaFreeAsync(err, s);
   };
-  if (cudaMalloc(&tmp, sizeof(float) * n * r) != cudaSuccess ||
-      cudaMalloc(&part, sizeof(double) * (static_cast<size_t>(nblk) * r * r + 2 * r * r)) != cudaSuccess ||
-      cudaMalloc(&err, 2 * sizeof(int)) != cudaSuccess) {
+  if (cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(float) * n * r, s) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void**>(&part),
+                      sizeof(double) * (static_cast<size_t>(nblk) * r * r + 2 * r * r), s) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void**>(&err), 2 * sizeof(int), s) != cudaSuccess) {
     cleanup();
     return fail(LRS_ERR_OOM, "lrs_orthonormalize: scratch allocation failed");
   }
@@ -1273,6 +1282,7 @@ lrs_status lrs_destroy(lrs_t h) {
     return LRS_OK;
   }
   free_all(h);
+  if (h->stream) cudaStreamSynchronize(h->stream);
   delete h;
   return LRS_OK;
 }

@@ -64,6 +64,17 @@ struct SweepArgs {
 // A s, LS + residual, final column pass, output writes.
 constexpr int kTracePhases = 12;
 
+// Largest dynamic shared memory a CTA may request on the current device.
+// Kernels shared by every handle get this as their limit once and for all:
+// a per-handle value would race with handles of other sizes launching
+// concurrently on other streams.
+inline int smem_optin_limit() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v > 0 ? v : 232448;
+}
+
 // Sweep kernel (sweep_gauss.cu).
 size_t sweep_smem_bytes(const GaussLayout& L, int resident, int nthreads);
 cudaError_t sweep_launch(const SweepArgs& a, int nthreads, cudaStream_t s);

@@ -167,12 +167,11 @@ size_t sweep_smem_bytes(const GaussLayout& L, int resident, int /*nthreads*/) {
   return carve(L, resident).total;
 }
 
-cudaError_t sweep_prepare(const GaussLayout& L, int nthreads) {
+cudaError_t sweep_prepare(const GaussLayout& L, int /*nthreads*/) {
   for (int res = 0; res < 2; ++res) {
     void* f = pick_kernel(L.r, res, L.et);
-    const size_t sm = sweep_smem_bytes(L, res, nthreads);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(sm));
+                                         smem_optin_limit());
     if (e != cudaSuccess) cudaGetLastError();
     e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) cudaGetLastError();

@@ -89,8 +89,9 @@ size_t task_smem_bytes(int R, int /*et*/, int m_max, int ns_max, int rho_max, in
 }
 
 cudaError_t task_prepare(int R, int et, size_t smem) {
+  (void)smem;
   return cudaFuncSetAttribute(pick(R, et), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(smem));
+                              smem_optin_limit());
 }
 
 int task_ctas_per_sm(int R, int et, size_t smem) {

@@ -40,7 +40,7 @@ class lrs_options(ctypes.Structure):
                 ("slab_mode", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("engine", ctypes.c_int32), ("inflight", ctypes.c_int32),
                 ("task_kib", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("autotune", ctypes.c_int32)]
+                ("autotune", ctypes.c_int32), ("grid", ctypes.c_int32)]
 
 
 _lib = None
