@@ -181,11 +181,12 @@ def run_ours(args):
     Y = np.ascontiguousarray(inst.Y)
     n, q, r, m, rho = cfg["n"], cfg["q"], cfg["r"], cfg["m"], cfg["rho"]
     stream = torch.cuda.Stream()
-    s = L.Solver(n, m, q, r, rho, stream=stream, profile=1)
-    desc = L.lrs_describe(s.h)
+    # autotune: the first iterate call times the task shapes (inside the warm-up)
+    s = L.Solver(n, m, q, r, rho, stream=stream, profile=1, autotune=1)
     s.set_measurements(Y, A)
     s.init()
     s.iterate(args.warmup)
+    desc = L.lrs_describe(s.h)
     L.lrs_phase_times(s.h)
     # ---- timed region: K GDmin iterations, inputs resident in HBM ----------
     def barrier():
@@ -218,7 +219,7 @@ def run_ours(args):
     T_e2e = max(1, args.e2e_iters)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    s2 = L.Solver(n, m, q, r, rho, stream=stream)
+    s2 = L.Solver(n, m, q, r, rho, stream=stream, autotune=1)  # the shape chosen above (cached)
     s2.set_measurements(Y, A)
     s2.init()
     s2.iterate(T_e2e)
@@ -245,6 +246,7 @@ def run_ours(args):
             "config": {"workload": "gaussian n=1000 q=1000 r=5 m=150 rho=10 (float32 A_k, 600 MB)",
                        "l2": "inputs larger than L2 (A 600 MB)", "iterations_per_step": 1,
                        "engine": desc.get("engine"),
+                       "task_shape": {k: desc.get(k) for k in ("grid", "inflight", "w_tasks", "g_tasks", "rows_per_piece")},
                        "rel_err_after": {"iterations": args.warmup + args.steps, "rel_err": rel_err}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
@@ -276,13 +278,14 @@ def run_c2(args):
     inst = DeviceGaussianInstance(**cfg)
     n, q, r, m, rho = cfg["n"], cfg["q"], cfg["r"], cfg["m"], cfg["rho"]
     stream = torch.cuda.Stream()
-    s = L.Solver(n, m, q, r, rho, stream=stream, profile=1, a_dtype=A_DTYPES[args.a_dtype])
-    desc = L.lrs_describe(s.h)
+    s = L.Solver(n, m, q, r, rho, stream=stream, profile=1, a_dtype=A_DTYPES[args.a_dtype],
+                 autotune=1)
     s.set_measurements(inst.Y, inst.A)
     inst.free()
     torch.cuda.empty_cache()
     s.init()
     s.iterate(args.warmup)
+    desc = L.lrs_describe(s.h)
     L.lrs_phase_times(s.h)
     with ClockSampler(0) as clk:
         torch.cuda.synchronize()

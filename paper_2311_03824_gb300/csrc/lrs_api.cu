@@ -489,7 +489,7 @@ lrs_status alloc_split(lrs_ctx* h, int nsm) {
 }
 
 // Task sizes the autotuner tries (KiB of A_k per task).
-constexpr int kTuneKib[3] = {128, 256, 512};
+constexpr int kTuneKib[4] = {128, 256, 512, 1024};
 
 // Problem tables (one per sweep mode) and seeds for `task_kib` KiB per task
 // and F columns in flight, uploaded to the device.

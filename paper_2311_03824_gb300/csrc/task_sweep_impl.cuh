@@ -145,6 +145,9 @@ __device__ __forceinline__ int ld_acquire_(const int* p) {
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void st_relaxed(int* p, int v) {
+  asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // ---- queue -----------------------------------------------------------------------
 // Publish n tasks (thread 0 of the consumers).  More tasks than the launch
@@ -159,6 +162,21 @@ __device__ __forceinline__ void push_tasks(const TaskQueue& Q, int k, int prob, 
   for (int i = 0; i < n; ++i) Q.tasks[t0 + i] = tdesc(k, prob, type, ph, i);
   __threadfence();
   for (int i = 0; i < n; ++i) st_release(&Q.seq[t0 + i], 1);
+}
+
+// Publish n tasks at tickets [t0, t0 + n) reserved earlier (thread 0 of the
+// consumers, after the barrier that ends the step): the descriptors, one
+// fence that also covers the CTA's writes ordered by that barrier, then the
+// flags.
+__device__ __forceinline__ void publish_reserved(const TaskQueue& Q, int t0, int k, int prob,
+                                                 int type, int ph, int n) {
+  if (t0 < 0 || t0 + n > Q.total) {
+    set_abort(&Q.ctr[3], Q.probs[prob].err);
+    return;
+  }
+  for (int i = 0; i < n; ++i) Q.tasks[t0 + i] = tdesc(k, prob, type, ph, i);
+  __threadfence();
+  for (int i = 0; i < n; ++i) st_relaxed(&Q.seq[t0 + i], 1);
 }
 
 // problem owning global column c (the table is ordered by col0)
@@ -552,6 +570,14 @@ __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int typ
   };
   const int tid = threadIdx.x, m = P.L.m;
   const bool project = P.mode != kModeInit;
+  const int te = P.tau_eff, lastph = last_phase(P);
+  // what follows is known now: admit the next column (the column is done) or
+  // the next pass's tasks, whose tickets thread 0 reserves at once so that the
+  // atomic's round trip overlaps the step
+  const bool admit = type == kTaskF || (type == kTaskW && P.mode == kModeLS) || ph >= lastph;
+  const int n_next = admit ? 0 : phase_tasks(P, ph + 1);
+  int t_res = -1;
+  if (tid == 0 && n_next > 0) t_res = atomicAdd(&Q.ctr[1], n_next);
   Ctx C;
   small_ctx(C, P, k, smem, cv);
   if (ET >= 2) {
@@ -563,7 +589,6 @@ __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int typ
     }
   }
   float* uout = P.uvec + static_cast<size_t>(k) * m;
-  const int te = P.tau_eff, lastph = last_phase(P);
   int next_type = -1;  // what to publish after this step
 
   if (type == kTaskW) {
@@ -655,17 +680,18 @@ __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int typ
     store_output_support(C, P, k);
     next_type = -2;
   }
-  // publish: all writes of this step first
-  __threadfence();
+  // publish: the barrier orders every write of this step before thread 0's
+  // fence (cumulative), which comes before the flags of the next tasks
   csync();
   if (tid == 0) {
     P.cnt[k] = 0;
-    if (next_type == -2 || ph >= lastph) {
+    if (admit) {
+      __threadfence();
       admit_next(Q);
     } else {
       const int nph = ph + 1;
       const int nt = next_type == kTaskNop ? kTaskNop : phase_type(P, nph);
-      push_tasks(Q, k, prob, nt, nph, phase_tasks(P, nph));
+      publish_reserved(Q, t_res, k, prob, nt, nph, n_next);
     }
   }
   csync();
@@ -831,13 +857,17 @@ __global__ void __launch_bounds__(kThreadsAll, R <= 6 ? 3 : 2) task_kernel(const
       prof[type == kTaskW ? 1 : 2] += c0 - c1;
       prof[8] += 1;
     }
-    // completion of the task; the last task of the pass runs the column step
-    __threadfence();
+    // completion of the task; the last task of the pass runs the column step.
+    // The barrier orders the CTA's writes of this task before thread 0's
+    // fence (cumulative) and count; the last one's second fence orders the
+    // other tasks' writes before the step reads them.
     csync();
     if (tid == 0) {
-      const int done = atomicAdd(&P.cnt[k], 1) + 1;
-      *T.bcast = done == phase_tasks(P, ph) ? 1 : 0;
       __threadfence();
+      const int done = atomicAdd(&P.cnt[k], 1) + 1;
+      const int last = done == phase_tasks(P, ph) ? 1 : 0;
+      if (last) __threadfence();
+      *T.bcast = last;
     }
     csync();
     if (*T.bcast) {
