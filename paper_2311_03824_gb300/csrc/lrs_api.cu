@@ -558,6 +558,7 @@ lrs_status alloc_task_engine(lrs_ctx* h) {
   const int kib_min = std::min(kib, kTuneKib[0]);
   int ncw_max = 1, n0_max = 1;
   int64_t total_max = 0;
+  const size_t wstride = static_cast<size_t>((m * R + 3) & ~3);  // as task_plan sets it
   for (int mode = 0; mode < 3; ++mode) {
     TaskProblem P{};
     P.L = h->L;
@@ -573,7 +574,7 @@ lrs_status alloc_task_engine(lrs_ctx* h) {
   h->t_total_max = total_max;
   h->seed_stride = q * static_cast<size_t>(n0_max);
   lrs_status st = LRS_OK;
-  if ((st = dalloc(&h->tWk, q * m * R, h->stream)) || (st = dalloc(&h->tWp, q * ncw_max * m * R, h->stream)) ||
+  if ((st = dalloc(&h->tWk, q * wstride, h->stream)) || (st = dalloc(&h->tWp, q * ncw_max * wstride, h->stream)) ||
       (st = dalloc(&h->tGi, q * 16 * 16, h->stream)) || (st = dalloc(&h->tu, q * m, h->stream)) ||
       (st = dalloc(&h->tg, q * ns, h->stream)) || (st = dalloc(&h->tsupj, q * rho1, h->stream)) ||
       (st = dalloc(&h->tsupv, q * rho1, h->stream)) || (st = dalloc(&h->tnsup, q, h->stream)) ||

@@ -113,8 +113,8 @@ struct TaskProblem {
   float* H;             // q x n
   int* err;
   // per-column scratch
-  float* Wk;            // q x m x R
-  float* Wp;            // q x ncw x m x R partial W per column chunk
+  float* Wk;            // q x wstride (m x R)
+  float* Wp;            // q x ncw x wstride: partial W per column chunk
   double* Gi;           // q x kMaxR x kMaxR  G^{-1} (FP64)
   float* uvec;          // q x m  vector of the next A^T pass
   float* g;             // q x ns result of the IHT pass
@@ -130,6 +130,8 @@ struct TaskProblem {
   int TBW, ncw;         // tiles per W task, W column chunks
   int col0;             // index of this problem's first column in the launch
   int tasks_per_col;
+  int wstride;          // floats per column of Wk and per column chunk of Wp (m R rounded
+                        // up to 4: every block starts on a 16-byte boundary)
 };
 
 struct TaskQueue {

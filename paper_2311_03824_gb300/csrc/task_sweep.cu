@@ -64,7 +64,7 @@ int task_rows_per_piece(int et, int m, int piece_cap) {
   return round8((m + nrc - 1) / nrc);
 }
 
-void task_plan(TaskProblem& P, int /*R*/, size_t task_bytes, int rp) {
+void task_plan(TaskProblem& P, int R, size_t task_bytes, int rp) {
   const GaussLayout& L = P.L;
   const int m = L.m, eb = elem_bytes(L.et), ntile = L.ns / kTW;
   P.rp = rp;
@@ -81,6 +81,7 @@ void task_plan(TaskProblem& P, int /*R*/, size_t task_bytes, int rp) {
   int tot = 0;
   for (int ph = 0; ph <= last_phase(P); ++ph) tot += phase_tasks(P, ph);
   P.tasks_per_col = tot;
+  P.wstride = (m * R + 3) & ~3;
 }
 
 size_t task_smem_bytes(int R, int /*et*/, int m_max, int ns_max, int rho_max, int stages,

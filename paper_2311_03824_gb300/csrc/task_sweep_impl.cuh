@@ -50,7 +50,7 @@ __host__ __device__ inline TCarve tcarve(int R, int m, int ns, int rho, int stag
   TCarve c;
   size_t o = 0;
   rho = rho > 0 ? rho : 1;
-  c.bars = o;  o += a16(8 * (2 * kMaxStages + 4));
+  c.bars = o;  o += a16(8 * (2 * kMaxStages + 6));  // ring, task slots, step copies
   c.task = o;  o += a16(2 * 8);
   c.stage = a16(static_cast<size_t>(piece_bytes) + static_cast<size_t>(kTW) * R * 4);
   c.ring = o;  o += c.stage * stages;
@@ -281,7 +281,7 @@ __device__ __forceinline__ void consume_w(TCtx& T, const TaskProblem& P, int k, 
     }
     release_piece(T);
   }
-  float* out = P.Wp + (static_cast<size_t>(k) * P.ncw + cc) * m * R;
+  float* out = P.Wp + (static_cast<size_t>(k) * P.ncw + cc) * P.wstride;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     const int i = wid * RBw + 4 * t + ro;
@@ -402,21 +402,35 @@ __device__ __forceinline__ void small_ctx(Ctx& C, const TaskProblem& P, int k, u
 
 // load y_k, W_k, G^{-1} (optional) and the support into shared memory
 enum SupportSource : int { kSupNone = 0, kSupInput = 1, kSupState = 2 };
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async;" ::: "memory");
+}
+
 // y_k, W_k, G^{-1} (optional), the support and (optional) the IHT pass result
-// g into shared memory; all loads are issued together (one round trip to L2).
+// g into shared memory.  W_k, G^{-1} and g (16-byte aligned blocks) come by
+// TMA bulk copies that thread 0 issues while the threads load the rest; the
+// proxy fence orders this CTA's earlier generic accesses to those buffers
+// (and the other CTAs' writes it has acquired) before the copies.
 template <int R>
 __device__ __forceinline__ void load_column(Ctx& C, const TaskProblem& P, int k, bool with_w,
-                                            bool with_gi, int source, bool with_g = false) {
+                                            bool with_gi, int source, bool with_g,
+                                            uint64_t* sbar, unsigned& sphase, int* abort) {
   const int m = C.m, tid = threadIdx.x, rho = C.rho, ns = P.L.ns, n = P.L.n;
+  const bool bulk = with_w || with_gi || with_g;
+  if (bulk) {
+    fence_proxy_async();
+    csync();
+    if (tid == 0) {
+      const unsigned bw = with_w ? static_cast<unsigned>(P.wstride) * 4u : 0u;
+      const unsigned bgi = with_gi ? static_cast<unsigned>(kMaxR * kMaxR * 8) : 0u;
+      const unsigned bg = with_g ? static_cast<unsigned>(ns) * 4u : 0u;
+      mbar_arrive_expect_tx(sbar, bw + bgi + bg);
+      if (bw) bulk_copy_g2s(C.W, P.Wk + static_cast<size_t>(k) * P.wstride, bw, sbar);
+      if (bgi) bulk_copy_g2s(C.Gi, P.Gi + static_cast<size_t>(k) * kMaxR * kMaxR, bgi, sbar);
+      if (bg) bulk_copy_g2s(C.gs, P.g + static_cast<size_t>(k) * ns, bg, sbar);
+    }
+  }
   for (int i = tid; i < m; i += kNT) C.yv[i] = __ldcg(P.y + static_cast<size_t>(k) * m + i);
-  if (with_w)
-    for (int t = tid; t < m * R; t += kNT) C.W[t] = __ldcg(P.Wk + static_cast<size_t>(k) * m * R + t);
-  if (with_gi)
-    for (int t = tid; t < kMaxR * kMaxR; t += kNT)
-      C.Gi[t] = __ldcg(P.Gi + static_cast<size_t>(k) * kMaxR * kMaxR + t);
-  if (with_g)
-    for (int j = tid; j < ns; j += kNT)
-      C.gs[j] = j < n ? __ldcg(P.g + static_cast<size_t>(k) * ns + j) : 0.f;
   for (int j = tid; j < ns; j += kNT) C.sl[j] = 0.f;
   if (source == kSupState) {
     for (int e = tid; e < rho; e += kNT) {
@@ -448,7 +462,11 @@ __device__ __forceinline__ void load_column(Ctx& C, const TaskProblem& P, int k,
   } else if (tid == 0) {
     *C.nloc = 0;
   }
+  if (bulk && tid == 0) wait_bar(sbar, sphase, C.err, abort);  // on expiry the launch aborts
+  if (bulk) sphase ^= 1u;
   csync();
+  if (with_g)
+    for (int j = n + tid; j < ns; j += kNT) C.gs[j] = 0.f;
   for (int e = tid; e < *C.nloc; e += kNT) C.sl[C.sup_j[e]] = C.sup_v[e];
   csync();
 }
@@ -557,7 +575,8 @@ __device__ __forceinline__ void store_output_support(const Ctx& C, const TaskPro
 // Thread 0 publishes what follows.
 template <int R, int ET>
 __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int type,
-                            unsigned char* smem, const TCarve& cv) {
+                            unsigned char* smem, const TCarve& cv, uint64_t* sbar,
+                            unsigned& sphase) {
   const TaskProblem& P = Q.probs[prob];
   long long* sprof = reinterpret_cast<long long*>(smem + cv.prof);
   long long tlast = clock64();
@@ -593,13 +612,13 @@ __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int typ
 
   if (type == kTaskW) {
     // W_k = sum of the column-chunk partials (fixed order), Gram, Cholesky
-    load_column<R>(C, P, k, false, false, kSupInput);
+    load_column<R>(C, P, k, false, false, kSupInput, false, sbar, sphase, Q.ctr + 3);
     for (int t = tid; t < m * R; t += kNT) {
       float s = 0.f;
       for (int cc = 0; cc < P.ncw; ++cc)
-        s += __ldcg(P.Wp + (static_cast<size_t>(k) * P.ncw + cc) * m * R + t);
+        s += __ldcg(P.Wp + (static_cast<size_t>(k) * P.ncw + cc) * P.wstride + t);
       C.W[t] = s;
-      P.Wk[static_cast<size_t>(k) * m * R + t] = s;
+      P.Wk[static_cast<size_t>(k) * P.wstride + t] = s;
     }
     csync();
     gram_factor<R>(C);
@@ -622,7 +641,7 @@ __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int typ
     const bool zero_start = (P.mode == kModeInit && ph == 0);
     const int stop_in = zero_start ? 0 : __ldcg(P.stop + k);
     load_column<R>(C, P, k, project, project, zero_start ? kSupNone : kSupState,
-                   type != kTaskNop);
+                   type != kTaskNop, sbar, sphase, Q.ctr + 3);
     if (zero_start && tid == 0) P.stop[k] = 0;
     const int sweep = P.mode == kModeInit ? ph : ph - 1;  // 0-based IHT sweep just run
     bool stopped = stop_in != 0 || type == kTaskNop;
@@ -676,7 +695,7 @@ __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int typ
     }
     mark(13);
   } else {  // kTaskF: H row written by the tasks; outputs
-    load_column<R>(C, P, k, false, false, kSupState);
+    load_column<R>(C, P, k, false, false, kSupState, false, sbar, sphase, Q.ctr + 3);
     store_output_support(C, P, k);
     next_type = -2;
   }
@@ -746,6 +765,7 @@ __global__ void __launch_bounds__(kThreadsAll, R <= 6 ? 3 : 2) task_kernel(const
       mbar_init(&T.tfull[s], 1);
       mbar_init(&T.tempty[s], kNW);
     }
+    mbar_init(bars + 2 * kMaxStages + 4, 1);  // the steps' bulk copies
   }
   __syncthreads();
 
@@ -798,6 +818,8 @@ __global__ void __launch_bounds__(kThreadsAll, R <= 6 ? 3 : 2) task_kernel(const
   }
 
   // ---------------- consumer warps ----------------
+  uint64_t* sbar = bars + 2 * kMaxStages + 4;
+  unsigned sphase = 0;
   for (unsigned it = 0;; ++it) {
     const unsigned ts = it & 1u, use = it >> 1;
     // one thread waits for the descriptor, so that leaving is uniform
@@ -871,7 +893,7 @@ __global__ void __launch_bounds__(kThreadsAll, R <= 6 ? 3 : 2) task_kernel(const
     }
     csync();
     if (*T.bcast) {
-      column_step<R, ET>(Q, prob, k, ph, type, smem, cv);
+      column_step<R, ET>(Q, prob, k, ph, type, smem, cv, sbar, sphase);
       c1 = clock64();
       if (Q.prof && tid == 0) {
         prof[type == kTaskW ? 4 : type == kTaskF ? 6 : 5] += c1 - c0;
