@@ -38,6 +38,13 @@ A_DTYPES = {"fp32": 0, "bf16": 1, "fp8_hi": 2, "fp8_hilo": 3}
 A_BYTES = {"fp32": 4.0, "bf16": 2.0, "fp8_hi": 1.0, "fp8_hilo": 2.0}
 
 
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one task_kernel
+# launch of the n=1000, q=1000, r=5, m=150, rho=10 iteration (the tuned shape:
+# 3 W tasks and 2 A^T tasks per pass), from one ncu --set full capture of the
+# kernel as it stands; to be re-taken whenever the kernel changes.
+TASK_KERNEL_DRAM_BYTES = 3.621331e9 + 29.446912e6
+
 def b_alg_per_col_iter(n, m, r, rho, a_bytes=4, scales=0):
     """Algorithmic HBM bytes of one column-iteration: A_k once (plus its row
     scales for the FP8 forms), y_k, h_k write, s_k (index + value) and b_k."""
@@ -249,7 +256,9 @@ def run_ours(args):
                        "task_shape": {k: desc.get(k) for k in ("grid", "inflight", "w_tasks", "g_tasks", "rows_per_piece")},
                        "rel_err_after": {"iterations": args.warmup + args.steps, "rel_err": rel_err}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / peak,
+                         "traffic": TASK_KERNEL_DRAM_BYTES if desc.get("engine") == "task" else None,
+                         "peak_kind": peak_kind,
                          "kernel": "task_kernel" if desc.get("engine") == "task" else "sweep_kernel",
                          "kernel_ms": sweep_ms, "bytes_per_launch": bytes_launch},
             "phases_ms_per_step": {k: ph[k] / max(1, ph["iters"]) for k in ("sweep_ms", "grad_ms", "qr_ms")},
