@@ -8,11 +8,14 @@ r=5, m=150, rho=10 (A_k resident in HBM, 600 MB > L2).  Inputs are synthetic
 and seeded (lrsgen).  One JSON line is printed by rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c1|c2] [--a-dtype fp32|bf16|fp8_hi|fp8_hilo]
+                  [--workload c1|c2|c3|c4] [--a-dtype fp32|bf16|fp8_hi|fp8_hilo]
 
 --workload c2 measures the precision forms on the Gaussian problem n=4096,
 q=2048, r=10, m=512, rho=40 (A_k drawn on the device, 17.2 GB in float32):
 device-timed column-iterations/s and the final relative error against X*.
+--workload c3 measures the 2D-DFT operator on 128 x 128 complex frames
+(q=256, r=6, m=2048, rho=82): column-iterations/s and the sweep kernel's FFT
+and sparse-DFT flops against the FP32 FMA peak (the sweep is ALU-bound).
 --workload c4 runs the serving mix (--requests problems, 70 % Gaussian with
 BF16-stored A_k, 30 % DFT, T=100 each): first all at once to measure the
 saturation throughput, then with Poisson arrivals at 0.8 x that rate; p50 /
@@ -20,6 +23,7 @@ p99 latency (arrival to completion, input generation included).
 """
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -334,6 +338,111 @@ def run_c2(args):
     return 0
 
 
+def fourier_flops_per_col_iter(n, m, rho, tau=3):
+    """Flops of one column-iteration of the 2D-DFT sweep: tau inverse 2D FFTs
+    of the zero-filled frame (A^H u of each IHT pass, 5 n log2 n each) and
+    2 tau + 1 direct sparse DFTs at the m sampled frequencies (A g_G and A s
+    of each pass, A s before the LS; one complex multiply-add, 8 flops, per
+    sample and support entry).  The r forward FFTs of U and r inverse FFTs of
+    the gradient per iteration are shared by all frames and not counted."""
+    return tau * 5.0 * n * math.log2(n) + (2 * tau + 1) * 8.0 * m * rho
+
+
+def fp32_peak_tflops(sm_mhz, nsm=152):
+    """FP32 FMA peak from unit counts and the clock: 128 FP32 lanes per SM,
+    2 flops per FMA."""
+    return nsm * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def run_c3(args):
+    """The 2D-DFT operator: 128 x 128 complex frames (n = 16384), q = 256,
+    r = 6, m = 2048 sampled frequencies (variable density), rho = 82 (blobs)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2311_03824_gb300 import build
+    build.build()
+    from paper_2311_03824_gb300 import lrs as L
+    from lrsgen import C3, FourierInstance
+    cfg = {k: v for k, v in C3.items() if k != "T"}
+    inst = FourierInstance(**cfg)
+    n, q, r, m, rho = inst.n, inst.q, inst.r, inst.m, inst.rho
+    Y = np.ascontiguousarray(inst.Y, np.complex64)
+    masks = np.ascontiguousarray(inst.masks, np.int32)
+    stream = torch.cuda.Stream()
+    s = L.Solver(n, m, q, r, rho, kind=L.LRS_OP_DFT2D_MASK, nx=inst.nx, ny=inst.ny,
+                 stream=stream, profile=1)
+    s.set_measurements(Y, masks)
+    s.init()
+    s.iterate(args.warmup)
+    L.lrs_phase_times(s.h)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.iterate(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ph = L.lrs_phase_times(s.h)
+    X = s.X()
+    rel_err = float(np.linalg.norm(X - inst.Xstar) / np.linalg.norm(inst.Xstar))
+    s.close()
+    # end to end: host buffers in, initialisation, iterations, outputs back
+    T_e2e = max(1, args.e2e_iters)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s2 = L.Solver(n, m, q, r, rho, kind=L.LRS_OP_DFT2D_MASK, nx=inst.nx, ny=inst.ny,
+                  stream=stream)
+    s2.set_measurements(Y, masks)
+    s2.init()
+    s2.iterate(T_e2e)
+    U_, B_, Si_, Sv_ = s2.get()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    s2.close()
+    clocks = clk.summary()
+    sweep_ms = ph["sweep_ms"] / max(1, ph["iters"])
+    flops_launch = q * fourier_flops_per_col_iter(n, m, rho)
+    achieved = flops_launch / (sweep_ms / 1000.0) / 1e12
+    peak = fp32_peak_tflops(clocks.get("sm_max_mhz") or 2070.0)
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle.altgdmin_lrs as O
+        ks = np.arange(32)
+        op = O.FourierOperator(inst.masks[ks], inst.nx, inst.ny)
+        st, _, _, _ = O.init_alg1(op, inst.Y[ks], r, rho)
+        t0 = time.perf_counter()
+        O.iterate_alg1(op, inst.Y[ks], st, rho)
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(ks) / dt, "unit": "column-iters/s", "cores": cores_used(),
+               "kind": "oracle",
+               "sample": f"one GDmin iteration of the FP64 oracle on the first {len(ks)} frames "
+                         f"of the same instance, after its own initialisation ({dt:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": q * args.steps / (ms / 1000.0), "unit": "column-iters/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+        "data": "synthetic",
+        "config": {"workload": "2D-DFT 128x128 frames q=256 r=6 m=2048 rho=82 (variable-density masks, blob supports)",
+                   "l2": "inputs (16 MB) L2-resident: the sweep is bound by FP32 ALU and shared memory",
+                   "rel_err_after": {"iterations": args.warmup + args.steps, "rel_err": rel_err}},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_kind": "FP32 FMA rate from unit counts and the maximum SM clock",
+                     "kernel": "fsweep_kernel", "kernel_ms": sweep_ms,
+                     "flops_per_launch": flops_launch},
+        "phases_ms_per_step": {k: ph[k] / max(1, ph["iters"]) for k in ("sweep_ms", "grad_ms", "qr_ms")},
+        "e2e": {"value": q * T_e2e / t_e2e, "unit": "column-iters/s",
+                "h2d_bytes_per_step": Y.nbytes + masks.nbytes,
+                "d2h_bytes_per_step": U_.nbytes + B_.nbytes + Si_.nbytes + Sv_.nbytes,
+                "iterations": T_e2e,
+                "includes": "lrs_set_measurements(host) + lrs_init + lrs_iterate + lrs_get(host)"},
+        "gpu_launches": 11 * args.steps, "clocks": clocks, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_c4(args):
     """Serving mix: saturation throughput, then Poisson arrivals at 0.8 x."""
     import torch
@@ -375,7 +484,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-iters", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c1", choices=["c1", "c2", "c4"])
+    ap.add_argument("--workload", default="c1", choices=["c1", "c2", "c3", "c4"])
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--a-dtype", default="fp32", choices=list(A_DTYPES))
@@ -386,6 +495,8 @@ def main():
         return run_reference(args)
     if args.workload == "c2":
         return run_c2(args)
+    if args.workload == "c3":
+        return run_c3(args)
     if args.workload == "c4":
         return run_c4(args)
     return run_ours(args)

@@ -1257,20 +1257,27 @@ int fourier_init(FourierSolver* F, std::string* msg) {
   return fourier_check_error(F, msg);
 }
 
-int fourier_iterate(FourierSolver* F, int iters, std::string* msg) {
+// evs (optional): 4 events per iteration, recorded before FU = F2 U, after
+// the per-frame sweep, after the gradient and after the QR.
+int fourier_iterate(FourierSolver* F, int iters, std::string* msg, cudaEvent_t* evs) {
   const int n = F->g.n, r = F->r;
   for (int i = 0; i < iters; ++i) {
+    cudaEvent_t* ev = evs ? evs + 4 * static_cast<size_t>(i) : nullptr;
+    if (ev) cudaEventRecord(ev[0], F->s);
     cudaError_t e = fft_frames(F, F->U, F->FU, r, false);            // FU = F2 U
     if (e == cudaSuccess) e = launch_fsweep(F, kModeIter, F->tau);   // per-frame work
+    if (ev) cudaEventRecord(ev[1], F->s);
     kspace_kernel<<<(n + 255) / 256, 256, 0, F->s>>>(n, F->m, r, F->iptr, F->ilist, F->RES, F->B, F->K);
     if (e == cudaSuccess) e = fft_frames(F, F->K, F->grad, r, true);  // grad = F2^H K
     if (e == cudaSuccess && F->t == 0) {
       cgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, F->grad, nullptr, nullptr, nullptr, F->part);
       ceta_kernel<<<1, 32, 0, F->s>>>(r, F->nblk, F->part, F->c_eta, F->eta);
     }
+    if (ev) cudaEventRecord(ev[2], F->s);
     // Z = U - eta grad, then complex Cholesky-QR2
     cgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, F->U, F->grad, F->eta, F->Z, F->part);
     if (e == cudaSuccess) e = ccholqr2(F, F->Z, F->U);
+    if (ev) cudaEventRecord(ev[3], F->s);
     if (e != cudaSuccess) {
       *msg = cudaGetErrorString(e);
       return 4;

@@ -28,7 +28,7 @@ void fourier_destroy(FourierSolver* F);
 int fourier_set_measurements(FourierSolver* F, const void* y, const void* mask, int mem_kind,
                              std::string* msg);
 int fourier_init(FourierSolver* F, std::string* msg);
-int fourier_iterate(FourierSolver* F, int iters, std::string* msg);
+int fourier_iterate(FourierSolver* F, int iters, std::string* msg, cudaEvent_t* evs);
 int fourier_get(FourierSolver* F, void* U, void* B, int* S_idx, void* S_val, int mem_kind);
 int fourier_set_state(FourierSolver* F, const void* U, const void* B, const int* S_idx,
                       const void* S_val, int t, double eta, int mem_kind);
@@ -901,11 +901,32 @@ lrs_status lrs_iterate(lrs_t h, int32_t iters, double* err_log) {
   if (err_log && !h->Xref) return fail(LRS_ERR_ARG, "lrs_iterate: err_log needs lrs_set_reference");
   if (h->F) {
     if (err_log) return fail(LRS_ERR_UNSUPPORTED, "lrs_iterate: no error log for the DFT operator");
+    const bool fprof = h->opt.profile != 0;
+    if (fprof) {
+      while (h->ev.size() < 4 * static_cast<size_t>(iters)) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e));
+        h->ev.push_back(e);
+      }
+    }
     std::string msg;
-    const int st = fourier_iterate(h->F, iters, &msg);
+    const int st = fourier_iterate(h->F, iters, &msg, fprof ? h->ev.data() : nullptr);
     h->t = fourier_t(h->F);
     h->state = kIterating;
     if (st) return fail(static_cast<lrs_status>(st), "lrs_iterate: " + msg);
+    if (fprof && iters > 0) {  // the stream is synchronised by the error check above
+      for (int i = 0; i < iters; ++i) {
+        float a = 0, b = 0, c = 0;
+        cudaEvent_t* evs = &h->ev[4 * static_cast<size_t>(i)];
+        CUDA_TRY(cudaEventElapsedTime(&a, evs[0], evs[1]));
+        CUDA_TRY(cudaEventElapsedTime(&b, evs[1], evs[2]));
+        CUDA_TRY(cudaEventElapsedTime(&c, evs[2], evs[3]));
+        h->phase_ms[0] += a;
+        h->phase_ms[1] += b;
+        h->phase_ms[2] += c;
+      }
+      h->phase_iters += iters;
+    }
     return LRS_OK;
   }
   if (h->opt.autotune && h->engine == 2 && !h->tuned && iters > 0) {
