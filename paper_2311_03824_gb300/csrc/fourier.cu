@@ -721,22 +721,28 @@ __global__ void cchol_fin_kernel(int r, int nblk, const double2* __restrict__ pa
   __shared__ double2 N[kMaxR * kMaxR], Lw[kMaxR * kMaxR], Li[kMaxR * kMaxR];
   __shared__ double iL[kMaxR];
   __shared__ int okf;
-  const int lane = threadIdx.x;
-  for (int t = lane; t < r * r; t += 32) {
+  // the partials of each entry: one warp per entry, lanes over the blocks,
+  // butterfly sum (fixed order); then warp 0 factors
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int t = threadIdx.x >> 5; t < r * r; t += nw) {
     const int a = t / r, b = t - a * r;
-    if (b <= a) {
-      double sx = 0, sy = 0;
-      for (int k = 0; k < nblk; ++k) {
-        const double2 v = part[static_cast<size_t>(k) * r * r + a * r + b];
-        sx += v.x;
-        sy += v.y;
-      }
+    if (b > a) continue;
+    double sx = 0, sy = 0;
+    for (int k = lane; k < nblk; k += 32) {
+      const double2 v = part[static_cast<size_t>(k) * r * r + a * r + b];
+      sx += v.x;
+      sy += v.y;
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) {
       // N[a][b] = sum conj(x_a) x_b ; N[b][a] = conj(N[a][b])
       N[a * kMaxR + b] = make_double2(sx, sy);
       N[b * kMaxR + a] = make_double2(sx, -sy);
     }
   }
-  __syncwarp();
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
   // X^H X = N^T?  (X^H X)[i][j] = sum conj(x_i) x_j = N[i][j]: factor N = L L^H
   if (lane == 0) {
     int ok = 1;
@@ -1166,10 +1172,10 @@ static cudaError_t ccholqr2(FourierSolver* F, const float2* Zin, float2* Uout) {
   const int n = F->g.n, r = F->r;
   const unsigned nb = static_cast<unsigned>((static_cast<size_t>(n) * r + 255) / 256);
   cgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, Zin, nullptr, nullptr, nullptr, F->part);
-  cchol_fin_kernel<<<1, 32, 0, F->s>>>(r, F->nblk, F->part, F->rfac, F->err);
+  cchol_fin_kernel<<<1, 256, 0, F->s>>>(r, F->nblk, F->part, F->rfac, F->err);
   capply_kernel<<<nb, 256, 0, F->s>>>(n, r, Zin, F->rfac, F->Z2);
   cgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, F->Z2, nullptr, nullptr, nullptr, F->part);
-  cchol_fin_kernel<<<1, 32, 0, F->s>>>(r, F->nblk, F->part, F->rfac + r * r, F->err);
+  cchol_fin_kernel<<<1, 256, 0, F->s>>>(r, F->nblk, F->part, F->rfac + r * r, F->err);
   capply_kernel<<<nb, 256, 0, F->s>>>(n, r, F->Z2, F->rfac + r * r, Uout);
   return cudaGetLastError();
 }
@@ -1219,10 +1225,10 @@ int fourier_init(FourierSolver* F, std::string* msg) {
   const unsigned nb = static_cast<unsigned>((nr + 255) / 256);
   auto dqr = [&](const double2* Zin, double2* Uout, float2* Uf) {
     cdgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, Zin, F->part);
-    cchol_fin_kernel<<<1, 32, 0, F->s>>>(r, F->nblk, F->part, F->rfac, F->err);
+    cchol_fin_kernel<<<1, 256, 0, F->s>>>(r, F->nblk, F->part, F->rfac, F->err);
     cdapply_kernel<<<nb, 256, 0, F->s>>>(n, r, Zin, F->rfac, Td, nullptr);
     cdgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, Td, F->part);
-    cchol_fin_kernel<<<1, 32, 0, F->s>>>(r, F->nblk, F->part, F->rfac + r * r, F->err);
+    cchol_fin_kernel<<<1, 256, 0, F->s>>>(r, F->nblk, F->part, F->rfac + r * r, F->err);
     cdapply_kernel<<<nb, 256, 0, F->s>>>(n, r, Td, F->rfac + r * r, Uout, Uf);
   };
   if (e == cudaSuccess) dqr(Zd, Ud, nullptr);

@@ -126,23 +126,30 @@ __global__ void __launch_bounds__(256) gram_part_kernel(int n, int r, const floa
   if (a < r && b <= a) part[static_cast<size_t>(blockIdx.x) * r * r + a * r + b] = acc;
 }
 
-// Sum the partial Grams (fixed block order), Cholesky G = L L^T, and write
-// Rinv = L^{-T} (upper triangular, r x r row-major, FP64).  One warp.
+// Sum the partial Grams (fixed order: lanes over blocks, then a butterfly),
+// Cholesky G = L L^T, and write Rinv = L^{-T} (upper triangular, r x r
+// row-major, FP64).  One block of 256 threads; warp 0 factors.
 __global__ void chol_fin_kernel(int r, int nblk, const double* __restrict__ part,
                                 double* __restrict__ Rinv, int* err) {
   __shared__ double G[kMaxR * kMaxR], L[kMaxR * kMaxR], Li[kMaxR * kMaxR], iL[kMaxR];
-  for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+  // the partials of each entry: one warp per entry, lanes over the blocks,
+  // butterfly sum (fixed order); then warp 0 factors
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int t = threadIdx.x >> 5; t < r * r; t += nw) {
     const int a = t / r, b = t - a * r;
-    if (b <= a) {
-      double s = 0.0;
-      for (int k = 0; k < nblk; ++k) s += part[static_cast<size_t>(k) * r * r + a * r + b];
+    if (b > a) continue;
+    double s = 0.0;
+    for (int k = lane; k < nblk; k += 32) s += part[static_cast<size_t>(k) * r * r + a * r + b];
+    s = warp_sum(s);
+    if (lane == 0) {
       G[a * kMaxR + b] = s;
       G[b * kMaxR + a] = s;
     }
   }
-  __syncwarp();
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
   if (!chol_inverse_warp(G, L, Li, iL, r, kMaxR) && threadIdx.x == 0) report_error(err, kErrNotSPD, -1);
-  for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+  for (int t = lane; t < r * r; t += 32) {
     const int a = t / r, b = t - a * r;
     Rinv[a * r + b] = Li[b * kMaxR + a];
   }
@@ -445,10 +452,10 @@ cudaError_t dcholqr2(const GlobalWork& g, const double* Zin, double* Ztmp, doubl
   const size_t tot = static_cast<size_t>(g.n) * g.r;
   const unsigned nb = static_cast<unsigned>((tot + 255) / 256);
   dgram_part_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, Zin, g.part);
-  chol_fin_kernel<<<1, 32, 0, s>>>(g.r, g.nblk, g.part, R1, err);
+  chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R1, err);
   dapply_kernel<<<nb, 256, 0, s>>>(g.n, g.r, Zin, R1, Ztmp, nullptr, nullptr, 0);
   dgram_part_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, Ztmp, g.part);
-  chol_fin_kernel<<<1, 32, 0, s>>>(g.r, g.nblk, g.part, R2, err);
+  chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R2, err);
   dapply_kernel<<<nb, 256, 0, s>>>(g.n, g.r, Ztmp, R2, Uout, Uf, Uf ? g.Upad : nullptr, g.rpad);
   return cudaGetLastError();
 }
@@ -510,9 +517,9 @@ cudaError_t cholqr2(const GlobalWork& g, const float* Zin, float* Uout, int* err
   double* R1 = g.small;
   double* R2 = g.small + rr;
   gram_part_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, Zin, nullptr, nullptr, nullptr, g.part);
-  chol_fin_kernel<<<1, 32, 0, s>>>(g.r, g.nblk, g.part, R1, err);
+  chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R1, err);
   apply_rinv_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, Zin, R1, g.Z, g.part);
-  chol_fin_kernel<<<1, 32, 0, s>>>(g.r, g.nblk, g.part, R2, err);
+  chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R2, err);
   apply_rinv_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, g.Z, R2, Uout, nullptr, g.Upad, g.rpad);
   return cudaGetLastError();
 }
@@ -531,9 +538,9 @@ cudaError_t cholqr2_into(int n, int r, const float* Z, float* Q, float* tmp, dou
   double* R1 = rfac;
   double* R2 = rfac + r * r;
   gram_part_kernel<<<nblk, 256, 0, s>>>(n, r, Z, nullptr, nullptr, nullptr, part);
-  chol_fin_kernel<<<1, 32, 0, s>>>(r, nblk, part, R1, err);
+  chol_fin_kernel<<<1, 256, 0, s>>>(r, nblk, part, R1, err);
   apply_rinv_kernel<<<nblk, 256, 0, s>>>(n, r, Z, R1, tmp, part);
-  chol_fin_kernel<<<1, 32, 0, s>>>(r, nblk, part, R2, err);
+  chol_fin_kernel<<<1, 256, 0, s>>>(r, nblk, part, R2, err);
   apply_rinv_kernel<<<nblk, 256, 0, s>>>(n, r, tmp, R2, Q, nullptr);
   return cudaGetLastError();
 }
@@ -545,10 +552,10 @@ cudaError_t qr_step(const GlobalWork& g, float* U, const double* eta_dev, int* e
   double* R2 = g.small + rr;
   // Z = U - eta grad, Gram(Z)
   gram_part_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, U, g.grad, eta_dev, g.Z, g.part);
-  chol_fin_kernel<<<1, 32, 0, s>>>(g.r, g.nblk, g.part, R1, err);
+  chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R1, err);
   // Q1 = Z R1^{-1} (into grad's buffer: grad is no longer needed), Gram(Q1)
   apply_rinv_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, g.Z, R1, g.grad, g.part);
-  chol_fin_kernel<<<1, 32, 0, s>>>(g.r, g.nblk, g.part, R2, err);
+  chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R2, err);
   apply_rinv_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, g.grad, R2, U, nullptr, g.Upad, g.rpad);
   return cudaGetLastError();
 }
