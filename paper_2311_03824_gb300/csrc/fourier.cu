@@ -664,22 +664,33 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
   }
 }
 
-// K[l][w] = sum over the (k, i) with mask_k[i] = w (fixed order) of
-// res_k[i] conj(b_k[l])
+// K[l][w] = sum over the (k, i) with mask_k[i] = w of res_k[i] conj(b_k[l]).
+// One warp per frequency w (a frequency every frame samples has q entries,
+// most have a few): lanes take entries lane, lane + 32, ... of its list, then
+// a butterfly per component (fixed order).
 __global__ void kspace_kernel(int n, int m, int r, const int* __restrict__ ptr,
                               const int* __restrict__ list, const float2* __restrict__ RES,
                               const float2* __restrict__ B, float2* __restrict__ K) {
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= n) return;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= n) return;  // uniform over the warp
   float2 acc[kMaxR];
+#pragma unroll
   for (int l = 0; l < kMaxR; ++l) acc[l] = make_float2(0.f, 0.f);
-  for (int t = ptr[w]; t < ptr[w + 1]; ++t) {
+  for (int t = ptr[w] + lane; t < ptr[w + 1]; t += 32) {
     const int ki = list[t];
     const int k = ki / m;
     const float2 rv = RES[ki];
-    for (int l = 0; l < r; ++l) acc[l] = cfma(rv, cconj(B[static_cast<size_t>(k) * r + l]), acc[l]);
+#pragma unroll
+    for (int l = 0; l < kMaxR; ++l)
+      if (l < r) acc[l] = cfma(rv, cconj(B[static_cast<size_t>(k) * r + l]), acc[l]);
   }
-  for (int l = 0; l < r; ++l) K[static_cast<size_t>(l) * n + w] = acc[l];
+#pragma unroll
+  for (int l = 0; l < kMaxR; ++l) {
+    if (l < r) {
+      const float x = warp_sum(acc[l].x), y = warp_sum(acc[l].y);
+      if (lane == 0) K[static_cast<size_t>(l) * n + w] = make_float2(x, y);
+    }
+  }
 }
 
 // ---- complex column-reduced ops on r x n column-major matrices (l-major) ----
@@ -703,15 +714,31 @@ __global__ void cgram_part_kernel(int n, int r, const float2* __restrict__ X,
     __syncthreads();
   }
   const float2* Y = Xout ? Xout : X;
-  const int t = threadIdx.x, a = t / kMaxR, b = t - (t / kMaxR) * kMaxR;
-  if (a >= r || b > a) return;
+  // entry p of the lower triangle (row-major) and row group g: the block's
+  // rows g, g + ng, ... ; the groups are added in order afterwards
+  __shared__ double2 red[256];
+  const int npair = r * (r + 1) / 2, ng = max(1, static_cast<int>(blockDim.x) / npair);
+  const int t = threadIdx.x, p = t % npair, g = t / npair;
+  int a = 0, b = p;
+  while (b > a) b -= ++a;
   double sx = 0, sy = 0;
-  for (int j = lo; j < hi; ++j) {
-    const float2 xa = Y[static_cast<size_t>(a) * n + j], xb = Y[static_cast<size_t>(b) * n + j];
-    sx += static_cast<double>(xa.x) * xb.x + static_cast<double>(xa.y) * xb.y;   // conj(x_a) x_b
-    sy += static_cast<double>(xa.x) * xb.y - static_cast<double>(xa.y) * xb.x;
+  if (g < ng) {
+    for (int j = lo + g; j < hi; j += ng) {
+      const float2 xa = Y[static_cast<size_t>(a) * n + j], xb = Y[static_cast<size_t>(b) * n + j];
+      sx += static_cast<double>(xa.x) * xb.x + static_cast<double>(xa.y) * xb.y;  // conj(x_a) x_b
+      sy += static_cast<double>(xa.x) * xb.y - static_cast<double>(xa.y) * xb.x;
+    }
+    red[t] = make_double2(sx, sy);
   }
-  part[static_cast<size_t>(blockIdx.x) * r * r + a * r + b] = make_double2(sx, sy);
+  __syncthreads();
+  if (t < npair) {
+    double2 s = red[t];
+    for (int gg = 1; gg < ng; ++gg) {
+      s.x += red[gg * npair + t].x;
+      s.y += red[gg * npair + t].y;
+    }
+    part[static_cast<size_t>(blockIdx.x) * r * r + a * r + b] = s;
+  }
 }
 // M = sum of partials (M[a][b] for a >= b = sum conj(x_a) x_b), Hermitian;
 // M = R^H R with R = L^H (L lower from the Cholesky of M^T... we factor the
@@ -1273,7 +1300,7 @@ int fourier_iterate(FourierSolver* F, int iters, std::string* msg, cudaEvent_t* 
     cudaError_t e = fft_frames(F, F->U, F->FU, r, false);            // FU = F2 U
     if (e == cudaSuccess) e = launch_fsweep(F, kModeIter, F->tau);   // per-frame work
     if (ev) cudaEventRecord(ev[1], F->s);
-    kspace_kernel<<<(n + 255) / 256, 256, 0, F->s>>>(n, F->m, r, F->iptr, F->ilist, F->RES, F->B, F->K);
+    kspace_kernel<<<(n + 7) / 8, 256, 0, F->s>>>(n, F->m, r, F->iptr, F->ilist, F->RES, F->B, F->K);
     if (e == cudaSuccess) e = fft_frames(F, F->K, F->grad, r, true);  // grad = F2^H K
     if (e == cudaSuccess && F->t == 0) {
       cgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, F->grad, nullptr, nullptr, nullptr, F->part);
