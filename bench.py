@@ -120,6 +120,28 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(base, rank):
+    """Each rank solves its own problem (weak scaling): the workload's seed
+    offset by the rank."""
+    return base + rank
+
+
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time, returned to every rank (no-op on one rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, q, steps, ms):
+    """Column-iterations/s of the whole job: every rank ran `steps`
+    iterations over its q columns within the slowest rank's `ms`."""
+    return world * q * steps / (ms / 1000.0)
+
+
 def oracle_sample(cfg, iters=1):
     """The FP64 oracle as it stands, on the workload's full instance: its own
     initialisation (untimed), then `iters` timed GDmin iterations."""
@@ -186,7 +208,7 @@ def run_ours(args):
     from lrsgen import GaussianInstance
 
     cfg = dict(WORKLOAD)
-    cfg["seed"] = WORKLOAD["seed"] + rank          # one independent problem per rank
+    cfg["seed"] = rank_seed(WORKLOAD["seed"], rank)  # one independent problem per rank
     inst = GaussianInstance(**cfg)
     A = np.ascontiguousarray(inst.A)
     Y = np.ascontiguousarray(inst.Y)
@@ -216,11 +238,8 @@ def run_ours(args):
     ph = L.lrs_phase_times(s.h)
     X = s.X()
     rel_err = float(np.linalg.norm(X - inst.Xstar) / np.linalg.norm(inst.Xstar))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * q * args.steps / (ms / 1000.0)
+    ms = max_over_ranks(ms, world, "cuda")
+    value = whole_job_value(world, q, args.steps, ms)
     # ---- roofline of the dominant kernel (the per-column sweep) ------------
     peak, peak_kind = load_peaks()
     sweep_ms = ph["sweep_ms"] / max(1, ph["iters"])
