@@ -191,7 +191,7 @@ struct TaskShape {  // launch configuration chosen on the host
 // so no warp ever waits on a barrier phase more than one ahead.
 constexpr int kTaskStages = 8;
 constexpr int kTileCols = 32;       // columns per tile of the slab layout
-constexpr int kMaxTaskPieces = 64;  // pieces of one A^T task (tiles x row chunks)
+constexpr int kMaxTaskPieces = 128;  // pieces of one A^T task (tiles x row chunks)
 // Fill the task fields of P (nrc, rpw, TB, ...) for target task bytes and
 // rp rows per A^T piece.
 void task_plan(TaskProblem& P, int R, size_t task_bytes, int rp);

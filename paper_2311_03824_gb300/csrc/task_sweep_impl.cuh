@@ -62,7 +62,10 @@ __host__ __device__ inline TCarve tcarve(int R, int m, int ns, int rho, int stag
   c.gs = o;    o += a16(static_cast<size_t>(ns) * 4);
   c.sl = o;    o += a16(static_cast<size_t>(ns) * 4);
   c.vv = o;    o += a16(static_cast<size_t>(ns) * 4);
-  c.gpart = o; o += a16(static_cast<size_t>(kMaxTaskPieces) * kTW * 4);
+  // per-piece sums of one A^T task: at most kMaxTaskPieces, and at most the
+  // column's tiles x row chunks (rows per piece >= 8)
+  const int max_pieces = min(kMaxTaskPieces, (ns / kTW) * ((m + 7) / 8));
+  c.gpart = o; o += a16(static_cast<size_t>(max_pieces) * kTW * 4);
   c.hist = o;  o += a16(256 * 4 + 64);
   c.tie = o;   o += a16(static_cast<size_t>(ns + 2 * rho + 8) * 4);
   c.Gm = o;    o += a16(3 * kMaxR * kMaxR * 8);
