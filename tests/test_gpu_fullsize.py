@@ -1,5 +1,6 @@
 """Parity at the full benchmark sizes, in the launch configuration bench.py
-times (default options: the task engine, every column in flight).
+times (the task engine, every column in flight, the task shape chosen by the
+autotuner on the first iteration for the Gaussian cases).
 
 * n=1000, q=1000, r=5, m=150, rho=10 (float32 A_k): from the GPU's own
   iterates t = 0 (after lrs_init), 20 and 60, one GDmin iteration on the GPU
@@ -75,7 +76,7 @@ def test_one_step_gaussian_n1000_q1000():
     cfg = {k: v for k, v in C1.items() if k != "T"}
     inst = GaussianInstance(**cfg)
     op = O.GaussianOperator(inst.A)
-    s = new_solver(inst)
+    s = new_solver(inst, autotune=1)
     s.init()
     t, whole = 0, 0
     try:
@@ -107,7 +108,7 @@ def test_sampled_columns_gaussian_n4096_q2048():
     dev = DeviceGaussianInstance(**cfg)
     stream = torch.cuda.Stream()
     n, q, r, m, rho = cfg["n"], cfg["q"], cfg["r"], cfg["m"], cfg["rho"]
-    s = Solver(n, m, q, r, rho, stream=stream)
+    s = Solver(n, m, q, r, rho, stream=stream, autotune=1)
     try:
         s.set_measurements(dev.Y, dev.A)
         s.init()
