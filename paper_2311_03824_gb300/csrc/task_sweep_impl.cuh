@@ -504,16 +504,21 @@ __device__ __forceinline__ void ht_single(Ctx& C, bool keep_values) {
   csync();
 }
 
-// G = W^T W (FP64, fixed order) and its Cholesky inverse into C.Gi
+// G = W^T W and G^{-1} into C.Gi.  FP64 arithmetic costs hundreds of cycles
+// per dependent operation on this part, so the Gram is summed in FP32 (lane
+// partials in row order, then a butterfly: a fixed order) and inverted by
+// Cholesky in FP32 followed by one Newton-Schulz step X <- X (2I - G X) in
+// FP64: the FP32 inverse has a relative error of about cond(G) 1e-7 and the
+// step squares it.  A pivot FP32 cannot take (G close to singular) falls back
+// to the FP64 Cholesky of factor_gram.
 template <int R>
 __device__ __forceinline__ void gram_factor(Ctx& C) {
   const int r = C.r, lane = threadIdx.x & 31;
   for (int t = threadIdx.x >> 5; t < r * r; t += kNW) {
     const int p = t / r, q2 = t - p * r;
     if (q2 > p) continue;
-    double s = 0.0;
-    for (int i = lane; i < C.m; i += 32)
-      s = dfma(static_cast<double>(C.W[i * R + p]), static_cast<double>(C.W[i * R + q2]), s);
+    float s = 0.f;
+    for (int i = lane; i < C.m; i += 32) s = fmaf(C.W[i * R + p], C.W[i * R + q2], s);
     s = warp_sum(s);
     if (lane == 0) {
       C.G[p * kMaxR + q2] = s;
@@ -522,8 +527,85 @@ __device__ __forceinline__ void gram_factor(Ctx& C) {
   }
   if (threadIdx.x == 0) C.flags[0] = 0;
   csync();
-  factor_gram(C);
+  if (threadIdx.x < 32) {
+    float* Lf = reinterpret_cast<float*>(C.Lc);  // L (FP32), then L^{-1} after it
+    float* Lif = Lf + kMaxR * kMaxR;
+    float* iLf = reinterpret_cast<float*>(C.fv + 32);
+    int ok = 1;
+    if (lane == 0) {
+      for (int j = 0; j < r && ok; ++j) {
+        const float gjj = static_cast<float>(C.G[j * kMaxR + j]);
+        float sj = gjj;
+        for (int p = 0; p < j; ++p) sj = fmaf(-Lf[j * kMaxR + p], Lf[j * kMaxR + p], sj);
+        if (!(sj > 1e-5f * gjj) || !(sj < 1e30f)) { ok = 0; break; }
+        const float ij = rsqrtf(sj);
+        Lf[j * kMaxR + j] = sj * ij;
+        iLf[j] = ij;
+        for (int i = j + 1; i < r; ++i) {
+          float t = static_cast<float>(C.G[i * kMaxR + j]);
+          for (int p = 0; p < j; ++p) t = fmaf(-Lf[i * kMaxR + p], Lf[j * kMaxR + p], t);
+          Lf[i * kMaxR + j] = t * ij;
+        }
+      }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    if (!ok) {
+      factor_gram(C);  // FP64 path (also reports a pivot that is not positive)
+    } else {
+      if (lane < r) {  // L^{-1}, one column per lane
+        const int cc = lane;
+        for (int i = 0; i < r; ++i) {
+          float t = (i == cc) ? 1.f : 0.f;
+          for (int p = cc; p < i; ++p) t = fmaf(-Lf[i * kMaxR + p], Lif[p * kMaxR + cc], t);
+          Lif[i * kMaxR + cc] = (i < cc) ? 0.f : t * iLf[i];
+        }
+      }
+      __syncwarp();
+      for (int t = lane; t < r * r; t += 32) {  // X0 = L^{-T} L^{-1} into Gi
+        const int a = t / r, b = t - a * r;
+        float x = 0.f;
+        for (int p = (a > b ? a : b); p < r; ++p) x = fmaf(Lif[p * kMaxR + a], Lif[p * kMaxR + b], x);
+        C.Gi[a * kMaxR + b] = x;
+      }
+      __syncwarp();
+      double* T = C.Lc;  // T = G X0 (FP64); the FP32 factors are no longer needed
+      for (int t = lane; t < r * r; t += 32) {
+        const int a = t / r, b = t - a * r;
+        double x = 0.0;
+        for (int p = 0; p < r; ++p) x = dfma(C.G[a * kMaxR + p], C.Gi[p * kMaxR + b], x);
+        T[a * kMaxR + b] = x;
+      }
+      __syncwarp();
+      for (int t = lane; t < r * r; t += 32) {  // X1 = 2 X0 - X0 T into G
+        const int a = t / r, b = t - a * r;
+        double x = 2.0 * C.Gi[a * kMaxR + b];
+        for (int p = 0; p < r; ++p) x = dfma(-C.Gi[a * kMaxR + p], T[p * kMaxR + b], x);
+        C.G[a * kMaxR + b] = x;
+      }
+      __syncwarp();
+      for (int t = lane; t < r * r; t += 32) {
+        const int a = t / r, b = t - a * r;
+        C.Gi[a * kMaxR + b] = C.G[a * kMaxR + b];
+      }
+    }
+  }
   csync();
+}
+
+// sum of squares of an m-vector in FP32 (warp butterflies, then the warps in
+// index order), returned to every consumer thread
+__device__ __forceinline__ float norm2_mf(const Ctx& C, const float* v) {
+  float acc = 0.f;
+  for (int i = threadIdx.x; i < C.m; i += kNT) acc = fmaf(v[i], v[i], acc);
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) C.redf[kNW * kMaxR + 16 + (threadIdx.x >> 5)] = acc;
+  csync();
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < kNW; ++i) s += C.redf[kNW * kMaxR + 16 + i];
+  csync();
+  return s;
 }
 
 // u = P_perp(A s - y) (project) into dv and out
@@ -659,29 +741,29 @@ __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int typ
       const int nl = *C.nloc;
       for (int e = tid; e < nl; e += kNT) C.vv[e] = C.gs[C.sup_j[e]];
       csync();
-      // ||g_G||^2 by warp 0 (FP64, fixed order), shared through fv[0]
+      // ||g_G||^2 by warp 0 (FP32, fixed order), shared through redf
+      float* numf = C.redf + kNW * kMaxR + 32;
       if (tid < 32) {
-        double t = 0.0;
-        for (int e = tid; e < nl; e += 32) t = dfma(static_cast<double>(C.vv[e]), C.vv[e], t);
+        float t = 0.f;
+        for (int e = tid; e < nl; e += 32) t = fmaf(C.vv[e], C.vv[e], t);
         t = warp_sum(t);
-        if (tid == 0) C.fv[0] = t;
+        if (tid == 0) *numf = t;
       }
       gather<ET>(C, C.vv, C.ev);
       csync();
-      const double num = C.fv[0];
+      const float num = *numf;
       if (project) proj<R>(C, C.ev);
-      const double den = norm2_m(C, C.ev);
+      const float den = norm2_mf(C, C.ev);
       mark(11);
-      if (!(den > 0.0)) {
+      if (!(den > 0.f)) {
         stopped = true;
         if (tid == 0) P.stop[k] = 1;
       } else {
-        double mu = num / den;
-        if (!isfinite(mu)) {
+        float muf = num / den;
+        if (!isfinite(muf)) {
           if (tid == 0) report_error(P.err, kErrNaN, k);
-          mu = 0.0;
+          muf = 0.f;
         }
-        const float muf = static_cast<float>(mu);
         for (int j = tid; j < P.L.n; j += kNT) C.vv[j] = fmaf(-muf, C.gs[j], C.sl[j]);
         csync();
         ht_single(C, true);
