@@ -116,6 +116,7 @@ struct lrs_ctx {
   int tuned = 0;                     // autotuner ran (or its cache was used)
   int trp = 0;                       // rows per A^T piece
   float *tWk = nullptr, *tWp = nullptr, *tu = nullptr, *tg = nullptr, *tsupv = nullptr;
+  float* tAs = nullptr;  // q x astride: A_k s_k (task engine)
   double* tGi = nullptr;
   int *tsupj = nullptr, *tnsup = nullptr, *tcnt = nullptr, *tstop = nullptr, *tseq = nullptr,
       *tctr = nullptr;
@@ -394,7 +395,7 @@ void free_all(lrs_ctx* h) {
     h->gexec[g] = nullptr;
     h->graph[g] = nullptr;
   }
-  void* ps2[] = {h->dtp, h->dseed, h->tWk, h->tWp, h->tu, h->tg, h->tsupv, h->tGi, h->tsupj,
+  void* ps2[] = {h->dtp, h->dseed, h->tWk, h->tWp, h->tu, h->tg, h->tsupv, h->tGi, h->tsupj, h->tAs,
                  h->tnsup, h->tcnt, h->tstop, h->tseq, h->tctr, h->ttasks, h->tprof};
   for (void* p : ps2)
     if (p) cudaFreeAsync(p, h->stream);
@@ -518,6 +519,7 @@ lrs_status plan_tables(lrs_ctx* h, int task_kib, int F) {
     P.Wp = h->tWp;
     P.Gi = h->tGi;
     P.uvec = h->tu;
+    P.As = h->tAs;
     P.g = h->tg;
     P.supj = h->tsupj;
     P.supv = h->tsupv;
@@ -576,6 +578,7 @@ lrs_status alloc_task_engine(lrs_ctx* h) {
   lrs_status st = LRS_OK;
   if ((st = dalloc(&h->tWk, q * wstride, h->stream)) || (st = dalloc(&h->tWp, q * ncw_max * wstride, h->stream)) ||
       (st = dalloc(&h->tGi, q * 16 * 16, h->stream)) || (st = dalloc(&h->tu, q * m, h->stream)) ||
+      (st = dalloc(&h->tAs, q * static_cast<size_t>((m + 3) & ~3), h->stream)) ||
       (st = dalloc(&h->tg, q * ns, h->stream)) || (st = dalloc(&h->tsupj, q * rho1, h->stream)) ||
       (st = dalloc(&h->tsupv, q * rho1, h->stream)) || (st = dalloc(&h->tnsup, q, h->stream)) ||
       (st = dalloc(&h->tcnt, q, h->stream)) || (st = dalloc(&h->tstop, q, h->stream)) || (st = dalloc(&h->tctr, 4, h->stream)) ||
@@ -586,6 +589,7 @@ lrs_status alloc_task_engine(lrs_ctx* h) {
     return st;
   CUDA_TRY(cudaMemsetAsync(h->tprof, 0, 16 * sizeof(unsigned long long), h->stream));
   CUDA_TRY(cudaMemsetAsync(h->tcnt, 0, q * sizeof(int), h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->tAs, 0, q * static_cast<size_t>((m + 3) & ~3) * sizeof(float), h->stream));
   CUDA_TRY(cudaMemsetAsync(h->tnsup, 0, q * sizeof(int), h->stream));
   CUDA_TRY(cudaMemsetAsync(h->tstop, 0, q * sizeof(int), h->stream));
   return plan_tables(h, kib, h->tF);

@@ -119,6 +119,7 @@ struct TaskProblem {
   float* uvec;          // q x m  vector of the next A^T pass
   float* g;             // q x ns result of the IHT pass
   int* supj;            // q x rho current support (global indices, key order)
+  float* As;            // q x astride: A_k s_k for the current support values (unprojected)
   float* supv;
   int* nsup;            // q
   int* cnt;             // q tasks completed in the current pass (zero between launches)
@@ -132,6 +133,7 @@ struct TaskProblem {
   int tasks_per_col;
   int wstride;          // floats per column of Wk and per column chunk of Wp (m R rounded
                         // up to 4: every block starts on a 16-byte boundary)
+  int astride;          // floats per column of As (m rounded up to 4)
 };
 
 struct TaskQueue {

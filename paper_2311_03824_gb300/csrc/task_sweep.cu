@@ -82,6 +82,7 @@ void task_plan(TaskProblem& P, int R, size_t task_bytes, int rp) {
   for (int ph = 0; ph <= last_phase(P); ++ph) tot += phase_tasks(P, ph);
   P.tasks_per_col = tot;
   P.wstride = (m * R + 3) & ~3;
+  P.astride = (m + 3) & ~3;
 }
 
 size_t task_smem_bytes(int R, int /*et*/, int m_max, int ns_max, int rho_max, int stages,

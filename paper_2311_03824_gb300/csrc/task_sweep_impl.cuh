@@ -43,7 +43,7 @@ __device__ __forceinline__ unsigned long long gtimer() {
 // ---- shared-memory carve -----------------------------------------------------
 struct TCarve {
   size_t bars, task, ring, stage, W, yv, dv, ev, uv, gs, sl, vv, gpart, hist, tie, Gm, fv,
-      flags, redf, sup, rsc, bcast, prof, total;
+      flags, redf, sup, rsc, asv, osup, bcast, prof, total;
 };
 __host__ __device__ inline TCarve tcarve(int R, int m, int ns, int rho, int stages,
                                          int piece_bytes) {
@@ -74,6 +74,8 @@ __host__ __device__ inline TCarve tcarve(int R, int m, int ns, int rho, int stag
   c.redf = o;  o += a16(static_cast<size_t>(kNW) * kMaxR * 4 + 256);
   c.sup = o;   o += a16(static_cast<size_t>(rho) * 12 + 16);
   c.rsc = o;   o += a16(static_cast<size_t>(2) * m * 4);
+  c.asv = o;   o += a16(static_cast<size_t>(m) * 4);              // A s of the column (step)
+  c.osup = o;  o += a16(static_cast<size_t>(rho + 4) * 4);        // support before HardThreshold
   c.bcast = o; o += 16;  // [0] last task of a pass, [1] descriptor arrived
   c.prof = o;  o += 16 * 8;
   c.total = o;
@@ -417,9 +419,10 @@ __device__ __forceinline__ void fence_proxy_async() {
 template <int R>
 __device__ __forceinline__ void load_column(Ctx& C, const TaskProblem& P, int k, bool with_w,
                                             bool with_gi, int source, bool with_g,
-                                            uint64_t* sbar, unsigned& sphase, int* abort) {
+                                            uint64_t* sbar, unsigned& sphase, int* abort,
+                                            float* asv = nullptr) {
   const int m = C.m, tid = threadIdx.x, rho = C.rho, ns = P.L.ns, n = P.L.n;
-  const bool bulk = with_w || with_gi || with_g;
+  const bool bulk = with_w || with_gi || with_g || asv;
   if (bulk) {
     fence_proxy_async();
     csync();
@@ -427,7 +430,9 @@ __device__ __forceinline__ void load_column(Ctx& C, const TaskProblem& P, int k,
       const unsigned bw = with_w ? static_cast<unsigned>(P.wstride) * 4u : 0u;
       const unsigned bgi = with_gi ? static_cast<unsigned>(kMaxR * kMaxR * 8) : 0u;
       const unsigned bg = with_g ? static_cast<unsigned>(ns) * 4u : 0u;
-      mbar_arrive_expect_tx(sbar, bw + bgi + bg);
+      const unsigned ba = asv ? static_cast<unsigned>(P.astride) * 4u : 0u;
+      mbar_arrive_expect_tx(sbar, bw + bgi + bg + ba);
+      if (ba) bulk_copy_g2s(asv, P.As + static_cast<size_t>(k) * P.astride, ba, sbar);
       if (bw) bulk_copy_g2s(C.W, P.Wk + static_cast<size_t>(k) * P.wstride, bw, sbar);
       if (bgi) bulk_copy_g2s(C.Gi, P.Gi + static_cast<size_t>(k) * kMaxR * kMaxR, bgi, sbar);
       if (bg) bulk_copy_g2s(C.gs, P.g + static_cast<size_t>(k) * ns, bg, sbar);
@@ -608,12 +613,18 @@ __device__ __forceinline__ float norm2_mf(const Ctx& C, const float* v) {
   return s;
 }
 
-// u = P_perp(A s - y) (project) into dv and out
+// u = P_perp(A s - y) (project) into dv and out.  A s is gathered, or already
+// in dv (as_ready); it is kept in As for the column's next step.
 template <int R, int ET>
-__device__ __forceinline__ void residual_u(Ctx& C, bool project, float* out) {
-  gather<ET>(C, C.sup_v, C.dv);
+__device__ __forceinline__ void residual_u(Ctx& C, const TaskProblem& P, int k, bool project,
+                                           float* out, bool as_ready = false) {
+  if (!as_ready) gather<ET>(C, C.sup_v, C.dv);
   csync();
-  for (int i = threadIdx.x; i < C.m; i += kNT) C.dv[i] -= C.yv[i];
+  float* As = P.As + static_cast<size_t>(k) * P.astride;
+  for (int i = threadIdx.x; i < C.m; i += kNT) {
+    As[i] = C.dv[i];
+    C.dv[i] -= C.yv[i];
+  }
   csync();
   if (project) proj<R>(C, C.dv);
   for (int i = threadIdx.x; i < C.m; i += kNT) out[i] = C.dv[i];
@@ -621,9 +632,10 @@ __device__ __forceinline__ void residual_u(Ctx& C, bool project, float* out) {
 
 // final stage before the last pass: A s, b = G^{-1} W^T (y - A s), e
 template <int R, int ET>
-__device__ __forceinline__ void final_prep(Ctx& C, const TaskProblem& P, int k, float* out) {
+__device__ __forceinline__ void final_prep(Ctx& C, const TaskProblem& P, int k, float* out,
+                                           bool as_ready = false) {
   const int m = C.m, tid = threadIdx.x;
-  gather<ET>(C, C.sup_v, C.dv);
+  if (!as_ready) gather<ET>(C, C.sup_v, C.dv);
   csync();
   for (int i = tid; i < m; i += kNT) C.dv[i] = C.yv[i] - C.dv[i];  // y - A s
   csync();
@@ -714,7 +726,7 @@ __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int typ
       final_prep<R, ET>(C, P, k, uout);
       next_type = -2;  // column done
     } else if (te > 0) {
-      residual_u<R, ET>(C, true, uout);
+      residual_u<R, ET>(C, P, k, true, uout);
       store_support(C, P, k);
       next_type = kTaskG;
     } else {
@@ -725,11 +737,18 @@ __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int typ
   } else if (type == kTaskG || type == kTaskNop) {
     const bool zero_start = (P.mode == kModeInit && ph == 0);
     const int stop_in = zero_start ? 0 : __ldcg(P.stop + k);
+    // A s of the current support, kept by the column's previous step: when
+    // HardThreshold keeps the support, the new values are s - mu g on it and
+    // A s_new = A s - mu A g_G, so the residual needs no gather
+    const bool may_update = !zero_start && type == kTaskG;
+    float* asv = reinterpret_cast<float*>(smem + cv.asv);
+    int* osup = reinterpret_cast<int*>(smem + cv.osup);
     load_column<R>(C, P, k, project, project, zero_start ? kSupNone : kSupState,
-                   type != kTaskNop, sbar, sphase, Q.ctr + 3);
+                   type != kTaskNop, sbar, sphase, Q.ctr + 3, may_update ? asv : nullptr);
     if (zero_start && tid == 0) P.stop[k] = 0;
     const int sweep = P.mode == kModeInit ? ph : ph - 1;  // 0-based IHT sweep just run
     bool stopped = stop_in != 0 || type == kTaskNop;
+    bool as_ready = false;  // A s of the new support values in dv
     mark(10);
     if (!stopped) {
       if (zero_start) {
@@ -739,7 +758,11 @@ __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int typ
       }
       // mu = ||g_G||^2 / ||P_perp A g_G||^2 on the current support G
       const int nl = *C.nloc;
-      for (int e = tid; e < nl; e += kNT) C.vv[e] = C.gs[C.sup_j[e]];
+      for (int e = tid; e < nl; e += kNT) {
+        C.vv[e] = C.gs[C.sup_j[e]];
+        osup[e] = C.sup_j[e];
+      }
+      if (tid == 0) osup[C.rho + 1] = 1;  // "support kept", cleared below if not
       csync();
       // ||g_G||^2 by warp 0 (FP32, fixed order), shared through redf
       float* numf = C.redf + kNW * kMaxR + 32;
@@ -752,6 +775,8 @@ __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int typ
       gather<ET>(C, C.vv, C.ev);
       csync();
       const float num = *numf;
+      if (may_update)  // A g_G before the projection
+        for (int i = tid; i < C.m; i += kNT) C.dv[i] = C.ev[i];
       if (project) proj<R>(C, C.ev);
       const float den = norm2_mf(C, C.ev);
       mark(11);
@@ -768,14 +793,28 @@ __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int typ
         csync();
         ht_single(C, true);
         store_support(C, P, k);
+        if (may_update) {
+          const int K = *C.nloc;
+          for (int e = tid; e < K; e += kNT) {
+            const int j = C.sup_j[e];
+            bool found = false;
+            for (int f = 0; f < nl; ++f) found |= osup[f] == j;
+            if (!found) osup[C.rho + 1] = 0;
+          }
+          csync();
+          if (K == nl && osup[C.rho + 1]) {
+            for (int i = tid; i < C.m; i += kNT) C.dv[i] = fmaf(-muf, C.dv[i], asv[i]);
+            as_ready = true;
+          }
+        }
       }
     }
     mark(12);
     if (sweep + 1 < te) {
-      if (!stopped) residual_u<R, ET>(C, project, uout);
+      if (!stopped) residual_u<R, ET>(C, P, k, project, uout, as_ready);
       next_type = stopped ? kTaskNop : kTaskG;
     } else {
-      final_prep<R, ET>(C, P, k, uout);
+      final_prep<R, ET>(C, P, k, uout, as_ready);
       next_type = kTaskF;
     }
     mark(13);
