@@ -64,8 +64,10 @@ __host__ __device__ inline TCarve tcarve(int R, int m, int ns, int rho, int stag
   c.vv = o;    o += a16(static_cast<size_t>(ns) * 4);
   // per-piece sums of one A^T task: at most kMaxTaskPieces, and at most the
   // column's tiles x row chunks (rows per piece >= 8)
+  // ... and the W tasks' cross-warp sums (kNW x 32 rows x R)
   const int max_pieces = min(kMaxTaskPieces, (ns / kTW) * ((m + 7) / 8));
-  c.gpart = o; o += a16(static_cast<size_t>(max_pieces) * kTW * 4);
+  const size_t gfl = max(static_cast<size_t>(max_pieces) * kTW, static_cast<size_t>(kNW) * 32 * R);
+  c.gpart = o; o += a16(gfl * 4);
   c.hist = o;  o += a16(256 * 4 + 64);
   c.tie = o;   o += a16(static_cast<size_t>(ns + 2 * rho + 8) * 4);
   c.Gm = o;    o += a16(3 * kMaxR * kMaxR * 8);
@@ -297,6 +299,80 @@ __device__ __forceinline__ void consume_w(TCtx& T, const TaskProblem& P, int k, 
       v += __shfl_xor_sync(0xffffffffu, v, 2);
       v += __shfl_xor_sync(0xffffffffu, v, 4);
       if ((l & 7) == q && 4 * t < RBw && i < nr) out[static_cast<size_t>(i0 + i) * R + l] = v;
+    }
+  }
+}
+
+// ---- consumer: W task, pieces to warps round-robin (8 <= R <= 12) ----------------------
+// Piece p of the task (tile b0 + p, rows i0..i0+nr) goes to warp p mod 8, as in
+// the A^T tasks; a lane owns rows lane, lane + 32, ... (at most 4) of the row
+// block over all 32 columns of its pieces (U of the tile read from the stage,
+// the same address for every lane).  The warps' partial rows are then added
+// in warp order through shared memory, 32 rows at a time.
+template <int R, int ET>
+__device__ __forceinline__ void consume_w_rr(TCtx& T, const TaskProblem& P, int k, int blk) {
+  const GaussLayout& L = P.L;
+  const int m = L.m, ntile = L.ns / kTW;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int rb = blk / P.ncw, cc = blk - rb * P.ncw;
+  const int i0 = rb * P.rpw, nr = min(m, i0 + P.rpw) - i0;
+  const int b0 = cc * P.TBW, b1 = min(ntile, b0 + P.TBW);
+  const int npieces = b1 - b0;
+  const float* sc1 = T.rsc + i0;
+  const float* sc2 = T.rsc + m + i0;
+  float acc[4][R];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int l = 0; l < R; ++l) acc[u][l] = 0.f;
+  const unsigned s0 = T.seq;
+  for (int p = wid; p < npieces; p += kNW) {
+    const unsigned sq = s0 + p, s = sq % T.stages, use = sq / T.stages;
+    const long long c0 = clock64();
+    wait_bar(&T.full[s], use & 1u, T.err, T.abort);
+    if (lane == 0) T.pw += clock64() - c0;
+    const unsigned char* st = T.ring + static_cast<size_t>(s) * T.stage;
+    const float* Us = reinterpret_cast<const float*>(st + T.stage - static_cast<size_t>(kTW) * R * 4);
+#pragma unroll 1
+    for (int q = 0; q < kTW / 4; ++q) {  // 16-byte chunk of 4 columns
+      float4 a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = lane + 32 * u;
+        a[u] = i < nr ? load4<ET>(st, nr, i, q, sc1, sc2) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+#pragma unroll
+        for (int l = 0; l < R; ++l) {
+          const float uv = Us[(4 * q + c) * R + l];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float av = c == 0 ? a[u].x : c == 1 ? a[u].y : c == 2 ? a[u].z : a[u].w;
+            acc[u][l] = fmaf(av, uv, acc[u][l]);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive_local_n(&T.empty[s], kNW);  // the piece is free
+  }
+  T.seq = s0 + npieces;
+  float* red = T.gpart;  // kNW x 32 x R
+  float* out = P.Wp + (static_cast<size_t>(k) * P.ncw + cc) * P.wstride;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (32 * u >= nr) break;
+    csync();
+#pragma unroll
+    for (int l = 0; l < R; ++l) red[(wid * 32 + lane) * R + l] = acc[u][l];
+    csync();
+    for (int t = threadIdx.x; t < 32 * R; t += kNT) {
+      const int row = t / R, l = t - row * R, i = 32 * u + row;
+      float sum = 0.f;
+#pragma unroll
+      for (int w = 0; w < kNW; ++w) sum += red[(w * 32 + row) * R + l];
+      if (i < nr) out[static_cast<size_t>(i0 + i) * R + l] = sum;
     }
   }
 }
@@ -977,7 +1053,10 @@ __global__ void __launch_bounds__(kThreadsAll, R <= 6 ? 3 : 2) task_kernel(const
       }
       if (type == kTaskW) {
         csync();
-        consume_w<R, ET>(T, P, k, blk);
+        if constexpr (R >= 8 && R <= 12)  // measured: faster for these widths only
+          consume_w_rr<R, ET>(T, P, k, blk);
+        else
+          consume_w<R, ET>(T, P, k, blk);
       } else {
         // the vector of this pass: -y (zero start of INIT), y (INIT with no IHT), or
         // the one the previous step published
