@@ -97,7 +97,7 @@ cudaError_t refine_residual(const GaussLayout& L, const float* A_exact, const vo
 // A persistent grid pops tasks from a global ticket queue; the CTA that
 // completes the last task of a column's pass runs that column's small step
 // (Gram + Cholesky, mu, HardThreshold, LS, projections) and pushes the next
-// pass.  Up to F columns are in flight (their A_k stays in L2 across passes).
+// pass.  Up to F columns are in flight (all q by default).
 enum TaskType : int { kTaskW = 0, kTaskG = 1, kTaskF = 2, kTaskNop = 3, kTaskExit = 4 };
 
 struct TaskProblem {

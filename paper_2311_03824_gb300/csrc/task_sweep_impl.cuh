@@ -17,8 +17,9 @@
 // consumer warps - Gram and Cholesky after W; mu and HardThreshold after an
 // IHT pass (Algorithm 2); the LS for b_k and the residual before the final
 // pass - and publishes the next pass's tasks.  A finished column admits the
-// next one, so at most F columns are in flight and their A_k stay in L2
-// between passes.
+// next one, so at most F columns are in flight (with few enough of them a
+// column's A_k can stay in L2 between its passes; with all of them in flight,
+// the default, each pass streams from HBM).
 //
 // Every wait is bounded (global timer); on expiry the CTA records
 // kErrTimeout and leaves, so a launch always ends.
