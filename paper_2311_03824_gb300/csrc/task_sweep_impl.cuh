@@ -403,14 +403,40 @@ __device__ __forceinline__ void consume_g(TCtx& T, const TaskProblem& P, int k, 
     const unsigned char* st = T.ring + static_cast<size_t>(s) * T.stage;
     const float* uu = T.uv + i0;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (ET >= 2) {
+      // FP8 forms: T.rsc holds the row scales times the pass vector, so an
+      // element costs one multiply-add per plane
+      const float* w1 = T.rsc + i0;
+      const float* w2 = T.rsc + m + i0;
 #pragma unroll 4
-    for (int i = ro; i < nr; i += 4) {
-      const float4 a = load4<ET>(st, nr, i, q, T.rsc + i0, T.rsc + m + i0);
-      const float w = uu[i];
-      acc.x = fmaf(a.x, w, acc.x);
-      acc.y = fmaf(a.y, w, acc.y);
-      acc.z = fmaf(a.z, w, acc.z);
-      acc.w = fmaf(a.w, w, acc.w);
+      for (int i = ro; i < nr; i += 4) {
+        const int off = i * kTW + ((q ^ (i & 7)) << 2);
+        const float4 fh = static_cast<float4>(*reinterpret_cast<const __nv_fp8x4_e4m3*>(st + off));
+        const float a1 = w1[i];
+        acc.x = fmaf(fh.x, a1, acc.x);
+        acc.y = fmaf(fh.y, a1, acc.y);
+        acc.z = fmaf(fh.z, a1, acc.z);
+        acc.w = fmaf(fh.w, a1, acc.w);
+        if constexpr (ET == 3) {
+          const float4 fl = static_cast<float4>(
+              *reinterpret_cast<const __nv_fp8x4_e4m3*>(st + static_cast<size_t>(nr) * kTW + off));
+          const float a2 = w2[i];
+          acc.x = fmaf(fl.x, a2, acc.x);
+          acc.y = fmaf(fl.y, a2, acc.y);
+          acc.z = fmaf(fl.z, a2, acc.z);
+          acc.w = fmaf(fl.w, a2, acc.w);
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int i = ro; i < nr; i += 4) {
+        const float4 a = load4<ET>(st, nr, i, q, T.rsc + i0, T.rsc + m + i0);
+        const float w = uu[i];
+        acc.x = fmaf(a.x, w, acc.x);
+        acc.y = fmaf(a.y, w, acc.y);
+        acc.z = fmaf(a.z, w, acc.z);
+        acc.w = fmaf(a.w, w, acc.w);
+      }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive_local_n(&T.empty[s], kNW);  // the piece is free
@@ -1071,6 +1097,10 @@ __global__ void __launch_bounds__(kThreadsAll, R <= 6 ? 3 : 2) task_kernel(const
             v = __ldcg(P.uvec + static_cast<size_t>(k) * m + i);
           }
           T.uv[i] = v;
+          if (ET >= 2) {  // this thread loaded the scales of row i above
+            T.rsc[i] *= v;
+            T.rsc[m + i] *= v;
+          }
         }
         csync();
         float* out = type == kTaskF ? P.H + static_cast<size_t>(k) * P.L.n
