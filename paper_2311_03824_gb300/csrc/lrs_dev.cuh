@@ -161,34 +161,39 @@ __device__ __forceinline__ double rsqrt_newton(double s) {
   return y;
 }
 
-// One warp: lower Cholesky factor of the SPD r x r matrix G (row-major, ld)
-// by lane 0 with inverse pivots from rsqrt_newton, then L^{-1} (lower, into
-// Li) with one column per lane.  Returns false (all lanes) when a pivot is not
-// positive relative to its diagonal; Li is then the identity.
+// One warp: lower Cholesky factor of the SPD r x r matrix G (row-major, ld),
+// then L^{-1} (lower, into Li) with one column per lane.  Column j of L: every
+// lane i >= j forms t_i = G_ij - sum_{p<j} L_ip L_jp at once (t_j is the
+// pivot), so a column costs one chain of j multiply-adds, the pivot's
+// reciprocal square root and one multiply (dependent FP64 operations are
+// slow).  Returns false (all lanes) when a pivot is not positive relative to
+// its diagonal; L and Li are then the identity.
 __device__ inline bool chol_inverse_warp(const double* G, double* L, double* Li, double* iL,
                                          int r, int ld) {
   const int lane = threadIdx.x & 31;
   int ok = 1;
-  if (lane == 0) {
-    for (int j = 0; j < r && ok; ++j) {
-      double s = G[j * ld + j];
-      for (int p = 0; p < j; ++p) s -= L[j * ld + p] * L[j * ld + p];
-      if (!(s > 1e-13 * G[j * ld + j]) || !(s < 1e300)) { ok = 0; break; }
-      const double ij = rsqrt_newton(s);
+  for (int j = 0; j < r; ++j) {
+    double t = 0.0;
+    if (lane >= j && lane < r) {
+      t = G[lane * ld + j];
+      for (int p = 0; p < j; ++p) t = __fma_rn(-L[lane * ld + p], L[j * ld + p], t);
+    }
+    const double s = __shfl_sync(0xffffffffu, t, j);
+    if (!(s > 1e-13 * G[j * ld + j]) || !(s < 1e300)) { ok = 0; break; }
+    const double ij = rsqrt_newton(s);
+    if (lane == j) {
       L[j * ld + j] = s * ij;
       iL[j] = ij;
-      for (int i = j + 1; i < r; ++i) {
-        double t = G[i * ld + j];
-        for (int p = 0; p < j; ++p) t -= L[i * ld + p] * L[j * ld + p];
-        L[i * ld + j] = t * ij;
-      }
+    } else if (lane > j && lane < r) {
+      L[lane * ld + j] = t * ij;
     }
-    if (!ok)
-      for (int i = 0; i < r; ++i) {
-        for (int p = 0; p < r; ++p) L[i * ld + p] = (i == p) ? 1.0 : 0.0;
-        iL[i] = 1.0;
-      }
+    __syncwarp();
   }
+  if (!ok && lane == 0)
+    for (int i = 0; i < r; ++i) {
+      for (int p = 0; p < r; ++p) L[i * ld + p] = (i == p) ? 1.0 : 0.0;
+      iL[i] = 1.0;
+    }
   ok = __shfl_sync(0xffffffffu, ok, 0);
   __syncwarp();
   if (lane < r) {
