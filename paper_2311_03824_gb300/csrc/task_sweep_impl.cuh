@@ -340,7 +340,13 @@ __device__ __forceinline__ void consume_w_rr(TCtx& T, const TaskProblem& P, int 
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int i = lane + 32 * u;
-        a[u] = i < nr ? load4<ET>(st, nr, i, q, sc1, sc2) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (ET == 2) {  // FP8 hi: raw values, the row scale applied once below
+          a[u] = i < nr ? static_cast<float4>(*reinterpret_cast<const __nv_fp8x4_e4m3*>(
+                              st + i * kTW + ((q ^ (i & 7)) << 2)))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+          a[u] = i < nr ? load4<ET>(st, nr, i, q, sc1, sc2) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -359,6 +365,15 @@ __device__ __forceinline__ void consume_w_rr(TCtx& T, const TaskProblem& P, int 
     if (lane == 0) mbar_arrive_local_n(&T.empty[s], kNW);  // the piece is free
   }
   T.seq = s0 + npieces;
+  if constexpr (ET == 2) {  // a lane's rows are the same in all its pieces
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = lane + 32 * u;
+      const float s1 = i < nr ? sc1[i] : 0.f;
+#pragma unroll
+      for (int l = 0; l < R; ++l) acc[u][l] *= s1;
+    }
+  }
   float* red = T.gpart;  // kNW x 32 x R
   float* out = P.Wp + (static_cast<size_t>(k) * P.ncw + cc) * P.wstride;
 #pragma unroll
