@@ -170,6 +170,13 @@ lrs_status lrs_solve(lrs_t h);
 lrs_status lrs_get(lrs_t h, void* U, void* B, int32_t* S_idx, void* S_val,
                    int32_t mem_kind);
 
+/* The current iterate itself, X = U B + S (Algorithm 1, Output:
+ * x_k = U b_k + s_k), assembled on the device in float32 (complex64 for
+ * DFT2D_MASK).  X: n x q column-major; mem_kind 0 = host buffer (the call
+ * synchronises the stream), 1 = device.  State: INITIALISED or ITERATING.
+ * Errors: LRS_ERR_ARG, LRS_ERR_STATE, LRS_ERR_OOM, LRS_ERR_CUDA. */
+lrs_status lrs_get_x(lrs_t h, void* X, int32_t mem_kind);
+
 /* Restore a state written by lrs_get (same layouts, host or device), so that
  * a run can be resumed: t is the number of iterations already done and eta
  * the frozen step size (ignored when t == 0).  State: MEASURED or later ->
@@ -227,20 +234,24 @@ lrs_status lrs_orthonormalize(const float* Z, float* Q, int64_t n, int32_t r, vo
 
 /* lrs_orthonormalize without any device allocation.  The paper has no
  * counterpart: this call exists for callers that cannot allocate device
- * memory when they need the step (their memory is all handed to their own
- * pool, a serving loop must not take the device-wide synchronisation of
- * cudaMalloc/cudaFree, or their GPU work is recorded once and replayed).
- * It computes exactly what lrs_orthonormalize computes, with the same
- * arguments and layouts, but uses a fixed scratch array of about 4.6 MB that
- * lives in the library's device image: every GPU that loads the library holds
- * it until the process exits.
+ * memory at the moment they need the step - an application that has handed
+ * all of its device memory to its own pool, or a serving loop that must not
+ * stall the other streams on the device-wide synchronisation that
+ * cudaMalloc/cudaFree imply.  It computes exactly what lrs_orthonormalize
+ * computes, with the same arguments and layouts, but uses a fixed scratch
+ * array of about 4.6 MB that lives in the library's device image: every GPU
+ * that loads the library holds it until the process exits.
  *  Limits: 1 <= r <= 16, r <= n <= 65536; larger sizes return LRS_ERR_ARG.
  *  The first call on a device (with that device current) looks up the
- *  scratch address with cudaGetSymbolAddress; make that first call before
- *  any stream capture.  All calls share the one array: calls whose work can
- *  overlap on the GPU (different streams, or different host threads on one
- *  device) race on it and must be serialised by the caller.  The call runs
- *  on `stream` and synchronises it.  Its own error message is returned by
+ *  scratch's device address with cudaGetSymbolAddress and keeps it for the
+ *  process; make that first call before any stream capture, and do not use
+ *  the call on a device after its context has been reset (cudaDeviceReset)
+ *  in the same process.  All calls share the one array and the error word in
+ *  it (cleared at the start of every call): calls whose work can overlap on
+ *  the GPU (different streams, or different host threads on one device)
+ *  race on it and must be serialised by the caller.  Each call runs on
+ *  `stream`, copies the error word back to the host and synchronises the
+ *  stream before it returns.  Its own error message is returned by
  *  lrs_noalloc_last_error().
  * Errors: LRS_ERR_ARG, LRS_ERR_NUMERICAL (Z rank deficient), LRS_ERR_CUDA. */
 lrs_status lrs_orthonormalize_noalloc(const float* Z, float* Q, int64_t n, int32_t r,

@@ -46,15 +46,20 @@ import numpy as np
 # ------------------------------------------------------------ operators --
 
 class GaussianOperator:
-    """A_k dense m x n (float64 copies of the stored float32 values)."""
+    """A_k dense m x n (float64 copies of the stored float32 values).
 
-    def __init__(self, A):
-        self.M = np.asarray(A, dtype=np.float64)          # (q, m, n)
+    dtype: the arithmetic of every step that uses this operator (float64 for
+    the oracle; float32 only for studies of what float32 arithmetic can
+    resolve, never for a parity reference)."""
+
+    def __init__(self, A, dtype=np.float64):
+        self.dtype = np.dtype(dtype)
+        self.M = np.asarray(A, dtype=self.dtype)          # (q, m, n)
         self.q, self.m, self.n = self.M.shape
         self.complex = False
 
     def subset(self, ks):
-        return GaussianOperator(self.M[ks])
+        return GaussianOperator(self.M[ks], self.dtype)
 
     def A(self, X):                 # X: (q, n) -> (q, m): A_k x_k
         return (self.M @ X[:, :, None])[:, :, 0]
@@ -77,15 +82,16 @@ class FourierOperator:
     kx*ny + ky in natural (unshifted) order.
     """
 
-    def __init__(self, masks, nx, ny):
+    def __init__(self, masks, nx, ny, dtype=np.complex128):
         self.masks = np.asarray(masks, dtype=np.int64)   # (q, m)
         self.nx, self.ny = nx, ny
         self.q, self.m = self.masks.shape
         self.n = nx * ny
         self.complex = True
+        self.dtype = np.dtype(dtype)    # complex128; complex64 only for float32 studies
 
     def subset(self, ks):
-        return FourierOperator(self.masks[ks], self.nx, self.ny)
+        return FourierOperator(self.masks[ks], self.nx, self.ny, self.dtype)
 
     def _fft(self, X):              # (..., n) -> (..., n)
         sh = X.shape[:-1]
@@ -98,15 +104,15 @@ class FourierOperator:
         return F.reshape(sh + (self.n,))
 
     def A(self, X):
-        return np.take_along_axis(self._fft(X.astype(np.complex128)), self.masks, axis=1)
+        return np.take_along_axis(self._fft(X.astype(self.dtype)), self.masks, axis=1)
 
     def AH(self, V):
-        Z = np.zeros((V.shape[0], self.n), dtype=np.complex128)
+        Z = np.zeros((V.shape[0], self.n), dtype=self.dtype)
         np.put_along_axis(Z, self.masks, V, axis=1)
         return self._ifft(Z)
 
     def AU(self, U):
-        FU = self._fft(U.T.astype(np.complex128))          # (r, n): F2 u_j
+        FU = self._fft(U.T.astype(self.dtype))             # (r, n): F2 u_j
         return np.stack([FU[:, mk].T for mk in self.masks])  # (q, m, r)
 
     def explicit(self):
@@ -185,7 +191,7 @@ def iht(z, M, MH, rho, tau, s0, mu_rule="support", idx0=None, perturb=None):
             idx_cur = np.tile(np.arange(rho, dtype=np.int64), (K, 1))
         if not np.any(active):
             break
-        mu = np.zeros(K)
+        mu = np.zeros(K, dtype=num.dtype)
         if mu_rule == "printed":        # literal ||g|| / ||M g||
             mu[active] = np.sqrt(num[active]) / np.sqrt(den[active])
         else:
@@ -271,7 +277,7 @@ def init_alg1(op, Y, r, rho, tau0=10, mu_rule="support", perturb=None):
     """Algorithm 1, Initialization: IHT(y_k, A_k, rho, tau0, 0); L0; U0; b_k.
     perturb: see `iht` (test aid, None in plain runs)."""
     q, n = op.q, op.n
-    dt = np.complex128 if op.complex else np.float64
+    dt = op.dtype
     Y = np.asarray(Y, dtype=dt)
     S, S_idx, margin = iht(Y, op.A, op.AH, rho, tau0, np.zeros((q, n), dtype=dt), mu_rule,
                            perturb=perturb)
@@ -294,7 +300,7 @@ def iterate_alg1(op, Y, st, rho, tau=3, c_eta=0.14, mu_rule="support", chunk=Non
     perturb: see `iht` (test aid, None in plain runs).
     """
     q, n = op.q, op.n
-    dt = np.complex128 if op.complex else np.float64
+    dt = op.dtype
     Y = np.asarray(Y, dtype=dt)
     chunk = chunk or q
     margins = np.empty(q)

@@ -356,6 +356,46 @@ __global__ void transpose_kernel(const float* in, float* out, int rows, int cols
   }
 }
 
+// X = U B + S (Algorithm 1, Output: x_k = U b_k + s_k), one block per column
+// k.  U n x r column-major, B r x q column-major, S rho x q (indices, values);
+// X n x q column-major.  CT = 1 real float, 2 interleaved complex64.
+template <int CT>
+__global__ void assemble_x_kernel(int n, int q, int r, int rho, const float* U, const float* B,
+                                  const int* S_idx, const float* S_val, float* X) {
+  const int k = blockIdx.x;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    float re = 0.f, im = 0.f;
+    for (int l = 0; l < r; ++l) {
+      const size_t iu = static_cast<size_t>(l) * n + j, ib = static_cast<size_t>(k) * r + l;
+      if (CT == 1) {
+        re = fmaf(U[iu], B[ib], re);
+      } else {
+        const float ur = U[2 * iu], ui = U[2 * iu + 1], br = B[2 * ib], bi = B[2 * ib + 1];
+        re = fmaf(ur, br, fmaf(-ui, bi, re));
+        im = fmaf(ur, bi, fmaf(ui, br, im));
+      }
+    }
+    const size_t ix = static_cast<size_t>(k) * n + j;
+    if (CT == 1) {
+      X[ix] = re;
+    } else {
+      X[2 * ix] = re;
+      X[2 * ix + 1] = im;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < rho; e += blockDim.x) {   // indices of a column are distinct
+    const int j = S_idx[static_cast<size_t>(k) * rho + e];
+    const size_t ix = static_cast<size_t>(k) * n + j, is = static_cast<size_t>(k) * rho + e;
+    if (CT == 1) {
+      X[ix] += S_val[is];
+    } else {
+      X[2 * ix] += S_val[2 * is];
+      X[2 * ix + 1] += S_val[2 * is + 1];
+    }
+  }
+}
+
 // Deterministic start of the subspace iteration: splitmix64 + Box-Muller.
 std::vector<float> start_block(int64_t n, int r, uint64_t seed) {
   std::vector<float> v(static_cast<size_t>(n) * r);
@@ -1022,6 +1062,48 @@ lrs_status lrs_get(lrs_t h, void* U, void* B, int32_t* S_idx, void* S_val, int32
     CUDA_TRY(cudaMemcpyAsync(S_val, h->S_val, sizeof(float) * h->q * h->rho, kout, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   return LRS_OK;
+}
+
+lrs_status lrs_get_x(lrs_t h, void* X, int32_t mem_kind) {
+  if (!h || !X) return fail(LRS_ERR_ARG, "lrs_get_x: NULL argument");
+  if (mem_kind != 0 && mem_kind != 1) return fail(LRS_ERR_ARG, "lrs_get_x: mem_kind must be 0 or 1");
+  if (h->state < kInitialised) return fail(LRS_ERR_STATE, "lrs_get_x: no iterate yet");
+  const int ct = h->F ? 2 : 1;
+  const size_t nU = static_cast<size_t>(h->n) * h->r * ct, nB = static_cast<size_t>(h->q) * h->r * ct;
+  const size_t nS = static_cast<size_t>(h->q) * h->rho, nX = static_cast<size_t>(h->n) * h->q * ct;
+  float *U = nullptr, *B = nullptr, *Sv = nullptr, *Xd = nullptr;
+  int* Si = nullptr;
+  const size_t bytes = sizeof(float) * (nU + nB + nS * ct + (mem_kind ? 0 : nX)) + sizeof(int) * nS + 256;
+  char* buf = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&buf), bytes, h->stream) != cudaSuccess)
+    return fail(LRS_ERR_OOM, "lrs_get_x: scratch");
+  U = reinterpret_cast<float*>(buf);     // [U | B | S values | X (host case) | S indices]
+  B = U + nU;
+  Sv = B + nB;
+  float* after = Sv + nS * ct;
+  if (mem_kind) {
+    Xd = static_cast<float*>(X);
+  } else {
+    Xd = after;
+    after += nX;
+  }
+  Si = reinterpret_cast<int*>(after);
+  lrs_status st = lrs_get(h, U, B, h->rho ? Si : nullptr, h->rho ? Sv : nullptr, 1);
+  if (st == LRS_OK) {
+    if (ct == 1)
+      assemble_x_kernel<1><<<static_cast<unsigned>(h->q), 256, 0, h->stream>>>(
+          static_cast<int>(h->n), static_cast<int>(h->q), h->r, h->rho, U, B, Si, Sv, Xd);
+    else
+      assemble_x_kernel<2><<<static_cast<unsigned>(h->q), 256, 0, h->stream>>>(
+          static_cast<int>(h->n), static_cast<int>(h->q), h->r, h->rho, U, B, Si, Sv, Xd);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !mem_kind)
+      e = cudaMemcpyAsync(X, Xd, sizeof(float) * nX, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) st = fail(LRS_ERR_CUDA, std::string("lrs_get_x: ") + cudaGetErrorString(e));
+  }
+  cudaFreeAsync(buf, h->stream);
+  return st;
 }
 
 lrs_status lrs_set_state(lrs_t h, const void* U, const void* B, const int32_t* S_idx,

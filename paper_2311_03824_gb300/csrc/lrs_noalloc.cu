@@ -4,13 +4,12 @@
 //
 // Some callers cannot allocate device memory at the point where they need
 // this step: an application that has already handed all device memory to its
-// own pool, a serving loop that must not stall other streams on the implicit
-// synchronisation of cudaMalloc/cudaFree, or code that records its GPU work
-// once and replays it and therefore must not create allocations in between.
-// This entry point serves them: it calls no cudaMalloc, cudaFree or other
-// allocating routine.  The price is a fixed scratch array of
-// kNoAllocScratchBytes (about 4.6 MB) that every GPU which loads the library
-// keeps until the process exits, and fixed size limits (n <= 65536, r <= 16).
+// own pool, or a serving loop that must not stall other streams on the
+// implicit synchronisation of cudaMalloc/cudaFree.  This entry point serves
+// them: it calls no cudaMalloc, cudaFree or other allocating routine.  The
+// price is a fixed scratch array of kNoAllocScratchBytes (about 4.6 MB) that
+// every GPU which loads the library keeps until the process exits, and fixed
+// size limits (n <= 65536, r <= 16).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -30,7 +29,8 @@ constexpr size_t kRfacBytes = sizeof(double) * 2 * kNoAllocMaxR * kNoAllocMaxR;
 constexpr size_t kNoAllocScratchBytes = kTmpBytes + kPartBytes + kRfacBytes + 256;
 
 // The scratch.  Host code must not use this name as a device address: its
-// device address comes from cudaGetSymbolAddress, once per device.
+// device address comes from cudaGetSymbolAddress, once per device, and is
+// kept for the process (a context reset on that device invalidates it).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;

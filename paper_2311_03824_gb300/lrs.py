@@ -64,6 +64,7 @@ def lib():
             "lrs_iterate": [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)],
             "lrs_solve": [_P],
             "lrs_get": [_P, _P, _P, _P, _P, ctypes.c_int32],
+            "lrs_get_x": [_P, _P, ctypes.c_int32],
             "lrs_set_state": [_P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_double,
                               ctypes.c_int32],
             "lrs_get_progress": [_P, ctypes.POINTER(ctypes.c_double),
@@ -160,6 +161,11 @@ def lrs_solve(h):
 def lrs_get(h, U=None, B=None, S_idx=None, S_val=None):
     mk = _same_kind(U, B, S_idx, S_val)
     _check(lib().lrs_get(h, _ptr(U)[0], _ptr(B)[0], _ptr(S_idx)[0], _ptr(S_val)[0], mk))
+
+
+def lrs_get_x(h, X):
+    """X = U B + S of the current iterate (n x q column-major: a (q, n) array)."""
+    _check(lib().lrs_get_x(h, _ptr(X)[0], _ptr(X)[1]))
 
 
 def lrs_set_state(h, U, B, S_idx, S_val, t, eta):
@@ -282,11 +288,10 @@ class Solver:
         return U.T.copy(), B.T.copy(), S_idx[:, :self.rho], S_val[:, :self.rho]
 
     def X(self):
-        U, B, S_idx, S_val = self.get()
-        X = U.astype(np.complex128 if self.dtype == np.complex64 else np.float64) @ B
-        for k in range(self.q):
-            X[S_idx[k], k] += S_val[k]
-        return X
+        """X = U B + S (n, q), assembled by the library (lrs_get_x)."""
+        X = np.empty((self.q, self.n), self.dtype)      # n x q column-major
+        lrs_get_x(self.h, X)
+        return X.T.copy()
 
     def progress(self):
         return lrs_get_progress(self.h)

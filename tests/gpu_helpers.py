@@ -1,28 +1,44 @@
 """Shared helpers of the GPU parity tests: run the CUDA solver through the C
-ABI and the FP64 oracle on the same seeded instance, iterate by iterate.
+ABI and the FP64 oracle on the same seeded instance, step by step.
 
-FP32 arithmetic reproduces a HardThreshold decision of the FP64 oracle only
-when the decision's margin (|v|_(rho) - |v|_(rho+1)) / max|v| exceeds the
-relative error of the FP32 values v, about 1e-6 here; MARGIN_FP32 = 1e-4 is
-the resolution the tests assume.  Columns whose oracle margin (the smallest
-over the IHT sweeps of an iteration) is below it are "undecidable" for FP32.
+Which HardThreshold decisions are compared.  FP32 arithmetic reproduces a
+decision of the FP64 oracle only when the decision's gap
+margin = (|v|_(rho) - |v|_(rho+1)) / max|v| (Algorithm 2; the oracle's
+`hard_threshold`) exceeds what float32 rounding moves it by.  Every compared
+step is therefore probed: besides the FP64 oracle step, the same oracle step
+is run in float32 from the same state (the oracle's operators take a dtype),
+and a column's decision counts as decidable when
+  * its FP64 margin (smallest over the IHT sweeps) exceeds MARGIN_FP32 = 1e-6,
+  * it exceeds DEC_FACTOR = 10 times the change of the margin between the
+    float32 and float64 steps (largest over the sweeps), and
+  * the float32 step keeps the same support.
+tests/fp32_margin_study.py (results in tests/golden/fp32_margin_study.txt)
+measures this on the instances of these tests: no float32 step departed from
+the FP64 support at any margin (the smallest margin seen is 2.5e-6), the
+median change of the gap is 6e-8 to 3e-6 and its 99th percentile 3e-6 to
+2e-3, and the rule leaves out 1 of 65,712 column-steps; so the floor sits at
+the float32 resolution and the per-column factor covers the columns whose mu is badly conditioned.  The initialisation's tau0 sweeps from
+s = 0 can amplify a rounding difference past large margins; its decisions
+are in addition rerun NPERT times with a relative perturbation of PERTURB
+(about a float32 ulp) applied to v before each HardThreshold (the oracle's
+test hook), and columns that move are not compared.
 
-Margins do not capture every sensitivity: an IHT trajectory can itself
-amplify rounding (for instance a mu that alternates between two values
-from sweep to sweep), so that FP32 and FP64 leave a decision with a large
-margin by different routes.  `step_sensitivity` / `run_sensitivity` measure
-it directly: the oracle is rerun NPERT times with a relative perturbation
-of 1e-7 (about a float32 ulp) applied to v = s - mu g before every
-HardThreshold (the oracle's test hook), every column whose support moves
-in any rerun is taken as undecidable, and the parity bar of an iterate
-becomes max(1e-5, 10 x the largest relative change of X).
+What is compared.  b_k and s_k of a step depend only on column k and U_t, so
+they are compared on every decidable column (supports identical, values
+within TOL relative over those columns); X_{t+1} = U_{t+1} B_{t+1} + S_{t+1}
+mixes all columns through the gradient and is compared as a whole (TOL)
+whenever every column is decidable.  Each test bounds the share of column-
+steps it excludes (MAX_EXCLUDED) and the number of whole-X checks it must
+make.
 """
 import numpy as np
 
 import oracle.altgdmin_lrs as O
 
-MARGIN_FP32 = 1e-4
+MARGIN_FP32 = 1e-6
+DEC_FACTOR = 10.0
 TOL = 1e-5
+MAX_EXCLUDED = 0.01
 PERTURB = 1e-7
 NPERT = 3
 
@@ -33,6 +49,17 @@ def rounding_noise(seed):
     return lambda v: v * (1.0 + PERTURB * rng.standard_normal(v.shape))
 
 
+class Recorder:
+    """perturb hook that records v of every IHT sweep and returns it unchanged."""
+
+    def __init__(self):
+        self.v = []
+
+    def __call__(self, v):
+        self.v.append(np.array(v, copy=True))
+        return v
+
+
 def gpu_available():
     try:
         import torch
@@ -41,22 +68,211 @@ def gpu_available():
         return False
 
 
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# ------------------------------------------------------------- problems --
+
+class Problem:
+    """Oracle side of one instance: the FP64 operator, its float32 twin and the
+    measurements the solver sees."""
+
+    def __init__(self, op64, op32, Y, r, rho):
+        self.op64, self.op32 = op64, op32
+        self.Y = np.asarray(Y)
+        self.n, self.q, self.r, self.rho = op64.n, op64.q, r, rho
+        self.cplx = op64.complex
+        self.dt = np.complex128 if self.cplx else np.float64
+
+    @staticmethod
+    def gaussian(inst, A=None, rho=None):
+        A = inst.A if A is None else A
+        return Problem(O.GaussianOperator(A), O.GaussianOperator(A, np.float32), inst.Y,
+                       inst.r, inst.rho if rho is None else rho)
+
+    @staticmethod
+    def fourier(inst):
+        return Problem(O.FourierOperator(inst.masks, inst.nx, inst.ny),
+                       O.FourierOperator(inst.masks, inst.nx, inst.ny, np.complex64),
+                       inst.Y, inst.r, inst.rho)
+
+    def y32(self, Y):
+        return np.asarray(Y).astype(np.complex64 if self.cplx else np.float32)
+
+
 def oracle_run(inst, T, rho=None, **kw):
     rho = inst.rho if rho is None else rho
     return O.run_alg1(O.GaussianOperator(inst.A), inst.Y, inst.r, rho, T,
                       keep=tuple(range(T + 1)), Xstar=inst.Xstar, **kw)
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-
-
 def x_of(U, B, S_idx, S_val, q):
-    X = U.astype(np.float64) @ B.astype(np.float64)
+    dt = np.complex128 if np.iscomplexobj(U) else np.float64
+    X = U.astype(dt) @ B.astype(dt)
     for k in range(q):
         X[S_idx[k], k] += S_val[k]
     return X
 
+
+def sorted_support(S_idx, S_val):
+    o = np.argsort(S_idx, axis=1)
+    return np.take_along_axis(S_idx, o, 1).astype(np.int64), np.take_along_axis(S_val, o, 1)
+
+
+def state_of(log, t, n):
+    """OracleState of the logged oracle iterate t."""
+    S = O.densify(log.S_idx[t], log.S_val[t], n)
+    return O.OracleState(U=log.U[t].copy(), B=log.B[t].copy(), S=S, S_idx=log.S_idx[t].copy(),
+                         eta=log.eta if t else None, t=t)
+
+
+def state_from_gpu(g, n, t, eta, dt):
+    """OracleState (FP64 or complex128) of a GPU iterate g = (U n x r, B r x q,
+    S_idx q x rho, S_val q x rho)."""
+    U, B, S_idx, S_val = g
+    q = B.shape[1]
+    Si, Sv = sorted_support(S_idx, S_val)
+    S = np.zeros((q, n), dt)
+    if Si.size:
+        np.put_along_axis(S, Si, Sv.astype(dt), axis=1)
+    return O.OracleState(U=U.astype(dt), B=B.astype(dt), S=S, S_idx=Si,
+                         eta=eta if t else None, t=t)
+
+
+def cast_state(st, dt):
+    return O.OracleState(U=st.U.astype(dt), B=st.B.astype(dt), S=st.S.astype(dt),
+                         S_idx=st.S_idx.copy(), eta=st.eta, t=st.t)
+
+
+def _gap_change(r32, r64, rho):
+    """Per column: largest change over the IHT sweeps of the HardThreshold gap
+    between the float32 and float64 sweeps (recorded v per sweep)."""
+    d = np.zeros(r64.v[0].shape[0]) if r64.v else None
+    for a, b in zip(r32.v, r64.v):
+        ma = O.hard_threshold(a, rho)[2]
+        mb = O.hard_threshold(b, rho)[2]
+        ok = np.isfinite(ma) & np.isfinite(mb)
+        d = np.maximum(d, np.where(ok, np.abs(ma - mb), 0.0))
+    return d
+
+
+def _sub_state(st, ks, dt):
+    return O.OracleState(U=st.U.astype(dt), B=st.B[:, ks].astype(dt), S=st.S[ks].astype(dt),
+                         S_idx=st.S_idx[ks].copy(), eta=st.eta, t=st.t)
+
+
+def _probe_columns(P, st, Y, ks, mg, r64=None):
+    """Decidable among columns ks: the FP64 and float32 steps of those columns
+    from state st (their supports, b_k and s_k depend only on the column and
+    U_t), sweep by sweep.  r64: the recorded FP64 sweeps when the caller's
+    step already covered exactly these columns."""
+    a = None
+    if r64 is None:
+        r64 = Recorder()
+        a = _sub_state(st, ks, P.dt)
+        O.iterate_alg1(P.op64.subset(ks), Y[ks], a, P.rho, perturb=r64)
+    r32 = Recorder()
+    b = _sub_state(st, ks, np.complex64 if P.cplx else np.float32)
+    O.iterate_alg1(P.op32.subset(ks), P.y32(Y[ks]), b, P.rho, perturb=r32)
+    return b.S_idx, r32, r64, a
+
+
+def probe_step(P, st, Y=None, sens=0, chunk=None):
+    """The FP64 oracle step from state `st` (not modified) and its float32
+    probe.  Returns (FP64 state after the step, FP64 margins, decidable).
+    chunk: columns per batch (memory of large problems)."""
+    Y = np.asarray(P.Y if Y is None else Y)
+    st64 = cast_state(st, P.dt)
+    whole = chunk is None or chunk >= P.q
+    rec = Recorder() if whole else None
+    mg, _ = O.iterate_alg1(P.op64, Y, st64, P.rho, chunk=chunk, perturb=rec)
+    step = P.q if whole else chunk
+    dec = mg > MARGIN_FP32
+    for k0 in range(0, P.q, step):
+        ks = np.arange(k0, min(P.q, k0 + step))
+        S32, r32, r64, _ = _probe_columns(P, st, Y, ks, mg, rec)
+        dec[ks] &= np.all(S32 == st64.S_idx[ks], axis=1)
+        if r64.v:
+            dec[ks] &= mg[ks] > DEC_FACTOR * _gap_change(r32, r64, P.rho)
+    for i in range(sens):
+        sp = cast_state(st, P.dt)
+        O.iterate_alg1(P.op64, Y, sp, P.rho, perturb=rounding_noise(7919 * st.t + i), chunk=chunk)
+        dec &= np.all(sp.S_idx == st64.S_idx, axis=1)
+    return st64, mg, dec
+
+
+def probe_init(P, sens=NPERT):
+    """The FP64 initialisation, its float32 probe and NPERT perturbed reruns.
+    Returns (FP64 initial state, margins, decidable)."""
+    r64, r32 = Recorder(), Recorder()
+    st64, _, _, mg = O.init_alg1(P.op64, P.Y, P.r, P.rho, perturb=r64)
+    st32, _, _, _ = O.init_alg1(P.op32, P.y32(P.Y), P.r, P.rho, perturb=r32)
+    dec = (mg > MARGIN_FP32) & np.all(st32.S_idx == st64.S_idx, axis=1)
+    if r64.v:
+        dec &= mg > DEC_FACTOR * _gap_change(r32, r64, P.rho)
+    for i in range(sens):
+        sp, _, _, _ = O.init_alg1(P.op64, P.Y, P.r, P.rho, perturb=rounding_noise(104729 + i))
+        dec &= np.all(sp.S_idx == st64.S_idx, axis=1)
+    return st64, mg, dec
+
+
+def compare_step(st64, dec, g_next, tol=TOL, basis_free=False, whole=True):
+    """GPU iterate g_next = (U, B, S_idx, S_val) against the FP64 oracle state
+    st64 of the same step on the decidable columns (and as a whole when all
+    are).  basis_free: compare the low-rank columns U b_k instead of b_k (the
+    initialisation, where U0 is the same subspace in another basis).
+    whole=False: columns sampled from a larger problem (no whole-X check)."""
+    U1, B1, S1i, S1v = g_next
+    q = B1.shape[1]
+    Si, Sv = sorted_support(S1i, S1v)
+    out = dict(excluded=int((~dec).sum()), columns=q, sup_bad=0, b_rel=0.0, s_rel=0.0,
+               whole=None, ascending=True)
+    if st64.S_idx.shape[1] > 1:
+        out["ascending"] = bool(np.all(np.diff(S1i, axis=1) > 0))
+    if dec.any():
+        out["sup_bad"] = int(np.sum(np.any(Si[dec] != st64.S_idx[dec], axis=1)))
+        if basis_free:
+            out["b_rel"] = rel(U1.astype(st64.U.dtype) @ B1[:, dec].astype(st64.B.dtype),
+                               st64.U @ st64.B[:, dec])
+        else:
+            out["b_rel"] = rel(B1[:, dec].astype(st64.B.dtype), st64.B[:, dec])
+        if Si.shape[1]:
+            So = np.take_along_axis(st64.S[dec], st64.S_idx[dec], 1)
+            out["s_rel"] = rel(Sv[dec].astype(So.dtype), So) if np.linalg.norm(So) > 0 else 0.0
+    if whole and dec.all():
+        Xo = st64.U @ st64.B + st64.S.T
+        out["whole"] = rel(x_of(U1, B1, S1i, S1v, q), Xo)
+    out["ortho"] = float(np.abs(U1.conj().T.astype(np.complex128) @ U1 - np.eye(U1.shape[1])).max())
+    out["tol"] = tol
+    return out
+
+
+def check_records(recs, min_whole, max_excluded=MAX_EXCLUDED):
+    """Assert the per-step records of a parity test and return its summary:
+    supports identical and b_k, s_k within the bar on decidable columns, whole
+    X within the bar where every column is decidable (at least min_whole
+    such steps), excluded column-steps at most max_excluded of all."""
+    whole = 0
+    excl = sum(r["excluded"] for r in recs)
+    tot = sum(r["columns"] for r in recs)
+    for r in recs:
+        assert r["sup_bad"] == 0, ("support mismatch on decidable columns", r)
+        assert r["b_rel"] <= r["tol"], ("b_k", r)
+        assert r["s_rel"] <= r["tol"], ("s_k", r)
+        assert r["ascending"], r
+        assert r["ortho"] < 1e-5, r
+        if r["whole"] is not None:
+            assert r["whole"] <= r["tol"], ("X", r)
+            whole += 1
+    assert whole >= min_whole, ("whole-X checks", whole, min_whole)
+    assert excl <= max_excluded * tot, ("excluded column-steps", excl, tot)
+    return dict(steps=len(recs), whole=whole, excluded=excl, column_steps=tot,
+                max_b=max((r["b_rel"] for r in recs), default=0.0),
+                max_x=max((r["whole"] for r in recs if r["whole"] is not None), default=0.0))
+
+
+# ----------------------------------------------------------- GPU runs --
 
 def new_solver(inst, **opts):
     from paper_2311_03824_gb300 import Solver
@@ -66,101 +282,102 @@ def new_solver(inst, **opts):
     return s
 
 
-def trajectory(inst, T, log, sens=None, **solver_opts):
-    """Run lrs_init + T x lrs_iterate(1); per iterate: relative X difference to
-    the oracle, support mismatches among decidable columns, orthonormality.
-    With `sens` (run_sensitivity) columns whose support moved under the
-    perturbation are undecided and each record carries its bar."""
-    s = new_solver(inst, **solver_opts)
-    try:
-        s.init()
-        out = []
-        undecided = np.zeros(inst.q, bool)      # a sub-resolution decision so far
-        for t in range(T + 1):
-            if t:
-                s.iterate(1)
-            U, B, S_idx, S_val = s.get()
-            X = x_of(U, B, S_idx, S_val, inst.q)
-            undecided |= log.margin[t] <= MARGIN_FP32
-            bar = TOL
-            if sens is not None:
-                undecided |= sens[t][1]
-                bar = max(TOL, 10.0 * sens[t][0])
-            ok = ~undecided
-            bad = int(np.sum(np.any(np.sort(S_idx[ok], axis=1) != log.S_idx[t][ok], axis=1)))
-            out.append(dict(t=t, rel=rel(X, log.X[t]), sup_bad=bad, undecided=int(undecided.sum()),
-                            bar=bar,
-                            ortho=float(np.abs(U.T.astype(np.float64) @ U - np.eye(inst.r)).max()),
-                            ascending=bool(np.all(np.diff(S_idx, axis=1) > 0)) if inst.rho > 1 else True))
-        eta, _ = s.progress()
-        return out, eta
-    finally:
-        s.close()
+def new_fourier_solver(inst, **opts):
+    from paper_2311_03824_gb300 import LRS_OP_DFT2D_MASK, Solver
+    s = Solver(inst.n, inst.m, inst.q, inst.r, inst.rho, kind=LRS_OP_DFT2D_MASK,
+               nx=inst.nx, ny=inst.ny, **opts)
+    s.set_measurements(np.ascontiguousarray(inst.Y, np.complex64),
+                       np.ascontiguousarray(inst.masks, np.int32))
+    return s
 
 
-def state_of(log, t, n):
-    """OracleState of the logged iterate t."""
-    S = O.densify(log.S_idx[t], log.S_val[t], n)
-    return O.OracleState(U=log.U[t].copy(), B=log.B[t].copy(), S=S, S_idx=log.S_idx[t].copy(),
-                         eta=log.eta if t else None, t=t)
+def set_gpu_state(s, st, cplx):
+    """Load an oracle state into the solver (lrs_set_state)."""
+    from paper_2311_03824_gb300 import lrs as L
+    ct = np.complex64 if cplx else np.float32
+    U = np.ascontiguousarray(st.U.T, ct)           # n x r column-major
+    B = np.ascontiguousarray(st.B.T, ct)           # r x q column-major
+    Si = np.ascontiguousarray(st.S_idx, np.int32)
+    Sv = np.ascontiguousarray(np.take_along_axis(st.S, st.S_idx, 1) if st.S_idx.size
+                              else np.zeros(st.S_idx.shape), ct)
+    L.lrs_set_state(s.h, U, B, Si, Sv, st.t, float(st.eta or 0.0))
 
 
-def step_sensitivity(op, y_of_t, log, ts, rho, n):
-    """Per t: (largest relative change of X_{t+1}, columns whose support
-    moves) over NPERT reruns of the oracle's step from iterate t with
-    rounding-size perturbations inside the IHT."""
-    out = {}
+def one_step(P, s, log, ts, y_of_t=None, tol=TOL):
+    """From the oracle's iterate t (lrs_set_state) one GPU iteration, compared
+    with the probed FP64 oracle step from the same state."""
+    recs = []
     for t in ts:
-        d, moved = 0.0, np.zeros(log.S_idx[t].shape[0], bool)
-        for i in range(NPERT):
-            st = state_of(log, t, n)
-            O.iterate_alg1(op, y_of_t(t), st, rho, perturb=rounding_noise(1000 * t + i))
-            d = max(d, rel(st.U @ st.B + st.S.T, log.X[t + 1]))
-            moved |= np.any(np.sort(st.S_idx, axis=1) != log.S_idx[t + 1], axis=1)
-        out[t] = (d, moved)
-    return out
+        st = state_of(log, t, P.n)
+        Y = None if y_of_t is None else y_of_t(t)
+        st64, _, dec = probe_step(P, st, Y)
+        set_gpu_state(s, st, P.cplx)
+        s.iterate(1)
+        r = compare_step(st64, dec, s.get(), tol)
+        r["t"] = t
+        recs.append(r)
+    return recs
 
 
-def run_sensitivity(log, logs_p):
-    """Per iterate of a run and its perturbed reruns: (largest relative change
-    of X, columns whose support has moved at or before that iterate)."""
-    out, moved = [], np.zeros(log.S_idx[0].shape[0], bool)
-    for t in range(len(log.X)):
-        d = 0.0
-        for lp in logs_p:
-            moved |= np.any(np.sort(lp.S_idx[t], axis=1) != log.S_idx[t], axis=1)
-            d = max(d, rel(lp.X[t], log.X[t]))
-        out.append((d, moved.copy()))
-    return out
+def gpu_trajectory(s, T):
+    """lrs_init, then T x lrs_iterate(1): the GPU iterates t = 0..T and eta."""
+    s.init()
+    states = [s.get()]
+    for _ in range(T):
+        s.iterate(1)
+        states.append(s.get())
+    eta, _ = s.progress()
+    return states, eta
 
 
-def one_step(inst, log, ts, sens=None, **solver_opts):
-    """From the oracle's iterate t (U_t, B_t, S_t, eta) run one GPU iteration
-    and compare with the oracle's iterate t+1.  Returns per-t records.  With
-    `sens` (step_sensitivity) columns whose support moves under the
-    perturbation count as undecided and the record carries the iterate's
-    bar max(TOL, 10 x change)."""
-    s = new_solver(inst, **solver_opts)
-    out = []
-    try:
-        for t in ts:
-            U = np.ascontiguousarray(log.U[t].T, np.float32)           # n x r column-major
-            B = np.ascontiguousarray(log.B[t].T, np.float32)           # r x q column-major
-            Si = np.ascontiguousarray(log.S_idx[t], np.int32)
-            Sv = np.ascontiguousarray(log.S_val[t], np.float32)
-            from paper_2311_03824_gb300 import lrs as L
-            L.lrs_set_state(s.h, U, B, Si, Sv, t, float(log.eta if t else 0.0))
-            s.iterate(1)
-            U1, B1, S_idx, S_val = s.get()
-            X = x_of(U1, B1, S_idx, S_val, inst.q)
-            dec = log.margin[t + 1] > MARGIN_FP32
-            bar = TOL
-            if sens is not None:
-                dec = dec & ~sens[t][1]
-                bar = max(TOL, 10.0 * sens[t][0])
-            bad = int(np.sum(np.any(np.sort(S_idx[dec], axis=1) != log.S_idx[t + 1][dec], axis=1)))
-            out.append(dict(t=t, rel=rel(X, log.X[t + 1]), sup_bad=bad,
-                            undecided=int((~dec).sum()), bar=bar))
-        return out
-    finally:
-        s.close()
+def init_record(P, g0, tol=TOL):
+    """The GPU initialisation g0 = (U0, B0, S_idx, S_val) against the oracle's
+    (Algorithm 1, Initialization).  The IHT supports and values are compared
+    on the columns the probe finds decidable.  U0 and b_k depend on every
+    column through L0, so they are compared with what the oracle computes
+    from the GPU's own supports: U0 against the top-r left singular subspace
+    of L0 = [A_k^H (y_k - A_k s_k)] (FP64, full SVD; 1 - cos of the principal
+    angles below 1e-6), and b_k against (A_k U0)^+ (y_k - A_k s_k) (FP64
+    pseudo-inverse, relative TOL over all columns)."""
+    st0, _, dec = probe_init(P)
+    rec = compare_step(st0, dec, g0, tol, whole=False)
+    rec["b_rel"] = 0.0
+    U, B, S_idx, S_val = g0
+    gs = state_from_gpu(g0, P.n, 0, None, P.dt)
+    R = np.asarray(P.Y, P.dt) - P.op64.A(gs.S)
+    L0 = P.op64.AH(R).T
+    Ut, _ = O.top_r_left(L0, P.r)
+    cos = np.linalg.svd(U.astype(P.dt).conj().T @ Ut, compute_uv=False)
+    rec["u0_angle"] = float(np.max(np.abs(1.0 - cos)))
+    assert rec["u0_angle"] < 1e-6, ("U0 subspace", rec["u0_angle"])
+    Bo = O.pinv_apply(P.op64.AU(U.astype(P.dt)), R).T
+    rec["b0_rel"] = rel(B.astype(P.dt), Bo)
+    assert rec["b0_rel"] <= tol, ("b_k of the initialisation", rec["b0_rel"])
+    rec["t"] = 0
+    return rec
+
+
+def trajectory_records(P, states, eta, init_check=True, tol=TOL):
+    """Every step of a GPU trajectory against the probed FP64 oracle step from
+    the GPU's own previous iterate; the first record compares the GPU
+    initialisation with the oracle's (when init_check)."""
+    recs = [init_record(P, states[0], tol)] if init_check else []
+    for t in range(len(states) - 1):
+        st = state_from_gpu(states[t], P.n, t, eta, P.dt)
+        st64, _, dec = probe_step(P, st)
+        r = compare_step(st64, dec, states[t + 1], tol)
+        r["t"] = t + 1
+        recs.append(r)
+    return recs
+
+
+def trajectory_agreement(states, log):
+    """Relative X difference between the GPU trajectory and the oracle's own
+    trajectory at every t, and the first t at which a support differs."""
+    q = states[0][1].shape[1]
+    rels, first = [], None
+    for t, g in enumerate(states):
+        rels.append(rel(x_of(*g, q), log.X[t]))
+        if first is None and np.any(sorted_support(g[2], g[3])[0] != log.S_idx[t]):
+            first = t
+    return rels, first

@@ -1,21 +1,28 @@
-"""CUDA solver (through the C ABI) against the FP64 oracle.
+"""CUDA solver (through the C ABI) against the FP64 oracle, step by step.
 
-Bars (float32 arithmetic against float64):
-  * one-step parity: from the oracle's iterate t, one GPU iteration matches
-    the oracle's iterate t+1 to ||dX||_F / ||X||_F <= 1e-5 with identical
-    supports, at every iterate whose HardThreshold decisions FP32 can resolve
-    (oracle margin > 1e-4);
-  * trajectory parity: a full GPU run matches the oracle at every iterate up
-    to the first sub-resolution decision, supports identical on decidable
-    columns throughout, and the final iterate matches within 1e-5;
-  * U orthonormal to float32 precision, S indices ascending, eta equal.
+Bars (float32 arithmetic against float64; tests/gpu_helpers.py says which
+HardThreshold decisions float32 can resolve and how that is probed):
+  * one-step parity: from the oracle's iterate t (lrs_set_state), one GPU
+    iteration against the FP64 oracle step from the same state: supports
+    identical and b_k, s_k within 1e-5 on every decidable column, the whole
+    X_{t+1} within 1e-5 whenever every column is decidable;
+  * trajectory parity: a GPU run from its own initialisation, every step
+    compared the same way with the oracle step from the GPU's own previous
+    iterate (so a column that float32 legitimately sends elsewhere does not
+    end the comparison), the initialisation compared with the oracle's, and
+    the whole trajectory within 1e-5 of the oracle's own trajectory up to the
+    first support that differs, and at the end;
+  * every test bounds the share of column-steps it leaves out (1 %) and the
+    number of whole-X checks it must make; U orthonormal, S ascending, eta
+    equal to 1e-4.
 """
 import numpy as np
 import pytest
 
 from lrsgen import GaussianInstance
-from tests.gpu_helpers import (MARGIN_FP32, TOL, gpu_available, one_step, oracle_run,
-                               trajectory)
+from tests.gpu_helpers import (TOL, Problem, check_records, gpu_available, gpu_trajectory,
+                               new_solver, one_step, oracle_run, trajectory_agreement,
+                               trajectory_records)
 
 pytestmark = pytest.mark.gpu
 
@@ -28,26 +35,34 @@ def _need_gpu():
     build.build()
 
 
-def check_trajectory(res, eta_gpu, log, tol=TOL, final_tol=TOL):
-    for r in res:
-        if r["undecided"] == 0:
-            assert r["rel"] <= max(tol, r.get("bar", tol)), ("iterate", r["t"], r["rel"])
-        assert r["sup_bad"] == 0, ("support mismatch on decidable columns", r)
-        assert r["ortho"] < 1e-5
-        assert r["ascending"]
-    assert res[-1]["rel"] <= final_tol, ("final iterate", res[-1]["rel"])
-    if log.eta is not None:
-        assert abs(eta_gpu - log.eta) <= 1e-4 * log.eta
+def run_one_step(inst, T, min_whole, rho=None, **opts):
+    P = Problem.gaussian(inst, rho=rho)
+    _, log = oracle_run(inst, T, rho=rho)
+    s = new_solver(inst, **opts)
+    try:
+        recs = one_step(P, s, log, range(T))
+    finally:
+        s.close()
+    return check_records(recs, min_whole)
 
 
-def check_one_step(res, tol=TOL):
-    n_checked = 0
-    for r in res:
-        assert r["sup_bad"] == 0, r
-        if r["undecided"] == 0:
-            assert r["rel"] <= max(tol, r.get("bar", tol)), r
-            n_checked += 1
-    assert n_checked >= len(res) // 2, "too few iterates with resolvable decisions"
+def run_trajectory(inst, T, min_whole, rho=None, **opts):
+    P = Problem.gaussian(inst, rho=rho)
+    _, log = oracle_run(inst, T, rho=rho)
+    s = new_solver(inst, **opts)
+    try:
+        states, eta = gpu_trajectory(s, T)
+    finally:
+        s.close()
+    summary = check_records(trajectory_records(P, states, eta), min_whole)
+    rels, first = trajectory_agreement(states, log)
+    upto = len(rels) if first is None else first
+    if upto:
+        assert max(rels[:upto]) <= TOL, ("trajectory before the first departure", max(rels[:upto]))
+    assert rels[-1] <= TOL, ("final iterate", rels[-1])
+    assert abs(eta - log.eta) <= 1e-4 * log.eta
+    summary["first_departure"] = first
+    return summary
 
 
 # Sweep engines and their launch shapes: engine 1 = one thread-block cluster
@@ -69,12 +84,10 @@ def shape_id(d):
 def test_one_step_ragged_all_shapes(shape):
     # n = 250: slabs of 32-column tiles with a ragged last tile and slab
     inst = GaussianInstance(n=250, q=40, r=3, m=36, rho=3, seed=101)
-    _, log = oracle_run(inst, 20)
     opts = dict(shape)
     if opts.get("engine") == 1:
         opts.setdefault("stages", 2)
-    res = one_step(inst, log, range(0, 20), **opts)
-    check_one_step(res)
+    run_one_step(inst, 20, min_whole=15, **opts)
 
 
 @pytest.mark.parametrize("shape", [dict(engine=2, task_kib=8, inflight=5), dict(engine=2)],
@@ -82,57 +95,58 @@ def test_one_step_ragged_all_shapes(shape):
 def test_one_step_tall_columns_task_engine(shape):
     """m = 300: several W row blocks and A^T row pieces per tile."""
     inst = GaussianInstance(n=140, q=24, r=4, m=300, rho=5, seed=102)
-    _, log = oracle_run(inst, 8)
-    res = one_step(inst, log, range(0, 8), **shape)
-    check_one_step(res)
+    run_one_step(inst, 8, min_whole=6, **shape)
 
 
 @pytest.mark.parametrize("engine", ENGINES)
 def test_trajectory_config0_full(engine):
-    """n=200, q=200, r=3, m=80, rho=4, 300 iterations, every iterate."""
+    """n=200, q=200, r=3, m=80, rho=4, 300 iterations, every step."""
     inst = GaussianInstance(n=200, q=200, r=3, m=80, rho=4, seed=1)
-    _, log = oracle_run(inst, 300)
-    res, eta = trajectory(inst, 300, log, engine=engine)
-    check_trajectory(res, eta, log)
-    assert log.err[-1] < 1e-6
+    run_trajectory(inst, 300, min_whole=290, engine=engine)
 
 
 @pytest.mark.parametrize("engine", ENGINES)
 def test_one_step_config0_every_iterate(engine):
     inst = GaussianInstance(n=200, q=200, r=3, m=80, rho=4, seed=1)
-    _, log = oracle_run(inst, 60)
-    res = one_step(inst, log, range(0, 60), engine=engine)
-    check_one_step(res)
+    run_one_step(inst, 60, min_whole=57, engine=engine)
 
 
 @pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("r,rho,m", [(1, 1, 20), (5, 0, 30), (8, 6, 40), (16, 2, 48)])
 def test_edge_ranks_and_sparsity(r, rho, m, engine):
     inst = GaussianInstance(n=70, q=30, r=r, m=m, rho=rho, seed=200 + r)
-    _, log = oracle_run(inst, 12)
-    res = one_step(inst, log, range(0, 12), engine=engine, cluster=1)
-    check_one_step(res, tol=1e-4 if r == 16 else TOL)
+    run_one_step(inst, 12, min_whole=9, engine=engine, cluster=1)
 
 
 @pytest.mark.parametrize("engine", ENGINES)
 def test_single_column_and_rho_equals_n(engine):
     inst = GaussianInstance(n=24, q=1, r=1, m=20, rho=24, seed=300)
-    _, log = oracle_run(inst, 5)
-    res = one_step(inst, log, range(0, 5), engine=engine)
-    check_one_step(res, tol=1e-4)
+    run_one_step(inst, 5, min_whole=5, engine=engine)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_unknown_rho_keeps_rho_max(engine):
+    """Section II-F: with rho unknown, HardThreshold keeps rho_max > rho
+    entries (here 8 for a true rho of 4); one-step parity over 20 steps and a
+    40-iteration trajectory against the oracle run with rho_max."""
+    inst = GaussianInstance(n=200, q=60, r=3, m=80, rho=4, seed=11)
+    run_one_step(inst, 20, min_whole=18, rho=8, engine=engine, rho_max=8)
+    run_trajectory(inst, 40, min_whole=38, rho=8, engine=engine, rho_max=8)
 
 
 @pytest.mark.parametrize("engine", ENGINES)
 def test_init_matches_oracle_subspace_and_supports(engine):
-    import oracle.altgdmin_lrs as O
-    from tests.gpu_helpers import new_solver
+    from tests.gpu_helpers import probe_init
     inst = GaussianInstance(n=200, q=200, r=3, m=80, rho=4, seed=1)
-    st, L0, sv, margin = O.init_alg1(O.GaussianOperator(inst.A), inst.Y, 3, 4)
+    P = Problem.gaussian(inst)
+    st, _, dec = probe_init(P)
     s = new_solver(inst, engine=engine)
     s.init()
     U, B, S_idx, S_val = s.get()
     s.close()
     cosines = np.linalg.svd(U.T.astype(np.float64) @ st.U, compute_uv=False)
     assert np.max(np.abs(1 - cosines)) < 1e-6, cosines  # same subspace (FP32 L0, FP32 U)
-    dec = margin > MARGIN_FP32
+    # the initialisation's ten sweeps from s = 0 leave about 8 % of these
+    # columns sensitive to rounding (float32 probe and perturbed reruns)
+    assert dec.sum() >= 0.9 * inst.q
     assert np.all(np.sort(S_idx[dec], 1) == st.S_idx[dec])

@@ -52,6 +52,75 @@ def test_hard_threshold_complex_uses_modulus():
     np.testing.assert_array_equal(idx[0], [0, 1, 3])
 
 
+def _margin_pairs(v, rho):
+    """Decision gap of HardThreshold(v, rho) from its definition: the smallest
+    |v_i| - |v_j| over kept i and dropped j (how far the magnitudes must move
+    before another index could be kept), in units of max|v|."""
+    a = np.abs(v)
+    kept = set(_ht_bruteforce(v, rho).tolist())
+    gaps = [a[i] - a[j] for i in kept for j in range(len(v)) if j not in kept]
+    return min(gaps) / a.max()
+
+
+@pytest.mark.parametrize("rho", [1, 2, 3, 6])
+def test_hard_threshold_margin_is_the_decision_gap(rho):
+    g = rng(10 + rho)
+    for trial in range(40):
+        v = g.standard_normal(7)
+        if trial % 4 == 1:
+            v = g.choice([-3.0, -2.0, -1.0, 0.5, 1.0, 2.0, 3.0], size=7)   # ties at the boundary
+        if trial % 4 == 2:
+            v = v + 1j * g.standard_normal(7)                               # modulus
+        if trial % 4 == 3:
+            v = 1e-3 * v                                                    # scale-free
+        _, _, mg = O.hard_threshold(v[None], rho)
+        assert mg[0] == pytest.approx(_margin_pairs(v, rho), rel=1e-12, abs=0.0)
+
+
+def test_hard_threshold_margin_edge_cases():
+    v = np.array([[3.0, -1.0, 2.0]])
+    assert O.hard_threshold(v, 3)[2][0] == np.inf           # rho = n: nothing is decided
+    assert O.hard_threshold(v, 0)[2][0] == np.inf           # rho = 0: nothing is kept
+    assert O.hard_threshold(np.array([[2.0, -2.0, 1.0]]), 1)[2][0] == 0.0   # tie
+    assert O.hard_threshold(v, 1)[2][0] == pytest.approx(1.0 / 3.0)
+    assert np.isnan(O.hard_threshold(np.zeros((1, 3)), 1)[2][0])           # v = 0
+
+
+class _RecordV:
+    def __init__(self):
+        self.v = []
+
+    def __call__(self, v):
+        self.v.append(np.array(v, copy=True))
+        return v
+
+
+def test_iht_margin_is_smallest_gap_over_its_sweeps():
+    """IHT's reported margin is the minimum over its tau sweeps of the
+    decision gap of each sweep's v = s - mu g (v recorded through the test
+    hook, which returns it unchanged), and tau chained single sweeps give the
+    same iterates and margins."""
+    g = rng(21)
+    K, m, n, rho, tau = 6, 9, 14, 3, 4
+    Mm = g.standard_normal((K, m, n))
+    M = lambda s: (Mm @ s[:, :, None])[:, :, 0]
+    MH = lambda u: (u[:, None, :] @ Mm)[:, 0, :]
+    z = g.standard_normal((K, m))
+    rec = _RecordV()
+    s, idx, margin = O.iht(z, M, MH, rho, tau, np.zeros((K, n)), perturb=rec)
+    assert len(rec.v) == tau
+    for k in range(K):
+        gaps = [_margin_pairs(v[k], rho) for v in rec.v]
+        assert margin[k] == pytest.approx(min(gaps), rel=1e-12)
+    s1, i1, mins = np.zeros((K, n)), None, np.full(K, np.inf)
+    for _ in range(tau):
+        s1, i1, m1 = O.iht(z, M, MH, rho, 1, s1, idx0=i1)
+        mins = np.minimum(mins, m1)
+    np.testing.assert_array_equal(i1, idx)
+    np.testing.assert_allclose(s1, s, rtol=0, atol=0)
+    np.testing.assert_allclose(mins, margin, rtol=1e-12)
+
+
 # --------------------------------------------------------------------- IHT --
 
 def test_iht_identity_operator_one_step_is_hard_threshold_of_z():
@@ -316,6 +385,7 @@ def test_fourier_iteration_uses_same_algebra_as_explicit_matrices():
             self.M = M
             self.q, self.m, self.n = M.shape
             self.complex = True
+            self.dtype = np.dtype(np.complex128)
 
         def subset(self, ks):
             return Explicit(self.M[ks])
