@@ -225,7 +225,7 @@ def run_ours(args):
     n, q, r, m, rho = cfg["n"], cfg["q"], cfg["r"], cfg["m"], cfg["rho"]
     stream = torch.cuda.Stream()
     # autotune: the first iterate call times the task shapes (inside the warm-up)
-    s = L.Solver(n, m, q, r, rho, stream=stream, profile=1, autotune=1)
+    s = L.Solver(n, m, q, r, rho, stream=stream, profile=1, autotune=1, engine=args.engine)
     s.set_measurements(Y, A)
     s.init()
     s.iterate(args.warmup)
@@ -260,7 +260,8 @@ def run_ours(args):
     A_h, Y_h = pinned_copy(A), pinned_copy(Y)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    s2 = L.Solver(n, m, q, r, rho, stream=stream, autotune=1)  # the shape chosen above (cached)
+    s2 = L.Solver(n, m, q, r, rho, stream=stream, autotune=1,  # the shape chosen above (cached)
+                  engine=args.engine)
     s2.set_measurements(Y_h, A_h)
     s2.init()
     s2.iterate(T_e2e)
@@ -474,24 +475,105 @@ def run_c3(args):
     return 0
 
 
+# ---- the serving workload: requests, arrivals and their inputs -------------
+
+def c4_requests(count: int, seed: int = 5, T: int = 100):
+    """The serving mix: 70 % Gaussian problems with BF16-stored A_k,
+    n = 64 round(2^U[8,12] / 64), q = 16 round(2^U[6,10] / 16), r ~ U{2..10},
+    m = round(U[0.15, 0.4] n), rho = round(U[0.01, 0.02] n); 30 % DFT problems
+    on 64 x 64 or 128 x 128 frames with the same laws for q, r, rho and m / n."""
+    from paper_2311_03824_gb300 import lrs as L
+    from paper_2311_03824_gb300.serve import Request
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        q = int(16 * round(2 ** rng.uniform(6, 10) / 16))
+        r = int(rng.integers(2, 11))
+        if rng.uniform() < 0.7:
+            n = int(64 * round(2 ** rng.uniform(8, 12) / 64))
+            m = int(round(rng.uniform(0.15, 0.4) * n))
+            rho = max(1, int(round(rng.uniform(0.01, 0.02) * n)))
+            out.append(Request(i, "gaussian", n, q, r, max(m, r), rho, seed * 100003 + i, T))
+        else:
+            side = 64 if rng.uniform() < 0.5 else 128
+            n = side * side
+            m = int(round(rng.uniform(0.15, 0.4) * n))
+            rho = max(1, int(round(rng.uniform(0.01, 0.02) * n)))
+            out.append(Request(i, "dft", n, q, r, m, rho, seed * 100003 + i, T, nx=side, ny=side,
+                               a_dtype=L.LRS_A_FP32))
+    return out
+
+
+def poisson_arrivals(reqs, rate, seed=6):
+    """Arrival times of a Poisson process of the given rate (requests/s)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    for rq in reqs:
+        t += rng.exponential(1.0 / rate)
+        rq.arrival = t
+    return reqs
+
+
+class C4Inputs:
+    """make_inputs of the serving loop: a request's synthetic inputs at its
+    arrival (Gaussian: drawn on the device; DFT: masks and measurements on the
+    host), and X* kept to score the result."""
+
+    def __init__(self):
+        self.xstar = {}
+
+    def __call__(self, rq):
+        import torch
+        from lrsgen import FourierInstance
+        from lrsgen.device import DeviceGaussianInstance
+        if rq.kind == "dft":
+            inst = FourierInstance(nx=rq.nx, ny=rq.ny, q=rq.q, r=rq.r, m=rq.m, rho=rq.rho,
+                                   seed=rq.seed)
+            self.xstar[rq.rid] = inst.Xstar
+            return (np.ascontiguousarray(inst.Y, np.complex64),
+                    np.ascontiguousarray(inst.masks, np.int32))
+        inst = DeviceGaussianInstance(rq.n, rq.q, rq.r, rq.m, rq.rho, rq.seed)
+        torch.cuda.current_stream().synchronize()     # the inputs are complete
+        self.xstar[rq.rid] = inst.Xstar
+        return inst.Y, inst.A
+
+    def score(self, results, reqs):
+        """Relative error of X = U B + S against X* for every finished request."""
+        by = {rq.rid: rq for rq in reqs}
+        for r in results:
+            if r.error is None and r.outputs is not None:
+                U, B, Si, Sv = r.outputs
+                dt = np.complex128 if by[r.rid].kind == "dft" else np.float64
+                X = U.astype(dt) @ B.astype(dt)
+                for k in range(B.shape[1]):
+                    X[Si[k], k] += Sv[k]
+                Xs = self.xstar.pop(r.rid)
+                r.rel_err = float(np.linalg.norm(X - Xs) / np.linalg.norm(Xs))
+                r.outputs = None
+
+
 def run_c4(args):
-    """Serving mix: saturation throughput, then Poisson arrivals at 0.8 x."""
+    """Serving mix through the native request server: saturation throughput
+    (every request at t = 0), then Poisson arrivals at 0.8 x that rate."""
     import torch
     torch.cuda.set_device(0)
     from paper_2311_03824_gb300 import build
     build.build()
     from paper_2311_03824_gb300 import serve as S
-    budget = int(0.8 * torch.cuda.mem_get_info()[0])
-    nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    reqs = S.c4_requests(args.requests, seed=5, T=100)
-    srv = S.Server(budget, slots=args.slots, sms=nsm)
-    res = srv.run(reqs)                     # every request at t = 0: saturation
+    budget = int(0.6 * torch.cuda.mem_get_info()[0])
+    reqs = c4_requests(args.requests, seed=5, T=100)
+    gen = C4Inputs()
+    srv = S.Server(budget, slots=args.slots, keep_outputs=True)
+    res = srv.run(reqs, gen)
+    gen.score(res, reqs)
     sat = S.summarize(res, srv.makespan, reqs)
     rate = 0.8 * sat["throughput_req_s"]
-    reqs = S.poisson_arrivals(S.c4_requests(args.requests, seed=5, T=100), rate, seed=6)
-    srv2 = S.Server(budget, slots=args.slots, sms=nsm)
+    reqs = poisson_arrivals(c4_requests(args.requests, seed=5, T=100), rate, seed=6)
+    gen2 = C4Inputs()
+    srv2 = S.Server(budget, slots=args.slots, keep_outputs=True)
     with ClockSampler(0) as clk:
-        res2 = srv2.run(reqs)
+        res2 = srv2.run(reqs, gen2)
+    gen2.score(res2, reqs)
     lat = S.summarize(res2, srv2.makespan, reqs)
     line = {
         "metric": "serving p99 latency", "value": lat["p99_latency_s"], "unit": "s",
@@ -519,6 +601,8 @@ def main():
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--a-dtype", default="fp32", choices=list(A_DTYPES))
+    ap.add_argument("--engine", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="Gaussian sweep engine (0: the library's choice)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

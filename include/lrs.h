@@ -76,7 +76,8 @@ typedef struct {
                                iterations (0 -> 8); see lrs_iterate          */
   int32_t cluster;          /* Gaussian sweep: CTAs per column (0 -> autotune) */
   int32_t power_iters;      /* cap on subspace iterations in lrs_init (0 -> 1000) */
-  double power_tol;         /* stop when ||(I - U_old U_old^T) U||_F < tol (0 -> 1e-11) */
+  double power_tol;         /* stop when ||(I - U_old U_old^T) U||_F < tol (0 -> 1e-6;
+                               float32 products resolve about 1e-7)      */
   int32_t use_graph;        /* 1: replay steady-state iterations as a CUDA graph */
   void* stream;             /* cudaStream_t for every launch (NULL = default)  */
   uint64_t seed;            /* seed of the subspace-iteration start            */
@@ -88,7 +89,11 @@ typedef struct {
   int32_t engine;           /* Gaussian sweep engine: 0 auto, 1 one thread-block
                                cluster per column, 2 persistent task engine
                                (passes over A_k split into tasks, columns
-                               in flight share the GPU)                      */
+                               in flight share the GPU), 3 register-resident
+                               cluster engine (each CTA keeps its 128
+                               columns of A_k in registers through the whole
+                               column sweep; float32 A_k, r <= 8, m <= 192,
+                               n <= 1024, rho_max <= 32)                     */
   int32_t inflight;         /* task engine: columns in flight (0 -> all q)    */
   int32_t task_kib;         /* task engine: A_k bytes per task in KiB (0 -> 256) */
   int32_t ctas_per_sm;      /* task engine: resident CTAs per SM (0 -> 2, or 1
@@ -98,7 +103,11 @@ typedef struct {
                                iteration unless this shape is cached         */
   int32_t grid;             /* task engine: CTAs of the persistent launch (0 ->
                                all that fit; fewer let concurrent handles on
-                               other streams share the GPU)                  */
+                               other streams share the GPU); resident engine:
+                               at most grid / cluster clusters             */
+  int32_t wait_ms;          /* bound of every device-side wait of the task and
+                               resident engines (0 -> 10000 ms); a wait that
+                               expires makes the call return LRS_ERR_TIMEOUT */
 } lrs_options;
 
 /* Create a solver for one problem (Section I-A sizes).
@@ -133,8 +142,8 @@ lrs_status lrs_set_measurements(lrs_t h, const void* y, const void* A_or_mask,
 
 /* Initialisation of Algorithm 1: s_k = IHT(y_k, A_k, rho, tau0, 0),
  * L0 = [A_k^T (y_k - A_k s_k)], U0 = top-r left singular subspace of L0
- * (subspace iteration with Cholesky-QR2 to power_tol), b_k = (A_k U0)^+ (y_k -
- * A_k s_k).  State: MEASURED or later -> INITIALISED.
+ * (subspace iteration: float32 products L0^T U and L0 P, Cholesky-QR2 with
+ * FP64 r x r factors, to power_tol), b_k = (A_k U0)^+ (y_k - A_k s_k).  State: MEASURED or later -> INITIALISED.
  * Errors: LRS_ERR_STATE, LRS_ERR_NUMERICAL (non-SPD Gram, NaN), LRS_ERR_CUDA. */
 lrs_status lrs_init(lrs_t h);
 
@@ -257,6 +266,95 @@ lrs_status lrs_orthonormalize(const float* Z, float* Q, int64_t n, int32_t r, vo
 lrs_status lrs_orthonormalize_noalloc(const float* Z, float* Q, int64_t n, int32_t r,
                                       void* stream);
 const char* lrs_noalloc_last_error(void);
+
+/* ---- serving (the paper has no counterpart: a request loop for many
+ * problems of Section I-A on one GPU) ------------------------------------ */
+
+/* One reconstruction problem for the server: the arguments of lrs_create and
+ * lrs_set_measurements, the iterations to run (opt.T, 0 -> 200) and where
+ * to put the result (as lrs_get; NULL pointers are skipped).  opt.stream is
+ * ignored (each worker has its own stream); opt.grid 0 lets the server
+ * share the SMs among the Gaussian requests running.  The input and output
+ * buffers belong to the caller and must stay valid until lrs_server_wait has
+ * returned the request's result.  Device inputs must be ready (their
+ * producing work complete) when the request is submitted. */
+typedef struct {
+  int64_t n, m, q;
+  int32_t r, rho;
+  lrs_op_kind kind;
+  lrs_options opt;
+  const void* y;
+  const void* A_or_mask;
+  int32_t mem_kind;         /* of y and A_or_mask: 0 host, 1 device           */
+  void* U;
+  void* B;
+  int32_t* S_idx;
+  void* S_val;
+  int32_t out_mem_kind;     /* of U, B, S_idx, S_val: 0 host, 1 device        */
+  void* user;               /* opaque, handed to a custom runner               */
+} lrs_request;
+
+/* Outcome of one request.  Times are seconds since lrs_server_create. */
+typedef struct {
+  lrs_status status;        /* of the request's own calls                     */
+  char message[256];        /* lrs_last_error() of the failing call, or ""    */
+  double submit_s, start_s, end_s;
+  size_t footprint;         /* device bytes reserved while it ran             */
+  int32_t worker;           /* slot that ran it                               */
+  int32_t grid;             /* SM share (CTAs) offered to its sweep           */
+  int64_t admitted;         /* its place in the order of admission (0, 1, ..) */
+} lrs_result;
+
+/* A replacement for the solver of one request (used to test the admission
+ * logic without a GPU): returns an lrs_status. */
+typedef int32_t (*lrs_runner)(void* ctx, const lrs_request* req, int32_t grid, int32_t worker);
+
+typedef struct {
+  size_t hbm_budget;        /* device bytes the requests in flight may hold
+                               (0 -> 85 % of the free memory at creation)    */
+  int32_t slots;            /* requests in flight at most (0 -> 8)            */
+  int32_t sms;              /* SMs shared by the sweeps (0 -> the device's)   */
+  lrs_runner runner;        /* NULL: the library's solver                     */
+  void* runner_ctx;
+} lrs_server_options;
+
+typedef struct lrs_server_s* lrs_server_t;
+
+/* Create a server: `slots` worker threads, each with its own CUDA stream,
+ * and a dispatcher.  Requests are admitted in submission order as soon as a
+ * slot is free and lrs_request_footprint(req) fits what the requests in
+ * flight leave of hbm_budget; each runs lrs_create, lrs_set_measurements,
+ * lrs_init, lrs_iterate(T) and lrs_get on its worker's stream, so the work
+ * of concurrent requests overlaps on the GPU, and a Gaussian request's
+ * persistent sweep gets max(16, 2 x SMs / requests running) CTAs.  The
+ * kernels' results depend neither on the other requests nor on that share:
+ * every result equals the request solved alone.
+ * Errors: LRS_ERR_ARG, LRS_ERR_CUDA (no device). */
+lrs_status lrs_server_create(const lrs_server_options* opt, lrs_server_t* out);
+
+/* Queue a request; *ticket identifies it for lrs_server_wait.  The request
+ * is copied (not its buffers).  Errors: LRS_ERR_ARG, LRS_ERR_OOM (larger
+ * than the whole budget), LRS_ERR_STATE (server being destroyed). */
+lrs_status lrs_server_submit(lrs_server_t s, const lrs_request* req, uint64_t* ticket);
+
+/* Wait until the request of `ticket` has finished (timeout_ms < 0: no
+ * limit) and copy its outcome to *res; the ticket is then released.
+ * Errors: LRS_ERR_ARG (unknown ticket), LRS_ERR_TIMEOUT (not finished in
+ * timeout_ms; the ticket stays valid). */
+lrs_status lrs_server_wait(lrs_server_t s, uint64_t ticket, int32_t timeout_ms, lrs_result* res);
+
+/* Stop accepting requests, run those already queued, join the workers and
+ * free the server.  Outcomes not yet waited for are discarded. */
+lrs_status lrs_server_destroy(lrs_server_t s);
+
+/* Device bytes the server reserves for a request while it runs (its stored
+ * operator, the exact copy of a low-precision form, the staging of host
+ * inputs, per-column scratch and the iterate, with 10 % and 64 MiB of
+ * headroom). */
+size_t lrs_request_footprint(const lrs_request* req);
+
+/* Thread-local message of the last failed server call ("" if none). */
+const char* lrs_server_last_error(void);
 
 /* Per-column SM cycle counts of the sweep phases accumulated by
  * lrs_iterate since the previous call (handle created with profile = 2;

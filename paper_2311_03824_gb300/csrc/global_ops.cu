@@ -318,171 +318,7 @@ __global__ void sum_fin_kernel(int nblk, const double* __restrict__ part, double
   }
 }
 
-// ---- FP64 subspace iteration for the spectral initialisation ---------------
-// P[k][l] = sum_j H[k][j] U[j][l]  (U FP64, one warp per column k)
-__global__ void __launch_bounds__(256) dproject_kernel(int n, int q, int r,
-                                                       const float* __restrict__ H,
-                                                       const double* __restrict__ U,
-                                                       double* __restrict__ P) {
-  const int lane = threadIdx.x & 31;
-  const int k = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (k >= q) return;
-  double acc[kMaxR];
-#pragma unroll
-  for (int l = 0; l < kMaxR; ++l) acc[l] = 0.0;
-  const float* h = H + static_cast<size_t>(k) * n;
-  for (int j = lane; j < n; j += 32) {
-    const double hv = h[j];
-    const double* u = U + static_cast<size_t>(j) * r;
-#pragma unroll
-    for (int l = 0; l < kMaxR; ++l)
-      if (l < r) acc[l] = __fma_rn(hv, u[l], acc[l]);
-  }
-#pragma unroll
-  for (int l = 0; l < kMaxR; ++l) {
-    if (l >= r) break;
-    const double s = warp_sum(acc[l]);
-    if (lane == 0) P[static_cast<size_t>(k) * r + l] = s;
-  }
-}
-// Z[j][l] = sum_k H[k][j] P[k][l]  (FP64; lane <-> j, warp w <-> k = w mod 8)
-__global__ void __launch_bounds__(256) dgrad_kernel(int n, int q, int r, const float* __restrict__ H,
-                                                    const double* __restrict__ P,
-                                                    double* __restrict__ Z) {
-  __shared__ double part[8][kMaxR][33];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int j = blockIdx.x * 32 + lane;
-  double acc[kMaxR];
-#pragma unroll
-  for (int l = 0; l < kMaxR; ++l) acc[l] = 0.0;
-  if (j < n) {
-    for (int k = w; k < q; k += 8) {
-      const double h = H[static_cast<size_t>(k) * n + j];
-      const double* pp = P + static_cast<size_t>(k) * r;
-#pragma unroll
-      for (int l = 0; l < kMaxR; ++l)
-        if (l < r) acc[l] = __fma_rn(h, pp[l], acc[l]);
-    }
-  }
-#pragma unroll
-  for (int l = 0; l < kMaxR; ++l) part[w][l][lane] = acc[l];
-  __syncthreads();
-  for (int t = threadIdx.x; t < 32 * r; t += blockDim.x) {
-    const int l = t / 32, jj = t - l * 32;
-    double s = 0.0;
-    for (int ww = 0; ww < 8; ++ww) s += part[ww][l][jj];
-    const int jg = blockIdx.x * 32 + jj;
-    if (jg < n) Z[static_cast<size_t>(jg) * r + l] = s;
-  }
-}
-// partial Grams of an FP64 n x r matrix (rows split over blocks)
-__global__ void __launch_bounds__(256) dgram_part_kernel(int n, int r, const double* __restrict__ X,
-                                                         double* __restrict__ part) {
-  const int rows = (n + gridDim.x - 1) / gridDim.x;
-  const int lo = blockIdx.x * rows, hi = min(n, lo + rows);
-  const int t = threadIdx.x, a = t / kMaxR, b = t - (t / kMaxR) * kMaxR;
-  if (a >= r || b > a) return;
-  double s = 0.0;
-  for (int i = lo; i < hi; ++i)
-    s = __fma_rn(X[static_cast<size_t>(i) * r + a], X[static_cast<size_t>(i) * r + b], s);
-  part[static_cast<size_t>(blockIdx.x) * r * r + a * r + b] = s;
-}
-// Y = X Rinv in FP64; optionally also the float copy and the padded float copy
-__global__ void __launch_bounds__(256) dapply_kernel(int n, int r, const double* __restrict__ X,
-                                                     const double* __restrict__ Rinv,
-                                                     double* __restrict__ Y, float* __restrict__ Yf,
-                                                     float* __restrict__ Ypad, int rpad) {
-  const size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
-  if (t >= static_cast<size_t>(n) * r) return;
-  const size_t i = t / r;
-  const int l = static_cast<int>(t - i * r);
-  double s = 0.0;
-  for (int p = 0; p <= l; ++p) s = __fma_rn(X[i * r + p], Rinv[p * r + l], s);
-  Y[t] = s;
-  if (Yf) Yf[t] = static_cast<float>(s);
-  if (Ypad) Ypad[i * rpad + l] = static_cast<float>(s);
-}
-// ||Unew - Uold (Uold^T Unew)||_F^2 in FP64 (both FP64 n x r), fixed order
-__global__ void __launch_bounds__(256) dchange_kernel(int n, int r, const double* __restrict__ Uo,
-                                                      const double* __restrict__ Un,
-                                                      const double* __restrict__ D,
-                                                      double* __restrict__ part) {
-  __shared__ double sD[kMaxR * kMaxR];
-  __shared__ double red[8];
-  for (int t = threadIdx.x; t < r * r; t += blockDim.x) sD[t] = D[t];
-  __syncthreads();
-  const int rows = (n + gridDim.x - 1) / gridDim.x;
-  const int lo = blockIdx.x * rows, hi = min(n, lo + rows);
-  double acc = 0.0;
-  for (int u = lo * r + threadIdx.x; u < hi * r; u += blockDim.x) {
-    const int i = u / r, l = u - i * r;
-    double s = Un[u];
-    for (int p = 0; p < r; ++p) s -= Uo[static_cast<size_t>(i) * r + p] * sD[p * r + l];
-    acc += s * s;
-  }
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    part[blockIdx.x] = s;
-  }
-}
-__global__ void __launch_bounds__(256) doverlap_part_kernel(int n, int r, const double* __restrict__ Ua,
-                                                            const double* __restrict__ Ub,
-                                                            double* __restrict__ part) {
-  const int rows = (n + gridDim.x - 1) / gridDim.x;
-  const int lo = blockIdx.x * rows, hi = min(n, lo + rows);
-  const int t = threadIdx.x, a = t / kMaxR, b = t - (t / kMaxR) * kMaxR;
-  if (a >= r || b >= r) return;
-  double s = 0.0;
-  for (int i = lo; i < hi; ++i)
-    s = __fma_rn(Ua[static_cast<size_t>(i) * r + a], Ub[static_cast<size_t>(i) * r + b], s);
-  part[static_cast<size_t>(blockIdx.x) * r * r + a * r + b] = s;
-}
-
 }  // namespace
-
-cudaError_t dcholqr2(const GlobalWork& g, const double* Zin, double* Ztmp, double* Uout,
-                     float* Uf, int* err, cudaStream_t s) {
-  const int rr = g.r * g.r;
-  double* R1 = g.small;
-  double* R2 = g.small + rr;
-  const size_t tot = static_cast<size_t>(g.n) * g.r;
-  const unsigned nb = static_cast<unsigned>((tot + 255) / 256);
-  dgram_part_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, Zin, g.part);
-  chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R1, err);
-  dapply_kernel<<<nb, 256, 0, s>>>(g.n, g.r, Zin, R1, Ztmp, nullptr, nullptr, 0);
-  dgram_part_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, Ztmp, g.part);
-  chol_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, R2, err);
-  dapply_kernel<<<nb, 256, 0, s>>>(g.n, g.r, Ztmp, R2, Uout, Uf, Uf ? g.Upad : nullptr, g.rpad);
-  return cudaGetLastError();
-}
-
-cudaError_t dsubspace_step(const GlobalWork& g, const float* H, const double* U, double* P,
-                           double* Z, cudaStream_t s) {
-  dproject_kernel<<<(g.q + 7) / 8, 256, 0, s>>>(g.n, g.q, g.r, H, U, P);
-  if (g.ks > 1 && g.dsplit) {
-    const int qc = (g.q + g.ks - 1) / g.ks;
-    kred_part_kernel<double><<<dim3((g.n + 31) / 32, g.ks), 256, 0, s>>>(g.n, g.q, g.r, qc, H, P,
-                                                                         g.dsplit);
-    const int nr = g.n * g.r;
-    kred_fin_kernel<double><<<(nr + 255) / 256, 256, 0, s>>>(nr, g.ks, g.dsplit, Z);
-  } else {
-    dgrad_kernel<<<(g.n + 31) / 32, 256, 0, s>>>(g.n, g.q, g.r, H, P, Z);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t dsubspace_change(const GlobalWork& g, const double* Uold, const double* Unew,
-                             double* D_rr, double* out, cudaStream_t s) {
-  doverlap_part_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, Uold, Unew, g.part);
-  overlap_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, D_rr);
-  dchange_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, Uold, Unew, D_rr, g.part);
-  sum_fin_kernel<<<1, 32, 0, s>>>(g.nblk, g.part, out);
-  return cudaGetLastError();
-}
 
 cudaError_t subspace_change(const GlobalWork& g, const float* Uold, const float* Unew,
                             double* D_rr, double* out, cudaStream_t s) {

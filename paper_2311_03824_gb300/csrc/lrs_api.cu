@@ -95,11 +95,12 @@ struct lrs_ctx {
   double* errpart = nullptr;
   int ks = 1;                // k-splits of the column reductions
   float* gsplit = nullptr;   // ks x n x r
-  double* dsplit = nullptr;  // ks x n x r
   unsigned long long* trace = nullptr;  // q x kTracePhases (profile = 2)
   int nblk = 0;
   int power_iters_done = 0;
   FourierSolver* F = nullptr;  // DFT2D_MASK operator
+  // register-resident cluster engine (engine == 3)
+  int res_CS = 0, res_ncl = 0;
   // persistent task engine (engine == 2)
   int engine = 1;
   TaskShape tshape{};
@@ -148,7 +149,6 @@ GlobalWork gw(lrs_ctx* h) {
   g.rpad = sweep_rpad(h->r);
   g.ks = h->ks;
   g.gsplit = h->gsplit;
-  g.dsplit = h->dsplit;
   return g;
 }
 
@@ -216,6 +216,16 @@ void choose_layout(lrs_ctx* h) {
   h->resident = 0;
 }
 
+// Row-major float A_k of columns k0 .. k0 + kc - 1 (device) into the
+// engine's layout.
+cudaError_t repack_a(lrs_ctx* h, const float* src, int64_t k0, int64_t kc) {
+  if (h->engine == 3)
+    return res_repack(src, static_cast<int>(h->n), static_cast<int>(h->m), static_cast<int>(k0),
+                      static_cast<int>(kc), static_cast<float*>(h->A), h->stream);
+  return repack_gauss(h->L, src, static_cast<int>(k0), static_cast<int>(kc), h->A, nullptr,
+                      h->stream);
+}
+
 lrs_status check_device_error(lrs_ctx* h, const char* where) {
   int e[2] = {0, 0};
   CUDA_TRY(cudaMemcpyAsync(e, h->err, sizeof(e), cudaMemcpyDeviceToHost, h->stream));
@@ -232,6 +242,30 @@ lrs_status check_device_error(lrs_ctx* h, const char* where) {
 }
 
 lrs_status launch_sweep(lrs_ctx* h, int mode, int tau) {
+  if (h->engine == 3) {
+    ResArgs a{};
+    a.n = static_cast<int>(h->n);
+    a.m = static_cast<int>(h->m);
+    a.q = static_cast<int>(h->q);
+    a.r = h->r;
+    a.rho = h->rho;
+    a.mode = mode;
+    a.tau = tau;
+    a.CS = h->res_CS;
+    a.nch4 = static_cast<int>((h->n + 3) / 4);
+    a.A = static_cast<const float*>(h->A);
+    a.y = h->y;
+    a.U = h->U;
+    a.S_idx = h->S_idx;
+    a.S_val = h->S_val;
+    a.B = h->Bk;
+    a.H = h->H;
+    a.err = h->err;
+    a.wait_ns = static_cast<unsigned long long>(h->opt.wait_ms > 0 ? h->opt.wait_ms : 10000) * 1000000ull;
+    a.prof = (h->opt.profile == 2 && mode == kModeIter) ? h->tprof : nullptr;
+    CUDA_TRY(res_launch(a, h->res_ncl, h->stream));
+    return LRS_OK;
+  }
   if (h->engine == 2) {
     TaskQueue Q{};
     Q.tasks = h->ttasks;
@@ -439,7 +473,7 @@ void free_all(lrs_ctx* h) {
                  h->tnsup, h->tcnt, h->tstop, h->tseq, h->tctr, h->ttasks, h->tprof};
   for (void* p : ps2)
     if (p) cudaFreeAsync(p, h->stream);
-  void* ps[] = {h->gsplit, h->dsplit, h->A, h->y, h->Aex, h->rscale, h->ycorr, h->U, h->Upad, h->Bk, h->S_idx, h->S_val, h->H, h->grad, h->Z,
+  void* ps[] = {h->gsplit, h->A, h->y, h->Aex, h->rscale, h->ycorr, h->U, h->Upad, h->Bk, h->S_idx, h->S_val, h->H, h->grad, h->Z,
                 h->U2, h->P, h->part, h->small, h->eta, h->err, h->Xref, h->errpart, h->trace};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, h->stream);
@@ -525,7 +559,7 @@ lrs_status alloc_split(lrs_ctx* h, int nsm) {
   if (ks <= 1) return LRS_OK;
   lrs_status st = LRS_OK;
   const size_t cnt = static_cast<size_t>(ks) * h->n * h->r;
-  if ((st = dalloc(&h->gsplit, cnt, h->stream)) || (st = dalloc(&h->dsplit, cnt, h->stream))) return st;
+  if ((st = dalloc(&h->gsplit, cnt, h->stream))) return st;
   return LRS_OK;
 }
 
@@ -661,7 +695,8 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
     if (m > n) return fail(LRS_ERR_ARG, "lrs_create: DFT needs m <= n");
   }
   if (o.tau0 < 0 || o.tau < 0 || o.T < 0 || o.rho_max < 0 || o.c_eta < 0 || o.cluster < 0 ||
-      o.power_iters < 0 || o.refine_every < 0 || o.grid < 0)
+      o.power_iters < 0 || o.refine_every < 0 || o.grid < 0 || o.wait_ms < 0 || o.engine < 0 ||
+      o.engine > 3)
     return fail(LRS_ERR_ARG, "lrs_create: negative option");
   if (o.cluster != 0 && o.cluster != 1 && o.cluster != 2 && o.cluster != 4 && o.cluster != 8 &&
       o.cluster != 16)
@@ -679,7 +714,7 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
   if (o.rho_max == 0) o.rho_max = rho;
   if (o.rho_max > n) return fail(LRS_ERR_ARG, "lrs_create: rho_max > n");
   if (o.power_iters == 0) o.power_iters = 1000;
-  if (o.power_tol == 0) o.power_tol = 1e-11;
+  if (o.power_tol == 0) o.power_tol = 1e-6;
   if (o.refine_every == 0) o.refine_every = 8;
 
   if (kind == LRS_OP_DFT2D_MASK) {
@@ -721,7 +756,18 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
   if (nsm <= 0) nsm = 148;
   // engine: the task engine unless the cluster sweep is asked for (or the
   // task engine has no shape and the cluster sweep has one)
-  h->engine = o.engine == 1 ? 1 : 2;
+  h->engine = o.engine == 1 ? 1 : (o.engine == 3 ? 3 : 2);
+  if (h->engine == 3 && !res_supported(static_cast<int>(n), static_cast<int>(m), r, o.rho_max,
+                                       static_cast<int>(o.a_dtype))) {
+    delete h;
+    return fail(LRS_ERR_UNSUPPORTED,
+                "lrs_create: the resident engine needs float32 A_k, r <= 8, m <= 192, n <= 1024, "
+                "rho_max <= 32");
+  }
+  if (h->engine == 3) {
+    h->L = gauss_shape(h, 1, 0);   // descriptive only: the engine keeps its own layout
+    h->res_CS = res_cluster(static_cast<int>(n));
+  }
   if (h->engine == 2) {
     h->L = gauss_shape(h, 1, 0);
     if (!plan_task_engine(h, nsm)) {
@@ -745,7 +791,9 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
     }
   }
   h->nblk = std::max(1, std::min<int>(nsm, static_cast<int>((n + 63) / 64)));
-  const size_t per_col = static_cast<size_t>(h->L.cs) * h->L.m * h->L.ns * elem_bytes(h->L.et);
+  const size_t per_col = h->engine == 3
+                             ? static_cast<size_t>(m) * 16 * static_cast<size_t>((n + 3) / 4)
+                             : static_cast<size_t>(h->L.cs) * h->L.m * h->L.ns * elem_bytes(h->L.et);
   lrs_status st = LRS_OK;
   const size_t upad_n = static_cast<size_t>(h->L.cs) * h->L.ns * sweep_rpad(r);
   const int lowp = h->L.et != 0, per_row = h->L.et == 3 ? 2 : 1;
@@ -769,15 +817,18 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
     return fail(st, "lrs_create: " + msg);
   }
   if (o.profile == 2) {
-    if ((st = dalloc(&h->trace, size_t(q) * kTracePhases, h->stream))) {
+    if ((st = dalloc(&h->trace, size_t(q) * kTracePhases, h->stream)) ||
+        (h->engine == 3 && (st = dalloc(&h->tprof, 16, h->stream)))) {
       free_all(h);
       delete h;
       return st;
     }
     cudaMemsetAsync(h->trace, 0, sizeof(unsigned long long) * size_t(q) * kTracePhases, h->stream);
+    if (h->engine == 3) cudaMemsetAsync(h->tprof, 0, sizeof(unsigned long long) * 16, h->stream);
   }
-  cudaError_t e = h->engine == 1 ? sweep_prepare(h->L, kThreads)
-                                 : task_prepare(sweep_rpad(r), h->L.et, h->tshape.smem);
+  cudaError_t e = h->engine == 1   ? sweep_prepare(h->L, kThreads)
+                  : h->engine == 3 ? res_prepare(res_rpad(r), static_cast<int>((m + 31) / 32))
+                                   : task_prepare(sweep_rpad(r), h->L.et, h->tshape.smem);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, 2 * sizeof(int), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->Upad, 0, sizeof(float) * upad_n, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->S_idx, 0, sizeof(int) * size_t(q) * std::max(1, h->rho), h->stream);
@@ -793,6 +844,19 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
     free_all(h);
     delete h;
     return fail(LRS_ERR_UNSUPPORTED, "lrs_create: sweep kernel shape cannot be scheduled");
+  }
+  if (h->engine == 3) {
+    const int R = res_rpad(r), MR = static_cast<int>((m + 31) / 32);
+    const size_t smem = res_smem_bytes(R, MR, static_cast<int>(m), h->rho, h->res_CS);
+    const int ncl = smem <= static_cast<size_t>(max_smem_optin())
+                        ? res_max_clusters(R, MR, h->res_CS, smem) : 0;
+    if (ncl <= 0) {
+      free_all(h);
+      delete h;
+      return fail(LRS_ERR_UNSUPPORTED, "lrs_create: resident engine shape cannot be scheduled");
+    }
+    h->res_ncl = static_cast<int>(std::min<int64_t>(ncl, q));
+    if (o.grid > 0) h->res_ncl = std::max(1, std::min(h->res_ncl, o.grid / h->res_CS));
   }
   if (h->engine == 2) {
     const int cps = task_ctas_per_sm(sweep_rpad(r), h->L.et, h->tshape.smem);
@@ -850,14 +914,14 @@ lrs_status lrs_set_measurements(lrs_t h, const void* y, const void* A_or_mask, i
     if (mem_kind == 0) {
       cudaError_t e = cudaMemcpyAsync(tmp, src, sizeof(float) * col_elems * kc,
                                       cudaMemcpyHostToDevice, h->stream);
-      if (e == cudaSuccess) e = repack_gauss(h->L, tmp, static_cast<int>(k0), static_cast<int>(kc), h->A, nullptr, h->stream);
+      if (e == cudaSuccess) e = repack_a(h, tmp, k0, kc);
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
       if (e != cudaSuccess) {
         cudaFreeAsync(tmp, h->stream);
         return fail(LRS_ERR_CUDA, std::string("lrs_set_measurements: ") + cudaGetErrorString(e));
       }
     } else {
-      CUDA_TRY(repack_gauss(h->L, src, static_cast<int>(k0), static_cast<int>(kc), h->A, nullptr, h->stream));
+      CUDA_TRY(repack_a(h, src, k0, kc));
     }
   }
   if (tmp) cudaFreeAsync(tmp, h->stream);
@@ -882,37 +946,23 @@ lrs_status lrs_init(lrs_t h) {
   // s_k = IHT(y_k, A_k, rho, tau0, 0); L0 column k = A_k^T (y_k - A_k s_k) -> H
   lrs_status st = launch_sweep(h, kModeInit, h->opt.tau0);
   if (st) return st;
-  // U0: top-r left singular subspace of L0 (= H^T) by subspace iteration in
-  // FP64 (U, L0^T U and L0 L0^T U held in FP64; L0 itself is the FP32 sweep
-  // output), Cholesky-QR2 after every product.
-  const int r = h->r;
-  const size_t nr = static_cast<size_t>(h->n) * r;
-  double *Ud = nullptr, *Uold = nullptr, *Zd = nullptr, *Pd = nullptr, *Td = nullptr;
-  auto free_d = [&]() {
-    for (double* p : {Td, Ud, Uold, Zd, Pd})
-      if (p) cudaFreeAsync(p, h->stream);
-  };
-  auto am = [&](double** p, size_t bytes) {
-    return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, h->stream) == cudaSuccess;
-  };
-  if (!am(&Ud, nr * 8) || !am(&Uold, nr * 8) || !am(&Zd, nr * 8) || !am(&Td, nr * 8) ||
-      !am(&Pd, static_cast<size_t>(h->q) * r * 8)) {
-    free_d();
-    return fail(LRS_ERR_OOM, "lrs_init: no device memory for the subspace iteration");
-  }
+  // U0: top-r left singular subspace of L0 (= H^T) by subspace iteration:
+  // FP32 products P = L0^T U and Z = L0 P, then Cholesky-QR2 of Z (FP64
+  // r x r Gram and factors), until the subspace moves by less than power_tol.
+  const size_t nr = static_cast<size_t>(h->n) * h->r;
   std::vector<float> U0f = start_block(h->n, h->r, h->opt.seed + 1);
-  std::vector<double> U0(U0f.begin(), U0f.end());
-  cudaError_t e = cudaMemcpyAsync(Zd, U0.data(), nr * 8, cudaMemcpyHostToDevice, h->stream);
+  cudaError_t e = cudaMemcpyAsync(h->U2, U0f.data(), nr * 4, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (e == cudaSuccess) e = dcholqr2(g, Zd, Td, Ud, nullptr, h->err, h->stream);
+  if (e == cudaSuccess) e = cholqr2(g, h->U2, h->U, h->err, h->stream);
   double* D = h->small + 2 * 16 * 16;
   int it = 0;
   for (; it < h->opt.power_iters && e == cudaSuccess; ++it) {
-    e = cudaMemcpyAsync(Uold, Ud, nr * 8, cudaMemcpyDeviceToDevice, h->stream);
-    if (e == cudaSuccess) e = dsubspace_step(g, h->H, Uold, Pd, Zd, h->stream);
-    if (e == cudaSuccess) e = dcholqr2(g, Zd, Td, Ud, nullptr, h->err, h->stream);
+    e = cudaMemcpyAsync(h->U2, h->U, nr * 4, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = project_cols(g, h->H, h->U2, h->P, h->stream);
+    if (e == cudaSuccess) e = grad_reduce(g, h->H, h->P, h->stream);
+    if (e == cudaSuccess) e = cholqr2(g, h->grad, h->U, h->err, h->stream);
     if (e == cudaSuccess && ((it % 5) == 4 || it + 1 == h->opt.power_iters)) {
-      e = dsubspace_change(g, Uold, Ud, D, D + 16 * 16, h->stream);
+      e = subspace_change(g, h->U2, h->U, D, D + 16 * 16, h->stream);
       double chg2 = 0.0;
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(&chg2, D + 16 * 16, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -920,11 +970,7 @@ lrs_status lrs_init(lrs_t h) {
       if (e == cudaSuccess && std::sqrt(std::max(0.0, chg2)) < h->opt.power_tol) break;
     }
   }
-  // final orthonormalisation writes the FP32 U and its padded copy
-  if (e == cudaSuccess) e = cudaMemcpyAsync(Zd, Ud, nr * 8, cudaMemcpyDeviceToDevice, h->stream);
-  if (e == cudaSuccess) e = dcholqr2(g, Zd, Td, Ud, h->U, h->err, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  free_d();
   if (e != cudaSuccess) return fail(LRS_ERR_CUDA, std::string("lrs_init: ") + cudaGetErrorString(e));
   h->power_iters_done = it;
   // b_k = (A_k U0)^+ (y_k - A_k s_k)
@@ -1178,10 +1224,10 @@ lrs_status lrs_phase_times(lrs_t h, double* out4) {
 
 lrs_status lrs_sweep_trace(lrs_t h, uint64_t* out, int64_t len) {
   if (!h || !out || len < 0) return fail(LRS_ERR_ARG, "lrs_sweep_trace: bad argument");
-  if (h->engine == 2 && h->opt.profile == 2) {
-    const int64_t n = std::min<int64_t>(len, kTaskProf);
+  if ((h->engine == 2 || h->engine == 3) && h->opt.profile == 2) {
+    const int64_t n = std::min<int64_t>(len, h->engine == 3 ? kResProf : kTaskProf);
     CUDA_TRY(cudaMemcpyAsync(out, h->tprof, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(cudaMemsetAsync(h->tprof, 0, sizeof(uint64_t) * kTaskProf, h->stream));
+    CUDA_TRY(cudaMemsetAsync(h->tprof, 0, sizeof(uint64_t) * 16, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     return LRS_OK;
   }
@@ -1198,6 +1244,16 @@ lrs_status lrs_describe(lrs_t h, char* buf, int32_t len) {
   if (h->F) {
     snprintf(buf, static_cast<size_t>(len), "{\"op\": \"dft2d\", \"nx\": %d, \"ny\": %d, \"cta_per_frame\": 1}",
              h->opt.nx, h->opt.ny);
+    return LRS_OK;
+  }
+  if (h->engine == 3) {
+    const int R = res_rpad(h->r), MR = static_cast<int>((h->m + 31) / 32);
+    snprintf(buf, static_cast<size_t>(len),
+             "{\"op\": \"gaussian\", \"engine\": \"resident\", \"cluster\": %d, "
+             "\"clusters\": %d, \"rows_per_lane\": %d, \"rank_width\": %d, "
+             "\"smem_per_cta\": %zu}",
+             h->res_CS, h->res_ncl, MR, R,
+             res_smem_bytes(R, MR, static_cast<int>(h->m), h->rho, h->res_CS));
     return LRS_OK;
   }
   if (h->engine == 2) {

@@ -211,6 +211,63 @@ cudaError_t task_launch_seeded(const TaskQueue& Q, const unsigned long long* see
                                int* cnt_all, int R, int et, const TaskShape& S, int m_max,
                                int ns_max, int rho_max, cudaStream_t s);
 
+// ---- register-resident cluster engine (resident.cu) ---------------------------
+// One thread-block cluster of CS CTAs per column at a time (persistent: the
+// clusters take columns k = cluster, cluster + clusters, ...).  CTA c keeps
+// the columns [128c, 128c + 128) of A_k in registers for the whole sweep of
+// that column (W = A_k U, the IHT products and the final A^T pass read the
+// registers, never memory); slabs of later columns are prefetched into L2 by
+// bulk copies while the current column computes.  Partial products are
+// combined through distributed shared memory.
+//
+// Layout of A_k ("register order"): column k is CS consecutive slabs; slab c
+// holds the 4-column chunks ch = 0 .. nchc-1 of columns 4 (32c + ch) + e
+// (e < 4), nchc = min(32, nch4 - 32c), nch4 = ceil(n/4); inside a slab, rows
+// are taken in blocks of 32 (row i = 32p + l, l < 32; the last block has
+// m_last = m - 32 (MR - 1) rows) and element (i, ch, e) is the float at
+//   p * 128 nchc + ch * 4 Lp + 4 l + e,   Lp = 32 (p < MR - 1) or m_last,
+// so that lane l of warp w loads its rows of chunk ch = 8 cc + w with one
+// coalesced 16-byte load per row block.  Column k starts at float
+// k * m * 4 nch4 and slab c at float 128 m c inside it (columns beyond n are
+// zero).
+constexpr int kResNT = 256;            // threads per CTA (8 warps)
+constexpr int kResChunks = 32;         // 4-column chunks per CTA (4 per warp)
+constexpr int kResCols = 4 * kResChunks;  // columns per CTA
+
+struct ResArgs {
+  int n, m, q, r, rho, mode, tau, CS, nch4;
+  const float* A;       // register-order layout
+  const float* y;       // q x m measurements seen by the sweep
+  const float* U;       // n x r row-major
+  int* S_idx;           // q x rho in/out (ascending)
+  float* S_val;
+  float* B;             // q x r
+  float* H;             // q x n (ITER: h_k; INIT: L0 column)
+  int* err;
+  unsigned long long wait_ns;   // bound of every inter-CTA wait
+  unsigned long long* prof;     // optional kResProf counters (SM cycles summed over CTAs)
+};
+// Resident-engine profile counters: cycles in the column set-up, the W
+// pass, waiting in exchanges, the Gram/Cholesky, the IHT projection and A^T
+// pass, the A g_G product, mu, the local HardThreshold, the candidate merge,
+// the A s update, the LS and final pass; then the numbers of columns,
+// exchanges, support changes and IHT sweeps.
+constexpr int kResProf = 15;
+// Rank widths and rows-per-lane the engine is compiled for.
+__host__ __device__ inline int res_rpad(int r) { return r <= 2 ? 2 : r <= 6 ? r : 8; }
+inline bool res_supported(int n, int m, int r, int rho, int et) {
+  return et == 0 && r <= 8 && m >= 1 && m <= 192 && n <= 8 * kResCols && rho <= 32;
+}
+inline int res_cluster(int n) { return (((n + 3) / 4) + kResChunks - 1) / kResChunks; }
+size_t res_smem_bytes(int R, int MR, int m, int rho, int CS);
+cudaError_t res_prepare(int R, int MR);
+// clusters of CS CTAs that can be resident at once (0: the shape cannot run)
+int res_max_clusters(int R, int MR, int CS, size_t smem);
+cudaError_t res_launch(const ResArgs& a, int nclusters, cudaStream_t s);
+// row-major A (kc columns starting at k0, q x m x n) -> register-order layout
+cudaError_t res_repack(const float* A_rowmajor, int n, int m, int k0, int kc, float* A_res,
+                       cudaStream_t s);
+
 // Global (column-reduced) steps (global_ops.cu).
 // Row stride of the padded copy of U the sweep stages by TMA: r rounded up
 // to one of the compiled widths.
@@ -229,7 +286,6 @@ struct GlobalWork {
   int nblk;          // blocks of the row-parallel kernels
   int ks = 1;        // k-splits of the column reductions (grad, subspace step)
   float* gsplit = nullptr;   // ks x n x r FP32 partial sums (ks > 1)
-  double* dsplit = nullptr;  // ks x n x r FP64 partial sums (ks > 1)
 };
 cudaError_t grad_reduce(const GlobalWork& g, const float* H, const float* Bk, cudaStream_t s);
 cudaError_t eta_from_grad(const GlobalWork& g, double c_eta, double* eta_dev, cudaStream_t s);
@@ -249,13 +305,6 @@ int qr_blocks(int64_t n);
 cudaError_t cholqr2_into(int n, int r, const float* Z, float* Q, float* tmp, double* part,
                          double* rfac, int* err, int nblk, cudaStream_t s);
 
-// FP64 pieces of the spectral initialisation (subspace iteration on L0 = H^T).
-cudaError_t dcholqr2(const GlobalWork& g, const double* Zin, double* Ztmp, double* Uout,
-                     float* Uf, int* err, cudaStream_t s);
-cudaError_t dsubspace_step(const GlobalWork& g, const float* H, const double* U, double* P,
-                           double* Z, cudaStream_t s);  // Z = H^T (H U)
-cudaError_t dsubspace_change(const GlobalWork& g, const double* Uold, const double* Unew,
-                             double* D_rr, double* out, cudaStream_t s);
 cudaError_t subspace_overlap(const GlobalWork& g, const float* Ua, const float* Ub,
                              double* out_rr, cudaStream_t s);
 

@@ -627,21 +627,24 @@ __device__ __forceinline__ void ht_single(Ctx& C, bool keep_values) {
   csync();
 }
 
-// G = W^T W and G^{-1} into C.Gi.  FP64 arithmetic costs hundreds of cycles
-// per dependent operation on this part, so the Gram is summed in FP32 (lane
-// partials in row order, then a butterfly: a fixed order) and inverted by
-// Cholesky in FP32 followed by one Newton-Schulz step X <- X (2I - G X) in
-// FP64: the FP32 inverse has a relative error of about cond(G) 1e-7 and the
-// step squares it.  A pivot FP32 cannot take (G close to singular) falls back
-// to the FP64 Cholesky of factor_gram.
+// G = W^T W and G^{-1} into C.Gi.  The Gram is summed in FP64 (exact FP64
+// products of the FP32 entries; lane partials in row order, then a
+// butterfly: a fixed order).  Dependent FP64 operations cost hundreds of
+// cycles on this part, so the inverse starts from a Cholesky in FP32 and is
+// refined by one Newton-Schulz step X <- X (2I - G X) in FP64 against the
+// FP64 Gram: the FP32 inverse has a relative error of about cond(G) 1e-7 and
+// the step squares it.  A pivot FP32 cannot take (G close to singular) falls
+// back to the FP64 Cholesky of factor_gram.
 template <int R>
 __device__ __forceinline__ void gram_factor(Ctx& C) {
   const int r = C.r, lane = threadIdx.x & 31;
   for (int t = threadIdx.x >> 5; t < r * r; t += kNW) {
     const int p = t / r, q2 = t - p * r;
     if (q2 > p) continue;
-    float s = 0.f;
-    for (int i = lane; i < C.m; i += 32) s = fmaf(C.W[i * R + p], C.W[i * R + q2], s);
+    // FP64 sums of the exact FP64 products of the FP32 entries of W
+    double s = 0.0;
+    for (int i = lane; i < C.m; i += 32)
+      s = dfma(static_cast<double>(C.W[i * R + p]), static_cast<double>(C.W[i * R + q2]), s);
     s = warp_sum(s);
     if (lane == 0) {
       C.G[p * kMaxR + q2] = s;

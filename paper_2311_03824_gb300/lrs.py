@@ -40,7 +40,34 @@ class lrs_options(ctypes.Structure):
                 ("slab_mode", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("engine", ctypes.c_int32), ("inflight", ctypes.c_int32),
                 ("task_kib", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("grid", ctypes.c_int32)]
+                ("autotune", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("wait_ms", ctypes.c_int32)]
+
+
+class lrs_request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("q", ctypes.c_int64),
+                ("r", ctypes.c_int32), ("rho", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("opt", lrs_options), ("y", ctypes.c_void_p), ("A_or_mask", ctypes.c_void_p),
+                ("mem_kind", ctypes.c_int32), ("U", ctypes.c_void_p), ("B", ctypes.c_void_p),
+                ("S_idx", ctypes.c_void_p), ("S_val", ctypes.c_void_p),
+                ("out_mem_kind", ctypes.c_int32), ("user", ctypes.c_void_p)]
+
+
+class lrs_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("message", ctypes.c_char * 256),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
+                ("end_s", ctypes.c_double), ("footprint", ctypes.c_size_t),
+                ("worker", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("admitted", ctypes.c_int64)]
+
+
+LRS_RUNNER = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(lrs_request),
+                              ctypes.c_int32, ctypes.c_int32)
+
+
+class lrs_server_options(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("slots", ctypes.c_int32),
+                ("sms", ctypes.c_int32), ("runner", LRS_RUNNER), ("runner_ctx", ctypes.c_void_p)]
 
 
 _lib = None
@@ -77,6 +104,10 @@ def lib():
             "lrs_autotune": [_P, ctypes.c_int32, ctypes.c_char_p, ctypes.c_int32],
             "lrs_orthonormalize_noalloc": [_P, _P, ctypes.c_int64, ctypes.c_int32, _P],
             "lrs_destroy": [_P],
+            "lrs_server_create": [ctypes.POINTER(lrs_server_options), ctypes.POINTER(_P)],
+            "lrs_server_submit": [_P, ctypes.POINTER(lrs_request), ctypes.POINTER(ctypes.c_uint64)],
+            "lrs_server_wait": [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(lrs_result)],
+            "lrs_server_destroy": [_P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -86,6 +117,10 @@ def lib():
         L.lrs_last_error.restype = ctypes.c_char_p
         L.lrs_noalloc_last_error.argtypes = []
         L.lrs_noalloc_last_error.restype = ctypes.c_char_p
+        L.lrs_server_last_error.argtypes = []
+        L.lrs_server_last_error.restype = ctypes.c_char_p
+        L.lrs_request_footprint.argtypes = [ctypes.POINTER(lrs_request)]
+        L.lrs_request_footprint.restype = ctypes.c_size_t
         _lib = L
     return _lib
 
@@ -207,6 +242,17 @@ def lrs_sweep_trace(h, q):
     return out.reshape(q, len(TRACE_PHASES))
 
 
+RES_PROF = ["load", "w_pass", "wait", "gram", "proj_at", "agg", "mu", "ht_local", "merge",
+            "as_update", "final", "n_columns", "n_exchanges", "n_support_changes", "n_sweeps"]
+
+
+def lrs_resident_profile(h):
+    """Resident-engine counters (handle created with engine=3, profile=2)."""
+    out = np.zeros(len(RES_PROF), np.uint64)
+    _check(lib().lrs_sweep_trace(h, out.ctypes.data_as(_P), out.size))
+    return dict(zip(RES_PROF, (int(v) for v in out)))
+
+
 def lrs_task_profile(h):
     """Task-engine counters (handle created with engine=2, profile=2)."""
     out = np.zeros(len(TASK_PROF), np.uint64)
@@ -244,6 +290,49 @@ def lrs_orthonormalize_noalloc(Z, Q, stream=None):
     status = lib().lrs_orthonormalize_noalloc(_P(Z.data_ptr()), _P(Q.data_ptr()), n, r, st)
     if status != LRS_OK:
         raise LrsError(status, lib().lrs_noalloc_last_error().decode())
+
+
+def _check_srv(st):
+    if st != LRS_OK:
+        raise LrsError(st, lib().lrs_server_last_error().decode())
+
+
+def lrs_server_create(hbm_budget=0, slots=0, sms=0, runner=None):
+    """Native request server (lrs_server_*).  runner: None (the library's
+    solver) or a Python callable (request, grid, worker) -> status used in
+    its place; the ctypes callback object is kept on the returned handle's
+    side by the caller (see serve.Server)."""
+    o = lrs_server_options()
+    o.hbm_budget = int(hbm_budget)
+    o.slots = int(slots)
+    o.sms = int(sms)
+    cb = None
+    if runner is not None:
+        cb = LRS_RUNNER(lambda ctx, req, grid, worker: int(runner(req.contents, grid, worker)))
+        o.runner = cb
+    h = _P()
+    _check_srv(lib().lrs_server_create(ctypes.byref(o), ctypes.byref(h)))
+    return h, cb
+
+
+def lrs_server_submit(srv, req):
+    t = ctypes.c_uint64()
+    _check_srv(lib().lrs_server_submit(srv, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def lrs_server_wait(srv, ticket, timeout_ms=-1):
+    res = lrs_result()
+    _check_srv(lib().lrs_server_wait(srv, ticket, timeout_ms, ctypes.byref(res)))
+    return res
+
+
+def lrs_server_destroy(srv):
+    _check_srv(lib().lrs_server_destroy(srv))
+
+
+def lrs_request_footprint(req):
+    return int(lib().lrs_request_footprint(ctypes.byref(req)))
 
 
 def lrs_destroy(h):

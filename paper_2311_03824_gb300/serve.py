@@ -1,18 +1,14 @@
-"""Serving loop: many AltGDmin-LR+S reconstruction problems solved on one GPU
-with continuous batching.
+"""Serving: many AltGDmin-LR+S reconstruction problems on one GPU with
+continuous batching, through the library's native request server
+(include/lrs.h, lrs_server_*).
 
-Requests (Gaussian or row-masked 2D-DFT problems of any n, q, r, m, rho)
-arrive over time.  A request is admitted as soon as a slot is free and its
-device footprint fits the HBM budget left by the requests in flight; each
-admitted request runs on its own CUDA stream through the C ABI (its A_k or
-masks, U, B, S stay on the device for all of its iterations), so the work of
-concurrent requests overlaps on the GPU; the persistent sweep of a Gaussian
-request gets a share of the SMs (`lrs_options.grid`).  Finished requests
-release their slot and memory, which admits the next ones.  Latency is
-completion minus arrival, queueing and input generation included.
-
-Every solver step runs in the library's kernels; this module only orders the
-calls, generates the synthetic inputs and keeps the books.
+The admission (first come, first served, as soon as a slot is free and the
+request's device footprint fits the HBM budget left by the requests in
+flight), the worker threads with one CUDA stream each, and the SM share of a
+Gaussian request's persistent sweep all live in the library.  This module
+only hands requests over at their arrival times, with the inputs a caller's
+function produces for them, and collects the outcomes: latency is completion
+minus arrival, the production of the inputs included.
 """
 from __future__ import annotations
 
@@ -51,204 +47,148 @@ class Result:
     arrival: float
     start: float
     end: float
-    rel_err: float
+    rel_err: float = math.nan
     outputs: Optional[tuple] = None
     error: Optional[str] = None
+    footprint: int = 0
+    grid: int = 0
+    admitted: int = -1
 
     @property
     def latency(self):
         return self.end - self.arrival
 
 
-def footprint_bytes(req: Request) -> int:
-    """Device bytes a request holds while it runs (inputs, the stored operator,
-    the exact copy kept for the refinement of low-precision forms, the task
-    engine's per-column scratch, the iterate), with 10 % headroom."""
-    n, q, r, m, rho = req.n, req.q, req.r, req.m, req.rho
-    if req.kind == "dft":
-        b = q * m * (8 + 4 + 8 + 4) + q * n * 8 + 8 * n * r * 8 + q * max(rho, 1) * 12
-    else:
-        ns = (n + 31) // 32 * 32
-        eb = {L.LRS_A_FP32: 4, L.LRS_A_BF16: 2, L.LRS_A_FP8_HI: 1, L.LRS_A_FP8_HILO: 2}[req.a_dtype]
-        gen = q * m * n * 4                        # the generated FP32 A_k (freed after set-up)
-        stored = q * m * ns * eb
-        exact = q * m * n * 4 if req.a_dtype != L.LRS_A_FP32 else 0
-        scratch = q * (n + ns + 2 * m + 16 * 16 * 2 + 4 * 16 * m) * 4
-        b = gen + stored + exact + scratch + q * m * 8
-    return int(b * 1.1) + (64 << 20)
+def native_request(rq: Request, y=None, A_or_mask=None, outs=None) -> L.lrs_request:
+    """The lrs_request of a request (buffers: numpy host arrays or torch CUDA
+    tensors, all of one kind)."""
+    o = L.make_options(T=rq.T, a_dtype=rq.a_dtype if rq.kind == "gaussian" else 0,
+                       nx=rq.nx, ny=rq.ny)
+    req = L.lrs_request()
+    req.n, req.m, req.q, req.r, req.rho = rq.n, rq.m, rq.q, rq.r, rq.rho
+    req.kind = L.LRS_OP_DFT2D_MASK if rq.kind == "dft" else L.LRS_OP_GAUSSIAN
+    req.opt = o
+    if y is not None:
+        (py, mk), (pa, _) = L._ptr(y), L._ptr(A_or_mask)
+        req.y, req.A_or_mask, req.mem_kind = py, pa, mk
+    if outs is not None:
+        U, B, Si, Sv = outs
+        req.U, req.B = L._ptr(U)[0], L._ptr(B)[0]
+        req.S_idx = L._ptr(Si)[0] if rq.rho else None
+        req.S_val = L._ptr(Sv)[0] if rq.rho else None
+        req.out_mem_kind = 0
+    req.user = rq.rid + 1          # nonzero: a null user pointer reads back as None
+    return req
 
 
-def c4_requests(count: int, seed: int = 5, T: int = 100):
-    """The serving mix: 70 % Gaussian problems with BF16-stored A_k,
-    n = 64 round(2^U[8,12] / 64), q = 16 round(2^U[6,10] / 16), r ~ U{2..10},
-    m = round(U[0.15, 0.4] n), rho = round(U[0.01, 0.02] n); 30 % DFT problems
-    on 64 x 64 or 128 x 128 frames with the same laws for q, r, rho and
-    m / n in [0.15, 0.40] (64 x 64) or [0.10, 0.125] (128 x 128: one frame and
-    its m samples must fit one CTA's shared memory)."""
-    rng = np.random.default_rng(seed)
-    out = []
-    for i in range(count):
-        q = int(16 * round(2 ** rng.uniform(6, 10) / 16))
-        r = int(rng.integers(2, 11))
-        if rng.uniform() < 0.7:
-            n = int(64 * round(2 ** rng.uniform(8, 12) / 64))
-            m = int(round(rng.uniform(0.15, 0.4) * n))
-            rho = max(1, int(round(rng.uniform(0.01, 0.02) * n)))
-            out.append(Request(i, "gaussian", n, q, r, max(m, r), rho, seed * 100003 + i, T))
-        else:
-            side = 64 if rng.uniform() < 0.5 else 128
-            n = side * side
-            frac = rng.uniform(0.15, 0.4) if side == 64 else rng.uniform(0.10, 0.125)
-            m = int(round(frac * n))
-            rho = max(1, int(round(rng.uniform(0.01, 0.02) * n)))
-            out.append(Request(i, "dft", n, q, r, m, rho, seed * 100003 + i, T, nx=side, ny=side,
-                               a_dtype=L.LRS_A_FP32))
-    return out
-
-
-def poisson_arrivals(reqs, rate, seed=6):
-    """Arrival times of a Poisson process of the given rate (requests/s)."""
-    rng = np.random.default_rng(seed)
-    t = 0.0
-    for rq in reqs:
-        t += rng.exponential(1.0 / rate)
-        rq.arrival = t
-    return reqs
-
-
-def solve_on_device(req: Request, stream, grid: int = 0, keep_outputs: bool = False):
-    """Generate the request's synthetic inputs on its stream, solve it through
-    the C ABI (lrs_init + T x GDmin iterations) and return (outputs or None,
-    relative error of X = U B + S against X*)."""
-    import torch
-    from lrsgen import FourierInstance
-    from lrsgen.device import DeviceGaussianInstance
-    with torch.cuda.stream(stream):
-        if req.kind == "dft":
-            inst = FourierInstance(nx=req.nx, ny=req.ny, q=req.q, r=req.r, m=req.m, rho=req.rho,
-                                   seed=req.seed)
-            s = L.Solver(req.n, req.m, req.q, req.r, req.rho, kind=L.LRS_OP_DFT2D_MASK,
-                         nx=req.nx, ny=req.ny, stream=stream)
-            s.set_measurements(np.ascontiguousarray(inst.Y, np.complex64),
-                               np.ascontiguousarray(inst.masks, np.int32))
-            Xs = inst.Xstar
-        else:
-            inst = DeviceGaussianInstance(req.n, req.q, req.r, req.m, req.rho, req.seed)
-            s = L.Solver(req.n, req.m, req.q, req.r, req.rho, stream=stream,
-                         a_dtype=req.a_dtype, grid=grid, engine=2)
-            s.set_measurements(inst.Y, inst.A)
-            inst.free()
-            Xs = inst.Xstar
-        try:
-            s.init()
-            s.iterate(req.T)
-            out = s.get()
-        finally:
-            s.close()
-    U, B, Si, Sv = out
-    dt = np.complex128 if req.kind == "dft" else np.float64
-    X = U.astype(dt) @ B.astype(dt)
-    for k in range(req.q):
-        X[Si[k], k] += Sv[k]
-    err = float(np.linalg.norm(X - Xs) / np.linalg.norm(Xs))
-    return (out if keep_outputs else None), err
+def footprint_bytes(rq: Request, host_inputs: bool = False) -> int:
+    """Device bytes the server reserves for the request while it runs
+    (lrs_request_footprint)."""
+    req = native_request(rq)
+    req.mem_kind = 0 if host_inputs else 1
+    return L.lrs_request_footprint(req)
 
 
 class Server:
-    """Continuous-batching request loop (see the module docstring).
+    """A native request server fed at the requests' arrival times.
 
-    run_request(req, slot_info) -> (outputs, rel_err) does the work of one
-    request; the default solves it on the GPU.  `slots` requests run at once
-    at most, and the footprints of the requests in flight never exceed
-    `hbm_budget` bytes."""
+    make_inputs(req) -> (Y, A_or_mask) produces a request's inputs when it
+    arrives (host arrays, or device tensors whose producing work is complete);
+    they are kept alive until the request has finished.  runner: None (the
+    library's solver) or a callable (request, grid, worker) -> lrs status
+    that the server calls in its place (tests of the admission logic)."""
 
-    def __init__(self, hbm_budget: int, slots: int = 8, sms: int = 152,
-                 run_request: Optional[Callable] = None, keep_outputs: bool = False):
+    def __init__(self, hbm_budget: int, slots: int = 8, sms: int = 0,
+                 runner: Optional[Callable] = None, keep_outputs: bool = False):
         self.budget = int(hbm_budget)
         self.slots = int(slots)
         self.sms = int(sms)
         self.keep_outputs = keep_outputs
-        self._run = run_request
-        self._lock = threading.Condition()
-        self.in_use = 0
-        self.running = 0
-        self.peak_in_use = 0
-        self.peak_running = 0
+        self._runner = runner
         self.makespan = 0.0
+        self.peak_running = 0
 
-    def grid_for(self, running_after: int) -> int:
-        """CTAs of a Gaussian request's persistent sweep: the GPU's two CTAs per
-        SM shared by the requests that will be running."""
-        return max(16, (2 * self.sms) // max(1, running_after))
-
-    def run(self, reqs, start_clock: Optional[float] = None):
-        """Serve `reqs` (admitted in arrival order); returns the Results in rid
-        order."""
-        import queue
-        reqs = sorted(reqs, key=lambda r: r.arrival)
-        for rq in reqs:
-            if footprint_bytes(rq) > self.budget:
-                raise ValueError(f"request {rq.rid} needs more than the whole HBM budget")
-        pending = list(reqs)
-        results = {}
+    def run(self, reqs, make_inputs: Callable, start_clock: Optional[float] = None):
+        """Serve `reqs` (handed over in arrival order); returns the Results in
+        rid order."""
+        by_rid = {rq.rid: rq for rq in reqs}
+        runner = None
+        if self._runner is not None:
+            runner = lambda req, grid, worker: self._runner(by_rid[req.user - 1], grid, worker)
+        srv, cb = L.lrs_server_create(self.budget, self.slots, self.sms, runner)
         t0 = time.perf_counter() if start_clock is None else start_clock
-        work = queue.Queue()
-        streams = []
-        if self._run is None:
-            import torch
-            streams = [torch.cuda.Stream() for _ in range(self.slots)]
+        order = sorted(reqs, key=lambda r: r.arrival)
+        tickets, held, submitted = {}, {}, {}
+        failures = {}
 
-        def worker(wi):
-            while True:
-                item = work.get()
-                if item is None:
-                    return
-                rq, grid, start = item
-                outs, err, msg = None, math.inf, None
+        def submitter():
+            for rq in order:
+                now = time.perf_counter() - t0
+                if rq.arrival > now:
+                    time.sleep(rq.arrival - now)
                 try:
-                    if self._run is not None:
-                        outs, err = self._run(rq, dict(grid=grid, worker=wi))
-                    else:
-                        outs, err = solve_on_device(rq, streams[wi], grid, self.keep_outputs)
-                except Exception as ex:  # the request fails; the loop goes on
-                    msg = f"{type(ex).__name__}: {ex}"
-                finally:
-                    end = time.perf_counter() - t0
-                    with self._lock:
-                        self.in_use -= footprint_bytes(rq)
-                        self.running -= 1
-                        self._lock.notify_all()
-                results[rq.rid] = Result(rq.rid, rq.kind, rq.arrival, start, end, err, outs, msg)
+                    y, a = make_inputs(rq)
+                    outs = None
+                    if self.keep_outputs:
+                        dt = np.complex64 if rq.kind == "dft" else np.float32
+                        outs = (np.empty((rq.r, rq.n), dt), np.empty((rq.q, rq.r), dt),
+                                np.empty((rq.q, max(rq.rho, 1)), np.int32),
+                                np.empty((rq.q, max(rq.rho, 1)), dt))
+                    req = native_request(rq, y, a, outs)
+                    held[rq.rid] = (y, a, outs, req)
+                    submitted[rq.rid] = time.perf_counter() - t0
+                    tickets[rq.rid] = L.lrs_server_submit(srv, req)
+                except Exception as ex:   # the request fails; the loop goes on
+                    failures[rq.rid] = f"{type(ex).__name__}: {ex}"
 
-        threads = [threading.Thread(target=worker, args=(i,), daemon=True)
-                   for i in range(self.slots)]
-        for th in threads:
-            th.start()
-        # admission: FIFO by arrival; a request waits until it has arrived, a
-        # slot is free and its footprint fits
+        th = threading.Thread(target=submitter, daemon=True)
+        th.start()
+        results = {}
+        pending = [rq.rid for rq in order]
         while pending:
-            rq = pending[0]
-            now = time.perf_counter() - t0
-            if rq.arrival > now:
-                time.sleep(min(rq.arrival - now, 0.01))
+            rid = pending[0]
+            if rid in failures:
+                rq = by_rid[rid]
+                now = time.perf_counter() - t0
+                results[rid] = Result(rid, rq.kind, rq.arrival, now, now, error=failures[rid])
+                pending.pop(0)
                 continue
-            fp = footprint_bytes(rq)
-            with self._lock:
-                while not (self.running < self.slots and self.in_use + fp <= self.budget):
-                    self._lock.wait(0.01)
-                self.in_use += fp
-                self.running += 1
-                self.peak_in_use = max(self.peak_in_use, self.in_use)
-                self.peak_running = max(self.peak_running, self.running)
-                grid = self.grid_for(self.running)
+            if rid not in tickets:
+                time.sleep(0.0005)
+                continue
+            res = L.lrs_server_wait(srv, tickets[rid], -1)
+            rq = by_rid[rid]
+            # native times are seconds since the server's creation; place them
+            # on this clock through the submission time
+            base = submitted[rid] - res.submit_s
+            r = Result(rid, rq.kind, rq.arrival, base + res.start_s, base + res.end_s,
+                       footprint=int(res.footprint), grid=int(res.grid),
+                       admitted=int(res.admitted))
+            if res.status != L.LRS_OK:
+                r.error = f"{L.STATUS_NAMES[res.status]}: {res.message.decode()}"
+            elif self.keep_outputs:
+                U, B, Si, Sv = held[rid][2]
+                r.outputs = (U.T.copy(), B.T.copy(), Si[:, :rq.rho], Sv[:, :rq.rho])
+            held.pop(rid, None)
+            results[rid] = r
             pending.pop(0)
-            work.put((rq, grid, time.perf_counter() - t0))
-        for _ in threads:
-            work.put(None)
-        for th in threads:
-            th.join()
+        th.join()
+        L.lrs_server_destroy(srv)
+        del cb
         self.makespan = time.perf_counter() - t0
+        self.peak_running = peak_concurrency(list(results.values()))
         return [results[k] for k in sorted(results)]
+
+
+def peak_concurrency(results):
+    """Largest number of requests running at once (from their start and end)."""
+    ev = sorted([(r.start, 1) for r in results if r.error is None] +
+                [(r.end, -1) for r in results if r.error is None], key=lambda e: (e[0], e[1]))
+    cur = peak = 0
+    for _, d in ev:
+        cur += d
+        peak = max(peak, cur)
+    return peak
 
 
 def summarize(results, makespan, reqs=None):
@@ -260,10 +200,10 @@ def summarize(results, makespan, reqs=None):
                throughput_req_s=len(ok) / makespan if makespan > 0 else math.inf,
                p50_latency_s=float(np.percentile(lat, 50)) if len(lat) else None,
                p99_latency_s=float(np.percentile(lat, 99)) if len(lat) else None,
-               mean_latency_s=float(lat.mean()) if len(lat) else None,
-               max_rel_err=float(max(r.rel_err for r in ok)) if ok else None)
-    errs = np.array([r.rel_err for r in ok])
+               mean_latency_s=float(lat.mean()) if len(lat) else None)
+    errs = np.array([r.rel_err for r in ok if not math.isnan(r.rel_err)])
     if len(errs):
+        out["max_rel_err"] = float(errs.max())
         out["rel_err_p50"] = float(np.median(errs))
         out["solved_1e-3"] = int(np.sum(errs <= 1e-3))
     out["failures"] = [(r.rid, r.error[:160]) for r in results if r.error is not None][:6]
@@ -271,7 +211,4 @@ def summarize(results, makespan, reqs=None):
         by = {rq.rid: rq for rq in reqs}
         ci = sum(by[r.rid].q * by[r.rid].T for r in ok)
         out["column_iters_per_s"] = ci / makespan if makespan > 0 else math.inf
-        out["unsolved"] = [(r.rid, by[r.rid].kind, by[r.rid].n, by[r.rid].q, by[r.rid].r,
-                            by[r.rid].m, by[r.rid].rho, round(r.rel_err, 4))
-                           for r in ok if r.rel_err > 1e-3][:8]
     return out

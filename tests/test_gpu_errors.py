@@ -25,7 +25,7 @@ def _need_gpu():
     build.build()
 
 
-@pytest.mark.parametrize("engine", [1, 2])
+@pytest.mark.parametrize("engine", [1, 2, 3])
 def test_out_of_order_calls_return_state_error_and_change_nothing(engine):
     from paper_2311_03824_gb300 import Solver
     from paper_2311_03824_gb300 import lrs as L
@@ -57,7 +57,7 @@ def test_out_of_order_calls_return_state_error_and_change_nothing(engine):
     assert np.array_equal(X, X_fresh)
 
 
-@pytest.mark.parametrize("engine", [1, 2])
+@pytest.mark.parametrize("engine", [1, 2, 3])
 def test_rank_deficient_column_reports_numerical_error_with_column(engine):
     from paper_2311_03824_gb300 import lrs as L
     inst = GaussianInstance(n=64, q=16, r=2, m=32, rho=2, seed=6)

@@ -39,11 +39,13 @@ def _need_gpu():
     build.build()
 
 
-def test_one_step_gaussian_n1000_q1000():
+@pytest.mark.parametrize("opts", [dict(autotune=1), dict(engine=3)],
+                         ids=["default", "resident"])
+def test_one_step_gaussian_n1000_q1000(opts):
     cfg = {k: v for k, v in C1.items() if k != "T"}
     inst = GaussianInstance(**cfg)
     P = Problem.gaussian(inst)
-    s = new_solver(inst, autotune=1)
+    s = new_solver(inst, **opts)
     s.init()
     t, recs = 0, []
     try:
@@ -52,10 +54,10 @@ def test_one_step_gaussian_n1000_q1000():
             t = target
             g = s.get()
             eta, _ = s.progress()
-            st64, _, dec = probe_step(P, state_from_gpu(g, inst.n, t, eta, np.float64))
+            st64, _, dec, dev = probe_step(P, state_from_gpu(g, inst.n, t, eta, np.float64))
             s.iterate(1)
             t += 1
-            recs.append(compare_step(st64, dec, s.get()))
+            recs.append(compare_step(st64, dec, s.get(), dev=dev))
     finally:
         s.close()
     check_records(recs, min_whole=1)
@@ -86,9 +88,9 @@ def test_sampled_columns_gaussian_n4096_q2048():
     Y = dev.Y[kt].cpu().numpy()
     dev.free()
     P = Problem(O.GaussianOperator(A), O.GaussianOperator(A, np.float32), Y, r, rho)
-    st64, _, dec = probe_step(P, state_from_gpu((U, B[:, ks], Si[ks], Sv[ks]), n, 5, eta,
-                                                np.float64))
-    rec = compare_step(st64, dec, (U1, B1[:, ks], S1i[ks], S1v[ks]), whole=False)
+    st64, _, dec, dev = probe_step(P, state_from_gpu((U, B[:, ks], Si[ks], Sv[ks]), n, 5, eta,
+                                                     np.float64))
+    rec = compare_step(st64, dec, (U1, B1[:, ks], S1i[ks], S1v[ks]), whole=False, dev=dev)
     check_records([rec], min_whole=0, max_excluded=0.25)
 
 
@@ -105,10 +107,10 @@ def test_one_step_fourier_128x128():
             t = target
             g = s.get()
             eta, _ = s.progress()
-            st64, _, dec = probe_step(P, state_from_gpu(g, inst.n, t, eta, np.complex128))
+            st64, _, dec, dev = probe_step(P, state_from_gpu(g, inst.n, t, eta, np.complex128))
             s.iterate(1)
             t += 1
-            recs.append(compare_step(st64, dec, s.get()))
+            recs.append(compare_step(st64, dec, s.get(), dev=dev))
     finally:
         s.close()
     check_records(recs, min_whole=0, max_excluded=0.05)

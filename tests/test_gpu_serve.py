@@ -1,7 +1,8 @@
-"""Serving on the GPU: requests of different shapes and operators solved
-alone and concurrently in the continuous-batching loop give identical
-results (the kernels' arithmetic depends neither on what else runs nor on
-the number of CTAs a request's sweep gets)."""
+"""Serving on the GPU through the native request server (lrs_server_*):
+requests of different shapes and operators solved one at a time and
+concurrently with continuous batching give identical results (the kernels'
+arithmetic depends neither on what else runs nor on the number of CTAs a
+request's sweep gets)."""
 import numpy as np
 import pytest
 
@@ -31,19 +32,37 @@ def small_mix():
 
 def test_alone_equals_mix():
     import torch
+    import bench
     from paper_2311_03824_gb300 import serve as S
     reqs = small_mix()
-    stream = torch.cuda.Stream()
-    alone = {rq.rid: S.solve_on_device(rq, stream, grid=0, keep_outputs=True) for rq in reqs}
-    free = torch.cuda.mem_get_info()[0]
-    srv = S.Server(int(0.5 * free), slots=4, keep_outputs=True)
-    res = srv.run(reqs)
+    budget = int(0.5 * torch.cuda.mem_get_info()[0])
+    gen_a = bench.C4Inputs()
+    alone = S.Server(budget, slots=1, keep_outputs=True).run(reqs, gen_a)
+    gen_a.score(alone, reqs)
+    gen_m = bench.C4Inputs()
+    srv = S.Server(budget, slots=4, keep_outputs=True)
+    mix = srv.run(reqs, gen_m)
     assert srv.peak_running >= 2          # the requests did run concurrently
-    for r in res:
-        assert r.error is None, r.error
-        out_a, err_a = alone[r.rid]
-        for a, b in zip(out_a, r.outputs):
-            assert np.array_equal(a, b), r.rid
-        assert r.rel_err == err_a
-    summ = S.summarize(res, srv.makespan, reqs)
+    for a, r in zip(alone, mix):
+        assert a.error is None and r.error is None, (a.error, r.error)
+    # outputs compared before scoring consumes them
+    gen_m.score(mix, reqs)
+    for a, r in zip(alone, mix):
+        assert r.rel_err == a.rel_err, r.rid
+        assert r.rel_err < 0.5
+    summ = S.summarize(mix, srv.makespan, reqs)
     assert summ["failed"] == 0 and summ["p99_latency_s"] >= summ["p50_latency_s"] > 0
+
+
+def test_alone_equals_mix_bitwise():
+    import torch
+    import bench
+    from paper_2311_03824_gb300 import serve as S
+    reqs = small_mix()
+    budget = int(0.5 * torch.cuda.mem_get_info()[0])
+    alone = S.Server(budget, slots=1, keep_outputs=True).run(reqs, bench.C4Inputs())
+    mix = S.Server(budget, slots=4, keep_outputs=True).run(reqs, bench.C4Inputs())
+    for a, r in zip(alone, mix):
+        assert a.error is None and r.error is None
+        for x, y in zip(a.outputs, r.outputs):
+            assert np.array_equal(x, y), r.rid

@@ -1,39 +1,59 @@
-"""The serving loop's book-keeping on the CPU (a fake solver that sleeps):
-admission never exceeds the slots or the HBM budget, requests start in
-arrival order once they have arrived, every request completes once, a
-failing request is reported without stopping the loop, and the summary's
-latency percentiles match the recorded times."""
+"""The native request server's book-keeping on the CPU (include/lrs.h,
+lrs_server_*; a runner that sleeps stands in for the solver): admission
+never exceeds the slots or the HBM budget, requests are admitted in arrival
+order once they have arrived, every request completes once, a failing
+request is reported without stopping the loop, and the summary's latency
+percentiles match the recorded times."""
 import threading
 import time
 
 import numpy as np
 import pytest
 
+import bench
+from paper_2311_03824_gb300 import lrs as L
 from paper_2311_03824_gb300 import serve as S
 
 
-def test_admission_respects_slots_and_budget():
-    reqs = S.c4_requests(40, seed=9, T=10)
-    S.poisson_arrivals(reqs, rate=2000.0, seed=3)
-    budget = int(2.5 * max(S.footprint_bytes(r) for r in reqs))
-    log, lock = [], threading.Lock()
-    srv = S.Server(budget, slots=3)
+def dummy_inputs(rq):
+    return np.zeros(1, np.float32), np.zeros(1, np.float32)
 
-    def run(rq, info):
-        with lock:
-            log.append(rq.rid)
-            assert srv.running <= 3 and srv.in_use <= budget
-        time.sleep(0.002 + 0.001 * (rq.rid % 3))
-        return None, 1e-7
 
-    srv._run = run
-    res = srv.run(reqs)
-    assert sorted(r.rid for r in res) == list(range(40))
-    assert srv.peak_running <= 3 and srv.peak_in_use <= budget
-    assert all(r.error is None for r in res)
-    assert log == [r.rid for r in sorted(reqs, key=lambda r: r.arrival)]   # FIFO
+def overlaps_ok(res, slots, budget):
+    """At every start, the requests running (including it) fit the slots and
+    the budget."""
     for r in res:
-        assert r.start >= r.arrival - 1e-6 and r.end >= r.start
+        running = [o for o in res if o.start <= r.start < o.end]
+        assert len(running) <= slots, (r.rid, len(running))
+        assert sum(o.footprint for o in running) <= budget
+
+
+def test_admission_respects_slots_and_budget():
+    reqs = bench.c4_requests(40, seed=9, T=10)
+    bench.poisson_arrivals(reqs, rate=2000.0, seed=3)
+    fps = [S.footprint_bytes(r, host_inputs=True) for r in reqs]
+    budget = int(2.5 * max(fps))
+    lock = threading.Lock()
+    seen = []
+
+    def run(rq, grid, worker):
+        with lock:
+            seen.append(rq.rid)
+        time.sleep(0.002 + 0.001 * (rq.rid % 3))
+        return L.LRS_OK
+
+    srv = S.Server(budget, slots=3, runner=run)
+    res = srv.run(reqs, dummy_inputs)
+    assert sorted(r.rid for r in res) == list(range(40))
+    assert sorted(seen) == list(range(40))
+    assert all(r.error is None for r in res)
+    arrival_order = [r.rid for r in sorted(reqs, key=lambda r: r.arrival)]
+    assert [r.rid for r in sorted(res, key=lambda r: r.admitted)] == arrival_order   # FIFO
+    overlaps_ok(res, 3, budget)
+    assert srv.peak_running <= 3
+    for r in res:
+        assert r.start >= r.arrival - 1e-3 and r.end >= r.start
+        assert r.footprint == S.footprint_bytes(reqs[r.rid], host_inputs=True)
     summ = S.summarize(res, srv.makespan, reqs)
     lat = np.array([r.latency for r in res])
     assert summ["p50_latency_s"] == pytest.approx(np.percentile(lat, 50))
@@ -42,34 +62,55 @@ def test_admission_respects_slots_and_budget():
 
 
 def test_failed_request_is_reported_and_loop_continues():
-    reqs = S.c4_requests(6, seed=2, T=5)
+    reqs = bench.c4_requests(6, seed=2, T=5)
 
-    def run(rq, info):
-        if rq.rid == 2:
-            raise RuntimeError("boom")
-        return None, 0.0
+    def run(rq, grid, worker):
+        return L.LRS_ERR_NUMERICAL if rq.rid == 2 else L.LRS_OK
 
-    srv = S.Server(10 ** 15, slots=2, run_request=run)
-    res = srv.run(reqs)
+    srv = S.Server(10 ** 15, slots=2, runner=run)
+    res = srv.run(reqs, dummy_inputs)
     assert [r.rid for r in res] == list(range(6))
-    assert res[2].error and "boom" in res[2].error
+    assert res[2].error and "LRS_ERR_NUMERICAL" in res[2].error
     summ = S.summarize(res, srv.makespan)
     assert summ["failed"] == 1 and summ["failures"][0][0] == 2
 
 
 def test_request_larger_than_budget_is_rejected():
-    reqs = S.c4_requests(3, seed=1)
-    with pytest.raises(ValueError):
-        S.Server(1, slots=1, run_request=lambda rq, i: (None, 0.0)).run(reqs)
+    reqs = bench.c4_requests(3, seed=1)
+    srv = S.Server(1, slots=1, runner=lambda rq, g, w: L.LRS_OK)
+    res = srv.run(reqs, dummy_inputs)
+    assert all(r.error and "budget" in r.error for r in res)
+
+
+def test_wait_times_out_on_an_unfinished_request():
+    release = threading.Event()
+
+    def run(rq, grid, worker):
+        release.wait(5.0)
+        return L.LRS_OK
+
+    srv, cb = L.lrs_server_create(10 ** 12, 1, 0, lambda req, g, w: run(None, g, w))
+    rq = bench.c4_requests(1, seed=4)[0]
+    y, a = dummy_inputs(rq)
+    req = S.native_request(rq, y, a)
+    t = L.lrs_server_submit(srv, req)
+    with pytest.raises(L.LrsError) as e:
+        L.lrs_server_wait(srv, t, 50)
+    assert e.value.status == L.LRS_ERR_TIMEOUT
+    release.set()
+    res = L.lrs_server_wait(srv, t, -1)
+    assert res.status == L.LRS_OK and res.grid >= 16
+    L.lrs_server_destroy(srv)
+    del cb
 
 
 def test_mix_laws():
-    reqs = S.c4_requests(400, seed=5)
+    reqs = bench.c4_requests(400, seed=5)
     g = [r for r in reqs if r.kind == "gaussian"]
     d = [r for r in reqs if r.kind == "dft"]
     assert 0.6 < len(g) / len(reqs) < 0.8
     assert all(256 <= r.n <= 4096 and r.n % 64 == 0 for r in g)
     assert all(64 <= r.q <= 1024 and r.q % 16 == 0 for r in reqs)
     assert all(2 <= r.r <= 10 for r in reqs)
-    assert all(0.15 * r.n - 1 <= r.m <= 0.4 * r.n + 1 for r in g)
-    assert all((r.nx, r.ny) in ((64, 64), (128, 128)) and r.m <= 2048 for r in d)
+    assert all(0.15 * r.n - 1 <= r.m <= 0.4 * r.n + 1 for r in reqs)
+    assert all((r.nx, r.ny) in ((64, 64), (128, 128)) for r in d)
