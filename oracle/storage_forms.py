@@ -88,7 +88,9 @@ def encode(A, form):
         return dec_hi, s1
     if form != "fp8_hilo":
         raise ValueError(form)
-    res = _f32(A - dec_hi)
+    # the residual A - s1 * hi taken exactly (float64 holds the product and the
+    # difference without rounding) and rounded once to float32
+    res = _f32(A.astype(np.float64) - hi.astype(np.float64) * s1.astype(np.float64))
     rmax = np.abs(res).max(axis=2, keepdims=True)
     s2 = np.where(rmax > 0, _f32(rmax / np.float32(E4M3_MAX)), np.float32(1.0)).astype(np.float32)
     lo = e4m3_round(_f32(res / s2))

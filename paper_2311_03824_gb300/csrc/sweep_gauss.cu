@@ -50,7 +50,8 @@ __device__ __forceinline__ float e4m3_value(unsigned char c) {
 // Per-row scales of the FP8 forms for columns [k0, k0 + kc): one warp per row
 // (k, i).  hi = e4m3(A / s1) with s1 = max_j |A(i, j)| / 448 (the largest
 // finite e4m3 value); for the hi/lo form, lo = e4m3((A - s1 hi) / s2) with
-// s2 = max_j |A(i, j) - s1 hi(i, j)| / 448.  An all-zero row takes scale 1.
+// s2 = max_j |A(i, j) - s1 hi(i, j)| / 448, the residual A - s1 hi rounded once
+// (fused multiply-add).  An all-zero row takes scale 1.
 __global__ void rowscale_kernel(GaussLayout L, const float* __restrict__ Ain, int k0, int kc,
                                 float* __restrict__ rscale) {
   const int lane = threadIdx.x & 31;
@@ -67,7 +68,7 @@ __global__ void rowscale_kernel(GaussLayout L, const float* __restrict__ Ain, in
     if (per == 2) {
       float mr = 0.f;
       for (int j = lane; j < L.n; j += 32)
-        mr = fmaxf(mr, fabsf(a[j] - e4m3_value(to_e4m3(a[j] / s1)) * s1));
+        mr = fmaxf(mr, fabsf(fmaf(-e4m3_value(to_e4m3(a[j] / s1)), s1, a[j])));
       mr = warp_max(mr);
       s2 = mr > 0.f ? mr / 448.f : 1.f;
     }
@@ -112,7 +113,7 @@ __global__ void repack_kernel(GaussLayout L, const float* __restrict__ Ain, int 
       dst[0] = hi;
       if constexpr (ET == 3) {
         const float s2 = rscale[ro + 1];
-        dst[static_cast<size_t>(L.m) * kTW] = to_e4m3((v - e4m3_value(hi) * s1) / s2);
+        dst[static_cast<size_t>(L.m) * kTW] = to_e4m3(fmaf(-e4m3_value(hi), s1, v) / s2);
       }
     }
   }
