@@ -60,6 +60,22 @@ typedef enum {
   LRS_A_FP8_HILO = 3        /* e4m3 hi + e4m3 lo of the remainder, row scale   */
 } lrs_a_dtype;
 
+/* Column-sharded solves (Section II-E: the columns are split across nodes
+ * and only n x r sums travel): a handle holds a contiguous range of the
+ * columns of a larger problem, and at every column reduction (each
+ * subspace-iteration step of lrs_init, each gradient of lrs_iterate) the
+ * library calls this function with its partial sums: nb_mine blocks of
+ * n x w float32 (row-major, one block per grad_block columns, in column
+ * order; host memory).  It must write into `all` (room for cap blocks) the
+ * partial blocks of every shard in global column order and return how many
+ * it wrote, or a negative value on failure (the call then returns
+ * LRS_ERR_ARG).  The library adds the blocks in that order, so a solve whose
+ * shards start at multiples of grad_block gives bit for bit the result of
+ * one handle over all columns with the same grad_block.  Every shard makes
+ * the same sequence of calls. */
+typedef int32_t (*lrs_reducer)(void* ctx, const float* mine, int32_t nb_mine, int64_t n,
+                               int32_t w, float* all, int32_t cap);
+
 /* Options.  A zero-initialised struct selects the paper's defaults
  * (Algorithm 1 and Section II-F): tau0 = 10, tau = 3, T = 200, c_eta = 0.14,
  * rho_max = rho, float32 A_k. */
@@ -69,7 +85,7 @@ typedef struct {
   int32_t T;                /* iterations run by lrs_solve (0 -> 200)          */
   double c_eta;             /* eta = c_eta / ||grad_U f(U0,B1,S1)||_2 (0 -> 0.14) */
   int32_t rho_max;          /* entries HardThreshold keeps (0 -> rho)          */
-  int32_t nx, ny;           /* DFT frame: n = nx*ny, both powers of two        */
+  int32_t nx, ny;           /* DFT frame: n = nx*ny (powers of two, or n <= 4096) */
   lrs_a_dtype a_dtype;      /* storage of A_k for the sweeps                   */
   int32_t refine_every;     /* low-precision A_k: defect correction of y_k with
                                the exact FP32 operator every this many
@@ -108,11 +124,22 @@ typedef struct {
   int32_t wait_ms;          /* bound of every device-side wait of the task and
                                resident engines (0 -> 10000 ms); a wait that
                                expires makes the call return LRS_ERR_TIMEOUT */
+  int32_t grad_block;       /* columns per partial sum of the column reductions
+                               (0 -> chosen for the grid; fixed when a
+                               reducer is set or results must match a
+                               column-sharded solve)                         */
+  lrs_reducer reduce;       /* column-sharded solve (see lrs_reducer); NULL for
+                               a handle that holds the whole problem; needs
+                               grad_block > 0 and use_graph = 0             */
+  void* reduce_ctx;         /* first argument of reduce                        */
+  int32_t reduce_cap;       /* partial blocks of all shards together (the `cap`
+                               of reduce)                                    */
 } lrs_options;
 
 /* Create a solver for one problem (Section I-A sizes).
  * n, m, q >= 1; 1 <= r <= 16 and r <= min(m, n); 0 <= rho <= n; for
- * LRS_OP_DFT2D_MASK, opt->nx * opt->ny == n with both powers of two (m may
+ * LRS_OP_DFT2D_MASK, opt->nx * opt->ny == n with both powers of two, or
+ * n <= 4096 for other sides (a direct DFT along those) (m may
  * exceed n only for the Gaussian operator's special cases; for the DFT
  * m <= n).  opt may be NULL (paper defaults).  On success *out holds a new
  * handle in state CREATED.  Errors: LRS_ERR_ARG, LRS_ERR_OOM, LRS_ERR_CUDA. */
@@ -147,6 +174,27 @@ lrs_status lrs_set_measurements(lrs_t h, const void* y, const void* A_or_mask,
  * Errors: LRS_ERR_STATE, LRS_ERR_NUMERICAL (non-SPD Gram, NaN), LRS_ERR_CUDA. */
 lrs_status lrs_init(lrs_t h);
 
+/* Automatic rank (Section II-F, parameter setting): the b% energy threshold
+ * on the leading singular values of L0.  Runs the IHT of the initialisation
+ * (s_k = IHT(y_k, A_k, rho, tau0, 0), L0 = [A_k^T (y_k - A_k s_k)], which does
+ * not depend on r), estimates the first N = max(1, floor(min(n, q, m) / 10))
+ * singular values of L0 by subspace iteration in blocks of 16 columns (the
+ * widest the r x r kernels hold; one block of min(16, n, q) when N <= 16),
+ * each block deflated by the ones before it (float32 products, FP64
+ * Cholesky-QR2 factors and Rayleigh-Ritz values), and returns in *r_out the
+ * smallest r <= N with sigma_1^2 + ... + sigma_r^2 >= energy * (sigma_1^2 +
+ * ... + sigma_N^2).  N is capped at 64 (four blocks).
+ * sv: NULL or a host array of sv_len doubles that receives the first
+ * min(N, sv_len) singular values (descending); *n_sv (if not NULL) = N.
+ * The handle's rank is the one it was created with: to solve at the
+ * estimated rank, create a handle with r = *r_out.  The call leaves the
+ * handle in state MEASURED (call it before lrs_init).  Gaussian operators.
+ * Errors: LRS_ERR_ARG (energy outside (0, 1], r_out NULL), LRS_ERR_STATE (not
+ * MEASURED), LRS_ERR_UNSUPPORTED (DFT operator), LRS_ERR_NUMERICAL,
+ * LRS_ERR_CUDA. */
+lrs_status lrs_estimate_rank(lrs_t h, double energy, int32_t* r_out, double* sv,
+                             int32_t sv_len, int32_t* n_sv);
+
 /* Run `iters` GDmin iterations of Algorithm 1 (t continues from the last
  * call): P_perp-projected IHT for s_k (tau sweeps), LS for b_k,
  * grad = sum_k A_k^T (A_k(U b_k + s_k) - y_k) b_k^T, eta from the t = 1
@@ -164,6 +212,19 @@ lrs_status lrs_init(lrs_t h);
  * Errors: LRS_ERR_ARG (iters < 0, err_log without reference), LRS_ERR_STATE,
  * LRS_ERR_NUMERICAL (column id in lrs_last_error), LRS_ERR_CUDA. */
 lrs_status lrs_iterate(lrs_t h, int32_t iters, double* err_log);
+
+/* `iters` GDmin iterations of several problems at once: every sweep is one
+ * persistent launch of the task engine whose work table holds the columns of
+ * all nh handles (Section II-E: the per-column work is independent, so
+ * uneven problems share the GPU's SMs in one launch); each handle then runs
+ * its own gradient, step size and QR on its own stream.  Every handle ends
+ * exactly as lrs_iterate(h, iters, NULL) would leave it alone, bit for bit.
+ * hs: nh distinct handles (1 <= nh <= 64), INITIALISED or later, Gaussian,
+ * task engine (engine 2), one rank width class and one A_k form, no reducer.
+ * The call returns when every handle's work is done.  State -> ITERATING.
+ * Errors: LRS_ERR_ARG, LRS_ERR_STATE, LRS_ERR_UNSUPPORTED (handles that
+ * cannot share a launch), LRS_ERR_NUMERICAL, LRS_ERR_TIMEOUT, LRS_ERR_CUDA. */
+lrs_status lrs_iterate_batch(lrs_t* hs, int32_t nh, int32_t iters);
 
 /* lrs_init followed by lrs_iterate(h, T, NULL).  State: MEASURED or later. */
 lrs_status lrs_solve(lrs_t h);

@@ -56,6 +56,7 @@ class GaussianInstance:
     alpha: float = 6.0
     y_float64: bool = False    # keep y_k in float64 (exact-recovery checks)
     identity_A: bool = False   # A_k = I (robust-PCA special case, m = n)
+    noise: float = 0.0         # y_k = A_k x*_k + noise * ||x*_k|| * N(0, I_m)
     Ustar: np.ndarray = field(repr=False, default=None)
     Bstar: np.ndarray = field(repr=False, default=None)
     S_idx: np.ndarray = field(repr=False, default=None)   # (q, rho) ascending
@@ -111,7 +112,11 @@ class GaussianInstance:
 
     def y_col(self, k, A_k=None):
         A_k = self.A_col(k) if A_k is None else A_k
-        y = A_k.astype(np.float64) @ self.x_col(k)
+        x = self.x_col(k)
+        y = A_k.astype(np.float64) @ x
+        if self.noise:
+            # relative to ||x*_k||, the RMS of y_k's entries for Gaussian A_k
+            y = y + self.noise * np.linalg.norm(x) * normals(self.seed, TAG_NOISE, k, len(y))
         return y if self.y_float64 else y.astype(np.float32)
 
     @property

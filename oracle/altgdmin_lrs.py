@@ -243,6 +243,48 @@ def top_r_left(L0, r):
     return Uf[:, :r], sv
 
 
+def rank_count(n, q, m):
+    """How many leading singular values of L0 the automatic rank looks at
+    (Section II-F, parameter setting): the first min(n/10, q/10, m/10), taken
+    as floor(min(n, q, m) / 10) and at least one."""
+    return max(1, min(n, q, m) // 10)
+
+
+def rank_from_singular_values(sv, N, energy=0.65):
+    """The b% energy threshold (Section II-F) on the first N singular values
+    sv (descending): the smallest r in 1..N whose leading r values hold at
+    least the fraction `energy` of the energy sum_{i<=N} sigma_i^2."""
+    e = np.asarray(sv, dtype=np.float64)[:N] ** 2
+    total = e.sum()
+    if not total > 0:
+        return 1
+    acc = 0.0
+    for j in range(len(e)):
+        acc += e[j]
+        if acc >= energy * total:
+            return j + 1
+    return len(e)
+
+
+def auto_rank(L0, m, energy=0.65):
+    """Automatic rank of Section II-F from L0 (n x q): the energy threshold
+    on the first rank_count(n, q, m) singular values of the full SVD.
+    Returns (r, the singular values used)."""
+    n, q = L0.shape
+    N = rank_count(n, q, m)
+    sv = np.linalg.svd(L0, compute_uv=False)[:N]
+    return rank_from_singular_values(sv, N, energy), sv
+
+
+def init_L0(op, Y, rho, tau0=10, mu_rule="support"):
+    """L0 of Algorithm 1, Initialization: s_k = IHT(y_k, A_k, rho, tau0, 0)
+    and column k = A_k^H (y_k - A_k s_k) (n x q).  It does not depend on r."""
+    dt = op.dtype
+    Y = np.asarray(Y, dtype=dt)
+    S, _, _ = iht(Y, op.A, op.AH, rho, tau0, np.zeros((op.q, op.n), dtype=dt), mu_rule)
+    return op.AH(Y - op.A(S)).T
+
+
 def spectral_norm(G):
     return float(np.linalg.norm(G, 2)) if G.size else 0.0
 

@@ -70,60 +70,109 @@ __device__ __forceinline__ float warp_sumf(float v) {
 }
 
 // ------------------------------------------------------------ 2D FFT --
+// Sides that are not powers of two take a direct DFT (frames of at most
+// kDirectPer * blockDim.x pixels): each thread keeps its outputs in
+// registers until every thread has read the frame.
+constexpr int kDirectPer = 8;
+
+__device__ void dft_direct_smem(float2* X, int nx, int ny, bool rows, const float2* tw,
+                                bool inverse) {
+  const int ld = ny + 1, n = nx * ny, len = rows ? ny : nx;
+  float2 acc[kDirectPer];
+#pragma unroll
+  for (int u = 0; u < kDirectPer; ++u) {
+    const int e = threadIdx.x + u * blockDim.x;
+    float2 s = make_float2(0.f, 0.f);
+    if (e < n) {
+      const int row = e / ny, col = e - row * ny;
+      const int j = rows ? col : row;  // output frequency along the transformed side
+      int idx = 0;                     // j * k mod len
+      for (int k = 0; k < len; ++k) {
+        float2 w = tw[idx];
+        if (inverse) w.y = -w.y;
+        s = cfma(rows ? X[row * ld + k] : X[k * ld + col], w, s);
+        idx += j;
+        if (idx >= len) idx -= len;
+      }
+    }
+    acc[u] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < kDirectPer; ++u) {
+    const int e = threadIdx.x + u * blockDim.x;
+    if (e < n) {
+      const int row = e / ny, col = e - row * ny;
+      X[row * ld + col] = acc[u];
+    }
+  }
+  __syncthreads();
+}
+
 // In-place unitary 2D FFT of the frame X (nx rows x ny columns, row stride
-// ny + 1 complex) in shared memory by radix-2 decimation in time along the
-// rows, then along the columns.  tx[k] = exp(-2 pi i k / nx), k < nx (same for
-// ty); inverse uses the conjugate twiddles.  All threads of the CTA call it.
+// ny + 1 complex) in shared memory: along the rows, then along the columns,
+// each by radix-2 decimation in time (a power-of-two side, lny / lnx its
+// log2) or a direct DFT (lny / lnx = -1).  tx[k] = exp(-2 pi i k / nx),
+// k < nx (same for ty); inverse uses the conjugate twiddles.  All threads of
+// the CTA call it.
 __device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const float2* tx,
                           const float2* ty, bool inverse) {
   const int ld = ny + 1, n = nx * ny;
-  // rows: bit reversal, then lny stages
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int row = e / ny, j = e - row * ny;
-    const int p = static_cast<int>(__brev(static_cast<unsigned>(j)) >> (32 - lny));
-    if (lny > 0 && p > j) {
-      const float2 t = X[row * ld + j];
-      X[row * ld + j] = X[row * ld + p];
-      X[row * ld + p] = t;
-    }
-  }
-  __syncthreads();
-  for (int s = 0; s < lny; ++s) {
-    const int half = 1 << s, step = ny >> (s + 1);
-    for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
-      const int row = b / (ny / 2), t = b - row * (ny / 2);
-      const int j = t & (half - 1), i1 = ((t >> s) << (s + 1)) + j, i2 = i1 + half;
-      float2 w = ty[j * step];
-      if (inverse) w.y = -w.y;
-      const float2 a = X[row * ld + i1], c = cmul(X[row * ld + i2], w);
-      X[row * ld + i1] = cadd(a, c);
-      X[row * ld + i2] = csub(a, c);
+  if (lny < 0) {
+    dft_direct_smem(X, nx, ny, true, ty, inverse);
+  } else {
+    // rows: bit reversal, then lny stages
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int row = e / ny, j = e - row * ny;
+      const int p = static_cast<int>(__brev(static_cast<unsigned>(j)) >> (32 - lny));
+      if (lny > 0 && p > j) {
+        const float2 t = X[row * ld + j];
+        X[row * ld + j] = X[row * ld + p];
+        X[row * ld + p] = t;
+      }
     }
     __syncthreads();
-  }
-  // columns: bit reversal, then lnx stages
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int i = e / ny, col = e - i * ny;
-    const int p = static_cast<int>(__brev(static_cast<unsigned>(i)) >> (32 - lnx));
-    if (lnx > 0 && p > i) {
-      const float2 t = X[i * ld + col];
-      X[i * ld + col] = X[p * ld + col];
-      X[p * ld + col] = t;
+    for (int s = 0; s < lny; ++s) {
+      const int half = 1 << s, step = ny >> (s + 1);
+      for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
+        const int row = b / (ny / 2), t = b - row * (ny / 2);
+        const int j = t & (half - 1), i1 = ((t >> s) << (s + 1)) + j, i2 = i1 + half;
+        float2 w = ty[j * step];
+        if (inverse) w.y = -w.y;
+        const float2 a = X[row * ld + i1], c = cmul(X[row * ld + i2], w);
+        X[row * ld + i1] = cadd(a, c);
+        X[row * ld + i2] = csub(a, c);
+      }
+      __syncthreads();
     }
   }
-  __syncthreads();
-  for (int s = 0; s < lnx; ++s) {
-    const int half = 1 << s, step = nx >> (s + 1);
-    for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
-      const int col = b % ny, t = b / ny;
-      const int j = t & (half - 1), i1 = ((t >> s) << (s + 1)) + j, i2 = i1 + half;
-      float2 w = tx[j * step];
-      if (inverse) w.y = -w.y;
-      const float2 a = X[i1 * ld + col], c = cmul(X[i2 * ld + col], w);
-      X[i1 * ld + col] = cadd(a, c);
-      X[i2 * ld + col] = csub(a, c);
+  if (lnx < 0) {
+    dft_direct_smem(X, nx, ny, false, tx, inverse);
+  } else {
+    // columns: bit reversal, then lnx stages
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int i = e / ny, col = e - i * ny;
+      const int p = static_cast<int>(__brev(static_cast<unsigned>(i)) >> (32 - lnx));
+      if (lnx > 0 && p > i) {
+        const float2 t = X[i * ld + col];
+        X[i * ld + col] = X[p * ld + col];
+        X[p * ld + col] = t;
+      }
     }
     __syncthreads();
+    for (int s = 0; s < lnx; ++s) {
+      const int half = 1 << s, step = nx >> (s + 1);
+      for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
+        const int col = b % ny, t = b / ny;
+        const int j = t & (half - 1), i1 = ((t >> s) << (s + 1)) + j, i2 = i1 + half;
+        float2 w = tx[j * step];
+        if (inverse) w.y = -w.y;
+        const float2 a = X[i1 * ld + col], c = cmul(X[i2 * ld + col], w);
+        X[i1 * ld + col] = cadd(a, c);
+        X[i2 * ld + col] = csub(a, c);
+      }
+      __syncthreads();
+    }
   }
   const float sc = rsqrtf(static_cast<float>(n));
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
@@ -135,8 +184,16 @@ __device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const flo
 }
 
 struct Geo {
-  int nx, ny, lnx, lny, n;
+  int nx, ny, lnx, lny, n;  // lnx / lny: log2 of a power-of-two side, else -1
 };
+
+// row, column of pixel e = row * ny + column, and an index modulo nx (ny)
+__device__ __forceinline__ int frow(const Geo& g, int e) { return g.lny >= 0 ? e >> g.lny : e / g.ny; }
+__device__ __forceinline__ int fcol(const Geo& g, int e) {
+  return g.lny >= 0 ? e & (g.ny - 1) : e - (e / g.ny) * g.ny;
+}
+__device__ __forceinline__ int fwrapx(const Geo& g, int v) { return g.lnx >= 0 ? v & (g.nx - 1) : v % g.nx; }
+__device__ __forceinline__ int fwrapy(const Geo& g, int v) { return g.lny >= 0 ? v & (g.ny - 1) : v % g.ny; }
 
 // out[f] = F2(in[f]) (or F2^H) for frames f; frames are n-vectors in natural
 // row-major order (pixel kx*ny + ky), frame f at in + f*n.
@@ -244,12 +301,12 @@ __device__ void sparse_dft(const FCtx& C, const int* p, const float2* v, int nnz
   const float sc = rsqrtf(static_cast<float>(C.g.n));
   for (int i = threadIdx.x; i < C.m; i += blockDim.x) {
     const int om = C.msk[i];
-    const int kx = om >> C.g.lny, ky = om & (C.g.ny - 1);
+    const int kx = frow(C.g, om), ky = fcol(C.g, om);
     float2 acc = make_float2(0.f, 0.f);
     for (int e = 0; e < nnz; ++e) {
       const int pe = p[e];
-      const int px = pe >> C.g.lny, py = pe & (C.g.ny - 1);
-      const float2 w = cmul(C.tx[(kx * px) & (C.g.nx - 1)], C.ty[(ky * py) & (C.g.ny - 1)]);
+      const int px = frow(C.g, pe), py = fcol(C.g, pe);
+      const float2 w = cmul(C.tx[fwrapx(C.g, kx * px)], C.ty[fwrapy(C.g, ky * py)]);
       acc = cfma(w, v[e], acc);
     }
     out[i] = make_float2(acc.x * sc, acc.y * sc);
@@ -433,7 +490,7 @@ __device__ void fhard_threshold(const FCtx& C, bool keep_values) {
       const int e = e0 + lane;
       unsigned key = 0u;
       if (e < n) {
-        const int row = e >> C.g.lny, col = e & (C.g.ny - 1);
+        const int row = frow(C.g, e), col = fcol(C.g, e);
         key = __float_as_uint(cabs2(C.X[row * ld + col]));
       }
       const bool in = e < n && (key & mask) == prefix;
@@ -478,7 +535,7 @@ __device__ void fhard_threshold(const FCtx& C, bool keep_values) {
   if (threadIdx.x == 0) { info[2] = 0; info[3] = 0; }
   __syncthreads();
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int row = e >> C.g.lny, col = e & (C.g.ny - 1);
+    const int row = frow(C.g, e), col = fcol(C.g, e);
     const unsigned key = __float_as_uint(cabs2(C.X[row * ld + col]));
     if (key > T) sel[atomicAdd(&info[3], 1)] = e;
     else if (key == T) {
@@ -501,7 +558,7 @@ __device__ void fhard_threshold(const FCtx& C, bool keep_values) {
     const int e = sel[t];
     int pos = 0;
     for (int u = 0; u < rho; ++u) pos += sel[u] < e;
-    const int row = e >> C.g.lny, col = e & (C.g.ny - 1);
+    const int row = frow(C.g, e), col = fcol(C.g, e);
     C.sp[pos] = e;
     C.sv[pos] = keep_values ? C.X[row * ld + col] : make_float2(0.f, 0.f);
   }
@@ -575,7 +632,7 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
     __syncthreads();
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       const int om = C.msk[i];
-      C.X[(om >> C.g.lny) * ld + (om & (C.g.ny - 1))] = C.dv[i];
+      C.X[(frow(C.g, om)) * ld + (fcol(C.g, om))] = C.dv[i];
     }
     __syncthreads();
     fft2_smem(C.X, C.g.nx, C.g.ny, C.g.lnx, C.g.lny, C.tx, C.ty, true);
@@ -586,7 +643,7 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
     __syncthreads();
     for (int e = threadIdx.x; e < rho; e += blockDim.x) {
       const int p = C.sp[e];
-      C.gv[e] = C.X[(p >> C.g.lny) * ld + (p & (C.g.ny - 1))];
+      C.gv[e] = C.X[(frow(C.g, p)) * ld + (fcol(C.g, p))];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -616,7 +673,7 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
     __syncthreads();
     for (int e = threadIdx.x; e < rho; e += blockDim.x) {
       const int p = C.sp[e];
-      float2& x = C.X[(p >> C.g.lny) * ld + (p & (C.g.ny - 1))];
+      float2& x = C.X[(frow(C.g, p)) * ld + (fcol(C.g, p))];
       x = cadd(x, C.sv[e]);
     }
     __syncthreads();
@@ -632,12 +689,12 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
     __syncthreads();
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       const int om = C.msk[i];
-      C.X[(om >> C.g.lny) * ld + (om & (C.g.ny - 1))] = C.dv[i];
+      C.X[(frow(C.g, om)) * ld + (fcol(C.g, om))] = C.dv[i];
     }
     __syncthreads();
     fft2_smem(C.X, C.g.nx, C.g.ny, C.g.lnx, C.g.lny, C.tx, C.ty, true);
     float2* Hk = a.H + static_cast<size_t>(k) * n;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) Hk[e] = C.X[(e >> C.g.lny) * ld + (e & (C.g.ny - 1))];
+    for (int e = threadIdx.x; e < n; e += blockDim.x) Hk[e] = C.X[(frow(C.g, e)) * ld + (fcol(C.g, e))];
   } else {
     fls_solve(C, C.dv);  // b = G^{-1} W^H (y - A s)
     if (threadIdx.x < r) {
@@ -1029,10 +1086,11 @@ static cudaError_t fft_frames(FourierSolver* F, const float2* in, float2* out, i
   return cudaGetLastError();
 }
 
+// log2 of a power of two, -1 for any other side (direct DFT)
 static int ilog2(int v) {
   int l = 0;
   while ((1 << l) < v) ++l;
-  return l;
+  return (1 << l) == v ? l : -1;
 }
 
 FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int tau0, int tau,

@@ -191,19 +191,10 @@ __global__ void __launch_bounds__(256) apply_rinv_kernel(int n, int r, const flo
   if (part && a < r && b <= a) part[static_cast<size_t>(blockIdx.x) * r * r + a * r + b] = acc;
 }
 
-// eta = c_eta / sqrt(lambda_max(G)), G = grad^T grad (sum of partials), by
-// cyclic Jacobi rotations on the r x r FP64 matrix.
-__global__ void eta_kernel(int r, int nblk, const double* __restrict__ part, double c_eta,
-                           double* __restrict__ eta, int* err) {
-  if (threadIdx.x != 0) return;
-  double A[kMaxR][kMaxR];
-  for (int a = 0; a < r; ++a)
-    for (int b = 0; b <= a; ++b) {
-      double s = 0.0;
-      for (int k = 0; k < nblk; ++k) s += part[static_cast<size_t>(k) * r * r + a * r + b];
-      A[a][b] = s;
-      A[b][a] = s;
-    }
+// Cyclic Jacobi rotations on the symmetric r x r FP64 matrix A, in place,
+// until the off-diagonal part is negligible: the diagonal then holds the
+// eigenvalues.
+__device__ void jacobi_sweeps(double (&A)[kMaxR][kMaxR], int r) {
   for (int sweep = 0; sweep < 60; ++sweep) {
     double off = 0.0, diag = 0.0;
     for (int a = 0; a < r; ++a)
@@ -227,11 +218,53 @@ __global__ void eta_kernel(int r, int nblk, const double* __restrict__ part, dou
         }
       }
   }
+}
+
+// the symmetric r x r matrix summed from nblk partials (partial k at part + k r r)
+__device__ void sum_partials(double (&A)[kMaxR][kMaxR], int r, int nblk,
+                             const double* __restrict__ part) {
+  for (int a = 0; a < r; ++a)
+    for (int b = 0; b <= a; ++b) {
+      double s = 0.0;
+      for (int k = 0; k < nblk; ++k) s += part[static_cast<size_t>(k) * r * r + a * r + b];
+      A[a][b] = s;
+      A[b][a] = s;
+    }
+}
+
+// eta = c_eta / sqrt(lambda_max(G)), G = grad^T grad (sum of partials), by
+// cyclic Jacobi rotations on the r x r FP64 matrix.
+__global__ void eta_kernel(int r, int nblk, const double* __restrict__ part, double c_eta,
+                           double* __restrict__ eta, int* err) {
+  if (threadIdx.x != 0) return;
+  double A[kMaxR][kMaxR];
+  sum_partials(A, r, nblk, part);
+  jacobi_sweeps(A, r);
   double lmax = 0.0;
   for (int a = 0; a < r; ++a) lmax = fmax(lmax, A[a][a]);
   const double nrm = sqrt(lmax);
   if (!(nrm < 1e300)) report_error(err, kErrNaN, -1);
   *eta = (nrm > 0.0) ? c_eta / nrm : 0.0;
+}
+
+// Rayleigh-Ritz values: the eigenvalues of the r x r FP64 Gram P^T P (sum of
+// partials) in descending order; for P = L0^T U with U an orthonormal basis of
+// a converged dominant subspace they are the squared singular values of L0.
+__global__ void ritz_kernel(int r, int nblk, const double* __restrict__ part,
+                            double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double A[kMaxR][kMaxR];
+  sum_partials(A, r, nblk, part);
+  jacobi_sweeps(A, r);
+  double ev[kMaxR];
+  for (int a = 0; a < r; ++a) ev[a] = A[a][a];
+  for (int a = 1; a < r; ++a)  // insertion sort, descending
+    for (int b = a; b > 0 && ev[b] > ev[b - 1]; --b) {
+      const double t = ev[b];
+      ev[b] = ev[b - 1];
+      ev[b - 1] = t;
+    }
+  for (int a = 0; a < r; ++a) out[a] = ev[a];
 }
 
 // P[k][l] = sum_j H[k][j] U[j][l]: one warp per column k.
@@ -329,9 +362,22 @@ cudaError_t subspace_change(const GlobalWork& g, const float* Uold, const float*
   return cudaGetLastError();
 }
 
+cudaError_t grad_partials(const GlobalWork& g, const float* H, const float* Bk, cudaStream_t s) {
+  const int qc = g.qc > 0 ? g.qc : (g.q + g.ks - 1) / g.ks;
+  kred_part_kernel<float><<<dim3((g.n + 31) / 32, g.ks), 256, 0, s>>>(g.n, g.q, g.r, qc, H, Bk,
+                                                                      g.gsplit);
+  return cudaGetLastError();
+}
+
+cudaError_t sum_blocks(int n, int r, int nb, const float* parts, float* out, cudaStream_t s) {
+  const int nr = n * r;
+  kred_fin_kernel<float><<<(nr + 255) / 256, 256, 0, s>>>(nr, nb, parts, out);
+  return cudaGetLastError();
+}
+
 cudaError_t grad_reduce(const GlobalWork& g, const float* H, const float* Bk, cudaStream_t s) {
-  if (g.ks > 1 && g.gsplit) {
-    const int qc = (g.q + g.ks - 1) / g.ks;
+  if ((g.ks > 1 || g.qc > 0) && g.gsplit) {
+    const int qc = g.qc > 0 ? g.qc : (g.q + g.ks - 1) / g.ks;
     kred_part_kernel<float><<<dim3((g.n + 31) / 32, g.ks), 256, 0, s>>>(g.n, g.q, g.r, qc, H, Bk,
                                                                         g.gsplit);
     const int nr = g.n * g.r;
@@ -399,6 +445,39 @@ cudaError_t qr_step(const GlobalWork& g, float* U, const double* eta_dev, int* e
 cudaError_t project_cols(const GlobalWork& g, const float* H, const float* U, float* P,
                          cudaStream_t s) {
   project_kernel<<<(g.q + 7) / 8, 256, 0, s>>>(g.n, g.q, g.r, H, U, P);
+  return cudaGetLastError();
+}
+
+// Z <- Z - Ua D with D = Ua^T Z (n x r row-major FP32, D r x r FP64): the
+// components of Z along the orthonormal columns of Ua removed.
+__global__ void __launch_bounds__(256) deflate_kernel(int n, int r, float* __restrict__ Z,
+                                                      const float* __restrict__ Ua,
+                                                      const double* __restrict__ D) {
+  __shared__ double sD[kMaxR * kMaxR];
+  for (int t = threadIdx.x; t < r * r; t += blockDim.x) sD[t] = D[t];
+  __syncthreads();
+  const size_t total = static_cast<size_t>(n) * r;
+  for (size_t u = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; u < total;
+       u += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t i = u / r;
+    const int b = static_cast<int>(u - i * r);
+    double acc = Z[u];
+    for (int a = 0; a < r; ++a) acc -= static_cast<double>(Ua[i * r + a]) * sD[a * r + b];
+    Z[u] = static_cast<float>(acc);
+  }
+}
+
+cudaError_t deflate(const GlobalWork& g, const float* Ua, float* Z, double* D, cudaStream_t s) {
+  overlap_part_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, Ua, Z, g.part);
+  overlap_fin_kernel<<<1, 256, 0, s>>>(g.r, g.nblk, g.part, D);
+  deflate_kernel<<<g.nblk, 256, 0, s>>>(g.n, g.r, Z, Ua, D);
+  return cudaGetLastError();
+}
+
+cudaError_t ritz_values(int rows, int r, const float* P, double* part, int nblk, double* out,
+                        cudaStream_t s) {
+  gram_part_kernel<<<nblk, 256, 0, s>>>(rows, r, P, nullptr, nullptr, nullptr, part);
+  ritz_kernel<<<1, 32, 0, s>>>(r, nblk, part, out);
   return cudaGetLastError();
 }
 

@@ -94,7 +94,11 @@ struct lrs_ctx {
   float* Xref = nullptr;   // q x n (error log)
   double* errpart = nullptr;
   int ks = 1;                // k-splits of the column reductions
+  int qc = 0;                // columns per k-split when fixed (grad_block)
   float* gsplit = nullptr;   // ks x n x r
+  // column-sharded solves: this shard's partial sums and every shard's
+  // (pinned host), and every shard's on the device
+  float *rd_mine = nullptr, *rd_all = nullptr, *rd_dev = nullptr;
   unsigned long long* trace = nullptr;  // q x kTracePhases (profile = 2)
   int nblk = 0;
   int power_iters_done = 0;
@@ -149,6 +153,7 @@ GlobalWork gw(lrs_ctx* h) {
   g.rpad = sweep_rpad(h->r);
   g.ks = h->ks;
   g.gsplit = h->gsplit;
+  g.qc = h->qc;
   return g;
 }
 
@@ -303,6 +308,8 @@ lrs_status launch_sweep(lrs_ctx* h, int mode, int tau) {
   return LRS_OK;
 }
 
+lrs_status column_reduce(lrs_ctx* h, const GlobalWork& g, const float* H, const float* Bk);
+
 // One GDmin iteration (Algorithm 1): sweep, gradient, eta at t = 1, QR.
 // With `evs` (4 events) the phase boundaries are recorded on the stream.
 // Low-precision forms of A_k first refresh the defect-corrected measurements
@@ -317,7 +324,8 @@ lrs_status enqueue_iteration(lrs_ctx* h, bool first, cudaEvent_t* evs = nullptr,
   if (st != LRS_OK) return st;
   if (evs) CUDA_TRY(cudaEventRecord(evs[1], h->stream));
   GlobalWork g = gw(h);
-  CUDA_TRY(grad_reduce(g, h->H, h->Bk, h->stream));
+  st = column_reduce(h, g, h->H, h->Bk);
+  if (st != LRS_OK) return st;
   if (evs) CUDA_TRY(cudaEventRecord(evs[2], h->stream));
   if (first) CUDA_TRY(eta_from_grad(g, h->opt.c_eta, h->eta, h->stream));
   CUDA_TRY(qr_step(g, h->U, h->eta, h->err, h->stream));
@@ -474,9 +482,13 @@ void free_all(lrs_ctx* h) {
   for (void* p : ps2)
     if (p) cudaFreeAsync(p, h->stream);
   void* ps[] = {h->gsplit, h->A, h->y, h->Aex, h->rscale, h->ycorr, h->U, h->Upad, h->Bk, h->S_idx, h->S_val, h->H, h->grad, h->Z,
-                h->U2, h->P, h->part, h->small, h->eta, h->err, h->Xref, h->errpart, h->trace};
+                h->U2, h->P, h->part, h->small, h->eta, h->err, h->Xref, h->errpart, h->trace,
+                h->rd_dev};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, h->stream);
+  if (h->rd_mine) cudaFreeHost(h->rd_mine);
+  if (h->rd_all) cudaFreeHost(h->rd_all);
+  h->rd_mine = h->rd_all = nullptr;
 }
 
 // ---- autotuner: shapes per problem, cached for the process -----------------------
@@ -555,11 +567,47 @@ lrs_status alloc_split(lrs_ctx* h, int nsm) {
   int ks = static_cast<int>(std::max<int64_t>(1, (4 * nsm + jb - 1) / jb));
   ks = std::min<int>(ks, 32);
   ks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ks, h->q / 8)));
+  if (h->opt.grad_block > 0) {  // fixed blocks of grad_block columns
+    h->qc = h->opt.grad_block;
+    ks = static_cast<int>((h->q + h->qc - 1) / h->qc);
+  }
   h->ks = ks;
-  if (ks <= 1) return LRS_OK;
+  if (ks <= 1 && h->qc == 0) return LRS_OK;
   lrs_status st = LRS_OK;
-  const size_t cnt = static_cast<size_t>(ks) * h->n * h->r;
-  if ((st = dalloc(&h->gsplit, cnt, h->stream))) return st;
+  const size_t blk = static_cast<size_t>(h->n) * h->r;
+  if ((st = dalloc(&h->gsplit, ks * blk, h->stream))) return st;
+  if (h->opt.reduce) {
+    const size_t cap = static_cast<size_t>(h->opt.reduce_cap) * blk;
+    CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&h->rd_mine), ks * blk * sizeof(float)));
+    CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&h->rd_all), cap * sizeof(float)));
+    if ((st = dalloc(&h->rd_dev, cap, h->stream))) return st;
+  }
+  return LRS_OK;
+}
+
+// A column reduction (Section II-A gradient, or the subspace step of the
+// initialisation): sum_k H[k]^T Bk[k] into g.grad (n x g.r).  With a reducer
+// (column-sharded solve) this shard's k-split partials go to the host, the
+// reducer returns every shard's in column order, and their fixed-order sum
+// is formed on the device.
+lrs_status column_reduce(lrs_ctx* h, const GlobalWork& g, const float* H, const float* Bk) {
+  if (!h->opt.reduce) {
+    CUDA_TRY(grad_reduce(g, H, Bk, h->stream));
+    return LRS_OK;
+  }
+  const size_t blk = static_cast<size_t>(h->n) * g.r;
+  CUDA_TRY(grad_partials(g, H, Bk, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->rd_mine, g.gsplit, g.ks * blk * sizeof(float),
+                           cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  const int nb = h->opt.reduce(h->opt.reduce_ctx, h->rd_mine, g.ks, h->n, g.r, h->rd_all,
+                               h->opt.reduce_cap);
+  if (nb < 1 || nb > h->opt.reduce_cap)
+    return fail(LRS_ERR_ARG, "column reduction: the reducer returned " + std::to_string(nb) +
+                                 " blocks (capacity " + std::to_string(h->opt.reduce_cap) + ")");
+  CUDA_TRY(cudaMemcpyAsync(h->rd_dev, h->rd_all, nb * blk * sizeof(float), cudaMemcpyHostToDevice,
+                           h->stream));
+  CUDA_TRY(sum_blocks(static_cast<int>(h->n), g.r, nb, h->rd_dev, g.grad, h->stream));
   return LRS_OK;
 }
 
@@ -690,14 +738,25 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
   lrs_options o{};
   if (opt) o = *opt;
   if (kind == LRS_OP_DFT2D_MASK) {
-    if (!is_pow2(o.nx) || !is_pow2(o.ny) || int64_t(o.nx) * o.ny != n)
-      return fail(LRS_ERR_ARG, "lrs_create: DFT frames need nx, ny powers of two, nx*ny = n");
+    if (o.nx <= 0 || o.ny <= 0 || int64_t(o.nx) * o.ny != n)
+      return fail(LRS_ERR_ARG, "lrs_create: DFT frames need nx, ny > 0 with nx*ny = n");
+    if ((!is_pow2(o.nx) || !is_pow2(o.ny)) && n > 4096)
+      return fail(LRS_ERR_ARG,
+                  "lrs_create: DFT frames need nx, ny powers of two, or nx*ny <= 4096");
     if (m > n) return fail(LRS_ERR_ARG, "lrs_create: DFT needs m <= n");
   }
   if (o.tau0 < 0 || o.tau < 0 || o.T < 0 || o.rho_max < 0 || o.c_eta < 0 || o.cluster < 0 ||
       o.power_iters < 0 || o.refine_every < 0 || o.grid < 0 || o.wait_ms < 0 || o.engine < 0 ||
-      o.engine > 3)
+      o.engine > 3 || o.grad_block < 0 || o.reduce_cap < 0)
     return fail(LRS_ERR_ARG, "lrs_create: negative option");
+  if (o.reduce) {
+    if (kind != LRS_OP_GAUSSIAN)
+      return fail(LRS_ERR_UNSUPPORTED, "lrs_create: column-sharded solves take Gaussian operators");
+    if (o.grad_block <= 0 || o.use_graph || o.autotune)
+      return fail(LRS_ERR_ARG, "lrs_create: a reducer needs grad_block > 0, use_graph = 0, autotune = 0");
+    if (int64_t(o.reduce_cap) < (q + o.grad_block - 1) / o.grad_block)
+      return fail(LRS_ERR_ARG, "lrs_create: reduce_cap below this shard's own partial blocks");
+  }
   if (o.cluster != 0 && o.cluster != 1 && o.cluster != 2 && o.cluster != 4 && o.cluster != 8 &&
       o.cluster != 16)
     return fail(LRS_ERR_ARG, "lrs_create: cluster must be 0, 1, 2, 4, 8 or 16");
@@ -959,7 +1018,10 @@ lrs_status lrs_init(lrs_t h) {
   for (; it < h->opt.power_iters && e == cudaSuccess; ++it) {
     e = cudaMemcpyAsync(h->U2, h->U, nr * 4, cudaMemcpyDeviceToDevice, h->stream);
     if (e == cudaSuccess) e = project_cols(g, h->H, h->U2, h->P, h->stream);
-    if (e == cudaSuccess) e = grad_reduce(g, h->H, h->P, h->stream);
+    if (e == cudaSuccess) {
+      st = column_reduce(h, g, h->H, h->P);
+      if (st) return st;
+    }
     if (e == cudaSuccess) e = cholqr2(g, h->grad, h->U, h->err, h->stream);
     if (e == cudaSuccess && ((it % 5) == 4 || it + 1 == h->opt.power_iters)) {
       e = subspace_change(g, h->U2, h->U, D, D + 16 * 16, h->stream);
@@ -981,6 +1043,146 @@ lrs_status lrs_init(lrs_t h) {
   h->state = kInitialised;
   h->t = 0;
   h->last_refine = -1;
+  return LRS_OK;
+}
+
+// problems of one batched launch (6 bits of a task descriptor)
+constexpr int kMaxBatch = 64;
+
+// automatic rank: subspace blocks of 16 columns, at most four
+constexpr int kRankBlock = 16;
+constexpr int kRankBlocks = 4;
+
+lrs_status lrs_estimate_rank(lrs_t h, double energy, int32_t* r_out, double* sv,
+                             int32_t sv_len, int32_t* n_sv) {
+  if (!h) return fail(LRS_ERR_ARG, "lrs_estimate_rank: NULL handle");
+  if (!r_out) return fail(LRS_ERR_ARG, "lrs_estimate_rank: r_out is NULL");
+  if (!(energy > 0.0 && energy <= 1.0))
+    return fail(LRS_ERR_ARG, "lrs_estimate_rank: energy must lie in (0, 1]");
+  if (h->state != kMeasured)
+    return fail(LRS_ERR_STATE, "lrs_estimate_rank: needs state MEASURED (before lrs_init)");
+  if (h->F) return fail(LRS_ERR_UNSUPPORTED, "lrs_estimate_rank: Gaussian operators only");
+  if (h->opt.reduce)
+    return fail(LRS_ERR_UNSUPPORTED, "lrs_estimate_rank: not on a column-sharded handle");
+  // L0 (= H^T) from the initialisation's IHT
+  lrs_status st = launch_sweep(h, kModeInit, h->opt.tau0);
+  if (st) return st;
+  st = check_device_error(h, "lrs_estimate_rank");
+  if (st) return st;
+  const int n = static_cast<int>(h->n), q = static_cast<int>(h->q);
+  const int64_t mnq = std::min<int64_t>(h->n, h->q);
+  const int64_t want = std::max<int64_t>(1, std::min<int64_t>(mnq, h->m) / 10);
+  // blocks of 16 (the widest the r x r kernels hold), at most four; a single
+  // block narrower than 16 when n or q is
+  const int B0 = static_cast<int>(std::min<int64_t>(kRankBlock, mnq));
+  const int N = static_cast<int>(std::min<int64_t>(want, kRankBlock * kRankBlocks));
+  const int nblocks = N <= B0 ? 1 : (N + kRankBlock - 1) / kRankBlock;
+  if (nblocks > 1 && mnq < static_cast<int64_t>(nblocks) * kRankBlock)
+    return fail(LRS_ERR_ARG, "lrs_estimate_rank: problem too small for the requested count");
+  const int nb_n = qr_blocks(n), nb_q = qr_blocks(q);
+  const size_t nw = static_cast<size_t>(n) * kRankBlock;
+  float *U2 = nullptr, *Ub = nullptr, *P = nullptr, *Zg = nullptr, *Zt = nullptr;
+  double *part = nullptr, *small = nullptr;
+  cudaStream_t s = h->stream;
+  auto release = [&]() {
+    for (void* p : {static_cast<void*>(U2), static_cast<void*>(Ub), static_cast<void*>(P),
+                    static_cast<void*>(Zg), static_cast<void*>(Zt), static_cast<void*>(part),
+                    static_cast<void*>(small)})
+      if (p) cudaFreeAsync(p, s);
+  };
+  st = dalloc(&U2, nw, s);
+  if (!st) st = dalloc(&Ub, nw * nblocks, s);  // the converged blocks, one after another
+  if (!st) st = dalloc(&P, static_cast<size_t>(q) * kRankBlock, s);
+  if (!st) st = dalloc(&Zg, nw, s);
+  if (!st) st = dalloc(&Zt, nw, s);
+  if (!st) st = dalloc(&part, static_cast<size_t>(std::max(nb_n, nb_q)) * kRankBlock * kRankBlock, s);
+  if (!st) st = dalloc(&small, static_cast<size_t>(4) * kRankBlock * kRankBlock + 8 + kRankBlock * kRankBlocks, s);
+  if (st) {
+    release();
+    return st;
+  }
+  constexpr int WW = kRankBlock * kRankBlock;
+  double* D = small + 2 * WW;          // small[0, 2 WW): the Cholesky-QR2 factors
+  double* chg = small + 3 * WW;        // subspace change
+  double* ritz = small + 3 * WW + 1;   // Ritz values, block after block
+  GlobalWork g{};
+  g.n = n;
+  g.q = q;
+  g.grad = Zg;
+  g.part = part;
+  g.small = small;
+  g.Z = Zt;
+  g.nblk = nb_n;
+  g.ks = 1;
+  cudaError_t e = cudaSuccess;
+  // Block b: subspace iteration on L0 L0^T deflated by the blocks before it
+  // (classical Gram-Schmidt, twice, after every product), as in lrs_init,
+  // then its Rayleigh-Ritz values.
+  for (int b = 0; b < nblocks && e == cudaSuccess; ++b) {
+    const int W = b == 0 ? B0 : kRankBlock;
+    g.r = W;
+    float* U = Ub + static_cast<size_t>(b) * nw;
+    auto deflate_all = [&](float* Z) {
+      cudaError_t x = cudaSuccess;
+      for (int pass = 0; pass < 2 && x == cudaSuccess; ++pass)
+        for (int j = 0; j < b && x == cudaSuccess; ++j)
+          x = deflate(g, Ub + static_cast<size_t>(j) * nw, Z, D, s);
+      return x;
+    };
+    std::vector<float> U0f = start_block(h->n, W, h->opt.seed + 2 + b);
+    e = cudaMemcpyAsync(U2, U0f.data(), static_cast<size_t>(n) * W * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = deflate_all(U2);
+    if (e == cudaSuccess) e = cholqr2(g, U2, U, h->err, s);
+    for (int it = 0; it < h->opt.power_iters && e == cudaSuccess; ++it) {
+      e = cudaMemcpyAsync(U2, U, static_cast<size_t>(n) * W * 4, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess) e = project_cols(g, h->H, U2, P, s);
+      if (e == cudaSuccess) e = grad_reduce(g, h->H, P, s);
+      if (e == cudaSuccess) e = deflate_all(Zg);
+      if (e == cudaSuccess) e = cholqr2(g, Zg, U, h->err, s);
+      if (e == cudaSuccess && ((it % 5) == 4 || it + 1 == h->opt.power_iters)) {
+        e = subspace_change(g, U2, U, D, chg, s);
+        double chg2 = 0.0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&chg2, chg, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && std::sqrt(std::max(0.0, chg2)) < h->opt.power_tol) break;
+      }
+    }
+    // Rayleigh-Ritz: P = L0^T U, eigenvalues of P^T P = sigma^2
+    if (e == cudaSuccess) e = project_cols(g, h->H, U, P, s);
+    if (e == cudaSuccess) e = ritz_values(q, W, P, part, nb_q, ritz + b * kRankBlock, s);
+  }
+  const int nval = nblocks == 1 ? B0 : nblocks * kRankBlock;
+  std::vector<double> lam(nval, 0.0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(lam.data(), ritz, nval * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  release();
+  if (e != cudaSuccess)
+    return fail(LRS_ERR_CUDA, std::string("lrs_estimate_rank: ") + cudaGetErrorString(e));
+  st = check_device_error(h, "lrs_estimate_rank");
+  if (st) return st;
+  std::sort(lam.begin(), lam.end(), [](double x, double y) { return x > y; });
+  // energy threshold on the first N values
+  double total = 0.0;
+  for (int j = 0; j < N; ++j) total += std::max(0.0, lam[j]);
+  int r = 1;
+  if (total > 0.0) {
+    double acc = 0.0;
+    r = N;
+    for (int j = 0; j < N; ++j) {
+      acc += std::max(0.0, lam[j]);
+      if (acc >= energy * total) {
+        r = j + 1;
+        break;
+      }
+    }
+  }
+  *r_out = r;
+  if (sv)
+    for (int j = 0; j < std::min(N, static_cast<int>(sv_len)); ++j)
+      sv[j] = std::sqrt(std::max(0.0, lam[j]));
+  if (n_sv) *n_sv = N;
   return LRS_OK;
 }
 
@@ -1078,6 +1280,159 @@ lrs_status lrs_iterate(lrs_t h, int32_t iters, double* err_log) {
     h->phase_iters += iters;
   }
   return check_device_error(h, "lrs_iterate");
+}
+
+lrs_status lrs_iterate_batch(lrs_t* hs, int32_t nh, int32_t iters) {
+  if (!hs || nh < 1 || nh > kMaxBatch)
+    return fail(LRS_ERR_ARG, "lrs_iterate_batch: need 1 <= nh <= 64 handles");
+  if (iters < 0) return fail(LRS_ERR_ARG, "lrs_iterate_batch: iters < 0");
+  for (int i = 0; i < nh; ++i) {
+    if (!hs[i]) return fail(LRS_ERR_ARG, "lrs_iterate_batch: NULL handle");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(LRS_ERR_ARG, "lrs_iterate_batch: a handle appears twice");
+    if (hs[i]->state < kInitialised)
+      return fail(LRS_ERR_STATE, "lrs_iterate_batch: call lrs_init on every handle first");
+  }
+  lrs_ctx* h0 = hs[0];
+  const int R = sweep_rpad(h0->r), et = h0->L.et;
+  for (int i = 0; i < nh; ++i) {
+    const lrs_ctx* h = hs[i];
+    if (h->F || h->engine != 2 || h->opt.reduce || sweep_rpad(h->r) != R || h->L.et != et)
+      return fail(LRS_ERR_UNSUPPORTED,
+                  "lrs_iterate_batch: Gaussian task-engine handles of one rank width and A_k form");
+  }
+  if (nh == 1) return lrs_iterate(h0, iters, nullptr);
+  // the launch's work table: every handle's ITER-mode problem, columns
+  // numbered across the handles in order; all columns in flight
+  std::vector<TaskProblem> P(nh);
+  int64_t cols = 0, total = 0, nseed = 0;
+  int m_max = 0, ns_max = 0, rho_max = 0, pb_max = 0;
+  for (int i = 0; i < nh; ++i) {
+    const lrs_ctx* h = hs[i];
+    P[i] = h->tp[kModeIter];
+    P[i].col0 = static_cast<int>(cols);
+    cols += h->q;
+    total += static_cast<int64_t>(P[i].tasks_per_col) * h->q;
+    nseed += static_cast<int64_t>(phase_tasks(P[i], 0)) * h->q;
+    m_max = std::max<int>(m_max, static_cast<int>(h->m));
+    ns_max = std::max(ns_max, h->L.ns);
+    rho_max = std::max(rho_max, h->rho);
+    pb_max = std::max(pb_max, h->tshape.piece_bytes);
+  }
+  if (total >= (int64_t(1) << 31) || cols >= (int64_t(1) << 30))
+    return fail(LRS_ERR_UNSUPPORTED, "lrs_iterate_batch: too many tasks for one launch");
+  int dev = 0, nsm = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  TaskShape shape = h0->tshape;
+  shape.stages = kTaskStages;
+  shape.piece_bytes = pb_max;
+  shape.smem = task_smem_bytes(R, et, m_max, ns_max, rho_max, kTaskStages, pb_max);
+  if (shape.smem > static_cast<size_t>(max_smem_optin()))
+    return fail(LRS_ERR_UNSUPPORTED, "lrs_iterate_batch: the problems' shared memory does not fit one CTA");
+  const int cps = std::min(2, task_ctas_per_sm(R, et, shape.smem));
+  if (cps < 1) return fail(LRS_ERR_UNSUPPORTED, "lrs_iterate_batch: no CTA fits an SM");
+  int grid = cps * nsm;
+  if (h0->opt.grid > 0) grid = std::min(grid, h0->opt.grid);
+  shape.grid = grid;
+  // device tables (freed at the end of the call, stream-ordered)
+  cudaStream_t s = h0->stream;
+  TaskProblem* dP = nullptr;
+  unsigned long long *dtasks = nullptr, *dseed = nullptr;
+  int *dseq = nullptr, *dctr = nullptr, *dcnt = nullptr;
+  lrs_status st = dalloc(&dP, nh, s);
+  if (!st) st = dalloc(&dtasks, total, s);
+  if (!st) st = dalloc(&dseq, total, s);
+  if (!st) st = dalloc(&dctr, 4, s);
+  if (!st) st = dalloc(&dcnt, cols, s);
+  if (!st) st = dalloc(&dseed, nseed, s);
+  auto release = [&]() {
+    for (void* p : {static_cast<void*>(dP), static_cast<void*>(dtasks), static_cast<void*>(dseed),
+                    static_cast<void*>(dseq), static_cast<void*>(dctr), static_cast<void*>(dcnt)})
+      if (p) cudaFreeAsync(p, s);
+  };
+  if (st) {
+    release();
+    return st;
+  }
+  std::vector<unsigned long long> seed;
+  seed.reserve(nseed);
+  for (int i = 0; i < nh; ++i) {
+    P[i].cnt = dcnt + P[i].col0;
+    const int n0 = phase_tasks(P[i], 0);
+    for (int64_t k = 0; k < hs[i]->q; ++k)
+      for (int t = 0; t < n0; ++t)
+        seed.push_back(tdesc(static_cast<int>(k), i, phase_type(P[i], 0), 0, t));
+  }
+  // every handle's stream waits for what was queued on it before; the
+  // shared sweep runs on the first handle's stream, each handle's gradient,
+  // step size and QR on its own stream after it
+  std::vector<cudaEvent_t> evs(nh + 1, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (auto& ev : evs)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dP, P.data(), nh * sizeof(TaskProblem), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dseed, seed.data(), nseed * 8, cudaMemcpyHostToDevice, s);
+  lrs_status rs = LRS_OK;
+  for (int it = 0; it < iters && e == cudaSuccess && rs == LRS_OK; ++it) {
+    for (int i = 1; i < nh && e == cudaSuccess; ++i) {
+      e = cudaEventRecord(evs[i], hs[i]->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, evs[i], 0);
+    }
+    for (int i = 0; i < nh && e == cudaSuccess; ++i) {
+      lrs_ctx* h = hs[i];
+      const bool refine = h->L.et != 0 &&
+                          (h->last_refine < 0 || h->t - h->last_refine >= h->opt.refine_every);
+      if (refine) {
+        h->last_refine = h->t;
+        e = refine_residual(h->L, h->Aex, h->A, h->rscale, h->U, h->Bk, h->S_idx, h->S_val, h->y,
+                            h->ycorr, h->H, s);
+      }
+    }
+    if (e != cudaSuccess) break;
+    TaskQueue Q{};
+    Q.tasks = dtasks;
+    Q.seq = dseq;
+    Q.ctr = dctr;
+    Q.total = static_cast<int>(total);
+    Q.ncols = static_cast<int>(cols);
+    Q.F = static_cast<int>(cols);
+    Q.nprob = nh;
+    Q.probs = dP;
+    Q.prof = nullptr;
+    e = task_launch_seeded(Q, dseed, static_cast<int>(nseed), dcnt, R, et, shape, m_max, ns_max,
+                           rho_max, s);
+    if (e == cudaSuccess) e = cudaEventRecord(evs[0], s);
+    for (int i = 0; i < nh && e == cudaSuccess && rs == LRS_OK; ++i) {
+      lrs_ctx* h = hs[i];
+      if (i > 0) e = cudaStreamWaitEvent(h->stream, evs[0], 0);
+      if (e != cudaSuccess) break;
+      GlobalWork g = gw(h);
+      rs = column_reduce(h, g, h->H, h->Bk);
+      if (rs == LRS_OK && h->t == 0) e = eta_from_grad(g, h->opt.c_eta, h->eta, h->stream);
+      if (rs == LRS_OK && e == cudaSuccess) e = qr_step(g, h->U, h->eta, h->err, h->stream);
+      h->t += 1;
+      h->state = kIterating;
+    }
+    // the next sweep reads every handle's new U
+    for (int i = 1; i < nh && e == cudaSuccess; ++i) {
+      e = cudaEventRecord(evs[i], hs[i]->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, evs[i], 0);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  release();
+  for (int i = 0; i < nh; ++i) cudaStreamSynchronize(hs[i]->stream);
+  for (auto ev : evs)
+    if (ev) cudaEventDestroy(ev);
+  if (rs != LRS_OK) return rs;
+  if (e != cudaSuccess)
+    return fail(LRS_ERR_CUDA, std::string("lrs_iterate_batch: ") + cudaGetErrorString(e));
+  for (int i = 0; i < nh; ++i) {
+    st = check_device_error(hs[i], "lrs_iterate_batch");
+    if (st) return st;
+  }
+  return LRS_OK;
 }
 
 lrs_status lrs_solve(lrs_t h) {
@@ -1282,6 +1637,8 @@ lrs_status lrs_autotune(lrs_t h, int32_t trial_iters, char* report, int32_t len)
   if (!h) return fail(LRS_ERR_ARG, "lrs_autotune: NULL handle");
   if (trial_iters < 1) return fail(LRS_ERR_ARG, "lrs_autotune: trial_iters < 1");
   if (h->F || h->engine != 2) return fail(LRS_ERR_UNSUPPORTED, "lrs_autotune: task engine only");
+  if (h->opt.reduce)
+    return fail(LRS_ERR_UNSUPPORTED, "lrs_autotune: not on a column-sharded handle");
   if (h->state < kInitialised) return fail(LRS_ERR_STATE, "lrs_autotune: call lrs_init first");
   const size_t nr = static_cast<size_t>(h->n) * h->r, qr = static_cast<size_t>(h->q) * h->r;
   const size_t qs = static_cast<size_t>(h->q) * std::max(1, h->rho);

@@ -285,9 +285,14 @@ struct GlobalWork {
   float* Z;          // n x r scratch (U - eta grad, Q1)
   int nblk;          // blocks of the row-parallel kernels
   int ks = 1;        // k-splits of the column reductions (grad, subspace step)
-  float* gsplit = nullptr;   // ks x n x r FP32 partial sums (ks > 1)
+  float* gsplit = nullptr;   // ks x n x r FP32 partial sums (ks > 1, or qc > 0)
+  int qc = 0;        // columns per k-split (0: ceil(q / ks)); > 0 always splits
 };
 cudaError_t grad_reduce(const GlobalWork& g, const float* H, const float* Bk, cudaStream_t s);
+// The k-split partial sums of grad_reduce alone (g.ks blocks of g.qc columns
+// into g.gsplit), and the fixed-order sum of nb such n x r blocks into out.
+cudaError_t grad_partials(const GlobalWork& g, const float* H, const float* Bk, cudaStream_t s);
+cudaError_t sum_blocks(int n, int r, int nb, const float* parts, float* out, cudaStream_t s);
 cudaError_t eta_from_grad(const GlobalWork& g, double c_eta, double* eta_dev, cudaStream_t s);
 cudaError_t qr_step(const GlobalWork& g, float* U, const double* eta_dev, int* err,
                     cudaStream_t s);
@@ -302,6 +307,13 @@ cudaError_t subspace_change(const GlobalWork& g, const float* Uold, const float*
 // scratch: tmp (n*r floats), part (nblk*r*r doubles), rfac (2*r*r doubles),
 // err (2 ints, zero on entry).  Blocks: qr_blocks(n).
 int qr_blocks(int64_t n);
+// Eigenvalues (descending) of the FP64 Gram P^T P of a rows x r FP32 matrix P
+// into out[0..r): nblk row blocks, part holds nblk r x r partials.
+cudaError_t ritz_values(int rows, int r, const float* P, double* part, int nblk, double* out,
+                        cudaStream_t s);
+// Z <- Z - Ua (Ua^T Z) for an n x r block Ua with orthonormal columns (g.n, g.r,
+// g.part, g.nblk); D receives Ua^T Z (r x r FP64).
+cudaError_t deflate(const GlobalWork& g, const float* Ua, float* Z, double* D, cudaStream_t s);
 cudaError_t cholqr2_into(int n, int r, const float* Z, float* Q, float* tmp, double* part,
                          double* rfac, int* err, int nblk, cudaStream_t s);
 

@@ -29,6 +29,11 @@ class LrsError(RuntimeError):
         self.status = status
 
 
+LRS_REDUCER = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
+                               ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                               ctypes.POINTER(ctypes.c_float), ctypes.c_int32)
+
+
 class lrs_options(ctypes.Structure):
     _fields_ = [("tau0", ctypes.c_int32), ("tau", ctypes.c_int32), ("T", ctypes.c_int32),
                 ("c_eta", ctypes.c_double), ("rho_max", ctypes.c_int32),
@@ -41,7 +46,9 @@ class lrs_options(ctypes.Structure):
                 ("engine", ctypes.c_int32), ("inflight", ctypes.c_int32),
                 ("task_kib", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("grid", ctypes.c_int32),
-                ("wait_ms", ctypes.c_int32)]
+                ("wait_ms", ctypes.c_int32), ("grad_block", ctypes.c_int32),
+                ("reduce", LRS_REDUCER), ("reduce_ctx", ctypes.c_void_p),
+                ("reduce_cap", ctypes.c_int32)]
 
 
 class lrs_request(ctypes.Structure):
@@ -88,8 +95,11 @@ def lib():
                            ctypes.POINTER(_P)],
             "lrs_set_measurements": [_P, _P, _P, ctypes.c_int32],
             "lrs_init": [_P],
+            "lrs_estimate_rank": [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_int32), _P,
+                                  ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
             "lrs_iterate": [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)],
             "lrs_solve": [_P],
+            "lrs_iterate_batch": [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32],
             "lrs_get": [_P, _P, _P, _P, _P, ctypes.c_int32],
             "lrs_get_x": [_P, _P, ctypes.c_int32],
             "lrs_set_state": [_P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_double,
@@ -180,6 +190,15 @@ def lrs_init(h):
     _check(lib().lrs_init(h))
 
 
+def lrs_estimate_rank(h, energy=0.65):
+    """(r, singular values used) of the automatic rank (lrs_estimate_rank)."""
+    r, nsv = ctypes.c_int32(0), ctypes.c_int32(0)
+    sv = np.zeros(64, np.float64)
+    _check(lib().lrs_estimate_rank(h, energy, ctypes.byref(r), sv.ctypes.data, len(sv),
+                                   ctypes.byref(nsv)))
+    return int(r.value), sv[:nsv.value].copy()
+
+
 def lrs_iterate(h, iters, err_log=None):
     buf = None
     if err_log is not None:
@@ -187,6 +206,12 @@ def lrs_iterate(h, iters, err_log=None):
     _check(lib().lrs_iterate(h, iters, buf))
     if err_log is not None:
         err_log[:] = list(buf)
+
+
+def lrs_iterate_batch(handles, iters):
+    """lrs_iterate_batch over the handles (lrs_t values)."""
+    arr = (_P * len(handles))(*handles)
+    _check(lib().lrs_iterate_batch(arr, len(handles), iters))
 
 
 def lrs_solve(h):
@@ -363,6 +388,10 @@ class Solver:
 
     def init(self):
         lrs_init(self.h)
+
+    def estimate_rank(self, energy=0.65):
+        """Automatic rank from L0 (before init): (r, singular values used)."""
+        return lrs_estimate_rank(self.h, energy)
 
     def iterate(self, iters=1, err_log=None):
         lrs_iterate(self.h, iters, err_log)

@@ -95,10 +95,10 @@ class Problem:
                        inst.r, inst.rho if rho is None else rho, A=np.asarray(A))
 
     @staticmethod
-    def fourier(inst):
+    def fourier(inst, rho=None):
         return Problem(O.FourierOperator(inst.masks, inst.nx, inst.ny),
                        O.FourierOperator(inst.masks, inst.nx, inst.ny, np.complex64),
-                       inst.Y, inst.r, inst.rho)
+                       inst.Y, inst.r, inst.rho if rho is None else rho)
 
     def y32(self, Y):
         return np.asarray(Y).astype(np.complex64 if self.cplx else np.float32)

@@ -51,6 +51,6 @@ def test_binding_loads_and_reports_argument_errors(libpath):
         L.lrs_create(100, 10, 10, 2, 101)      # rho > n
     assert e.value.status == L.LRS_ERR_ARG
     with pytest.raises(L.LrsError) as e:
-        L.lrs_create(96, 10, 10, 2, 1, L.LRS_OP_DFT2D_MASK, L.make_options(nx=12, ny=8))
-    assert e.value.status == L.LRS_ERR_ARG      # nx not a power of two
+        L.lrs_create(5120, 10, 10, 2, 1, L.LRS_OP_DFT2D_MASK, L.make_options(nx=80, ny=64))
+    assert e.value.status == L.LRS_ERR_ARG      # nx not a power of two, frame above 4096
     assert "power" in L.lrs_last_error()

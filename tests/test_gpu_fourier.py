@@ -29,7 +29,10 @@ def _need_gpu():
     build.build()
 
 
-@pytest.mark.parametrize("nx,ny,m,rho", [(16, 16, 96, 4), (32, 16, 160, 6), (8, 32, 100, 3)])
+# power-of-two sides (radix-2 FFT), sides of other lengths (direct DFT), and
+# one of each
+@pytest.mark.parametrize("nx,ny,m,rho", [(16, 16, 96, 4), (32, 16, 160, 6), (8, 32, 100, 3),
+                                         (20, 20, 120, 4), (12, 24, 110, 3), (16, 20, 100, 3)])
 def test_fourier_one_step_parity(nx, ny, m, rho):
     inst = FourierInstance(nx=nx, ny=ny, q=12, r=2, m=m, rho=rho, seed=41, center=4)
     T = 10
@@ -54,3 +57,20 @@ def test_fourier_trajectory_and_init():
     check_records(trajectory_records(Problem.fourier(inst), states, eta), min_whole=T - 2)
     rels, _ = trajectory_agreement(states, log)
     assert rels[-1] <= 1e-3, rels[-1]     # 25 iterations: both still converging
+
+
+def test_fourier_table1_frames_one_step():
+    """The Table 1 setting (Section III): 20 x 20 frames (n = 400), uniformly
+    random DFT rows, S1 values, r = 4, rho = 2 with rho_max = 5; one-step
+    parity from the oracle's iterates (rho_max kept by HardThreshold)."""
+    inst = FourierInstance(nx=20, ny=20, q=60, r=4, m=100, rho=2, seed=43, s_law="S1",
+                           mask_law="uniform", b_law="gauss")
+    T = 10
+    _, log = O.run_alg1(O.FourierOperator(inst.masks, 20, 20), inst.Y, 4, 5, T,
+                        keep=tuple(range(T + 1)), Xstar=inst.Xstar)
+    s = new_fourier_solver(inst, rho_max=5)
+    try:
+        recs = one_step(Problem.fourier(inst, rho=5), s, log, range(T))
+    finally:
+        s.close()
+    check_records(recs, min_whole=T // 2, max_excluded=0.03)

@@ -163,3 +163,28 @@ def test_init_matches_oracle_subspace_and_supports(engine):
     # columns sensitive to rounding (float32 probe and perturbed reruns)
     assert dec.sum() >= 0.85 * inst.q
     assert np.all(np.sort(S_idx[dec], 1) == st.S_idx[dec])
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_noisy_measurements(engine):
+    """y_k = A_k x*_k + w_k, w_k = 1e-3 ||x*_k|| N(0, I_m): one-step parity over
+    20 steps, and a 140-iteration trajectory whose final iterate equals the
+    oracle's (both at the fixed point the noise moves X* to) with the error
+    against X* at the oracle's noise floor (0.58e-3, below the noise level)."""
+    inst = GaussianInstance(n=200, q=60, r=3, m=80, rho=4, seed=12, noise=1e-3)
+    run_one_step(inst, 20, min_whole=15, engine=engine)
+    P = Problem.gaussian(inst)
+    _, log = oracle_run(inst, 140)
+    s = new_solver(inst, engine=engine)
+    try:
+        states, eta = gpu_trajectory(s, 140)
+    finally:
+        s.close()
+    check_records(trajectory_records(P, states, eta), 105)
+    rels, _ = trajectory_agreement(states, log)
+    assert rels[-1] <= TOL, ("final iterate", rels[-1])
+    U, B, S_idx, S_val = states[-1]
+    from tests.gpu_helpers import x_of
+    err = np.linalg.norm(x_of(U, B, S_idx, S_val, inst.q) - inst.Xstar) / np.linalg.norm(inst.Xstar)
+    assert abs(err - log.err[-1]) <= 1e-3 * log.err[-1], (err, log.err[-1])
+    assert err < inst.noise

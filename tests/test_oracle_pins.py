@@ -303,6 +303,70 @@ def test_top_r_left_singular_vectors_match_eigh():
     np.testing.assert_allclose(L0 @ (L0.T @ U), U * lam[None, :], atol=1e-9)
 
 
+# ------------------------------------------------------- automatic rank --
+
+def test_rank_count_is_a_tenth_of_the_smallest_dimension():
+    """Section II-F: the first min(n/10, q/10, m/10) singular values."""
+    assert O.rank_count(600, 600, 80) == 8
+    assert O.rank_count(1000, 1000, 150) == 15
+    assert O.rank_count(400, 400, 1000) == 40
+    assert O.rank_count(5, 5, 5) == 1
+    assert O.rank_count(200, 19, 300) == 1
+
+
+def test_rank_from_singular_values_closed_forms():
+    """The energy threshold on squared singular values of the first N only,
+    with 'at least' (>=): each case below gives a different answer under the
+    plausible misreadings (unsquared values, all values, strict inequality)."""
+    # squared: energies 9,1,...,1 (total 17), 0.65*17 = 11.05 -> r = 4;
+    # unsquared would give 6
+    assert O.rank_from_singular_values([3] + [1] * 8, 9) == 4
+    # first N = 4 only: energies 16,4,4,4 (28), 18.2 -> r = 2; all 8 would give 5
+    assert O.rank_from_singular_values([4] + [2] * 7, 4) == 2
+    # exactly at the threshold: energies 1,1, 0.5 * 2 = 1 -> r = 1 (strict: 2)
+    assert O.rank_from_singular_values([1, 1], 2, energy=0.5) == 1
+    assert O.rank_from_singular_values([5, 4, 3, 2, 1], 5, energy=1.0) == 5
+    assert O.rank_from_singular_values([5, 4, 3], 3, energy=1e-9) == 1
+    assert O.rank_from_singular_values([0.0, 0.0], 2) == 1
+
+
+def test_auto_rank_reads_the_singular_values_of_L0():
+    """L0 with prescribed singular values (random orthonormal factors): the
+    rank from the full SVD equals the rule applied to the prescribed values."""
+    g = rng(31)
+    n, q, m = 120, 90, 100                    # N = 9
+    sv = np.array([10, 6, 3, 2.5, 2, 1.5, 1, 0.5, 0.4, 0.3, 0.2, 0.1])
+    Uq = np.linalg.qr(g.standard_normal((n, len(sv))))[0]
+    Vq = np.linalg.qr(g.standard_normal((q, len(sv))))[0]
+    L0 = Uq @ np.diag(sv) @ Vq.T
+    r, used = O.auto_rank(L0, m)
+    assert len(used) == 9
+    np.testing.assert_allclose(used, sv[:9], rtol=1e-12)
+    # energies 100, 36, 9, ... of the first 9 (total 159.75): 0.65 * 159.75 =
+    # 103.8 -> r = 2
+    assert r == 2 == O.rank_from_singular_values(sv, 9)
+
+
+def test_init_L0_closed_forms():
+    """rho = 0: L0[:, k] = A_k^T y_k.  A_k = I (m = n): IHT from zero keeps
+    HardThreshold(y_k) (one step with mu = 1, then stationary), so
+    L0[:, k] = y_k - HardThreshold(y_k, rho)."""
+    inst = GaussianInstance(n=40, q=12, r=2, m=30, rho=3, seed=33)
+    op = O.GaussianOperator(inst.A)
+    L0 = O.init_L0(op, inst.Y, 0)
+    np.testing.assert_allclose(L0, np.einsum("kmn,km->nk", inst.A.astype(np.float64),
+                                             inst.Y.astype(np.float64)), rtol=1e-12, atol=1e-12)
+    g = rng(34)
+    Y = g.standard_normal((6, 25))
+    opI = O.GaussianOperator(np.broadcast_to(np.eye(25), (6, 25, 25)).copy())
+    L0 = O.init_L0(opI, Y, 4)
+    for k in range(6):
+        keep = np.argsort(-np.abs(Y[k]), kind="stable")[:4]
+        ht = np.zeros(25)
+        ht[keep] = Y[k, keep]
+        np.testing.assert_allclose(L0[:, k], Y[k] - ht, atol=1e-12)
+
+
 # --------------------------------------------------------- special cases --
 
 def _altgdmin_lrccs(A, Y, r, T, c_eta=0.14):
