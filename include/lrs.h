@@ -364,6 +364,9 @@ typedef struct {
   int32_t worker;           /* slot that ran it                               */
   int32_t grid;             /* SM share (CTAs) offered to its sweep           */
   int64_t admitted;         /* its place in the order of admission (0, 1, ..) */
+  int64_t group;            /* `admitted` of the first request of the batch it
+                               ran in (its own when it ran alone)            */
+  int32_t group_size;       /* requests of that batch                         */
 } lrs_result;
 
 /* A replacement for the solver of one request (used to test the admission
@@ -377,6 +380,10 @@ typedef struct {
   int32_t sms;              /* SMs shared by the sweeps (0 -> the device's)   */
   lrs_runner runner;        /* NULL: the library's solver                     */
   void* runner_ctx;
+  int32_t batch;            /* up to this many Gaussian requests admitted
+                               together run their iterations in one
+                               persistent launch per sweep (lrs_iterate_batch;
+                               0 or 1: every request alone)                 */
 } lrs_server_options;
 
 typedef struct lrs_server_s* lrs_server_t;
@@ -387,9 +394,13 @@ typedef struct lrs_server_s* lrs_server_t;
  * flight leave of hbm_budget; each runs lrs_create, lrs_set_measurements,
  * lrs_init, lrs_iterate(T) and lrs_get on its worker's stream, so the work
  * of concurrent requests overlaps on the GPU, and a Gaussian request's
- * persistent sweep gets max(16, 2 x SMs / requests running) CTAs.  The
- * kernels' results depend neither on the other requests nor on that share:
- * every result equals the request solved alone.
+ * persistent sweep gets max(16, 2 x SMs / requests running) CTAs.  With
+ * batch > 1, when the admitted request is Gaussian the queued requests right
+ * behind it of the same rank, A_k form and iteration count that also fit
+ * (slots, budget) are admitted with it, up to `batch` of them, and one
+ * worker runs their iterations together (lrs_iterate_batch).  The kernels'
+ * results depend neither on the other requests, nor on that share, nor on
+ * the batch: every result equals the request solved alone.
  * Errors: LRS_ERR_ARG, LRS_ERR_CUDA (no device). */
 lrs_status lrs_server_create(const lrs_server_options* opt, lrs_server_t* out);
 

@@ -62,7 +62,7 @@ struct lrs_server_s {
   std::condition_variable cv_done;    // waiters: a request finished
   std::condition_variable cv_work;    // workers: a job handed over
   std::deque<std::shared_ptr<Job>> pending;
-  std::deque<std::shared_ptr<Job>> ready;   // admitted, not yet taken by a worker
+  std::deque<std::vector<std::shared_ptr<Job>>> ready;   // admitted groups, not yet taken
   std::map<uint64_t, std::shared_ptr<Job>> jobs;
   uint64_t next_ticket = 1;
   int64_t next_admit = 0;
@@ -96,26 +96,85 @@ lrs_status run_request(const lrs_request& rq, int grid, cudaStream_t stream, std
   return st;
 }
 
+// Requests admitted together: each is created, given its measurements and
+// initialised on the worker's stream, then their iterations run in one
+// persistent launch per sweep (lrs_iterate_batch; each alone when the
+// handles cannot share a launch, with the same results), then the outputs.
+void run_group(const std::vector<std::shared_ptr<Job>>& g, int grid, cudaStream_t stream,
+               std::vector<lrs_status>* st, std::vector<std::string>* msg) {
+  const size_t n = g.size();
+  std::vector<lrs_t> hs(n, nullptr);
+  for (size_t i = 0; i < n; ++i) {
+    const lrs_request& rq = g[i]->req;
+    lrs_options o = rq.opt;
+    o.stream = stream;
+    if (o.grid == 0) o.grid = grid;
+    if (o.engine == 0) o.engine = 2;
+    lrs_status e = lrs_create(rq.n, rq.m, rq.q, rq.r, rq.rho, rq.kind, &o, &hs[i]);
+    if (e == LRS_OK) e = lrs_set_measurements(hs[i], rq.y, rq.A_or_mask, rq.mem_kind);
+    if (e == LRS_OK) e = lrs_init(hs[i]);
+    (*st)[i] = e;
+    if (e != LRS_OK) (*msg)[i] = lrs_last_error();
+  }
+  std::vector<lrs_t> ok;
+  std::vector<size_t> at;
+  for (size_t i = 0; i < n; ++i)
+    if ((*st)[i] == LRS_OK) {
+      ok.push_back(hs[i]);
+      at.push_back(i);
+    }
+  const int T = g[0]->req.opt.T > 0 ? g[0]->req.opt.T : 200;
+  if (!ok.empty()) {
+    lrs_status e = lrs_iterate_batch(ok.data(), static_cast<int32_t>(ok.size()), T);
+    if (e == LRS_ERR_UNSUPPORTED) {
+      for (size_t j = 0; j < ok.size(); ++j) {
+        (*st)[at[j]] = lrs_iterate(ok[j], T, nullptr);
+        if ((*st)[at[j]] != LRS_OK) (*msg)[at[j]] = lrs_last_error();
+      }
+    } else if (e != LRS_OK) {
+      const std::string m = lrs_last_error();
+      for (size_t j : at) {
+        (*st)[j] = e;
+        (*msg)[j] = m;
+      }
+    }
+  }
+  for (size_t i = 0; i < n; ++i) {
+    const lrs_request& rq = g[i]->req;
+    if ((*st)[i] == LRS_OK && (rq.U || rq.B || rq.S_idx || rq.S_val)) {
+      (*st)[i] = lrs_get(hs[i], rq.U, rq.B, rq.S_idx, rq.S_val, rq.out_mem_kind);
+      if ((*st)[i] != LRS_OK) (*msg)[i] = lrs_last_error();
+    }
+    lrs_destroy(hs[i]);
+  }
+}
+
 void worker_main(lrs_server_s* s, int wi) {
   cudaStream_t stream = nullptr;
   bool have_stream = false;
   for (;;) {
-    std::shared_ptr<Job> job;
+    std::vector<std::shared_ptr<Job>> group;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv_work.wait(lk, [&] { return s->dispatcher_done || !s->ready.empty(); });
       if (s->ready.empty()) break;   // stopping, and every request has been handed over
-      job = s->ready.front();
+      group = s->ready.front();
       s->ready.pop_front();
     }
-    const int grid = job->res.grid;
-    job->res.worker = wi;
-    job->res.start_s = s->seconds();
-    std::string msg;
-    lrs_status st;
+    const size_t n = group.size();
+    const int grid = group[0]->res.grid;
+    const double t_start = s->seconds();
+    for (auto& job : group) {
+      job->res.worker = wi;
+      job->res.start_s = t_start;
+    }
+    std::vector<lrs_status> st(n, LRS_OK);
+    std::vector<std::string> msg(n);
     if (s->opt.runner) {
-      st = static_cast<lrs_status>(s->opt.runner(s->opt.runner_ctx, &job->req, grid, wi));
-      if (st != LRS_OK) msg = "the runner reported a failure";
+      for (size_t i = 0; i < n; ++i) {
+        st[i] = static_cast<lrs_status>(s->opt.runner(s->opt.runner_ctx, &group[i]->req, grid, wi));
+        if (st[i] != LRS_OK) msg[i] = "the runner reported a failure";
+      }
     } else {
       if (!have_stream) {
         cudaSetDevice(s->device);
@@ -125,22 +184,44 @@ void worker_main(lrs_server_s* s, int wi) {
           cudaGetLastError();
         }
       }
-      st = have_stream ? run_request(job->req, grid, stream, &msg) : LRS_ERR_CUDA;
-      if (!have_stream) msg = "lrs_server: no CUDA stream for the worker";
+      if (!have_stream) {
+        for (size_t i = 0; i < n; ++i) {
+          st[i] = LRS_ERR_CUDA;
+          msg[i] = "lrs_server: no CUDA stream for the worker";
+        }
+      } else if (n == 1) {
+        st[0] = run_request(group[0]->req, grid, stream, &msg[0]);
+      } else {
+        run_group(group, grid, stream, &st, &msg);
+      }
     }
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      job->res.status = st;
-      std::snprintf(job->res.message, sizeof(job->res.message), "%s", msg.c_str());
-      job->res.end_s = s->seconds();
-      job->done = true;
-      s->in_use -= job->footprint;
-      s->running -= 1;
+      const double t_end = s->seconds();
+      for (size_t i = 0; i < n; ++i) {
+        Job& job = *group[i];
+        job.res.status = st[i];
+        std::snprintf(job.res.message, sizeof(job.res.message), "%s", msg[i].c_str());
+        job.res.end_s = t_end;
+        job.done = true;
+        s->in_use -= job.footprint;
+        s->running -= 1;
+      }
     }
     s->cv_done.notify_all();
     s->cv_admit.notify_all();
   }
   if (have_stream) cudaStreamDestroy(stream);
+}
+
+// Requests that may run their iterations in one launch: Gaussian, task
+// engine (or automatic), no reducer, same rank, A_k form and iteration count.
+bool batchable(const lrs_request& a) {
+  return a.kind == LRS_OP_GAUSSIAN && (a.opt.engine == 0 || a.opt.engine == 2) && !a.opt.reduce;
+}
+bool same_batch(const lrs_request& a, const lrs_request& b) {
+  return batchable(a) && batchable(b) && a.r == b.r && a.opt.a_dtype == b.opt.a_dtype &&
+         a.opt.T == b.opt.T;
 }
 
 // Admission: first come, first served; the head request starts when a slot
@@ -155,13 +236,28 @@ void dispatcher_main(lrs_server_s* s) {
       return s->running < s->opt.slots && s->in_use + j->footprint <= s->opt.hbm_budget;
     });
     if (s->pending.empty()) break;  // stopping with nothing queued
-    auto job = s->pending.front();
-    s->pending.pop_front();
-    s->in_use += job->footprint;
-    s->running += 1;
-    job->res.grid = std::max(16, (2 * s->sms) / std::max(1, s->running));
-    job->res.admitted = s->next_admit++;
-    s->ready.push_back(job);
+    std::vector<std::shared_ptr<Job>> group;
+    for (;;) {
+      auto job = s->pending.front();
+      s->pending.pop_front();
+      s->in_use += job->footprint;
+      s->running += 1;
+      job->res.admitted = s->next_admit++;
+      group.push_back(job);
+      if (static_cast<int>(group.size()) >= std::max(1, s->opt.batch) || s->pending.empty())
+        break;
+      const auto& nx = s->pending.front();
+      if (!same_batch(group[0]->req, nx->req) || s->running >= s->opt.slots ||
+          s->in_use + nx->footprint > s->opt.hbm_budget)
+        break;
+    }
+    const int grid = std::max(16, (2 * s->sms) / std::max(1, s->running - static_cast<int>(group.size()) + 1));
+    for (auto& job : group) {
+      job->res.grid = grid;
+      job->res.group = group[0]->res.admitted;
+      job->res.group_size = static_cast<int32_t>(group.size());
+    }
+    s->ready.push_back(std::move(group));
     s->cv_work.notify_one();
   }
   s->dispatcher_done = true;
@@ -196,7 +292,8 @@ lrs_status lrs_server_create(const lrs_server_options* opt, lrs_server_t* out) {
   *out = nullptr;
   lrs_server_options o{};
   if (opt) o = *opt;
-  if (o.slots < 0 || o.sms < 0) return srv_fail(LRS_ERR_ARG, "lrs_server_create: negative option");
+  if (o.slots < 0 || o.sms < 0 || o.batch < 0 || o.batch > 64)
+    return srv_fail(LRS_ERR_ARG, "lrs_server_create: negative option or batch above 64");
   if (o.slots == 0) o.slots = 8;
   int sms = o.sms;
   if (!o.runner) {

@@ -65,7 +65,8 @@ class lrs_result(ctypes.Structure):
                 ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
                 ("end_s", ctypes.c_double), ("footprint", ctypes.c_size_t),
                 ("worker", ctypes.c_int32), ("grid", ctypes.c_int32),
-                ("admitted", ctypes.c_int64)]
+                ("admitted", ctypes.c_int64), ("group", ctypes.c_int64),
+                ("group_size", ctypes.c_int32)]
 
 
 LRS_RUNNER = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(lrs_request),
@@ -74,7 +75,8 @@ LRS_RUNNER = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(lr
 
 class lrs_server_options(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("slots", ctypes.c_int32),
-                ("sms", ctypes.c_int32), ("runner", LRS_RUNNER), ("runner_ctx", ctypes.c_void_p)]
+                ("sms", ctypes.c_int32), ("runner", LRS_RUNNER), ("runner_ctx", ctypes.c_void_p),
+                ("batch", ctypes.c_int32)]
 
 
 _lib = None
@@ -322,7 +324,7 @@ def _check_srv(st):
         raise LrsError(st, lib().lrs_server_last_error().decode())
 
 
-def lrs_server_create(hbm_budget=0, slots=0, sms=0, runner=None):
+def lrs_server_create(hbm_budget=0, slots=0, sms=0, runner=None, batch=0):
     """Native request server (lrs_server_*).  runner: None (the library's
     solver) or a Python callable (request, grid, worker) -> status used in
     its place; the ctypes callback object is kept on the returned handle's
@@ -331,6 +333,7 @@ def lrs_server_create(hbm_budget=0, slots=0, sms=0, runner=None):
     o.hbm_budget = int(hbm_budget)
     o.slots = int(slots)
     o.sms = int(sms)
+    o.batch = int(batch)
     cb = None
     if runner is not None:
         cb = LRS_RUNNER(lambda ctx, req, grid, worker: int(runner(req.contents, grid, worker)))

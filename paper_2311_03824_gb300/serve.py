@@ -53,6 +53,8 @@ class Result:
     footprint: int = 0
     grid: int = 0
     admitted: int = -1
+    group: int = -1          # admission index of the first request of its batch
+    group_size: int = 1
 
     @property
     def latency(self):
@@ -96,13 +98,16 @@ class Server:
     arrives (host arrays, or device tensors whose producing work is complete);
     they are kept alive until the request has finished.  runner: None (the
     library's solver) or a callable (request, grid, worker) -> lrs status
-    that the server calls in its place (tests of the admission logic)."""
+    that the server calls in its place (tests of the admission logic).
+    batch: up to this many compatible Gaussian requests admitted together
+    share one persistent launch per sweep (lrs_server_options.batch)."""
 
     def __init__(self, hbm_budget: int, slots: int = 8, sms: int = 0,
-                 runner: Optional[Callable] = None, keep_outputs: bool = False):
+                 runner: Optional[Callable] = None, keep_outputs: bool = False, batch: int = 0):
         self.budget = int(hbm_budget)
         self.slots = int(slots)
         self.sms = int(sms)
+        self.batch = int(batch)
         self.keep_outputs = keep_outputs
         self._runner = runner
         self.makespan = 0.0
@@ -115,7 +120,7 @@ class Server:
         runner = None
         if self._runner is not None:
             runner = lambda req, grid, worker: self._runner(by_rid[req.user - 1], grid, worker)
-        srv, cb = L.lrs_server_create(self.budget, self.slots, self.sms, runner)
+        srv, cb = L.lrs_server_create(self.budget, self.slots, self.sms, runner, self.batch)
         t0 = time.perf_counter() if start_clock is None else start_clock
         order = sorted(reqs, key=lambda r: r.arrival)
         tickets, held, submitted = {}, {}, {}
@@ -163,7 +168,8 @@ class Server:
             base = submitted[rid] - res.submit_s
             r = Result(rid, rq.kind, rq.arrival, base + res.start_s, base + res.end_s,
                        footprint=int(res.footprint), grid=int(res.grid),
-                       admitted=int(res.admitted))
+                       admitted=int(res.admitted), group=int(res.group),
+                       group_size=int(res.group_size))
             if res.status != L.LRS_OK:
                 r.error = f"{L.STATUS_NAMES[res.status]}: {res.message.decode()}"
             elif self.keep_outputs:

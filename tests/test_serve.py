@@ -114,3 +114,32 @@ def test_mix_laws():
     assert all(2 <= r.r <= 10 for r in reqs)
     assert all(0.15 * r.n - 1 <= r.m <= 0.4 * r.n + 1 for r in reqs)
     assert all((r.nx, r.ny) in ((64, 64), (128, 128)) for r in d)
+
+
+def test_compatible_gaussian_requests_are_admitted_together():
+    """batch = 3: requests queued behind a Gaussian head with the same rank,
+    A_k form and iteration count join its batch (up to 3) while slots and
+    budget allow; any other request ends the batch; FIFO order is kept."""
+    blocker = S.Request(0, "gaussian", n=4096, q=2048, r=8, m=512, rho=40, seed=1, T=100,
+                        a_dtype=L.LRS_A_FP32)
+    g = dict(kind="gaussian", n=256, q=64, m=80, rho=3, seed=2, T=100)
+    reqs = [blocker] + [S.Request(i, r=3, **g) for i in (1, 2, 3, 4)] + \
+        [S.Request(5, r=4, **g)] + [S.Request(i, r=3, **g) for i in (6, 7)] + \
+        [S.Request(8, "dft", n=64 * 64, q=16, r=2, m=600, rho=20, seed=3, T=100, nx=64, ny=64)]
+    budget = S.footprint_bytes(blocker, host_inputs=True)
+    assert sum(S.footprint_bytes(r, host_inputs=True) for r in reqs[1:]) <= budget
+
+    def run(rq, grid, worker):
+        if rq.rid == 0:
+            time.sleep(0.3)            # everything else queues behind it meanwhile
+        return L.LRS_OK
+
+    res = S.Server(budget, slots=8, runner=run, batch=3).run(reqs, dummy_inputs)
+    by = {r.rid: r for r in res}
+    assert [by[i].admitted for i in range(9)] == list(range(9))
+    groups = {i: (by[i].group, by[i].group_size) for i in range(9)}
+    assert groups == {0: (0, 1), 1: (1, 3), 2: (1, 3), 3: (1, 3), 4: (4, 1), 5: (5, 1),
+                      6: (6, 2), 7: (6, 2), 8: (8, 1)}
+    assert all(r.error is None for r in res)
+    for i in (2, 3):                   # one worker, one start and end per batch
+        assert abs(by[i].start - by[1].start) < 1e-3 and abs(by[i].end - by[1].end) < 1e-3
