@@ -224,13 +224,14 @@ def run_ours(args):
     Y = np.ascontiguousarray(inst.Y)
     n, q, r, m, rho = cfg["n"], cfg["q"], cfg["r"], cfg["m"], cfg["rho"]
     stream = torch.cuda.Stream()
-    # autotune: the first iterate call times the task shapes (inside the warm-up)
-    s = L.Solver(n, m, q, r, rho, stream=stream, profile=1, autotune=1, engine=args.engine)
+    # autotune: the first iterate call times the task shapes (inside the
+    # warm-up); the steady iterations replay as a CUDA graph (captured at the
+    # second iteration, inside the warm-up)
+    s = L.Solver(n, m, q, r, rho, stream=stream, use_graph=1, autotune=1, engine=args.engine)
     s.set_measurements(Y, A)
     s.init()
     s.iterate(args.warmup)
     desc = L.lrs_describe(s.h)
-    L.lrs_phase_times(s.h)
     # ---- timed region: K GDmin iterations, inputs resident in HBM ----------
     def barrier():
         if world > 1:
@@ -245,12 +246,22 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
     ms = e0.elapsed_time(e1)
-    ph = L.lrs_phase_times(s.h)
     X = s.X()
     rel_err = float(np.linalg.norm(X - inst.Xstar) / np.linalg.norm(inst.Xstar))
+    s.close()
     ms = max_over_ranks(ms, world, "cuda")
     value = whole_job_value(world, q, args.steps, ms)
     # ---- roofline of the dominant kernel (the per-column sweep) ------------
+    # the same iterations launched one by one with CUDA events around each
+    # phase on the solver's stream (profile = 1; graphs off), same task shape
+    sp = L.Solver(n, m, q, r, rho, stream=stream, profile=1, autotune=1, engine=args.engine)
+    sp.set_measurements(Y, A)
+    sp.init()
+    sp.iterate(args.warmup)
+    L.lrs_phase_times(sp.h)
+    sp.iterate(min(args.steps, 50))
+    ph = L.lrs_phase_times(sp.h)
+    sp.close()
     peak, peak_kind = load_peaks()
     sweep_ms = ph["sweep_ms"] / max(1, ph["iters"])
     bytes_launch = q * b_alg_per_col_iter(n, m, r, rho)
@@ -272,7 +283,6 @@ def run_ours(args):
     e2e_value = world * q * T_e2e / t_e2e
     h2d = A.nbytes + Y.nbytes
     d2h = U_.nbytes + B_.nbytes + Si_.nbytes + Sv_.nbytes
-    s.close()
     line = None
     if rank == 0:
         cpu = None
@@ -287,7 +297,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": "gaussian n=1000 q=1000 r=5 m=150 rho=10 (float32 A_k, 600 MB)",
                        "l2": "inputs larger than L2 (A 600 MB)", "iterations_per_step": 1,
-                       "engine": desc.get("engine"),
+                       "engine": desc.get("engine"), "cuda_graph": True,
                        "task_shape": {k: desc.get(k) for k in ("grid", "inflight", "w_tasks", "g_tasks", "rows_per_piece")},
                        "rel_err_after": {"iterations": args.warmup + args.steps, "rel_err": rel_err}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -300,7 +310,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": "column-iters/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "iterations": T_e2e,
                     "includes": "lrs_set_measurements(pinned host) + lrs_init + lrs_iterate + lrs_get(host)"},
-            "gpu_launches": (8 if desc.get("engine") == "task" else 7) * args.steps,
+            "gpu_launches": int(desc.get("launches_per_iteration", 0)) * args.steps,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
         }
@@ -477,11 +487,12 @@ def run_c3(args):
 
 # ---- the serving workload: requests, arrivals and their inputs -------------
 
-def c4_requests(count: int, seed: int = 5, T: int = 100):
+def c4_requests(count: int, seed: int = 5, T: int = 100, form=None):
     """The serving mix: 70 % Gaussian problems with BF16-stored A_k,
     n = 64 round(2^U[8,12] / 64), q = 16 round(2^U[6,10] / 16), r ~ U{2..10},
     m = round(U[0.15, 0.4] n), rho = round(U[0.01, 0.02] n); 30 % DFT problems
-    on 64 x 64 or 128 x 128 frames with the same laws for q, r, rho and m / n."""
+    on 64 x 64 or 128 x 128 frames with the same laws for q, r, rho and m / n.
+    form: the Gaussian requests' stored A_k form (default BF16)."""
     from paper_2311_03824_gb300 import lrs as L
     from paper_2311_03824_gb300.serve import Request
     rng = np.random.default_rng(seed)
@@ -493,7 +504,10 @@ def c4_requests(count: int, seed: int = 5, T: int = 100):
             n = int(64 * round(2 ** rng.uniform(8, 12) / 64))
             m = int(round(rng.uniform(0.15, 0.4) * n))
             rho = max(1, int(round(rng.uniform(0.01, 0.02) * n)))
-            out.append(Request(i, "gaussian", n, q, r, max(m, r), rho, seed * 100003 + i, T))
+            rq = Request(i, "gaussian", n, q, r, max(m, r), rho, seed * 100003 + i, T)
+            if form is not None:
+                rq.a_dtype = form
+            out.append(rq)
         else:
             side = 64 if rng.uniform() < 0.5 else 128
             n = side * side
@@ -561,16 +575,27 @@ def run_c4(args):
     build.build()
     from paper_2311_03824_gb300 import serve as S
     budget = int(0.6 * torch.cuda.mem_get_info()[0])
-    reqs = c4_requests(args.requests, seed=5, T=100)
+    form = A_DTYPES[args.c4_form]
+    # saturation throughput (every request at t = 0) from a sample of the mix
+    n_sat = args.saturation_requests or args.requests
+    reqs = c4_requests(n_sat, seed=5, T=100, form=form)
     gen = C4Inputs()
-    srv = S.Server(budget, slots=args.slots, keep_outputs=True)
+    srv = S.Server(budget, slots=args.slots, keep_outputs=True, batch=args.batch)
     res = srv.run(reqs, gen)
     gen.score(res, reqs)
     sat = S.summarize(res, srv.makespan, reqs)
+    if args.saturation_only:
+        print(json.dumps({"metric": "serving saturation throughput", "value": sat["throughput_req_s"],
+                          "unit": "requests/s", "higher_is_better": True, "n_gpus": 1,
+                          "config": {"workload": f"serving mix, {n_sat} requests at t = 0",
+                                     "gaussian_form": args.c4_form,
+                                     "slots": args.slots, "batch": args.batch},
+                          "saturation": sat}), flush=True)
+        return 0
     rate = 0.8 * sat["throughput_req_s"]
-    reqs = poisson_arrivals(c4_requests(args.requests, seed=5, T=100), rate, seed=6)
+    reqs = poisson_arrivals(c4_requests(args.requests, seed=5, T=100, form=form), rate, seed=6)
     gen2 = C4Inputs()
-    srv2 = S.Server(budget, slots=args.slots, keep_outputs=True)
+    srv2 = S.Server(budget, slots=args.slots, keep_outputs=True, batch=args.batch)
     with ClockSampler(0) as clk:
         res2 = srv2.run(reqs, gen2)
     gen2.score(res2, reqs)
@@ -579,9 +604,9 @@ def run_c4(args):
         "metric": "serving p99 latency", "value": lat["p99_latency_s"], "unit": "s",
         "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
         "dtype": "bf16 storage (Gaussian), f32 compute",
-        "config": {"workload": f"serving mix, {args.requests} requests, 70% Gaussian BF16 / 30% DFT, T=100",
-                   "slots": args.slots, "hbm_budget_gb": budget / 1e9,
-                   "arrival_rate_req_s": rate},
+        "config": {"workload": f"serving mix, {args.requests} requests, 70% Gaussian {args.c4_form} / 30% DFT, T=100",
+                   "slots": args.slots, "batch": args.batch, "hbm_budget_gb": budget / 1e9,
+                   "arrival_rate_req_s": rate, "saturation_sample": n_sat},
         "saturation": sat, "poisson_0.8": lat, "clocks": clk.summary(),
         "peak_concurrent": srv2.peak_running,
     }
@@ -600,6 +625,13 @@ def main():
     ap.add_argument("--workload", default="c1", choices=["c1", "c2", "c3", "c4"])
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=8,
+                    help="c4: compatible Gaussian requests per persistent launch")
+    ap.add_argument("--saturation-requests", type=int, default=0,
+                    help="c4: requests of the saturation sample (0: --requests)")
+    ap.add_argument("--saturation-only", action="store_true")
+    ap.add_argument("--c4-form", default="bf16", choices=list(A_DTYPES),
+                    help="c4: stored A_k form of the Gaussian requests")
     ap.add_argument("--a-dtype", default="fp32", choices=list(A_DTYPES))
     ap.add_argument("--engine", type=int, default=0, choices=[0, 1, 2, 3],
                     help="Gaussian sweep engine (0: the library's choice)")

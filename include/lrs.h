@@ -134,6 +134,11 @@ typedef struct {
   void* reduce_ctx;         /* first argument of reduce                        */
   int32_t reduce_cap;       /* partial blocks of all shards together (the `cap`
                                of reduce)                                    */
+  int32_t test_withhold;    /* test aid for the failure path (0 in use): the
+                               task engine's queue holds one ticket that is
+                               never published, so the wait for it runs out
+                               after wait_ms and the call returns
+                               LRS_ERR_TIMEOUT with the device still usable  */
 } lrs_options;
 
 /* Create a solver for one problem (Section I-A sizes).
@@ -376,7 +381,7 @@ typedef int32_t (*lrs_runner)(void* ctx, const lrs_request* req, int32_t grid, i
 typedef struct {
   size_t hbm_budget;        /* device bytes the requests in flight may hold
                                (0 -> 85 % of the free memory at creation)    */
-  int32_t slots;            /* requests in flight at most (0 -> 8)            */
+  int32_t slots;            /* requests (or batches) in flight at most (0 -> 8) */
   int32_t sms;              /* SMs shared by the sweeps (0 -> the device's)   */
   lrs_runner runner;        /* NULL: the library's solver                     */
   void* runner_ctx;
@@ -397,8 +402,8 @@ typedef struct lrs_server_s* lrs_server_t;
  * persistent sweep gets max(16, 2 x SMs / requests running) CTAs.  With
  * batch > 1, when the admitted request is Gaussian the queued requests right
  * behind it of the same rank, A_k form and iteration count that also fit
- * (slots, budget) are admitted with it, up to `batch` of them, and one
- * worker runs their iterations together (lrs_iterate_batch).  The kernels'
+ * (budget) are admitted with it, up to `batch` of them, into the same slot,
+ * and its worker runs their iterations together (lrs_iterate_batch).  The kernels'
  * results depend neither on the other requests, nor on that share, nor on
  * the batch: every result equals the request solved alone.
  * Errors: LRS_ERR_ARG, LRS_ERR_CUDA (no device). */

@@ -235,6 +235,8 @@ struct FArgs {
   const float2* twx;
   const float2* twy;
   int* err;
+  float2* vecs;         // q x 3m: y, and the two m-vectors of the sweep, when
+                        // they do not fit shared memory beside the frame
 };
 
 struct FCarve {
@@ -243,16 +245,19 @@ struct FCarve {
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline FCarve fcarve(const Geo& g, int m, int rho) {
+// Shared-memory carve of the sweep; with vglob the three m-vectors (y, and
+// the sweep's two) live in global memory (FArgs::vecs) and take no space.
+__host__ __device__ inline FCarve fcarve(const Geo& g, int m, int rho, bool vglob = false) {
   FCarve c;
   size_t o = 0;
   const int rh = rho > 0 ? rho : 1;
+  const size_t mv = vglob ? 0 : al16(static_cast<size_t>(m) * 8);
   c.X = o;    o += al16(static_cast<size_t>(g.nx) * (g.ny + 1) * 8);
   c.tx = o;   o += al16(static_cast<size_t>(g.nx) * 8);
   c.ty = o;   o += al16(static_cast<size_t>(g.ny) * 8);
-  c.yv = o;   o += al16(static_cast<size_t>(m) * 8);
-  c.dv = o;   o += al16(static_cast<size_t>(m) * 8);
-  c.ev = o;   o += al16(static_cast<size_t>(m) * 8);
+  c.yv = o;   o += mv;
+  c.dv = o;   o += mv;
+  c.ev = o;   o += mv;
   c.msk = o;  o += al16(static_cast<size_t>(m) * 4);
   c.sp = o;   o += al16(static_cast<size_t>(rh) * 4 + 16);
   c.sv = o;   o += al16(static_cast<size_t>(rh) * 8);
@@ -567,7 +572,7 @@ __device__ void fhard_threshold(const FCtx& C, bool keep_values) {
 
 __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const FCarve cv = fcarve(a.g, a.m, a.rho);
+  const FCarve cv = fcarve(a.g, a.m, a.rho, a.vecs != nullptr);
   FCtx C;
   C.g = a.g;
   C.m = a.m;
@@ -577,9 +582,16 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
   C.X = reinterpret_cast<float2*>(sm + cv.X);
   C.tx = reinterpret_cast<float2*>(sm + cv.tx);
   C.ty = reinterpret_cast<float2*>(sm + cv.ty);
-  C.yv = reinterpret_cast<float2*>(sm + cv.yv);
-  C.dv = reinterpret_cast<float2*>(sm + cv.dv);
-  C.ev = reinterpret_cast<float2*>(sm + cv.ev);
+  if (a.vecs) {
+    float2* v = a.vecs + static_cast<size_t>(blockIdx.x) * 3 * a.m;
+    C.yv = v;
+    C.dv = v + a.m;
+    C.ev = v + 2 * static_cast<size_t>(a.m);
+  } else {
+    C.yv = reinterpret_cast<float2*>(sm + cv.yv);
+    C.dv = reinterpret_cast<float2*>(sm + cv.dv);
+    C.ev = reinterpret_cast<float2*>(sm + cv.ev);
+  }
   C.msk = reinterpret_cast<int*>(sm + cv.msk);
   C.sp = reinterpret_cast<int*>(sm + cv.sp);
   C.sv = reinterpret_cast<float2*>(sm + cv.sv);
@@ -1072,6 +1084,7 @@ struct FourierSolver {
   double2* rfac = nullptr;
   double* eta = nullptr;
   double* scal = nullptr;
+  float2* vecs = nullptr;  // the sweep's m-vectors in global memory (large m)
   size_t smem = 0;
 };
 
@@ -1119,8 +1132,11 @@ FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int 
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // the m-vectors go to global memory when they do not fit beside the frame
+  const bool vglob = F->smem > static_cast<size_t>(optin);
+  if (vglob) F->smem = fcarve(F->g, m, rho, true).total;
   if (F->smem > static_cast<size_t>(optin) || fft_smem(F->g) > static_cast<size_t>(optin)) {
-    *msg = "frame too large for one CTA's shared memory (n <= 16384 with m <= 2048 fits)";
+    *msg = "frame too large for one CTA's shared memory (n <= 16384 fits)";
     delete F;
     return nullptr;
   }
@@ -1149,7 +1165,9 @@ FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int 
             cudaMallocAsync(reinterpret_cast<void**>(&F->part), sizeof(double2) * F->nblk * rr, F->s) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&F->rfac), sizeof(double2) * 2 * rr, F->s) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&F->eta), sizeof(double), F->s) == cudaSuccess &&
-            cudaMallocAsync(reinterpret_cast<void**>(&F->scal), sizeof(double) * 4, F->s) == cudaSuccess;
+            cudaMallocAsync(reinterpret_cast<void**>(&F->scal), sizeof(double) * 4, F->s) == cudaSuccess &&
+            (!vglob || cudaMallocAsync(reinterpret_cast<void**>(&F->vecs),
+                                       sizeof(float2) * 3 * static_cast<size_t>(m) * q, F->s) == cudaSuccess);
   if (!ok) {
     *msg = "device allocation failed";
     return F;  // caller frees
@@ -1175,7 +1193,8 @@ FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int 
 void fourier_destroy(FourierSolver* F) {
   if (!F) return;
   void* ps[] = {F->y, F->mask, F->U, F->FU, F->B, F->S_idx, F->S_val, F->RES, F->H, F->K, F->grad,
-                F->Z, F->Z2, F->twx, F->twy, F->iptr, F->ilist, F->err, F->part, F->rfac, F->eta, F->scal};
+                F->Z, F->Z2, F->twx, F->twy, F->iptr, F->ilist, F->err, F->part, F->rfac, F->eta, F->scal,
+                F->vecs};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, F->s);
   cudaStreamSynchronize(F->s);
@@ -1248,6 +1267,7 @@ static cudaError_t launch_fsweep(FourierSolver* F, int mode, int tau) {
   a.twx = F->twx;
   a.twy = F->twy;
   a.err = F->err;
+  a.vecs = F->vecs;
   fsweep_kernel<<<F->q, kFT, F->smem, F->s>>>(a);
   return cudaGetLastError();
 }

@@ -246,6 +246,11 @@ lrs_status check_device_error(lrs_ctx* h, const char* where) {
   return fail(e[0] == kErrTimeout ? LRS_ERR_TIMEOUT : LRS_ERR_NUMERICAL, msg);
 }
 
+// Bound of every device-side wait of the task and resident engines.
+unsigned long long wait_bound_ns(const lrs_ctx* h) {
+  return static_cast<unsigned long long>(h->opt.wait_ms > 0 ? h->opt.wait_ms : 10000) * 1000000ull;
+}
+
 lrs_status launch_sweep(lrs_ctx* h, int mode, int tau) {
   if (h->engine == 3) {
     ResArgs a{};
@@ -266,7 +271,7 @@ lrs_status launch_sweep(lrs_ctx* h, int mode, int tau) {
     a.B = h->Bk;
     a.H = h->H;
     a.err = h->err;
-    a.wait_ns = static_cast<unsigned long long>(h->opt.wait_ms > 0 ? h->opt.wait_ms : 10000) * 1000000ull;
+    a.wait_ns = wait_bound_ns(h);
     a.prof = (h->opt.profile == 2 && mode == kModeIter) ? h->tprof : nullptr;
     CUDA_TRY(res_launch(a, h->res_ncl, h->stream));
     return LRS_OK;
@@ -276,8 +281,11 @@ lrs_status launch_sweep(lrs_ctx* h, int mode, int tau) {
     Q.tasks = h->ttasks;
     Q.seq = h->tseq;
     Q.ctr = h->tctr;
-    Q.total = h->total[mode];
+    // test_withhold: one ticket more than the launch's tasks, never published
+    // (room for it is allocated), so the wait for it runs out
+    Q.total = h->total[mode] + (h->opt.test_withhold ? 1 : 0);
     Q.ncols = static_cast<int>(h->q);
+    Q.wait_ns = wait_bound_ns(h);
     Q.F = h->tF;
     Q.nprob = 1;
     Q.probs = h->dtp + mode;
@@ -705,8 +713,8 @@ lrs_status alloc_task_engine(lrs_ctx* h) {
       (st = dalloc(&h->tsupv, q * rho1, h->stream)) || (st = dalloc(&h->tnsup, q, h->stream)) ||
       (st = dalloc(&h->tcnt, q, h->stream)) || (st = dalloc(&h->tstop, q, h->stream)) || (st = dalloc(&h->tctr, 4, h->stream)) ||
       (st = dalloc(&h->dtp, 3, h->stream)) || (st = dalloc(&h->tprof, 16, h->stream)) ||
-      (st = dalloc(&h->ttasks, static_cast<size_t>(total_max), h->stream)) ||
-      (st = dalloc(&h->tseq, static_cast<size_t>(total_max), h->stream)) ||
+      (st = dalloc(&h->ttasks, static_cast<size_t>(total_max) + 1, h->stream)) ||
+      (st = dalloc(&h->tseq, static_cast<size_t>(total_max) + 1, h->stream)) ||
       (st = dalloc(&h->dseed, 3 * h->seed_stride, h->stream)))
     return st;
   CUDA_TRY(cudaMemsetAsync(h->tprof, 0, 16 * sizeof(unsigned long long), h->stream));
@@ -1400,6 +1408,7 @@ lrs_status lrs_iterate_batch(lrs_t* hs, int32_t nh, int32_t iters) {
     Q.nprob = nh;
     Q.probs = dP;
     Q.prof = nullptr;
+    Q.wait_ns = wait_bound_ns(h0);
     e = task_launch_seeded(Q, dseed, static_cast<int>(nseed), dcnt, R, et, shape, m_max, ns_max,
                            rho_max, s);
     if (e == cudaSuccess) e = cudaEventRecord(evs[0], s);
@@ -1594,6 +1603,17 @@ lrs_status lrs_sweep_trace(lrs_t h, uint64_t* out, int64_t len) {
   return LRS_OK;
 }
 
+// Kernels one steady GDmin iteration launches (no refinement of the
+// measurements, step size already frozen): the sweep (task engine: queue
+// reset + persistent kernel), the gradient (k-split partials + their sum, or
+// one kernel), Cholesky-QR2 (Gram partials, two factorisations, two
+// applications).
+static int launches_per_iteration(const lrs_ctx* h) {
+  const int sweep = h->engine == 2 ? 2 : 1;
+  const int grad = (h->ks > 1 || h->qc > 0) ? 2 : 1;
+  return sweep + grad + 5;
+}
+
 lrs_status lrs_describe(lrs_t h, char* buf, int32_t len) {
   if (!h || !buf || len <= 0) return fail(LRS_ERR_ARG, "lrs_describe: bad argument");
   if (h->F) {
@@ -1606,9 +1626,10 @@ lrs_status lrs_describe(lrs_t h, char* buf, int32_t len) {
     snprintf(buf, static_cast<size_t>(len),
              "{\"op\": \"gaussian\", \"engine\": \"resident\", \"cluster\": %d, "
              "\"clusters\": %d, \"rows_per_lane\": %d, \"rank_width\": %d, "
-             "\"smem_per_cta\": %zu}",
+             "\"smem_per_cta\": %zu, \"launches_per_iteration\": %d}",
              h->res_CS, h->res_ncl, MR, R,
-             res_smem_bytes(R, MR, static_cast<int>(h->m), h->rho, h->res_CS));
+             res_smem_bytes(R, MR, static_cast<int>(h->m), h->rho, h->res_CS),
+             launches_per_iteration(h));
     return LRS_OK;
   }
   if (h->engine == 2) {
@@ -1617,9 +1638,10 @@ lrs_status lrs_describe(lrs_t h, char* buf, int32_t len) {
              "{\"op\": \"gaussian\", \"engine\": \"task\", \"grid\": %d, \"ctas_per_sm\": %d, "
              "\"stages\": %d, \"piece_bytes\": %d, \"smem_per_cta\": %zu, \"inflight\": %d, "
              "\"w_tasks\": %d, \"g_tasks\": %d, \"rows_per_piece\": %d, \"tiles_per_task\": %d, "
-             "\"a_dtype\": %d, \"refine_every\": %d}",
+             "\"a_dtype\": %d, \"refine_every\": %d, \"launches_per_iteration\": %d}",
              h->tshape.grid, h->tshape.ctas_per_sm, h->tshape.stages, h->tshape.piece_bytes,
-             h->tshape.smem, h->tF, P.nrb * P.ncw, P.ngb, P.rp, P.TB, h->L.et, h->opt.refine_every);
+             h->tshape.smem, h->tF, P.nrb * P.ncw, P.ngb, P.rp, P.TB, h->L.et, h->opt.refine_every,
+             launches_per_iteration(h));
     return LRS_OK;
   }
   const size_t sm = sweep_smem_bytes(h->L, h->resident, kThreads);
@@ -1627,9 +1649,9 @@ lrs_status lrs_describe(lrs_t h, char* buf, int32_t len) {
   snprintf(buf, static_cast<size_t>(len),
            "{\"op\": \"%s\", \"engine\": \"cluster\", \"cluster\": %d, \"ns\": %d, \"stages\": %d, \"resident\": %d, "
            "\"smem_per_cta\": %zu, \"max_active_clusters\": %d, \"a_dtype\": %d, "
-           "\"refine_every\": %d}",
+           "\"refine_every\": %d, \"launches_per_iteration\": %d}",
            h->kind == LRS_OP_GAUSSIAN ? "gaussian" : "dft2d", h->L.cs, h->L.ns, h->L.stages,
-           h->resident, sm, nc, h->L.et, h->opt.refine_every);
+           h->resident, sm, nc, h->L.et, h->opt.refine_every, launches_per_iteration(h));
   return LRS_OK;
 }
 

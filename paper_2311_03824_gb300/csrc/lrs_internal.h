@@ -146,6 +146,7 @@ struct TaskQueue {
   int nprob;
   const TaskProblem* probs;   // device copy
   unsigned long long* prof;   // optional kTaskProf counters (cycles summed over CTAs)
+  unsigned long long wait_ns = 10ull * 1000 * 1000 * 1000;  // bound of every device wait
 };
 // Task-engine profile counters: consumer cycles waiting for a task, in W
 // tasks, in A^T tasks, waiting for pieces (inside tasks), in the small steps

@@ -4,8 +4,9 @@
 //
 // A request is admitted in submission order as soon as a slot is free and
 // its device footprint fits what the requests in flight leave of the HBM
-// budget.  Each slot is a worker thread with its own CUDA stream; it runs the
-// request through the public calls (lrs_create, lrs_set_measurements,
+// budget; compatible Gaussian requests queued right behind it may join it as
+// one batch (batch > 1).  Each slot is a worker thread with its own CUDA
+// stream; it runs the request (or batch) through the public calls (lrs_create, lrs_set_measurements,
 // lrs_init, lrs_iterate, lrs_get, lrs_destroy), so the work of concurrent
 // requests overlaps on the GPU.  A Gaussian request's persistent sweep gets
 // a share of the SMs (lrs_options.grid) sized by the requests running when
@@ -205,8 +206,8 @@ void worker_main(lrs_server_s* s, int wi) {
         job.res.end_s = t_end;
         job.done = true;
         s->in_use -= job.footprint;
-        s->running -= 1;
       }
+      s->running -= 1;
     }
     s->cv_done.notify_all();
     s->cv_admit.notify_all();
@@ -236,22 +237,22 @@ void dispatcher_main(lrs_server_s* s) {
       return s->running < s->opt.slots && s->in_use + j->footprint <= s->opt.hbm_budget;
     });
     if (s->pending.empty()) break;  // stopping with nothing queued
+    // a slot runs one request, or one batch of requests
     std::vector<std::shared_ptr<Job>> group;
+    s->running += 1;
     for (;;) {
       auto job = s->pending.front();
       s->pending.pop_front();
       s->in_use += job->footprint;
-      s->running += 1;
       job->res.admitted = s->next_admit++;
       group.push_back(job);
       if (static_cast<int>(group.size()) >= std::max(1, s->opt.batch) || s->pending.empty())
         break;
       const auto& nx = s->pending.front();
-      if (!same_batch(group[0]->req, nx->req) || s->running >= s->opt.slots ||
-          s->in_use + nx->footprint > s->opt.hbm_budget)
+      if (!same_batch(group[0]->req, nx->req) || s->in_use + nx->footprint > s->opt.hbm_budget)
         break;
     }
-    const int grid = std::max(16, (2 * s->sms) / std::max(1, s->running - static_cast<int>(group.size()) + 1));
+    const int grid = std::max(16, (2 * s->sms) / std::max(1, s->running));
     for (auto& job : group) {
       job->res.grid = grid;
       job->res.group = group[0]->res.admitted;

@@ -33,7 +33,6 @@ namespace task {
 using namespace sweep;
 
 constexpr int kMaxStages = kTaskStages;
-constexpr unsigned long long kWaitNs = 10ull * 1000 * 1000 * 1000;  // 10 s
 
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
@@ -102,6 +101,7 @@ struct TCtx {
   int* bcast;
   int* err;
   int* abort;        // launch-wide: set once any wait of any CTA expired
+  unsigned long long wait_ns;  // bound of every wait of the launch
   long long pw;      // thread 0: cycles waiting for pieces (profile)
 };
 
@@ -115,15 +115,16 @@ __device__ __forceinline__ void set_abort(int* abort, int* err) {
   atomicExch(abort, 1);
 }
 
-// Bounded wait on a shared-memory barrier: false after kWaitNs or as soon as
+// Bounded wait on a shared-memory barrier: false after wait_ns or as soon as
 // the launch is aborted (the caller then runs on without the data; every
 // later wait returns at once, so all CTAs leave quickly).
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, unsigned parity, int* err, int* abort) {
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, unsigned parity, int* err, int* abort,
+                                         unsigned long long wait_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = gtimer();
   while (!mbar_try_wait(bar, parity)) {
     if (ld_relaxed(abort)) return false;
-    if (gtimer() - t0 > kWaitNs) {
+    if (gtimer() - t0 > wait_ns) {
       set_abort(abort, err);
       return false;
     }
@@ -135,7 +136,7 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, unsigned parity, int* er
 __device__ __forceinline__ const unsigned char* acquire_piece(TCtx& T, bool& ok) {
   const unsigned s = T.seq % T.stages, use = T.seq / T.stages;
   const long long c0 = clock64();
-  ok = wait_bar(&T.full[s], use & 1u, T.err, T.abort);
+  ok = wait_bar(&T.full[s], use & 1u, T.err, T.abort, T.wait_ns);
   T.pw += clock64() - c0;
   return T.ring + static_cast<size_t>(s) * T.stage;
 }
@@ -214,7 +215,7 @@ __device__ __forceinline__ void produce_task(TCtx& T, const TaskProblem& P, int 
   const unsigned char* col = static_cast<const unsigned char*>(P.A) + static_cast<size_t>(k) * ntile * tb;
   auto piece = [&](int b, int i0, int i1, bool with_u) {
     const unsigned s = pseq % T.stages, use = pseq / T.stages;
-    if (use > 0 && !wait_bar(&T.empty[s], (use - 1) & 1u, T.err, T.abort)) return false;
+    if (use > 0 && !wait_bar(&T.empty[s], (use - 1) & 1u, T.err, T.abort, T.wait_ns)) return false;
     unsigned char* dst = T.ring + static_cast<size_t>(s) * T.stage;
     const unsigned hb = static_cast<unsigned>((i1 - i0) * kTW * pb);
     const unsigned ub = with_u ? static_cast<unsigned>(kTW * R * 4) : 0u;
@@ -330,7 +331,7 @@ __device__ __forceinline__ void consume_w_rr(TCtx& T, const TaskProblem& P, int 
   for (int p = wid; p < npieces; p += kNW) {
     const unsigned sq = s0 + p, s = sq % T.stages, use = sq / T.stages;
     const long long c0 = clock64();
-    wait_bar(&T.full[s], use & 1u, T.err, T.abort);
+    wait_bar(&T.full[s], use & 1u, T.err, T.abort, T.wait_ns);
     if (lane == 0) T.pw += clock64() - c0;
     const unsigned char* st = T.ring + static_cast<size_t>(s) * T.stage;
     const float* Us = reinterpret_cast<const float*>(st + T.stage - static_cast<size_t>(kTW) * R * 4);
@@ -413,7 +414,7 @@ __device__ __forceinline__ void consume_g(TCtx& T, const TaskProblem& P, int k, 
     const int i0 = c * P.rp, nr = min(m, i0 + P.rp) - i0;
     const unsigned sq = s0 + p, s = sq % T.stages, use = sq / T.stages;
     const long long c0 = clock64();
-    wait_bar(&T.full[s], use & 1u, T.err, T.abort);
+    wait_bar(&T.full[s], use & 1u, T.err, T.abort, T.wait_ns);
     if (lane == 0) T.pw += clock64() - c0;
     const unsigned char* st = T.ring + static_cast<size_t>(s) * T.stage;
     const float* uu = T.uv + i0;
@@ -538,7 +539,7 @@ template <int R>
 __device__ __forceinline__ void load_column(Ctx& C, const TaskProblem& P, int k, bool with_w,
                                             bool with_gi, int source, bool with_g,
                                             uint64_t* sbar, unsigned& sphase, int* abort,
-                                            float* asv = nullptr) {
+                                            unsigned long long wait_ns, float* asv = nullptr) {
   const int m = C.m, tid = threadIdx.x, rho = C.rho, ns = P.L.ns, n = P.L.n;
   const bool bulk = with_w || with_gi || with_g || asv;
   if (bulk) {
@@ -588,7 +589,7 @@ __device__ __forceinline__ void load_column(Ctx& C, const TaskProblem& P, int k,
   } else if (tid == 0) {
     *C.nloc = 0;
   }
-  if (bulk && tid == 0) wait_bar(sbar, sphase, C.err, abort);  // on expiry the launch aborts
+  if (bulk && tid == 0) wait_bar(sbar, sphase, C.err, abort, wait_ns);  // on expiry the launch aborts
   if (bulk) sphase ^= 1u;
   csync();
   if (with_g)
@@ -830,7 +831,7 @@ __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int typ
 
   if (type == kTaskW) {
     // W_k = sum of the column-chunk partials (fixed order), Gram, Cholesky
-    load_column<R>(C, P, k, false, false, kSupInput, false, sbar, sphase, Q.ctr + 3);
+    load_column<R>(C, P, k, false, false, kSupInput, false, sbar, sphase, Q.ctr + 3, Q.wait_ns);
     for (int t = tid; t < m * R; t += kNT) {
       float s = 0.f;
       for (int cc = 0; cc < P.ncw; ++cc)
@@ -865,7 +866,7 @@ __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int typ
     float* asv = reinterpret_cast<float*>(smem + cv.asv);
     int* osup = reinterpret_cast<int*>(smem + cv.osup);
     load_column<R>(C, P, k, project, project, zero_start ? kSupNone : kSupState,
-                   type != kTaskNop, sbar, sphase, Q.ctr + 3, may_update ? asv : nullptr);
+                   type != kTaskNop, sbar, sphase, Q.ctr + 3, Q.wait_ns, may_update ? asv : nullptr);
     if (zero_start && tid == 0) P.stop[k] = 0;
     const int sweep = P.mode == kModeInit ? ph : ph - 1;  // 0-based IHT sweep just run
     bool stopped = stop_in != 0 || type == kTaskNop;
@@ -940,7 +941,7 @@ __device__ void column_step(const TaskQueue& Q, int prob, int k, int ph, int typ
     }
     mark(13);
   } else {  // kTaskF: H row written by the tasks; outputs
-    load_column<R>(C, P, k, false, false, kSupState, false, sbar, sphase, Q.ctr + 3);
+    load_column<R>(C, P, k, false, false, kSupState, false, sbar, sphase, Q.ctr + 3, Q.wait_ns);
     store_output_support(C, P, k);
     next_type = -2;
   }
@@ -988,6 +989,7 @@ __global__ void __launch_bounds__(kThreadsAll, R <= 6 ? 3 : 2) task_kernel(const
   T.bcast = reinterpret_cast<int*>(smem + cv.bcast);
   T.err = Q.probs[0].err;
   T.abort = &Q.ctr[3];
+  T.wait_ns = Q.wait_ns;
   T.pw = 0;
   long long* prof = reinterpret_cast<long long*>(smem + cv.prof);  // thread 0 / producer
   if (tid < kTaskProf) prof[tid] = 0;
@@ -1030,7 +1032,7 @@ __global__ void __launch_bounds__(kThreadsAll, R <= 6 ? 3 : 2) task_kernel(const
           while (ld_acquire_(&Q.seq[h]) == 0) {
             __nanosleep(200);
             if (ld_relaxed(T.abort)) { ok = false; break; }
-            if (gtimer() - t0 > kWaitNs) {
+            if (gtimer() - t0 > T.wait_ns) {
               set_abort(T.abort, T.err);
               ok = false;
               break;
@@ -1040,7 +1042,7 @@ __global__ void __launch_bounds__(kThreadsAll, R <= 6 ? 3 : 2) task_kernel(const
         if (ok) d = __ldcg(&Q.tasks[h]);
       }
       if (Q.prof) prof[7] += clock64() - c0;
-      if (use > 0 && !wait_bar(&T.tempty[ts], (use - 1) & 1u, T.err, T.abort))
+      if (use > 0 && !wait_bar(&T.tempty[ts], (use - 1) & 1u, T.err, T.abort, T.wait_ns))
         d = tdesc(0, 0, kTaskExit, 0, 0);
       T.tslot[ts] = d;
       mbar_arrive_local(&T.tfull[ts]);
@@ -1056,7 +1058,7 @@ __global__ void __launch_bounds__(kThreadsAll, R <= 6 ? 3 : 2) task_kernel(const
       const unsigned last = (pseq - 1 - s) / stages * stages + s;  // last piece on stage s
       const unsigned long long t0 = gtimer();
       while (!mbar_try_wait(&T.full[s], (last / stages) & 1u))
-        if (gtimer() - t0 > kWaitNs) break;
+        if (gtimer() - t0 > T.wait_ns) break;
     }
     flush_prof();
     return;
@@ -1069,7 +1071,7 @@ __global__ void __launch_bounds__(kThreadsAll, R <= 6 ? 3 : 2) task_kernel(const
     const unsigned ts = it & 1u, use = it >> 1;
     // one thread waits for the descriptor, so that leaving is uniform
     long long c0 = clock64();
-    if (tid == 0) T.bcast[1] = wait_bar(&T.tfull[ts], use & 1u, T.err, T.abort) ? 1 : 0;
+    if (tid == 0) T.bcast[1] = wait_bar(&T.tfull[ts], use & 1u, T.err, T.abort, T.wait_ns) ? 1 : 0;
     csync();
     if (!T.bcast[1]) {
       flush_prof();

@@ -48,7 +48,7 @@ class lrs_options(ctypes.Structure):
                 ("autotune", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("wait_ms", ctypes.c_int32), ("grad_block", ctypes.c_int32),
                 ("reduce", LRS_REDUCER), ("reduce_ctx", ctypes.c_void_p),
-                ("reduce_cap", ctypes.c_int32)]
+                ("reduce_cap", ctypes.c_int32), ("test_withhold", ctypes.c_int32)]
 
 
 class lrs_request(ctypes.Structure):

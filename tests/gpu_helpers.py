@@ -31,6 +31,9 @@ whenever every column is decidable.  Each test bounds the share of column-
 steps it excludes (MAX_EXCLUDED) and the number of whole-X checks it must
 make.
 """
+import json
+import os
+
 import numpy as np
 
 import oracle.altgdmin_lrs as O
@@ -155,8 +158,10 @@ def _gap_change(r32, r64, rho):
     for a, b in zip(r32.v, r64.v):
         ma = O.hard_threshold(a, rho)[2]
         mb = O.hard_threshold(b, rho)[2]
-        ok = np.isfinite(ma) & np.isfinite(mb)
-        d = np.maximum(d, np.where(ok, np.abs(ma - mb), 0.0))
+        ok = np.isfinite(ma) & np.isfinite(mb)     # (no gap when rho = n)
+        diff = np.zeros_like(d)
+        diff[ok] = np.abs(ma[ok] - mb[ok])
+        d = np.maximum(d, diff)
     return d
 
 
@@ -331,10 +336,16 @@ def check_records(recs, min_whole, max_excluded=MAX_EXCLUDED):
             whole += 1
     assert whole >= min_whole, ("whole-X checks", whole, min_whole)
     assert excl <= max_excluded * tot, ("excluded column-steps", excl, tot)
-    return dict(steps=len(recs), whole=whole, excluded=excl, column_steps=tot,
-                raised=sum(1 for r in recs if r["raised"]),
-                max_b=max((r["b_rel"] for r in recs), default=0.0),
-                max_x=max((r["whole"] for r in recs if r["whole"] is not None), default=0.0))
+    summary = dict(steps=len(recs), whole=whole, excluded=excl, column_steps=tot,
+                   raised=sum(1 for r in recs if r["raised"]),
+                   max_b=max((r["b_rel"] for r in recs), default=0.0),
+                   max_s=max((r["s_rel"] for r in recs), default=0.0),
+                   max_x=max((r["whole"] for r in recs if r["whole"] is not None), default=0.0))
+    log = os.environ.get("LRS_PARITY_LOG")
+    if log:                      # one JSON line per checked run (the excluded shares)
+        with open(log, "a") as f:
+            f.write(json.dumps(dict(test=os.environ.get("PYTEST_CURRENT_TEST", ""), **summary)) + "\n")
+    return summary
 
 
 # ----------------------------------------------------------- GPU runs --

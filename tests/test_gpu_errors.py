@@ -71,3 +71,31 @@ def test_rank_deficient_column_reports_numerical_error_with_column(engine):
         assert "column 5" in str(e.value), str(e.value)
     finally:
         s.close()
+
+
+def test_expired_device_wait_returns_timeout_and_the_device_stays_usable():
+    """Failure detection without a fault: the task engine's queue gets one
+    ticket that nothing publishes (test_withhold), the producer that pops it
+    waits 200 ms (wait_ms), sets the launch's abort flag, every other wait of
+    the launch returns, and the call reports LRS_ERR_TIMEOUT.  A solver
+    created afterwards runs normally."""
+    import time
+    from paper_2311_03824_gb300 import lrs as L
+    inst = GaussianInstance(n=64, q=16, r=2, m=32, rho=2, seed=7)
+    s = new_solver(inst, engine=2, wait_ms=200, test_withhold=1)
+    try:
+        t0 = time.time()
+        with pytest.raises(L.LrsError) as e:
+            s.init()
+        assert e.value.status == L.LRS_ERR_TIMEOUT, str(e.value)
+        assert time.time() - t0 < 30
+    finally:
+        s.close()
+    f = new_solver(inst, engine=2)
+    try:
+        f.init()
+        f.iterate(30)
+        X = f.X()
+    finally:
+        f.close()
+    assert np.linalg.norm(X - inst.Xstar) / np.linalg.norm(inst.Xstar) < 0.5

@@ -74,3 +74,18 @@ def test_fourier_table1_frames_one_step():
     finally:
         s.close()
     check_records(recs, min_whole=T // 2, max_excluded=0.03)
+
+
+def test_fourier_128x128_m_at_0p4n():
+    """m = 0.4 n on 128 x 128 frames (6554 sampled rows, the top of the
+    serving mix's law): the sweep keeps the frame in shared memory and its
+    m-vectors in global memory.  One-step parity from the oracle's iterates."""
+    inst = FourierInstance(nx=128, ny=128, q=12, r=4, m=6554, rho=200, seed=44)
+    T = 4
+    _, log = _oracle(inst, T)
+    s = new_fourier_solver(inst)
+    try:
+        recs = one_step(Problem.fourier(inst), s, log, range(T))
+    finally:
+        s.close()
+    check_records(recs, min_whole=T // 2)

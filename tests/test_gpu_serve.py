@@ -66,3 +66,28 @@ def test_alone_equals_mix_bitwise():
         assert a.error is None and r.error is None
         for x, y in zip(a.outputs, r.outputs):
             assert np.array_equal(x, y), r.rid
+
+
+def test_batched_requests_equal_alone_bitwise():
+    """batch = 4: the Gaussian requests of one rank and A_k form queued
+    together share one persistent launch per sweep; every output equals the
+    request solved alone."""
+    import torch
+    import bench
+    from paper_2311_03824_gb300 import serve as S
+    from paper_2311_03824_gb300.serve import Request
+    # request 0 (another rank) runs alone long enough for 1-4 to queue behind it
+    reqs = [Request(0, "gaussian", 2048, 512, 8, 400, 20, 20, T=20),
+            Request(1, "gaussian", 320, 48, 3, 96, 4, 22, T=20),
+            Request(2, "gaussian", 200, 100, 3, 70, 2, 23, T=20),
+            Request(3, "gaussian", 448, 32, 3, 120, 6, 24, T=20),
+            Request(4, "gaussian", 256, 64, 5, 80, 3, 25, T=20)]
+    budget = int(0.5 * torch.cuda.mem_get_info()[0])
+    alone = S.Server(budget, slots=1, keep_outputs=True).run(reqs, bench.C4Inputs())
+    srv = S.Server(budget, slots=1, keep_outputs=True, batch=4)   # the queue forms
+    batched = srv.run(reqs, bench.C4Inputs())
+    assert [r.group_size for r in batched] == [1, 3, 3, 3, 1], [(r.group, r.group_size) for r in batched]
+    for a, r in zip(alone, batched):
+        assert a.error is None and r.error is None, (a.error, r.error)
+        for x, y in zip(a.outputs, r.outputs):
+            assert np.array_equal(x, y), r.rid

@@ -118,8 +118,8 @@ def test_mix_laws():
 
 def test_compatible_gaussian_requests_are_admitted_together():
     """batch = 3: requests queued behind a Gaussian head with the same rank,
-    A_k form and iteration count join its batch (up to 3) while slots and
-    budget allow; any other request ends the batch; FIFO order is kept."""
+    A_k form and iteration count join its batch (up to 3, one slot) while the
+    budget allows; any other request ends the batch; FIFO order is kept."""
     blocker = S.Request(0, "gaussian", n=4096, q=2048, r=8, m=512, rho=40, seed=1, T=100,
                         a_dtype=L.LRS_A_FP32)
     g = dict(kind="gaussian", n=256, q=64, m=80, rho=3, seed=2, T=100)
