@@ -34,6 +34,9 @@ namespace fourier {
 
 constexpr int kFT = 512;   // threads of the frame kernels
 constexpr int kFW = kFT / 32;
+// sweep profile slots: set-up and Gram, sparse DFTs, projections and norms,
+// 2D FFTs with the frame's fills and scalings, HardThreshold, final stage
+constexpr int kFProf = 6;
 constexpr int kMaxR = 16;
 
 // ------------------------------------------------------------ complex --
@@ -62,6 +65,39 @@ __device__ __forceinline__ double2 dccmul(double2 a, double2 b) {  // conj(a) * 
   return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 __device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+// Double-float accumulation (a value carried as hi + lo, two float32 words:
+// about 48 bits of significand on the FP32 units, whose dependent operations
+// are far cheaper than FP64's on this part).  df_fma: (hi, lo) += a * b with
+// the product's rounding error from an fma and the sum's from Knuth's
+// two-sum.  df_add: (hi, lo) += (bh, bl).
+__device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float b) {
+  const float p = a * b;
+  const float pe = fmaf(a, b, -p);
+  const float s = hi + p;
+  const float bb = s - hi;
+  const float se = (hi - (s - bb)) + (p - bb);
+  hi = s;
+  lo += se + pe;
+}
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bb = s - hi;
+  const float se = (hi - (s - bb)) + (bh - bb);
+  hi = s;
+  lo += se + bl;
+}
+// warp sum of double-float values (xor butterfly: every lane ends with the
+// same value, the pairs added in a fixed order)
+__device__ __forceinline__ double warp_sum_df(float hi, float lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+    df_add(hi, lo, oh, ol);
+  }
+  return static_cast<double>(hi) + static_cast<double>(lo);
+}
 
 __device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
@@ -237,11 +273,15 @@ struct FArgs {
   int* err;
   float2* vecs;         // q x 3m: y, and the two m-vectors of the sweep, when
                         // they do not fit shared memory beside the frame
+  unsigned long long* prof;  // optional kFProf cycle counters (thread 0 of each CTA)
 };
 
 struct FCarve {
-  size_t X, tx, ty, yv, dv, ev, msk, sp, sv, gv, G, Gi, vec, red, hist, cand, total;
+  size_t X, tx, ty, yv, dv, ev, msk, sp, sv, gv, G, Gi, vec, red, hist, cand, cl, ck, total;
 };
+
+// HardThreshold candidates of the threshold filter (indices and keys)
+constexpr int kCandCap = 512;
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -263,10 +303,12 @@ __host__ __device__ inline FCarve fcarve(const Geo& g, int m, int rho, bool vglo
   c.sv = o;   o += al16(static_cast<size_t>(rh) * 8);
   c.gv = o;   o += al16(static_cast<size_t>(rh) * 8);
   c.G = o;    o += al16(4 * kMaxR * kMaxR * 16);     // G, L, Linv, Ginv (complex FP64)
-  c.vec = o;  o += al16(4 * kMaxR * 16);
+  c.vec = o;  o += al16((64 + kMaxR * kMaxR) * 16);   // c, x, scalars, iL; r x r products
   c.red = o;  o += al16(static_cast<size_t>(kFW) * 2 * kMaxR * 4 + 64);
   c.hist = o; o += al16(256 * 4 + 64);
   c.cand = o; o += al16(static_cast<size_t>(2 * rh + 64) * 4);
+  c.cl = o;   o += al16(static_cast<size_t>(kCandCap) * 4);
+  c.ck = o;   o += al16(static_cast<size_t>(kCandCap) * 4);
   c.total = o;
   return c;
 }
@@ -292,6 +334,8 @@ struct FCtx {
   float* red;
   int* hist;
   int* cand;
+  int* cl;         // threshold-filter candidates: pixels
+  unsigned* ck;    // and their keys
   const float2* FU;
   int* err;
 };
@@ -341,8 +385,8 @@ __device__ void fls_solve(const FCtx& C, const float2* v) {
     }
   }
   __syncthreads();
-  if (threadIdx.x < r) {
-    double sx = 0, sy = 0;
+  if (threadIdx.x < r) {  // the warps' partials in warp order (float32, like the sums)
+    float sx = 0.f, sy = 0.f;
     for (int ww = 0; ww < kFW; ++ww) {
       sx += C.red[(ww * kMaxR + threadIdx.x) * 2];
       sy += C.red[(ww * kMaxR + threadIdx.x) * 2 + 1];
@@ -350,12 +394,18 @@ __device__ void fls_solve(const FCtx& C, const float2* v) {
     C.vec[threadIdx.x] = make_double2(sx, sy);
   }
   __syncthreads();
+  // x = G^{-1} c (FP64): the r x r products in parallel, then each row's sum
+  double2* prod = C.vec + 64;
+  if (threadIdx.x < r * r) {
+    const int a = threadIdx.x / r, b = threadIdx.x - a * r;
+    prod[threadIdx.x] = dcmul(C.Gi[a * kMaxR + b], C.vec[b]);
+  }
+  __syncthreads();
   if (threadIdx.x < r) {
     double2 x = make_double2(0, 0);
     for (int b = 0; b < r; ++b) {
-      const double2 t = dcmul(C.Gi[threadIdx.x * kMaxR + b], C.vec[b]);
-      x.x += t.x;
-      x.y += t.y;
+      x.x += prod[threadIdx.x * r + b].x;
+      x.y += prod[threadIdx.x * r + b].y;
     }
     C.vec[16 + threadIdx.x] = x;
   }
@@ -388,28 +438,31 @@ __device__ double fnorm2(const FCtx& C, const float2* v) {
   __syncthreads();
   if ((threadIdx.x & 31) == 0) C.red[threadIdx.x >> 5] = acc;
   __syncthreads();
-  double s = 0.0;
+  float s = 0.f;  // the warps' partials in warp order
   for (int i = 0; i < kFW; ++i) s += C.red[i];
   __syncthreads();
   return s;
 }
 
-// Hermitian Gram G = W^H W (FP64), complex Cholesky G = L L^H (lane 0, inverse
-// pivots by Newton rsqrt), L^{-1} per lane, G^{-1} = L^{-H} L^{-1}.
+// Hermitian Gram G = W^H W (products exact, sums in double-float, stored as
+// FP64), complex Cholesky G = L L^H in FP64 (lane 0, inverse pivots by
+// Newton rsqrt), L^{-1} per lane, G^{-1} = L^{-H} L^{-1}.
 __device__ void fgram_factor(const FCtx& C) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, r = C.r;
   for (int t = w; t < r * r; t += kFW) {
     const int a = t / r, b = t - a * r;
     if (b > a) continue;
-    double sx = 0, sy = 0;
+    // conj(W_ib) W_ia summed in double-float: exact products, ~48-bit sums
+    float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f;
     for (int i = lane; i < C.m; i += 32) {
       const float2 wa = W_at(C, i, a), wb = W_at(C, i, b);
-      const double2 p = dccmul(make_double2(wb.x, wb.y), make_double2(wa.x, wa.y));  // conj(W_ib) W_ia
-      sx += p.x;
-      sy += p.y;
+      df_fma(xh, xl, wb.x, wa.x);
+      df_fma(xh, xl, wb.y, wa.y);
+      df_fma(yh, yl, wb.x, wa.y);
+      df_fma(yh, yl, -wb.y, wa.x);
     }
-    sx = warp_sum(sx);
-    sy = warp_sum(sy);
+    const double sx = warp_sum_df(xh, xl);
+    const double sy = warp_sum_df(yh, yl);
     if (lane == 0) {
       C.G[a * kMaxR + b] = make_double2(sx, sy);             // G[a][b] = sum conj(W_b) W_a ... (lower)
       C.G[b * kMaxR + a] = make_double2(sx, -sy);
@@ -486,6 +539,73 @@ __device__ void fgram_factor(const FCtx& C) {
 __device__ void fhard_threshold(const FCtx& C, bool keep_values) {
   const int n = C.g.n, ld = C.g.ny + 1, rho = C.rho, lane = threadIdx.x & 31;
   int* info = C.hist + 256;
+  int* sel = C.cand;            // rho entries
+  auto key_of = [&](int e) {
+    return __float_as_uint(cabs2(C.X[frow(C.g, e) * ld + fcol(C.g, e)]));
+  };
+  // Threshold filter (with a current support, after v = s - mu g): the rho
+  // entries of the support have keys >= T0, their smallest key, so the rho
+  // largest keys are all >= T0.  The entries at or above T0 are ranked by
+  // (key descending, pixel ascending), the order of the radix path below,
+  // unless there are more than kCandCap of them.
+  if (keep_values) {
+    if (threadIdx.x < 32) {
+      unsigned mn = 0xffffffffu;
+      for (int e = lane; e < rho; e += 32) mn = min(mn, key_of(C.sp[e]));
+      mn = __reduce_min_sync(0xffffffffu, mn);
+      if (lane == 0) {
+        info[4] = static_cast<int>(mn);
+        info[5] = 0;
+      }
+    }
+    __syncthreads();
+    const unsigned T0 = static_cast<unsigned>(info[4]);
+    for (int e0 = threadIdx.x - lane; e0 < n; e0 += blockDim.x) {
+      const int e = e0 + lane;
+      unsigned key = 0u;
+      bool c = false;
+      if (e < n) {
+        key = key_of(e);
+        c = key >= T0;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, c);
+      int base = 0;
+      if (lane == 0 && bal) base = atomicAdd(&info[5], __popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (c) {
+        const int pos = base + __popc(bal & ((1u << lane) - 1u));
+        if (pos < kCandCap) {
+          C.cl[pos] = e;
+          C.ck[pos] = key;
+        }
+      }
+    }
+    __syncthreads();
+    const int cnt = info[5];
+    if (cnt >= rho && cnt <= kCandCap) {
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int e = C.cl[t];
+        const unsigned ke = C.ck[t];
+        int rank = 0;
+        for (int u = 0; u < cnt; ++u) {
+          const unsigned ku = C.ck[u];
+          rank += (ku > ke) || (ku == ke && C.cl[u] < e);
+        }
+        if (rank < rho) sel[rank] = e;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < rho; t += blockDim.x) {  // ascending by pixel
+        const int e = sel[t];
+        int pos = 0;
+        for (int u = 0; u < rho; ++u) pos += sel[u] < e;
+        C.sp[pos] = e;
+        C.sv[pos] = C.X[frow(C.g, e) * ld + fcol(C.g, e)];
+      }
+      __syncthreads();
+      return;
+    }
+    __syncthreads();
+  }
   unsigned prefix = 0, mask = 0;
   if (threadIdx.x == 0) info[1] = rho;
   for (int shift = 24; shift >= 0; shift -= 8) {
@@ -534,7 +654,6 @@ __device__ void fhard_threshold(const FCtx& C, bool keep_values) {
   }
   const unsigned T = prefix;
   const int need = info[1];
-  int* sel = C.cand;            // rho entries
   int* ties = C.cand + rho + 8; // tie candidates (bounded below)
   const int tie_cap = 56;
   if (threadIdx.x == 0) { info[2] = 0; info[3] = 0; }
@@ -604,6 +723,8 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
   C.red = reinterpret_cast<float*>(sm + cv.red);
   C.hist = reinterpret_cast<int*>(sm + cv.hist);
   C.cand = reinterpret_cast<int*>(sm + cv.cand);
+  C.cl = reinterpret_cast<int*>(sm + cv.cl);
+  C.ck = reinterpret_cast<unsigned*>(sm + cv.ck);
   C.FU = a.FU;
   C.err = a.err;
   const int k = C.k, m = C.m, r = C.r, rho = C.rho, n = C.g.n, ld = C.g.ny + 1;
@@ -623,8 +744,19 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
     }
   }
   __syncthreads();
+  // phase cycle counters (profile): thread 0's clock between the CTA's phases
+  unsigned long long pc[kFProf] = {};
+  long long tl = clock64();
+  auto mark = [&](int slot) {
+    if (a.prof && threadIdx.x == 0) {
+      const long long t = clock64();
+      pc[slot] += static_cast<unsigned long long>(t - tl);
+      tl = t;
+    }
+  };
   const bool project = (a.mode != kModeInit);
   if (project) fgram_factor(C);
+  mark(0);
   const int tau = (a.mode == kModeLS || rho == 0) ? 0 : a.tau;
   for (int it = 0; it < tau; ++it) {
     const bool zero_start = (a.mode == kModeInit && it == 0);
@@ -637,7 +769,9 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
       __syncthreads();
       for (int i = threadIdx.x; i < m; i += blockDim.x) C.dv[i] = csub(C.dv[i], C.yv[i]);
       __syncthreads();
+      mark(1);
       if (project) fproj(C, C.dv);
+      mark(2);
     }
     // g = A^H u: zero-filled frame, inverse 2D FFT
     for (int e = threadIdx.x; e < C.g.nx * ld; e += blockDim.x) C.X[e] = make_float2(0.f, 0.f);
@@ -648,28 +782,33 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
     }
     __syncthreads();
     fft2_smem(C.X, C.g.nx, C.g.ny, C.g.lnx, C.g.lny, C.tx, C.ty, true);
+    mark(3);
     if (zero_start) {
       fhard_threshold(C, false);  // support of the zero start: the rho largest |g|
     }
     // g on the support, ||g_G||^2, A g_G
     __syncthreads();
+    mark(4);
     for (int e = threadIdx.x; e < rho; e += blockDim.x) {
       const int p = C.sp[e];
       C.gv[e] = C.X[(frow(C.g, p)) * ld + (fcol(C.g, p))];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int e = 0; e < rho; ++e)
-        s += static_cast<double>(C.gv[e].x) * C.gv[e].x + static_cast<double>(C.gv[e].y) * C.gv[e].y;
-      C.vec[48] = make_double2(s, 0.0);
+    if (threadIdx.x < 32) {  // ||g_G||^2: lanes over the support, a fixed butterfly
+      float s = 0.f;
+      for (int e = threadIdx.x; e < rho; e += 32) s += cabs2(C.gv[e]);
+      s = warp_sumf(s);
+      if (threadIdx.x == 0) C.vec[48] = make_double2(s, 0.0);
     }
     __syncthreads();
+    mark(2);
     sparse_dft(C, C.sp, C.gv, rho, C.ev);
     __syncthreads();
+    mark(1);
     if (project) fproj(C, C.ev);
     const double num = C.vec[48].x;
     const double den = fnorm2(C, C.ev);
+    mark(2);
     if (!(den > 0.0)) break;
     double mu = num / den;
     if (!isfinite(mu)) {
@@ -689,7 +828,9 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
       x = cadd(x, C.sv[e]);
     }
     __syncthreads();
+    mark(3);
     fhard_threshold(C, true);
+    mark(4);
   }
   // ---- final stage ----
   sparse_dft(C, C.sp, C.sv, rho, C.dv);  // A s
@@ -731,6 +872,9 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
       a.S_val[static_cast<size_t>(k) * rho + pos] = C.sv[e];
     }
   }
+  mark(5);
+  if (a.prof && threadIdx.x == 0)
+    for (int slot = 0; slot < kFProf; ++slot) atomicAdd(a.prof + slot, pc[slot]);
 }
 
 // K[l][w] = sum over the (k, i) with mask_k[i] = w of res_k[i] conj(b_k[l]).
@@ -1085,6 +1229,7 @@ struct FourierSolver {
   double* eta = nullptr;
   double* scal = nullptr;
   float2* vecs = nullptr;  // the sweep's m-vectors in global memory (large m)
+  unsigned long long* prof = nullptr;  // kFProf sweep cycle counters (profiling)
   size_t smem = 0;
 };
 
@@ -1194,7 +1339,7 @@ void fourier_destroy(FourierSolver* F) {
   if (!F) return;
   void* ps[] = {F->y, F->mask, F->U, F->FU, F->B, F->S_idx, F->S_val, F->RES, F->H, F->K, F->grad,
                 F->Z, F->Z2, F->twx, F->twy, F->iptr, F->ilist, F->err, F->part, F->rfac, F->eta, F->scal,
-                F->vecs};
+                F->vecs, F->prof};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, F->s);
   cudaStreamSynchronize(F->s);
@@ -1268,6 +1413,7 @@ static cudaError_t launch_fsweep(FourierSolver* F, int mode, int tau) {
   a.twy = F->twy;
   a.err = F->err;
   a.vecs = F->vecs;
+  a.prof = F->prof;
   fsweep_kernel<<<F->q, kFT, F->smem, F->s>>>(a);
   return cudaGetLastError();
 }
@@ -1431,5 +1577,26 @@ double fourier_eta(FourierSolver* F) {
   return F->t ? v : 0.0;
 }
 int fourier_t(FourierSolver* F) { return F->t; }
+
+// Sweep cycle counters: enable (allocate, zero) and read-and-zero.
+int fourier_prof_enable(FourierSolver* F) {
+  if (F->prof) return 0;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&F->prof), sizeof(unsigned long long) * kFProf, F->s) !=
+      cudaSuccess)
+    return 3;  // LRS_ERR_OOM
+  return cudaMemsetAsync(F->prof, 0, sizeof(unsigned long long) * kFProf, F->s) == cudaSuccess
+             ? 0
+             : 4;  // LRS_ERR_CUDA
+}
+int fourier_prof_read(FourierSolver* F, unsigned long long* out, int len) {
+  if (!F->prof) return 2;  // LRS_ERR_STATE
+  const int n = len < kFProf ? len : kFProf;
+  if (cudaMemcpyAsync(out, F->prof, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, F->s) !=
+          cudaSuccess ||
+      cudaMemsetAsync(F->prof, 0, sizeof(unsigned long long) * kFProf, F->s) != cudaSuccess ||
+      cudaStreamSynchronize(F->s) != cudaSuccess)
+    return 4;  // LRS_ERR_CUDA
+  return 0;
+}
 
 }  // namespace lrs

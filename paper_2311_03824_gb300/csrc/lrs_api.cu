@@ -34,6 +34,8 @@ int fourier_set_state(FourierSolver* F, const void* U, const void* B, const int*
                       const void* S_val, int t, double eta, int mem_kind);
 double fourier_eta(FourierSolver* F);
 int fourier_t(FourierSolver* F);
+int fourier_prof_enable(FourierSolver* F);
+int fourier_prof_read(FourierSolver* F, unsigned long long* out, int len);
 }  // namespace lrs
 
 namespace {
@@ -803,6 +805,14 @@ lrs_status lrs_create(int64_t n, int64_t m, int64_t q, int32_t r, int32_t rho, l
       if (h->F) fourier_destroy(h->F);
       delete h;
       return fail(st, "lrs_create: " + msg);
+    }
+    if (o.profile == 2) {
+      const int pst = fourier_prof_enable(h->F);
+      if (pst) {
+        fourier_destroy(h->F);
+        delete h;
+        return fail(static_cast<lrs_status>(pst), "lrs_create: profile counters");
+      }
     }
     *out = h;
     return LRS_OK;
@@ -1588,6 +1598,13 @@ lrs_status lrs_phase_times(lrs_t h, double* out4) {
 
 lrs_status lrs_sweep_trace(lrs_t h, uint64_t* out, int64_t len) {
   if (!h || !out || len < 0) return fail(LRS_ERR_ARG, "lrs_sweep_trace: bad argument");
+  if (h->F) {
+    if (h->opt.profile != 2) return fail(LRS_ERR_STATE, "lrs_sweep_trace: create the handle with profile = 2");
+    const int st = fourier_prof_read(h->F, reinterpret_cast<unsigned long long*>(out),
+                                     static_cast<int>(std::min<int64_t>(len, 1 << 20)));
+    if (st) return fail(static_cast<lrs_status>(st), "lrs_sweep_trace: reading the counters failed");
+    return LRS_OK;
+  }
   if ((h->engine == 2 || h->engine == 3) && h->opt.profile == 2) {
     const int64_t n = std::min<int64_t>(len, h->engine == 3 ? kResProf : kTaskProf);
     CUDA_TRY(cudaMemcpyAsync(out, h->tprof, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, h->stream));

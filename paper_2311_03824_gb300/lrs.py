@@ -287,6 +287,17 @@ def lrs_task_profile(h):
     return dict(zip(TASK_PROF, (int(v) for v in out)))
 
 
+FOURIER_PROF = ["setup_gram", "sparse_dft", "proj_norms", "fft", "hard_threshold", "final"]
+
+
+def lrs_fourier_profile(h):
+    """DFT sweep counters: thread-0 cycles of every CTA per phase (handle
+    created with profile=2)."""
+    out = np.zeros(len(FOURIER_PROF), np.uint64)
+    _check(lib().lrs_sweep_trace(h, out.ctypes.data_as(_P), out.size))
+    return dict(zip(FOURIER_PROF, (int(v) for v in out)))
+
+
 def lrs_describe(h):
     buf = ctypes.create_string_buffer(512)
     _check(lib().lrs_describe(h, buf, 512))
