@@ -221,6 +221,7 @@ __device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const flo
 
 struct Geo {
   int nx, ny, lnx, lny, n;  // lnx / lny: log2 of a power-of-two side, else -1
+  int L, sxL, syL, lL;      // L = lcm(nx, ny), L / nx, L / ny, log2 L (or -1)
 };
 
 // row, column of pixel e = row * ny + column, and an index modulo nx (ny)
@@ -230,6 +231,7 @@ __device__ __forceinline__ int fcol(const Geo& g, int e) {
 }
 __device__ __forceinline__ int fwrapx(const Geo& g, int v) { return g.lnx >= 0 ? v & (g.nx - 1) : v % g.nx; }
 __device__ __forceinline__ int fwrapy(const Geo& g, int v) { return g.lny >= 0 ? v & (g.ny - 1) : v % g.ny; }
+__device__ __forceinline__ int fwrapL(const Geo& g, int v) { return g.lL >= 0 ? v & (g.L - 1) : v % g.L; }
 
 // out[f] = F2(in[f]) (or F2^H) for frames f; frames are n-vectors in natural
 // row-major order (pixel kx*ny + ky), frame f at in + f*n.
@@ -270,6 +272,7 @@ struct FArgs {
   float2* H;            // q x n: L0 columns A^H (y - A s) (initialisation)
   const float2* twx;
   const float2* twy;
+  const float2* twl;    // exp(-2 pi i j / L), j < L = lcm(nx, ny)
   int* err;
   float2* vecs;         // q x 3m: y, and the two m-vectors of the sweep, when
                         // they do not fit shared memory beside the frame
@@ -277,7 +280,7 @@ struct FArgs {
 };
 
 struct FCarve {
-  size_t X, tx, ty, yv, dv, ev, msk, sp, sv, gv, G, Gi, vec, red, hist, cand, cl, ck, total;
+  size_t X, tx, ty, tl, yv, dv, ev, msk, sp, pq, spo, sv, gv, G, Gi, vec, red, hist, cand, cl, ck, total;
 };
 
 // HardThreshold candidates of the threshold filter (indices and keys)
@@ -295,11 +298,14 @@ __host__ __device__ inline FCarve fcarve(const Geo& g, int m, int rho, bool vglo
   c.X = o;    o += al16(static_cast<size_t>(g.nx) * (g.ny + 1) * 8);
   c.tx = o;   o += al16(static_cast<size_t>(g.nx) * 8);
   c.ty = o;   o += al16(static_cast<size_t>(g.ny) * 8);
+  c.tl = o;   o += al16(static_cast<size_t>(g.L) * 8);
   c.yv = o;   o += mv;
   c.dv = o;   o += mv;
   c.ev = o;   o += mv;
   c.msk = o;  o += al16(static_cast<size_t>(m) * 4);
   c.sp = o;   o += al16(static_cast<size_t>(rh) * 4 + 16);
+  c.pq = o;   o += al16(static_cast<size_t>(rh) * 8);
+  c.spo = o;  o += al16(static_cast<size_t>(rh) * 4);
   c.sv = o;   o += al16(static_cast<size_t>(rh) * 8);
   c.gv = o;   o += al16(static_cast<size_t>(rh) * 8);
   c.G = o;    o += al16(4 * kMaxR * kMaxR * 16);     // G, L, Linv, Ginv (complex FP64)
@@ -319,6 +325,9 @@ struct FCtx {
   float2* X;
   float2* tx;      // full-period twiddles exp(-2 pi i k / nx), k < nx
   float2* ty;
+  float2* tl;      // exp(-2 pi i j / L), j < L = lcm(nx, ny)
+  int2* pq;        // sparse DFT: a support pixel's row and column scaled to L
+  int* spo;        // the support before the last HardThreshold
   float2* yv;
   float2* dv;
   float2* ev;
@@ -345,18 +354,24 @@ __device__ __forceinline__ float2 W_at(const FCtx& C, int i, int l) {
 }
 
 // out[i] = (A x)[i] for the sparse frame x with pixels p[e], values v[e]
-// (direct DFT of the nonzeros at the sampled frequencies).
+// (direct DFT of the nonzeros at the sampled frequencies).  With L =
+// lcm(nx, ny), exp(-2 pi i (kx px / nx + ky py / ny)) is the one table entry
+// j = (kx px L/nx + ky py L/ny) mod L: one look-up and one complex
+// multiply-add per term.
 __device__ void sparse_dft(const FCtx& C, const int* p, const float2* v, int nnz, float2* out) {
   const float sc = rsqrtf(static_cast<float>(C.g.n));
+  for (int e = threadIdx.x; e < nnz; e += blockDim.x) {
+    const int pe = p[e];
+    C.pq[e] = make_int2(frow(C.g, pe) * C.g.sxL, fcol(C.g, pe) * C.g.syL);
+  }
+  __syncthreads();
   for (int i = threadIdx.x; i < C.m; i += blockDim.x) {
     const int om = C.msk[i];
     const int kx = frow(C.g, om), ky = fcol(C.g, om);
     float2 acc = make_float2(0.f, 0.f);
     for (int e = 0; e < nnz; ++e) {
-      const int pe = p[e];
-      const int px = frow(C.g, pe), py = fcol(C.g, pe);
-      const float2 w = cmul(C.tx[fwrapx(C.g, kx * px)], C.ty[fwrapy(C.g, ky * py)]);
-      acc = cfma(w, v[e], acc);
+      const int2 q = C.pq[e];
+      acc = cfma(C.tl[fwrapL(C.g, kx * q.x + ky * q.y)], v[e], acc);
     }
     out[i] = make_float2(acc.x * sc, acc.y * sc);
   }
@@ -701,6 +716,9 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
   C.X = reinterpret_cast<float2*>(sm + cv.X);
   C.tx = reinterpret_cast<float2*>(sm + cv.tx);
   C.ty = reinterpret_cast<float2*>(sm + cv.ty);
+  C.tl = reinterpret_cast<float2*>(sm + cv.tl);
+  C.pq = reinterpret_cast<int2*>(sm + cv.pq);
+  C.spo = reinterpret_cast<int*>(sm + cv.spo);
   if (a.vecs) {
     float2* v = a.vecs + static_cast<size_t>(blockIdx.x) * 3 * a.m;
     C.yv = v;
@@ -730,6 +748,7 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
   const int k = C.k, m = C.m, r = C.r, rho = C.rho, n = C.g.n, ld = C.g.ny + 1;
   for (int t = threadIdx.x; t < C.g.nx; t += blockDim.x) C.tx[t] = a.twx[t];
   for (int t = threadIdx.x; t < C.g.ny; t += blockDim.x) C.ty[t] = a.twy[t];
+  for (int t = threadIdx.x; t < C.g.L; t += blockDim.x) C.tl[t] = a.twl[t];
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     C.yv[i] = a.y[static_cast<size_t>(k) * m + i];
     C.msk[i] = a.mask[static_cast<size_t>(k) * m + i];
@@ -758,12 +777,24 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
   if (project) fgram_factor(C);
   mark(0);
   const int tau = (a.mode == kModeLS || rho == 0) ? 0 : a.tau;
+  // After a sweep whose HardThreshold kept the support, s_new = s - mu g_G on
+  // it, so the next u = P_perp(A s_new - y) is u - mu P_perp A g_G, both of
+  // which the sweep still holds (dv, ev): no sparse DFT or projection then.
+  bool kept = false;
+  float mu_prev = 0.f;
   for (int it = 0; it < tau; ++it) {
     const bool zero_start = (a.mode == kModeInit && it == 0);
     // u = P_perp (A s - y)
     if (zero_start) {
       for (int i = threadIdx.x; i < m; i += blockDim.x) C.dv[i] = make_float2(-C.yv[i].x, -C.yv[i].y);
       __syncthreads();
+    } else if (kept) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const float2 d = C.dv[i], e = C.ev[i];
+        C.dv[i] = make_float2(fmaf(-mu_prev, e.x, d.x), fmaf(-mu_prev, e.y, d.y));
+      }
+      __syncthreads();
+      mark(2);
     } else {
       sparse_dft(C, C.sp, C.sv, rho, C.dv);
       __syncthreads();
@@ -829,7 +860,13 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
     }
     __syncthreads();
     mark(3);
+    for (int e = threadIdx.x; e < rho; e += blockDim.x) C.spo[e] = C.sp[e];
+    __syncthreads();
     fhard_threshold(C, true);
+    int same = 1;
+    for (int e = threadIdx.x; e < rho; e += blockDim.x) same &= C.spo[e] == C.sp[e];
+    kept = __syncthreads_and(same) != 0;
+    mu_prev = muf;
     mark(4);
   }
   // ---- final stage ----
@@ -1222,6 +1259,7 @@ struct FourierSolver {
   // device
   float2 *y = nullptr, *U = nullptr, *FU = nullptr, *B = nullptr, *S_val = nullptr, *RES = nullptr,
          *H = nullptr, *K = nullptr, *grad = nullptr, *Z = nullptr, *Z2 = nullptr, *twx = nullptr,
+         *twl = nullptr,
          *twy = nullptr;
   int *mask = nullptr, *S_idx = nullptr, *iptr = nullptr, *ilist = nullptr, *err = nullptr;
   double2* part = nullptr;
@@ -1260,6 +1298,18 @@ FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int 
   F->g.lnx = ilog2(nx);
   F->g.lny = ilog2(ny);
   F->g.n = nx * ny;
+  {
+    int a = nx, b = ny;  // L = lcm(nx, ny) by Euclid's gcd
+    while (b) {
+      const int t = a % b;
+      a = b;
+      b = t;
+    }
+    F->g.L = nx / a * ny;
+    F->g.sxL = F->g.L / nx;
+    F->g.syL = F->g.L / ny;
+    F->g.lL = ilog2(F->g.L);
+  }
   F->m = m;
   F->q = q;
   F->r = r;
@@ -1303,6 +1353,7 @@ FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int 
             cudaMallocAsync(reinterpret_cast<void**>(&F->Z), sizeof(float2) * n * r, F->s) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&F->Z2), sizeof(float2) * n * r, F->s) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&F->twx), sizeof(float2) * nx, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->twl), sizeof(float2) * F->g.L, F->s) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&F->twy), sizeof(float2) * ny, F->s) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&F->iptr), sizeof(int) * (n + 1), F->s) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&F->ilist), sizeof(int) * m * q, F->s) == cudaSuccess &&
@@ -1328,6 +1379,12 @@ FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int 
     tw[k] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
   }
   cudaMemcpyAsync(F->twy, tw.data(), sizeof(float2) * ny, cudaMemcpyHostToDevice, F->s);
+  std::vector<float2> twl(F->g.L);
+  for (int k = 0; k < F->g.L; ++k) {
+    const double a = -2.0 * M_PI * k / F->g.L;
+    twl[k] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+  }
+  cudaMemcpyAsync(F->twl, twl.data(), sizeof(float2) * F->g.L, cudaMemcpyHostToDevice, F->s);
   cudaMemsetAsync(F->err, 0, 8, F->s);
   cudaMemsetAsync(F->S_idx, 0, sizeof(int) * q * std::max(1, rho), F->s);
   cudaMemsetAsync(F->S_val, 0, sizeof(float2) * q * std::max(1, rho), F->s);
@@ -1338,7 +1395,8 @@ FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int 
 void fourier_destroy(FourierSolver* F) {
   if (!F) return;
   void* ps[] = {F->y, F->mask, F->U, F->FU, F->B, F->S_idx, F->S_val, F->RES, F->H, F->K, F->grad,
-                F->Z, F->Z2, F->twx, F->twy, F->iptr, F->ilist, F->err, F->part, F->rfac, F->eta, F->scal,
+                F->Z, F->Z2, F->twx, F->twy, F->twl, F->iptr, F->ilist, F->err, F->part, F->rfac, F->eta,
+                F->scal,
                 F->vecs, F->prof};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, F->s);
@@ -1411,6 +1469,7 @@ static cudaError_t launch_fsweep(FourierSolver* F, int mode, int tau) {
   a.H = F->H;
   a.twx = F->twx;
   a.twy = F->twy;
+  a.twl = F->twl;
   a.err = F->err;
   a.vecs = F->vecs;
   a.prof = F->prof;
