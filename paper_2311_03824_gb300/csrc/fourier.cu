@@ -997,7 +997,6 @@ __global__ void cchol_fin_kernel(int r, int nblk, const double2* __restrict__ pa
                                  double2* __restrict__ Rinv, int* err) {
   __shared__ double2 N[kMaxR * kMaxR], Lw[kMaxR * kMaxR], Li[kMaxR * kMaxR];
   __shared__ double iL[kMaxR];
-  __shared__ int okf;
   // the partials of each entry: one warp per entry, lanes over the blocks,
   // butterfly sum (fixed order); then warp 0 factors
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -1047,7 +1046,6 @@ __global__ void cchol_fin_kernel(int r, int nblk, const double2* __restrict__ pa
         iL[i] = 1.0;
       }
     }
-    okf = ok;
   }
   __syncwarp();
   if (lane < r) {
@@ -1134,109 +1132,99 @@ __global__ void ceta_kernel(int r, int nblk, const double2* __restrict__ part, d
   *eta = (nrm > 0.0) ? c_eta / nrm : 0.0;
 }
 
-// ---- FP64 complex subspace iteration on L0 (rows of H are its columns) ----
-// P[k][l] = sum_j conj(H[k][j]) U[j][l]   (U FP64 complex, column-major l-major)
-__global__ void cdproject_kernel(int n, int q, int r, const float2* __restrict__ H,
-                                 const double2* __restrict__ U, double2* __restrict__ P) {
+// ---- subspace iteration of the initialisation: float32 products -----------
+// P[k][l] = sum_j conj(H[k][j]) U[l][j] (U column-major: column l contiguous)
+__global__ void cproject_kernel(int n, int q, int r, const float2* __restrict__ H,
+                                const float2* __restrict__ U, float2* __restrict__ P) {
   const int lane = threadIdx.x & 31;
   const int k = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (k >= q) return;
   for (int l = 0; l < r; ++l) {
-    double sx = 0, sy = 0;
+    float sx = 0.f, sy = 0.f;
     for (int j = lane; j < n; j += 32) {
       const float2 h = H[static_cast<size_t>(k) * n + j];
-      const double2 u = U[static_cast<size_t>(l) * n + j];
-      sx += h.x * u.x + h.y * u.y;
-      sy += h.x * u.y - h.y * u.x;
+      const float2 u = U[static_cast<size_t>(l) * n + j];
+      sx = fmaf(h.x, u.x, fmaf(h.y, u.y, sx));
+      sy = fmaf(h.x, u.y, fmaf(-h.y, u.x, sy));
     }
-    sx = warp_sum(sx);
-    sy = warp_sum(sy);
-    if (lane == 0) P[static_cast<size_t>(k) * r + l] = make_double2(sx, sy);
+    sx = warp_sumf(sx);
+    sy = warp_sumf(sy);
+    if (lane == 0) P[static_cast<size_t>(k) * r + l] = make_float2(sx, sy);
   }
 }
-// Z[j][l] = sum_k H[k][j] P[k][l]
-__global__ void cdgrad_kernel(int n, int q, int r, const float2* __restrict__ H,
-                              const double2* __restrict__ P, double2* __restrict__ Z) {
+// Z[l][j] = sum_k H[k][j] P[k][l] (k in order)
+__global__ void cgrad_kernel(int n, int q, int r, const float2* __restrict__ H,
+                             const float2* __restrict__ P, float2* __restrict__ Z) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  double2 acc[kMaxR];
-  for (int l = 0; l < kMaxR; ++l) acc[l] = make_double2(0, 0);
+  float2 acc[kMaxR];
+  for (int l = 0; l < kMaxR; ++l) acc[l] = make_float2(0.f, 0.f);
   for (int k = 0; k < q; ++k) {
     const float2 h = H[static_cast<size_t>(k) * n + j];
-    for (int l = 0; l < r; ++l) {
-      const double2 p = P[static_cast<size_t>(k) * r + l];
-      acc[l].x += h.x * p.x - h.y * p.y;
-      acc[l].y += h.x * p.y + h.y * p.x;
-    }
+    for (int l = 0; l < r; ++l) acc[l] = cfma(h, P[static_cast<size_t>(k) * r + l], acc[l]);
   }
   for (int l = 0; l < r; ++l) Z[static_cast<size_t>(l) * n + j] = acc[l];
 }
-__global__ void cdgram_part_kernel(int n, int r, const double2* __restrict__ X,
-                                   double2* __restrict__ part) {
+// subspace change ||Un - Uo (Uo^H Un)||_F^2 of float32 blocks, in FP64:
+// partials of D = Uo^H Un per row block, then per row block the residual
+// (every block adds the partials of D in block order), then their sum
+__global__ void coverlap_part_kernel(int n, int r, const float2* __restrict__ Uo,
+                                     const float2* __restrict__ Un, double2* __restrict__ part) {
   const int rows = (n + gridDim.x - 1) / gridDim.x;
   const int lo = blockIdx.x * rows, hi = min(n, lo + rows);
   const int t = threadIdx.x, a = t / kMaxR, b = t - (t / kMaxR) * kMaxR;
-  if (a >= r || b > a) return;
+  if (a >= r || b >= r) return;
   double sx = 0, sy = 0;
   for (int j = lo; j < hi; ++j) {
-    const double2 xa = X[static_cast<size_t>(a) * n + j], xb = X[static_cast<size_t>(b) * n + j];
-    sx += xa.x * xb.x + xa.y * xb.y;
-    sy += xa.x * xb.y - xa.y * xb.x;
+    const float2 x = Uo[static_cast<size_t>(a) * n + j], y = Un[static_cast<size_t>(b) * n + j];
+    sx += static_cast<double>(x.x) * y.x + static_cast<double>(x.y) * y.y;
+    sy += static_cast<double>(x.x) * y.y - static_cast<double>(x.y) * y.x;
   }
   part[static_cast<size_t>(blockIdx.x) * r * r + a * r + b] = make_double2(sx, sy);
 }
-__global__ void cdapply_kernel(int n, int r, const double2* __restrict__ X,
-                               const double2* __restrict__ Rinv, double2* __restrict__ Y,
-                               float2* __restrict__ Yf) {
-  const size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
-  if (t >= static_cast<size_t>(n) * r) return;
-  const int l = static_cast<int>(t / n), j = static_cast<int>(t - static_cast<size_t>(l) * n);
-  double sx = 0, sy = 0;
-  for (int p = 0; p <= l; ++p) {
-    const double2 x = X[static_cast<size_t>(p) * n + j];
-    const double2 q = Rinv[p * r + l];
-    sx += x.x * q.x - x.y * q.y;
-    sy += x.x * q.y + x.y * q.x;
-  }
-  Y[t] = make_double2(sx, sy);
-  if (Yf) Yf[t] = make_float2(static_cast<float>(sx), static_cast<float>(sy));
-}
-// ||Unew - Uold (Uold^H Unew)||_F^2 (FP64)
-__global__ void cdchange_kernel(int n, int r, const double2* __restrict__ Uo,
-                                const double2* __restrict__ Un, double* __restrict__ out) {
+__global__ void cresid_part_kernel(int n, int r, int nblk, const double2* __restrict__ part,
+                                   const float2* __restrict__ Uo, const float2* __restrict__ Un,
+                                   double* __restrict__ rpart) {
   __shared__ double2 D[kMaxR * kMaxR];
   __shared__ double red[32];
-  // D = Uo^H Un by one block (n small enough for this one-off check)
   for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
-    const int a = t / r, b = t - a * r;
-    double sx = 0, sy = 0;
-    for (int j = 0; j < n; ++j) {
-      const double2 x = Uo[static_cast<size_t>(a) * n + j], y = Un[static_cast<size_t>(b) * n + j];
-      sx += x.x * y.x + x.y * y.y;
-      sy += x.x * y.y - x.y * y.x;
+    double2 s = make_double2(0, 0);
+    for (int k = 0; k < nblk; ++k) {
+      s.x += part[static_cast<size_t>(k) * r * r + t].x;
+      s.y += part[static_cast<size_t>(k) * r * r + t].y;
     }
-    D[t] = make_double2(sx, sy);
+    D[t] = s;
   }
   __syncthreads();
+  const int rows = (n + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * rows, hi = min(n, lo + rows);
   double acc = 0.0;
-  for (size_t t = threadIdx.x; t < static_cast<size_t>(n) * r; t += blockDim.x) {
-    const int l = static_cast<int>(t / n), j = static_cast<int>(t - static_cast<size_t>(l) * n);
-    double2 s = Un[t];
+  for (int e = threadIdx.x; e < (hi - lo) * r; e += blockDim.x) {
+    const int l = e / (hi - lo), j = lo + (e - l * (hi - lo));
+    const float2 un = Un[static_cast<size_t>(l) * n + j];
+    double sx = un.x, sy = un.y;
     for (int p = 0; p < r; ++p) {
-      const double2 u = Uo[static_cast<size_t>(p) * n + j], d = D[p * r + l];
-      s.x -= u.x * d.x - u.y * d.y;
-      s.y -= u.x * d.y + u.y * d.x;
+      const float2 u = Uo[static_cast<size_t>(p) * n + j];
+      const double2 d = D[p * r + l];
+      sx -= u.x * d.x - u.y * d.y;
+      sy -= u.x * d.y + u.y * d.x;
     }
-    acc += s.x * s.x + s.y * s.y;
+    acc += sx * sx + sy * sy;
   }
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0;
-    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s += red[w];
-    *out = s;
+    double s2 = 0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s2 += red[w];
+    rpart[blockIdx.x] = s2;
   }
+}
+__global__ void csum_fin_kernel(int nblk, const double* __restrict__ rpart, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double s2 = 0;
+  for (int k = 0; k < nblk; ++k) s2 += rpart[k];
+  *out = s2;
 }
 
 }  // namespace fourier
@@ -1509,16 +1497,20 @@ int fourier_check_error(FourierSolver* F, std::string* msg) {
 int fourier_init(FourierSolver* F, std::string* msg) {
   const int n = F->g.n, q = F->q, r = F->r;
   cudaError_t e = launch_fsweep(F, kModeInit, F->tau0);  // s_k and the L0 columns in H
-  // FP64 complex subspace iteration for the top-r left singular vectors of L0
+  // Complex subspace iteration for the top-r left singular vectors of L0:
+  // float32 products P = L0^H U and Z = L0 P, complex Cholesky-QR2 of Z with
+  // FP64 r x r factors, until the subspace moves by less than power_tol or by
+  // less than the float32 resolution of U (4 eps sqrt(n r): a converged
+  // float32 iteration moves U by its rounding).
   const size_t nr = static_cast<size_t>(n) * r;
-  double2 *Ud = nullptr, *Uo = nullptr, *Zd = nullptr, *Td = nullptr, *Pd = nullptr;
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Ud), nr * 16, F->s);
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Uo), nr * 16, F->s);
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Zd), nr * 16, F->s);
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Td), nr * 16, F->s);
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Pd), static_cast<size_t>(q) * r * 16, F->s);
+  float2 *Uo = nullptr, *Zf = nullptr, *Pf = nullptr;
+  double* rpart = nullptr;
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Uo), nr * 8, F->s);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Zf), nr * 8, F->s);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Pf), static_cast<size_t>(q) * r * 8, F->s);
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&rpart), F->nblk * sizeof(double), F->s);
   // start: deterministic complex Gaussian block
-  std::vector<double2> st(nr);
+  std::vector<float2> st(nr);
   uint64_t sd = F->seed * 0x9E3779B97F4A7C15ull + 0x2545F4914F6CDD1Dull;
   auto nxt = [&]() {
     uint64_t z = (sd += 0x9E3779B97F4A7C15ull);
@@ -1529,37 +1521,33 @@ int fourier_init(FourierSolver* F, std::string* msg) {
   for (auto& v : st) {
     const double u1 = ((nxt() >> 11) + 1.0) * 0x1.0p-53, u2 = (nxt() >> 11) * 0x1.0p-53;
     const double rad = std::sqrt(-2.0 * std::log(u1));
-    v = make_double2(rad * std::cos(6.283185307179586 * u2), rad * std::sin(6.283185307179586 * u2));
+    v = make_float2(static_cast<float>(rad * std::cos(6.283185307179586 * u2)),
+                    static_cast<float>(rad * std::sin(6.283185307179586 * u2)));
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(Zd, st.data(), nr * 16, cudaMemcpyHostToDevice, F->s);
-  const unsigned nb = static_cast<unsigned>((nr + 255) / 256);
-  auto dqr = [&](const double2* Zin, double2* Uout, float2* Uf) {
-    cdgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, Zin, F->part);
-    cchol_fin_kernel<<<1, 256, 0, F->s>>>(r, F->nblk, F->part, F->rfac, F->err);
-    cdapply_kernel<<<nb, 256, 0, F->s>>>(n, r, Zin, F->rfac, Td, nullptr);
-    cdgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, Td, F->part);
-    cchol_fin_kernel<<<1, 256, 0, F->s>>>(r, F->nblk, F->part, F->rfac + r * r, F->err);
-    cdapply_kernel<<<nb, 256, 0, F->s>>>(n, r, Td, F->rfac + r * r, Uout, Uf);
-  };
-  if (e == cudaSuccess) dqr(Zd, Ud, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Zf, st.data(), nr * 8, cudaMemcpyHostToDevice, F->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(F->s);  // the host block may go
+  if (e == cudaSuccess) e = ccholqr2(F, Zf, F->U);
+  const double floor_tol = 4.0 * 0x1.0p-24 * std::sqrt(static_cast<double>(nr));
+  const double tol = std::max(F->power_tol, floor_tol);
   for (int it = 0; it < F->power_iters && e == cudaSuccess; ++it) {
-    e = cudaMemcpyAsync(Uo, Ud, nr * 16, cudaMemcpyDeviceToDevice, F->s);
-    cdproject_kernel<<<(q + 7) / 8, 256, 0, F->s>>>(n, q, r, F->H, Uo, Pd);
-    cdgrad_kernel<<<(n + 255) / 256, 256, 0, F->s>>>(n, q, r, F->H, Pd, Zd);
-    dqr(Zd, Ud, nullptr);
-    if (e == cudaSuccess) e = cudaGetLastError();
+    e = cudaMemcpyAsync(Uo, F->U, nr * 8, cudaMemcpyDeviceToDevice, F->s);
+    cproject_kernel<<<(q + 7) / 8, 256, 0, F->s>>>(n, q, r, F->H, Uo, Pf);
+    cgrad_kernel<<<(n + 255) / 256, 256, 0, F->s>>>(n, q, r, F->H, Pf, Zf);
+    if (e == cudaSuccess) e = ccholqr2(F, Zf, F->U);
     if (e == cudaSuccess && ((it % 5) == 4 || it + 1 == F->power_iters)) {
-      cdchange_kernel<<<1, 1024, 0, F->s>>>(n, r, Uo, Ud, F->scal);
+      coverlap_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, Uo, F->U, F->part);
+      cresid_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, F->nblk, F->part, Uo, F->U, rpart);
+      csum_fin_kernel<<<1, 32, 0, F->s>>>(F->nblk, rpart, F->scal);
       double chg2 = 0;
-      e = cudaMemcpyAsync(&chg2, F->scal, sizeof(double), cudaMemcpyDeviceToHost, F->s);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&chg2, F->scal, sizeof(double), cudaMemcpyDeviceToHost, F->s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(F->s);
-      if (e == cudaSuccess && std::sqrt(std::max(0.0, chg2)) < F->power_tol) break;
+      if (e == cudaSuccess && std::sqrt(std::max(0.0, chg2)) < tol) break;
     }
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(Zd, Ud, nr * 16, cudaMemcpyDeviceToDevice, F->s);
-  if (e == cudaSuccess) dqr(Zd, Ud, F->U);
   if (e == cudaSuccess) e = cudaStreamSynchronize(F->s);
-  for (double2* p : {Ud, Uo, Zd, Td, Pd})
+  for (void* p : {static_cast<void*>(Uo), static_cast<void*>(Zf), static_cast<void*>(Pf),
+                  static_cast<void*>(rpart)})
     if (p) cudaFreeAsync(p, F->s);
   // b_k = (A_k U0)^+ (y_k - A_k s_k)
   if (e == cudaSuccess) e = fft_frames(F, F->U, F->FU, r, false);

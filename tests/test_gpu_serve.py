@@ -83,13 +83,13 @@ def test_batched_requests_equal_alone_bitwise():
             Request(3, "gaussian", 448, 32, 3, 120, 6, 24, T=20),
             Request(4, "gaussian", 256, 64, 5, 80, 3, 25, T=20)]
     budget = int(0.5 * torch.cuda.mem_get_info()[0])
-    alone = S.Server(budget, slots=1, keep_outputs=True).run(reqs, bench.C4Inputs())
+    gen = bench.C4Inputs()
+    inputs = {rq.rid: gen(rq) for rq in reqs}     # made before: submissions take no time
+    alone = S.Server(budget, slots=1, keep_outputs=True).run(reqs, lambda rq: inputs[rq.rid])
     srv = S.Server(budget, slots=1, keep_outputs=True, batch=4)   # the queue forms
-    batched = srv.run(reqs, bench.C4Inputs())
-    # which of 1-4 have arrived when request 0 finishes depends on timing;
-    # the grouping rule itself is checked deterministically on the CPU
-    assert batched[0].group_size == 1 and batched[4].group_size == 1
-    assert max(r.group_size for r in batched) >= 2, [(r.group, r.group_size) for r in batched]
+    batched = srv.run(reqs, lambda rq: inputs[rq.rid])
+    # 1-4 are queued while request 0 runs: 1-3 (rank 3) form one batch
+    assert [r.group_size for r in batched] == [1, 3, 3, 3, 1], [(r.group, r.group_size) for r in batched]
     for a, r in zip(alone, batched):
         assert a.error is None and r.error is None, (a.error, r.error)
         for x, y in zip(a.outputs, r.outputs):
