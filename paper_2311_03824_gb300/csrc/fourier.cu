@@ -145,6 +145,29 @@ __device__ void dft_direct_smem(float2* X, int nx, int ny, bool rows, const floa
   __syncthreads();
 }
 
+// Two radix-2 decimation-in-time stages s and s + 1 on the quad x0, x1, x2,
+// x3 at offsets 0, h, 2h, 3h (h = 2^s) of a block of 4h: stage s pairs
+// (x0, x1) and (x2, x3) with twiddle w1, stage s + 1 pairs (x0, x2) with w2a
+// and (x1, x3) with w2b.  Every element gets the operations of the two
+// stages run one after the other, in the same order, so the result is that
+// of two single-stage passes, with one shared-memory round trip instead of two.
+__device__ __forceinline__ void stage_pair(float2& x0, float2& x1, float2& x2, float2& x3,
+                                           float2 w1, float2 w2a, float2 w2b, bool inverse) {
+  if (inverse) {
+    w1.y = -w1.y;
+    w2a.y = -w2a.y;
+    w2b.y = -w2b.y;
+  }
+  const float2 a0 = x0, a2 = x2;
+  const float2 c1 = cmul(x1, w1), c3 = cmul(x3, w1);
+  const float2 b0 = cadd(a0, c1), b1 = csub(a0, c1), b2 = cadd(a2, c3), b3 = csub(a2, c3);
+  const float2 d2 = cmul(b2, w2a), d3 = cmul(b3, w2b);
+  x0 = cadd(b0, d2);
+  x2 = csub(b0, d2);
+  x1 = cadd(b1, d3);
+  x3 = csub(b1, d3);
+}
+
 // In-place unitary 2D FFT of the frame X (nx rows x ny columns, row stride
 // ny + 1 complex) in shared memory: along the rows, then along the columns,
 // each by radix-2 decimation in time (a power-of-two side, lny / lnx its
@@ -168,7 +191,19 @@ __device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const flo
       }
     }
     __syncthreads();
-    for (int s = 0; s < lny; ++s) {
+    int s = 0;
+    for (; s + 1 < lny; s += 2) {  // stages s and s + 1 in one pass
+      const int h = 1 << s, q4 = ny / 4;
+      for (int b = threadIdx.x; b < n / 4; b += blockDim.x) {
+        const int row = b / q4, t = b - row * q4;
+        const int j = t & (h - 1), i0 = ((t >> s) << (s + 2)) + j;
+        float2* x = X + row * ld;
+        stage_pair(x[i0], x[i0 + h], x[i0 + 2 * h], x[i0 + 3 * h], ty[j * (ny >> (s + 1))],
+                   ty[j * (ny >> (s + 2))], ty[(j + h) * (ny >> (s + 2))], inverse);
+      }
+      __syncthreads();
+    }
+    if (s < lny) {  // a last single stage
       const int half = 1 << s, step = ny >> (s + 1);
       for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
         const int row = b / (ny / 2), t = b - row * (ny / 2);
@@ -196,7 +231,19 @@ __device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const flo
       }
     }
     __syncthreads();
-    for (int s = 0; s < lnx; ++s) {
+    int s = 0;
+    for (; s + 1 < lnx; s += 2) {  // stages s and s + 1 in one pass
+      const int h = 1 << s;
+      for (int b = threadIdx.x; b < n / 4; b += blockDim.x) {
+        const int col = b % ny, t = b / ny;
+        const int j = t & (h - 1), i0 = ((t >> s) << (s + 2)) + j;
+        stage_pair(X[i0 * ld + col], X[(i0 + h) * ld + col], X[(i0 + 2 * h) * ld + col],
+                   X[(i0 + 3 * h) * ld + col], tx[j * (nx >> (s + 1))], tx[j * (nx >> (s + 2))],
+                   tx[(j + h) * (nx >> (s + 2))], inverse);
+      }
+      __syncthreads();
+    }
+    if (s < lnx) {  // a last single stage
       const int half = 1 << s, step = nx >> (s + 1);
       for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
         const int col = b % ny, t = b / ny;
