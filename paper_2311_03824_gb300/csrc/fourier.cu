@@ -403,8 +403,9 @@ __device__ __forceinline__ float2 W_at(const FCtx& C, int i, int l) {
 // out[i] = (A x)[i] for the sparse frame x with pixels p[e], values v[e]
 // (direct DFT of the nonzeros at the sampled frequencies).  With L =
 // lcm(nx, ny), exp(-2 pi i (kx px / nx + ky py / ny)) is the one table entry
-// j = (kx px L/nx + ky py L/ny) mod L: one look-up and one complex
-// multiply-add per term.
+// j = (kx px L/nx + ky py L/ny) mod L: one look-up (or, along a run of
+// pixels in a row, one complex multiply) and one complex multiply-add per
+// term.
 __device__ void sparse_dft(const FCtx& C, const int* p, const float2* v, int nnz, float2* out) {
   const float sc = rsqrtf(static_cast<float>(C.g.n));
   for (int e = threadIdx.x; e < nnz; e += blockDim.x) {
@@ -415,10 +416,19 @@ __device__ void sparse_dft(const FCtx& C, const int* p, const float2* v, int nnz
   for (int i = threadIdx.x; i < C.m; i += blockDim.x) {
     const int om = C.msk[i];
     const int kx = frow(C.g, om), ky = fcol(C.g, om);
-    float2 acc = make_float2(0.f, 0.f);
+    // a pixel right after the previous one in its row (blob supports; the
+    // pixels are ascending) takes the previous twiddle times exp(-2 pi i ky / ny)
+    const float2 wy = C.tl[fwrapL(C.g, ky * C.g.syL)];
+    float2 acc = make_float2(0.f, 0.f), w = make_float2(1.f, 0.f);
+    int2 qp = make_int2(-1, -1);
     for (int e = 0; e < nnz; ++e) {
       const int2 q = C.pq[e];
-      acc = cfma(C.tl[fwrapL(C.g, kx * q.x + ky * q.y)], v[e], acc);
+      if (q.x == qp.x && q.y == qp.y + C.g.syL)  // the same for every lane
+        w = cmul(w, wy);
+      else
+        w = C.tl[fwrapL(C.g, kx * q.x + ky * q.y)];
+      qp = q;
+      acc = cfma(w, v[e], acc);
     }
     out[i] = make_float2(acc.x * sc, acc.y * sc);
   }
