@@ -34,9 +34,12 @@ namespace fourier {
 
 constexpr int kFT = 512;   // threads of the frame kernels
 constexpr int kFW = kFT / 32;
-// sweep profile slots: set-up and Gram, sparse DFTs, projections and norms,
-// 2D FFTs with the frame's fills and scalings, HardThreshold, final stage
-constexpr int kFProf = 6;
+// sweep profile slots: set-up and Gram, sparse DFTs, norms and vector
+// updates, 2D FFTs with the frame's fills and scalings, HardThreshold, final
+// stage, projections' W^H v and G^-1 solve, projections' v - W x
+constexpr int kFProf = 8;
+// static shared memory of the sweep (its profile counters), an upper bound
+constexpr size_t kFStaticSmem = 256;
 constexpr int kMaxR = 16;
 
 // ------------------------------------------------------------ complex --
@@ -498,11 +501,6 @@ __device__ void fapply_Wx(const FCtx& C, float2* v, float sign) {
   __syncthreads();
 }
 
-__device__ void fproj(const FCtx& C, float2* v) {
-  fls_solve(C, v);
-  fapply_Wx(C, v, -1.f);
-}
-
 __device__ double fnorm2(const FCtx& C, const float2* v) {
   float acc = 0.f;
   for (int i = threadIdx.x; i < C.m; i += blockDim.x) acc += cabs2(v[i]);
@@ -821,8 +819,13 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
   }
   __syncthreads();
   // phase cycle counters (profile): thread 0's clock between the CTA's phases
-  unsigned long long pc[kFProf] = {};
-  long long tl = clock64();
+  // (kept in shared memory: registers are scarce in this kernel)
+  __shared__ unsigned long long pc[kFProf];
+  __shared__ long long tl;
+  if (a.prof && threadIdx.x == 0) {
+    for (int slot = 0; slot < kFProf; ++slot) pc[slot] = 0ull;
+    tl = clock64();
+  }
   auto mark = [&](int slot) {
     if (a.prof && threadIdx.x == 0) {
       const long long t = clock64();
@@ -858,8 +861,12 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
       for (int i = threadIdx.x; i < m; i += blockDim.x) C.dv[i] = csub(C.dv[i], C.yv[i]);
       __syncthreads();
       mark(1);
-      if (project) fproj(C, C.dv);
-      mark(2);
+      if (project) {
+        fls_solve(C, C.dv);
+        mark(6);
+        fapply_Wx(C, C.dv, -1.f);
+        mark(7);
+      }
     }
     // g = A^H u: zero-filled frame, inverse 2D FFT
     for (int e = threadIdx.x; e < C.g.nx * ld; e += blockDim.x) C.X[e] = make_float2(0.f, 0.f);
@@ -893,7 +900,12 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
     sparse_dft(C, C.sp, C.gv, rho, C.ev);
     __syncthreads();
     mark(1);
-    if (project) fproj(C, C.ev);
+    if (project) {
+      fls_solve(C, C.ev);
+      mark(6);
+      fapply_Wx(C, C.ev, -1.f);
+      mark(7);
+    }
     const double num = C.vec[48].x;
     const double den = fnorm2(C, C.ev);
     mark(2);
@@ -1373,14 +1385,17 @@ FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   // the m-vectors go to global memory when they do not fit beside the frame
-  const bool vglob = F->smem > static_cast<size_t>(optin);
+  // (the sweep also holds kFStaticSmem bytes of static shared memory)
+  const size_t room = static_cast<size_t>(optin) - kFStaticSmem;
+  const bool vglob = F->smem > room;
   if (vglob) F->smem = fcarve(F->g, m, rho, true).total;
-  if (F->smem > static_cast<size_t>(optin) || fft_smem(F->g) > static_cast<size_t>(optin)) {
+  if (F->smem > room || fft_smem(F->g) > static_cast<size_t>(optin)) {
     *msg = "frame too large for one CTA's shared memory (n <= 16384 fits)";
     delete F;
     return nullptr;
   }
-  cudaFuncSetAttribute(fsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_limit());
+  cudaFuncSetAttribute(fsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       smem_optin_limit() - static_cast<int>(kFStaticSmem));
   cudaFuncSetAttribute(fft_frames_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        smem_optin_limit());
   const size_t rr = static_cast<size_t>(r) * r;

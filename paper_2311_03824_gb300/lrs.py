@@ -287,7 +287,8 @@ def lrs_task_profile(h):
     return dict(zip(TASK_PROF, (int(v) for v in out)))
 
 
-FOURIER_PROF = ["setup_gram", "sparse_dft", "proj_norms", "fft", "hard_threshold", "final"]
+FOURIER_PROF = ["setup_gram", "sparse_dft", "norms_updates", "fft", "hard_threshold", "final",
+                "proj_solve", "proj_apply"]
 
 
 def lrs_fourier_profile(h):
