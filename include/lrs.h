@@ -399,7 +399,8 @@ typedef struct lrs_server_s* lrs_server_t;
  * flight leave of hbm_budget; each runs lrs_create, lrs_set_measurements,
  * lrs_init, lrs_iterate(T) and lrs_get on its worker's stream, so the work
  * of concurrent requests overlaps on the GPU, and a Gaussian request's
- * persistent sweep gets max(16, 2 x SMs / requests running) CTAs.  With
+ * persistent sweep gets max(16, 2 x SMs / requests running) CTAs, and its
+ * steady iterations replay as a CUDA graph.  With
  * batch > 1, when the admitted request is Gaussian the queued requests right
  * behind it of the same rank, A_k form and iteration count that also fit
  * (budget) are admitted with it, up to `batch` of them, into the same slot,

@@ -85,6 +85,8 @@ lrs_status run_request(const lrs_request& rq, int grid, cudaStream_t stream, std
   lrs_options o = rq.opt;
   o.stream = stream;
   if (rq.kind == LRS_OP_GAUSSIAN && o.grid == 0) o.grid = grid;
+  // steady iterations replay as a CUDA graph (bit-identical to eager launches)
+  if (rq.kind == LRS_OP_GAUSSIAN && !o.reduce && !o.profile) o.use_graph = 1;
   lrs_t h = nullptr;
   lrs_status st = lrs_create(rq.n, rq.m, rq.q, rq.r, rq.rho, rq.kind, &o, &h);
   if (st == LRS_OK) st = lrs_set_measurements(h, rq.y, rq.A_or_mask, rq.mem_kind);

@@ -188,3 +188,42 @@ def test_noisy_measurements(engine):
     err = np.linalg.norm(x_of(U, B, S_idx, S_val, inst.q) - inst.Xstar) / np.linalg.norm(inst.Xstar)
     assert abs(err - log.err[-1]) <= 1e-3 * log.err[-1], (err, log.err[-1])
     assert err < inst.noise
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_ill_conditioned_least_squares(engine):
+    """m = r + 1 rows per column: the Grams G_k = W_k^T W_k of the LS step
+    (Eq. bk_LS) reach cond 1e4-2e5 at these iterates.  One-step parity as
+    everywhere, and per column of cond(G_k) > 1e3: b_k within max(1e-5, 10 x
+    the float32 step's own deviation of that column) of the FP64 step."""
+    import oracle.altgdmin_lrs as O
+    from tests.gpu_helpers import cast_state, probe_step, set_gpu_state, state_of
+    inst = GaussianInstance(n=40, q=200, r=6, m=7, rho=1, seed=77)
+    T = 4
+    P = Problem.gaussian(inst)
+    _, log = oracle_run(inst, T)
+    s = new_solver(inst, engine=engine)
+    checked, worst = 0, 0.0
+    try:
+        recs = one_step(P, s, log, range(T))
+        for t in range(1, T):
+            st = state_of(log, t, P.n)
+            st64, _, dec, _ = probe_step(P, st)
+            st32 = cast_state(st, np.float32)
+            O.iterate_alg1(P.op32, P.y32(P.Y), st32, P.rho)
+            set_gpu_state(s, st, False)
+            s.iterate(1)
+            _, B1, _, _ = s.get()
+            W = inst.A.astype(np.float64) @ st.U
+            cond = np.array([np.linalg.cond(w.T @ w) for w in W])
+            for k in np.where((cond > 1e3) & dec)[0]:
+                b64 = st64.B[:, k]
+                d32 = np.linalg.norm(st32.B[:, k] - b64) / np.linalg.norm(b64)
+                dg = np.linalg.norm(B1[:, k] - b64) / np.linalg.norm(b64)
+                assert dg <= max(1e-5, 10 * d32), (t, k, cond[k], dg, d32)
+                checked += 1
+                worst = max(worst, cond[k])
+    finally:
+        s.close()
+    check_records(recs, min_whole=2)
+    assert checked >= 20 and worst > 1e4, (checked, worst)
