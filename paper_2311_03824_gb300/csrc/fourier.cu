@@ -1088,27 +1088,35 @@ __global__ void cchol_fin_kernel(int r, int nblk, const double2* __restrict__ pa
   }
   __syncthreads();
   if (threadIdx.x >= 32) return;
-  // X^H X = N^T?  (X^H X)[i][j] = sum conj(x_i) x_j = N[i][j]: factor N = L L^H
-  if (lane == 0) {
-    int ok = 1;
-    for (int j = 0; j < r && ok; ++j) {
-      double s = N[j * kMaxR + j].x;
-      for (int p = 0; p < j; ++p) s -= Lw[j * kMaxR + p].x * Lw[j * kMaxR + p].x + Lw[j * kMaxR + p].y * Lw[j * kMaxR + p].y;
-      if (!(s > 1e-13 * N[j * kMaxR + j].x) || !(s < 1e300)) { ok = 0; break; }
-      const double ij = rsqrt_newton(s);
-      Lw[j * kMaxR + j] = make_double2(s * ij, 0);
-      iL[j] = ij;
-      for (int i = j + 1; i < r; ++i) {
-        double2 t = N[i * kMaxR + j];
-        for (int p = 0; p < j; ++p) {
-          const double2 a = Lw[i * kMaxR + p], b = Lw[j * kMaxR + p];
-          t.x -= a.x * b.x + a.y * b.y;
-          t.y -= a.y * b.x - a.x * b.y;
-        }
-        Lw[i * kMaxR + j] = make_double2(t.x * ij, t.y * ij);
+  // (X^H X)[i][j] = sum conj(x_i) x_j = N[i][j]: factor N = L L^H, column j
+  // by the lanes i >= j at once (lane j's entry is the pivot)
+  bool ok = true;
+  for (int j = 0; j < r; ++j) {
+    double2 t = make_double2(0.0, 0.0);
+    if (lane >= j && lane < r) {
+      t = N[lane * kMaxR + j];
+      for (int p = 0; p < j; ++p) {
+        const double2 a = Lw[lane * kMaxR + p], b = Lw[j * kMaxR + p];
+        t.x -= a.x * b.x + a.y * b.y;
+        t.y -= a.y * b.x - a.x * b.y;
       }
     }
-    if (!ok) {
+    const double s = __shfl_sync(0xffffffffu, t.x, j);
+    if (!(s > 1e-13 * N[j * kMaxR + j].x) || !(s < 1e300)) {
+      ok = false;
+      break;
+    }
+    const double ij = rsqrt_newton(s);
+    if (lane == j) {
+      Lw[j * kMaxR + j] = make_double2(s * ij, 0);
+      iL[j] = ij;
+    } else if (lane > j && lane < r) {
+      Lw[lane * kMaxR + j] = make_double2(t.x * ij, t.y * ij);
+    }
+    __syncwarp();
+  }
+  if (!ok) {
+    if (lane == 0) {
       report_error(err, kErrNotSPD, -1);
       for (int i = 0; i < r; ++i) {
         for (int p = 0; p < r; ++p) Lw[i * kMaxR + p] = make_double2(i == p ? 1.0 : 0.0, 0);
@@ -1153,86 +1161,158 @@ __global__ void capply_kernel(int n, int r, const float2* __restrict__ X,
   }
   Y[t] = make_float2(static_cast<float>(sx), static_cast<float>(sy));
 }
-// eta = c / sqrt(lambda_max(grad^H grad)) via the real 2r x 2r symmetric
-// embedding [[Re, -Im], [Im, Re]] of the Hermitian Gram (cyclic Jacobi).
+// eta = c / sqrt(lambda_max(grad^H grad)), from the real 2r x 2r symmetric
+// embedding [[Re, -Im], [Im, Re]] of the Hermitian Gram (every eigenvalue of
+// the Gram appears twice).  The embedding is summed in FP64; a cyclic Jacobi
+// in FP32 (normalised by the largest diagonal entry) gives an eigenvector v of
+// the largest eigenvalue, and lambda_max is the FP64 Rayleigh quotient
+// v^T A v / v^T v, whose error is second order in v's error.
 __global__ void ceta_kernel(int r, int nblk, const double2* __restrict__ part, double c_eta,
                             double* __restrict__ eta) {
-  if (threadIdx.x != 0) return;
-  double A[2 * kMaxR][2 * kMaxR];
-  const int R2 = 2 * r;
-  for (int a = 0; a < r; ++a)
-    for (int b = 0; b <= a; ++b) {
-      double sx = 0, sy = 0;
-      for (int k = 0; k < nblk; ++k) {
-        const double2 v = part[static_cast<size_t>(k) * r * r + a * r + b];
-        sx += v.x;
-        sy += v.y;
-      }
-      // N[a][b] = sx + i sy, N[b][a] = sx - i sy
-      A[a][b] = sx; A[b][a] = sx; A[a + r][b + r] = sx; A[b + r][a + r] = sx;
-      A[a + r][b] = sy; A[b][a + r] = sy; A[a][b + r] = -sy; A[b + r][a] = -sy;
+  __shared__ double A[2 * kMaxR][2 * kMaxR];
+  __shared__ float Af[2 * kMaxR][2 * kMaxR + 1], V[2 * kMaxR][2 * kMaxR + 1];
+  __shared__ int best;
+  const int R2 = 2 * r, lane = threadIdx.x;
+  if (lane >= 32) return;
+  // entries of the lower triangle, each summed over the blocks in order
+  for (int t = lane; t < r * r; t += 32) {
+    const int a = t / r, b = t - a * r;
+    if (b > a) continue;
+    double sx = 0, sy = 0;
+    for (int k = 0; k < nblk; ++k) {
+      const double2 v = part[static_cast<size_t>(k) * r * r + a * r + b];
+      sx += v.x;
+      sy += v.y;
     }
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0, diag = 0.0;
-    for (int a = 0; a < R2; ++a)
-      for (int b = 0; b < R2; ++b) (a == b ? diag : off) += A[a][b] * A[a][b];
-    if (off <= 1e-30 * diag) break;
-    for (int p = 0; p < R2 - 1; ++p)
-      for (int q2 = p + 1; q2 < R2; ++q2) {
-        if (A[p][q2] == 0.0) continue;
-        const double th = (A[q2][q2] - A[p][p]) / (2.0 * A[p][q2]);
-        const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
-        for (int kk = 0; kk < R2; ++kk) {
-          const double akp = A[kk][p], akq = A[kk][q2];
-          A[kk][p] = cs * akp - sn * akq;
-          A[kk][q2] = sn * akp + cs * akq;
-        }
-        for (int kk = 0; kk < R2; ++kk) {
-          const double apk = A[p][kk], aqk = A[q2][kk];
-          A[p][kk] = cs * apk - sn * aqk;
-          A[q2][kk] = sn * apk + cs * aqk;
-        }
-      }
+    // N[a][b] = sx + i sy, N[b][a] = sx - i sy
+    A[a][b] = sx; A[b][a] = sx; A[a + r][b + r] = sx; A[b + r][a + r] = sx;
+    A[a + r][b] = sy; A[b][a + r] = sy; A[a][b + r] = -sy; A[b + r][a] = -sy;
   }
-  double lmax = 0.0;
-  for (int a = 0; a < R2; ++a) lmax = fmax(lmax, A[a][a]);
-  const double nrm = sqrt(lmax);
-  *eta = (nrm > 0.0) ? c_eta / nrm : 0.0;
+  __syncwarp();
+  if (lane == 0) {
+    double dmax = 0.0;
+    for (int a = 0; a < R2; ++a) dmax = fmax(dmax, A[a][a]);
+    const double sc = dmax > 0.0 ? 1.0 / dmax : 0.0;
+    for (int a = 0; a < R2; ++a)
+      for (int b = 0; b < R2; ++b) {
+        Af[a][b] = static_cast<float>(A[a][b] * sc);
+        V[a][b] = a == b ? 1.f : 0.f;
+      }
+    for (int sweep = 0; sweep < 30; ++sweep) {
+      float off = 0.f, diag = 0.f;
+      for (int a = 0; a < R2; ++a)
+        for (int b = 0; b < R2; ++b) (a == b ? diag : off) += Af[a][b] * Af[a][b];
+      if (off <= 1e-13f * diag) break;
+      for (int p = 0; p < R2 - 1; ++p)
+        for (int q2 = p + 1; q2 < R2; ++q2) {
+          const float apq = Af[p][q2];
+          if (apq == 0.f) continue;
+          const float th = (Af[q2][q2] - Af[p][p]) / (2.f * apq);
+          const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
+          const float cs = 1.f / sqrtf(t * t + 1.f), sn = t * cs;
+          for (int kk = 0; kk < R2; ++kk) {
+            const float akp = Af[kk][p], akq = Af[kk][q2];
+            Af[kk][p] = cs * akp - sn * akq;
+            Af[kk][q2] = sn * akp + cs * akq;
+            const float vkp = V[kk][p], vkq = V[kk][q2];
+            V[kk][p] = cs * vkp - sn * vkq;
+            V[kk][q2] = sn * vkp + cs * vkq;
+          }
+          for (int kk = 0; kk < R2; ++kk) {
+            const float apk = Af[p][kk], aqk = Af[q2][kk];
+            Af[p][kk] = cs * apk - sn * aqk;
+            Af[q2][kk] = sn * apk + cs * aqk;
+          }
+        }
+    }
+    int bi = 0;
+    for (int a = 1; a < R2; ++a)
+      if (Af[a][a] > Af[bi][bi]) bi = a;
+    best = bi;
+  }
+  __syncwarp();
+  // Rayleigh quotient in FP64: lane a holds (A v)_a v_a and v_a^2
+  double num = 0.0, den = 0.0;
+  if (lane < R2) {
+    double y = 0.0;
+    for (int b = 0; b < R2; ++b) y += A[lane][b] * static_cast<double>(V[b][best]);
+    const double va = V[lane][best];
+    num = y * va;
+    den = va * va;
+  }
+  num = warp_sum(num);
+  den = warp_sum(den);
+  if (lane == 0) {
+    const double lmax = den > 0.0 ? fmax(0.0, num / den) : 0.0;
+    const double nrm = sqrt(lmax);
+    *eta = (nrm > 0.0) ? c_eta / nrm : 0.0;
+  }
 }
 
 // ---- subspace iteration of the initialisation: float32 products -----------
-// P[k][l] = sum_j conj(H[k][j]) U[l][j] (U column-major: column l contiguous)
-__global__ void cproject_kernel(int n, int q, int r, const float2* __restrict__ H,
-                                const float2* __restrict__ U, float2* __restrict__ P) {
-  const int lane = threadIdx.x & 31;
-  const int k = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (k >= q) return;
-  for (int l = 0; l < r; ++l) {
-    float sx = 0.f, sy = 0.f;
-    for (int j = lane; j < n; j += 32) {
-      const float2 h = H[static_cast<size_t>(k) * n + j];
-      const float2 u = U[static_cast<size_t>(l) * n + j];
-      sx = fmaf(h.x, u.x, fmaf(h.y, u.y, sx));
-      sy = fmaf(h.x, u.y, fmaf(-h.y, u.x, sy));
-    }
-    sx = warp_sumf(sx);
-    sy = warp_sumf(sy);
-    if (lane == 0) P[static_cast<size_t>(k) * r + l] = make_float2(sx, sy);
+// P[k][l] = sum_j conj(H[k][j]) U[l][j] (U column-major: column l contiguous):
+// one block per column k, threads over j with all r sums at once (H read
+// once), then the warps' sums added in warp order
+__global__ void __launch_bounds__(256) cproject_kernel(int n, int q, int r,
+                                                       const float2* __restrict__ H,
+                                                       const float2* __restrict__ U,
+                                                       float2* __restrict__ P) {
+  __shared__ float2 red[8][kMaxR];
+  const int k = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float2 acc[kMaxR];
+#pragma unroll
+  for (int l = 0; l < kMaxR; ++l) acc[l] = make_float2(0.f, 0.f);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const float2 h = H[static_cast<size_t>(k) * n + j];
+#pragma unroll
+    for (int l = 0; l < kMaxR; ++l)
+      if (l < r) acc[l] = ccfma(h, U[static_cast<size_t>(l) * n + j], acc[l]);
+  }
+#pragma unroll
+  for (int l = 0; l < kMaxR; ++l) {
+    if (l >= r) break;
+    const float sx = warp_sumf(acc[l].x), sy = warp_sumf(acc[l].y);
+    if (lane == 0) red[w][l] = make_float2(sx, sy);
+  }
+  __syncthreads();
+  if (threadIdx.x < r) {
+    float2 s = make_float2(0.f, 0.f);
+    for (int ww = 0; ww < static_cast<int>(blockDim.x >> 5); ++ww) s = cadd(s, red[ww][threadIdx.x]);
+    P[static_cast<size_t>(k) * r + threadIdx.x] = s;
   }
 }
 // Z[l][j] = sum_k H[k][j] P[k][l] (k in order)
-__global__ void cgrad_kernel(int n, int q, int r, const float2* __restrict__ H,
-                             const float2* __restrict__ P, float2* __restrict__ Z) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+// Z[l][j] = sum_k H[k][j] P[k][l]: a block holds 32 columns j; its 8 warps
+// take contiguous runs of k, and their sums are added in warp (k) order
+__global__ void __launch_bounds__(256) cgrad_kernel(int n, int q, int r,
+                                                    const float2* __restrict__ H,
+                                                    const float2* __restrict__ P,
+                                                    float2* __restrict__ Z) {
+  __shared__ float2 red[8][kMaxR][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  const int per = (q + 7) / 8, k0 = w * per, k1 = min(q, k0 + per);
   float2 acc[kMaxR];
+#pragma unroll
   for (int l = 0; l < kMaxR; ++l) acc[l] = make_float2(0.f, 0.f);
-  for (int k = 0; k < q; ++k) {
-    const float2 h = H[static_cast<size_t>(k) * n + j];
-    for (int l = 0; l < r; ++l) acc[l] = cfma(h, P[static_cast<size_t>(k) * r + l], acc[l]);
-  }
-  for (int l = 0; l < r; ++l) Z[static_cast<size_t>(l) * n + j] = acc[l];
+  if (j < n)
+    for (int k = k0; k < k1; ++k) {
+      const float2 h = H[static_cast<size_t>(k) * n + j];
+#pragma unroll
+      for (int l = 0; l < kMaxR; ++l)
+        if (l < r) acc[l] = cfma(h, P[static_cast<size_t>(k) * r + l], acc[l]);
+    }
+#pragma unroll
+  for (int l = 0; l < kMaxR; ++l)
+    if (l < r) red[w][l][lane] = acc[l];
+  __syncthreads();
+  // thread (l, lane) of the first r warps adds the 8 runs in order
+  if (w < 8 && j < n)
+    for (int l = w; l < r; l += 8) {
+      float2 s = red[0][l][lane];
+      for (int ww = 1; ww < 8; ++ww) s = cadd(s, red[ww][l][lane]);
+      Z[static_cast<size_t>(l) * n + j] = s;
+    }
 }
 // subspace change ||Un - Uo (Uo^H Un)||_F^2 of float32 blocks, in FP64:
 // partials of D = Uo^H Un per row block, then per row block the residual
@@ -1603,8 +1683,8 @@ int fourier_init(FourierSolver* F, std::string* msg) {
   const double tol = std::max(F->power_tol, floor_tol);
   for (int it = 0; it < F->power_iters && e == cudaSuccess; ++it) {
     e = cudaMemcpyAsync(Uo, F->U, nr * 8, cudaMemcpyDeviceToDevice, F->s);
-    cproject_kernel<<<(q + 7) / 8, 256, 0, F->s>>>(n, q, r, F->H, Uo, Pf);
-    cgrad_kernel<<<(n + 255) / 256, 256, 0, F->s>>>(n, q, r, F->H, Pf, Zf);
+    cproject_kernel<<<q, 256, 0, F->s>>>(n, q, r, F->H, Uo, Pf);
+    cgrad_kernel<<<(n + 31) / 32, 256, 0, F->s>>>(n, q, r, F->H, Pf, Zf);
     if (e == cudaSuccess) e = ccholqr2(F, Zf, F->U);
     if (e == cudaSuccess && ((it % 5) == 4 || it + 1 == F->power_iters)) {
       coverlap_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, Uo, F->U, F->part);
