@@ -183,9 +183,11 @@ __device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const flo
   if (lny < 0) {
     dft_direct_smem(X, nx, ny, true, ty, inverse);
   } else {
-    // rows: bit reversal, then lny stages
+    // rows: bit reversal, then lny stages.  Consecutive threads take the
+    // same position in consecutive rows: the row stride ny + 1 puts them in
+    // distinct banks, and they share the twiddle (a broadcast)
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
-      const int row = e / ny, j = e - row * ny;
+      const int j = lnx >= 0 ? e >> lnx : e / nx, row = e - j * nx;
       const int p = static_cast<int>(__brev(static_cast<unsigned>(j)) >> (32 - lny));
       if (lny > 0 && p > j) {
         const float2 t = X[row * ld + j];
@@ -196,9 +198,9 @@ __device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const flo
     __syncthreads();
     int s = 0;
     for (; s + 1 < lny; s += 2) {  // stages s and s + 1 in one pass
-      const int h = 1 << s, q4 = ny / 4;
+      const int h = 1 << s;
       for (int b = threadIdx.x; b < n / 4; b += blockDim.x) {
-        const int row = b / q4, t = b - row * q4;
+        const int t = lnx >= 0 ? b >> lnx : b / nx, row = b - t * nx;
         const int j = t & (h - 1), i0 = ((t >> s) << (s + 2)) + j;
         float2* x = X + row * ld;
         stage_pair(x[i0], x[i0 + h], x[i0 + 2 * h], x[i0 + 3 * h], ty[j * (ny >> (s + 1))],
@@ -209,7 +211,7 @@ __device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const flo
     if (s < lny) {  // a last single stage
       const int half = 1 << s, step = ny >> (s + 1);
       for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
-        const int row = b / (ny / 2), t = b - row * (ny / 2);
+        const int t = lnx >= 0 ? b >> lnx : b / nx, row = b - t * nx;
         const int j = t & (half - 1), i1 = ((t >> s) << (s + 1)) + j, i2 = i1 + half;
         float2 w = ty[j * step];
         if (inverse) w.y = -w.y;
@@ -225,7 +227,7 @@ __device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const flo
   } else {
     // columns: bit reversal, then lnx stages
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
-      const int i = e / ny, col = e - i * ny;
+      const int i = lny >= 0 ? e >> lny : e / ny, col = e - i * ny;
       const int p = static_cast<int>(__brev(static_cast<unsigned>(i)) >> (32 - lnx));
       if (lnx > 0 && p > i) {
         const float2 t = X[i * ld + col];
@@ -238,7 +240,7 @@ __device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const flo
     for (; s + 1 < lnx; s += 2) {  // stages s and s + 1 in one pass
       const int h = 1 << s;
       for (int b = threadIdx.x; b < n / 4; b += blockDim.x) {
-        const int col = b % ny, t = b / ny;
+        const int t = lny >= 0 ? b >> lny : b / ny, col = b - t * ny;
         const int j = t & (h - 1), i0 = ((t >> s) << (s + 2)) + j;
         stage_pair(X[i0 * ld + col], X[(i0 + h) * ld + col], X[(i0 + 2 * h) * ld + col],
                    X[(i0 + 3 * h) * ld + col], tx[j * (nx >> (s + 1))], tx[j * (nx >> (s + 2))],
@@ -249,7 +251,7 @@ __device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const flo
     if (s < lnx) {  // a last single stage
       const int half = 1 << s, step = nx >> (s + 1);
       for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
-        const int col = b % ny, t = b / ny;
+        const int t = lny >= 0 ? b >> lny : b / ny, col = b - t * ny;
         const int j = t & (half - 1), i1 = ((t >> s) << (s + 1)) + j, i2 = i1 + half;
         float2 w = tx[j * step];
         if (inverse) w.y = -w.y;
@@ -409,6 +411,7 @@ __device__ __forceinline__ float2 W_at(const FCtx& C, int i, int l) {
 // j = (kx px L/nx + ky py L/ny) mod L: one look-up (or, along a run of
 // pixels in a row, one complex multiply) and one complex multiply-add per
 // term.
+constexpr int kSdPer = 4;
 __device__ void sparse_dft(const FCtx& C, const int* p, const float2* v, int nnz, float2* out) {
   const float sc = rsqrtf(static_cast<float>(C.g.n));
   for (int e = threadIdx.x; e < nnz; e += blockDim.x) {
@@ -416,24 +419,44 @@ __device__ void sparse_dft(const FCtx& C, const int* p, const float2* v, int nnz
     C.pq[e] = make_int2(frow(C.g, pe) * C.g.sxL, fcol(C.g, pe) * C.g.syL);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < C.m; i += blockDim.x) {
-    const int om = C.msk[i];
-    const int kx = frow(C.g, om), ky = fcol(C.g, om);
-    // a pixel right after the previous one in its row (blob supports; the
-    // pixels are ascending) takes the previous twiddle times exp(-2 pi i ky / ny)
-    const float2 wy = C.tl[fwrapL(C.g, ky * C.g.syL)];
-    float2 acc = make_float2(0.f, 0.f), w = make_float2(1.f, 0.f);
+  // each thread takes kSdPer frequencies at once, so that a term's index and
+  // value (shared-memory broadcasts) serve all of them
+  const int bd = blockDim.x;
+  for (int i0 = threadIdx.x; i0 < C.m; i0 += kSdPer * bd) {
+    int kx[kSdPer], ky[kSdPer];
+    float2 wy[kSdPer], acc[kSdPer], w[kSdPer];
+#pragma unroll
+    for (int u = 0; u < kSdPer; ++u) {
+      const int i = i0 + u * bd;
+      const int om = i < C.m ? C.msk[i] : 0;
+      kx[u] = frow(C.g, om);
+      ky[u] = fcol(C.g, om);
+      // a pixel right after the previous one in its row (blob supports; the
+      // pixels are ascending) takes the previous twiddle times exp(-2 pi i ky / ny)
+      wy[u] = C.tl[fwrapL(C.g, ky[u] * C.g.syL)];
+      acc[u] = make_float2(0.f, 0.f);
+      w[u] = make_float2(1.f, 0.f);
+    }
     int2 qp = make_int2(-1, -1);
     for (int e = 0; e < nnz; ++e) {
       const int2 q = C.pq[e];
-      if (q.x == qp.x && q.y == qp.y + C.g.syL)  // the same for every lane
-        w = cmul(w, wy);
-      else
-        w = C.tl[fwrapL(C.g, kx * q.x + ky * q.y)];
+      const float2 ve = v[e];
+      if (q.x == qp.x && q.y == qp.y + C.g.syL) {  // the same for every lane
+#pragma unroll
+        for (int u = 0; u < kSdPer; ++u) w[u] = cmul(w[u], wy[u]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < kSdPer; ++u) w[u] = C.tl[fwrapL(C.g, kx[u] * q.x + ky[u] * q.y)];
+      }
       qp = q;
-      acc = cfma(w, v[e], acc);
+#pragma unroll
+      for (int u = 0; u < kSdPer; ++u) acc[u] = cfma(w[u], ve, acc[u]);
     }
-    out[i] = make_float2(acc.x * sc, acc.y * sc);
+#pragma unroll
+    for (int u = 0; u < kSdPer; ++u) {
+      const int i = i0 + u * bd;
+      if (i < C.m) out[i] = make_float2(acc[u].x * sc, acc[u].y * sc);
+    }
   }
 }
 
