@@ -328,6 +328,8 @@ struct FArgs {
   int* err;
   float2* vecs;         // q x 3m: y, and the two m-vectors of the sweep, when
                         // they do not fit shared memory beside the frame
+  float2* Wk;           // q x r x m: W_k = (F2 U)[Omega_k], gathered once per
+                        // frame and sweep (row l of frame k contiguous)
   unsigned long long* prof;  // optional kFProf cycle counters (thread 0 of each CTA)
 };
 
@@ -335,8 +337,10 @@ struct FCarve {
   size_t X, tx, ty, tl, yv, dv, ev, msk, sp, pq, spo, sv, gv, G, Gi, vec, red, hist, cand, cl, ck, total;
 };
 
-// HardThreshold candidates of the threshold filter (indices and keys)
+// HardThreshold candidates of the threshold filter (indices and keys; the
+// sort needs one thread per candidate)
 constexpr int kCandCap = 512;
+static_assert(kCandCap <= kFT, "one thread per threshold-filter candidate");
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -398,11 +402,12 @@ struct FCtx {
   int* cl;         // threshold-filter candidates: pixels
   unsigned* ck;    // and their keys
   const float2* FU;
+  float2* Wk;      // this frame's W_k (r x m, row l contiguous)
   int* err;
 };
 
 __device__ __forceinline__ float2 W_at(const FCtx& C, int i, int l) {
-  return __ldg(C.FU + static_cast<size_t>(l) * C.g.n + C.msk[i]);
+  return C.Wk[static_cast<size_t>(l) * C.m + i];
 }
 
 // out[i] = (A x)[i] for the sparse frame x with pixels p[e], values v[e]
@@ -424,19 +429,19 @@ __device__ void sparse_dft(const FCtx& C, const int* p, const float2* v, int nnz
   const int bd = blockDim.x;
   for (int i0 = threadIdx.x; i0 < C.m; i0 += kSdPer * bd) {
     int kx[kSdPer], ky[kSdPer];
-    float2 wy[kSdPer], acc[kSdPer], w[kSdPer];
+    float2 wy[kSdPer], acc[kSdPer];
 #pragma unroll
     for (int u = 0; u < kSdPer; ++u) {
       const int i = i0 + u * bd;
       const int om = i < C.m ? C.msk[i] : 0;
       kx[u] = frow(C.g, om);
       ky[u] = fcol(C.g, om);
-      // a pixel right after the previous one in its row (blob supports; the
-      // pixels are ascending) takes the previous twiddle times exp(-2 pi i ky / ny)
-      wy[u] = C.tl[fwrapL(C.g, ky[u] * C.g.syL)];
+      wy[u] = C.tl[fwrapL(C.g, ky[u] * C.g.syL)];  // exp(-2 pi i ky / ny)
       acc[u] = make_float2(0.f, 0.f);
-      w[u] = make_float2(1.f, 0.f);
     }
+    // a pixel right after the previous one in its row (blob supports; the
+    // pixels are ascending) takes the previous twiddle times exp(-2 pi i ky / ny)
+    float2 w[kSdPer];
     int2 qp = make_int2(-1, -1);
     for (int e = 0; e < nnz; ++e) {
       const int2 q = C.pq[e];
@@ -542,20 +547,39 @@ __device__ double fnorm2(const FCtx& C, const float2* v) {
 // Newton rsqrt), L^{-1} per lane, G^{-1} = L^{-H} L^{-1}.
 __device__ void fgram_factor(const FCtx& C) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, r = C.r;
-  for (int t = w; t < r * r; t += kFW) {
-    const int a = t / r, b = t - a * r;
-    if (b > a) continue;
+  // entry t of the lower triangle: (a, b), b <= a; a lane's rows i are
+  // spread over four independent double-float chains
+  for (int t = w; t < r * (r + 1) / 2; t += kFW) {
+    int a = 0, b = t;
+    while (b > a) b -= ++a;
     // conj(W_ib) W_ia summed in double-float: exact products, ~48-bit sums
-    float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f;
-    for (int i = lane; i < C.m; i += 32) {
-      const float2 wa = W_at(C, i, a), wb = W_at(C, i, b);
-      df_fma(xh, xl, wb.x, wa.x);
-      df_fma(xh, xl, wb.y, wa.y);
-      df_fma(yh, yl, wb.x, wa.y);
-      df_fma(yh, yl, -wb.y, wa.x);
+    constexpr int kCh = 4;
+    float xh[kCh], xl[kCh], yh[kCh], yl[kCh];
+#pragma unroll
+    for (int hh = 0; hh < kCh; ++hh) xh[hh] = xl[hh] = yh[hh] = yl[hh] = 0.f;
+    for (int i0 = lane; i0 < C.m; i0 += 32 * kCh) {
+      float2 wa[kCh], wb[kCh];
+#pragma unroll
+      for (int hh = 0; hh < kCh; ++hh) {
+        const int i = i0 + 32 * hh;
+        wa[hh] = i < C.m ? W_at(C, i, a) : make_float2(0.f, 0.f);
+        wb[hh] = i < C.m ? W_at(C, i, b) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int hh = 0; hh < kCh; ++hh) {
+        df_fma(xh[hh], xl[hh], wb[hh].x, wa[hh].x);
+        df_fma(xh[hh], xl[hh], wb[hh].y, wa[hh].y);
+        df_fma(yh[hh], yl[hh], wb[hh].x, wa[hh].y);
+        df_fma(yh[hh], yl[hh], -wb[hh].y, wa[hh].x);
+      }
     }
-    const double sx = warp_sum_df(xh, xl);
-    const double sy = warp_sum_df(yh, yl);
+#pragma unroll
+    for (int hh = 1; hh < kCh; ++hh) {
+      df_add(xh[0], xl[0], xh[hh], xl[hh]);
+      df_add(yh[0], yl[0], yh[hh], yl[hh]);
+    }
+    const double sx = warp_sum_df(xh[0], xl[0]);
+    const double sy = warp_sum_df(yh[0], yl[0]);
     if (lane == 0) {
       C.G[a * kMaxR + b] = make_double2(sx, sy);             // G[a][b] = sum conj(W_b) W_a ... (lower)
       C.G[b * kMaxR + a] = make_double2(sx, -sy);
@@ -564,38 +588,40 @@ __device__ void fgram_factor(const FCtx& C) {
   __syncthreads();
   if (threadIdx.x < 32) {
     double* iL = reinterpret_cast<double*>(C.vec + 32);
-    int ok = 1;
-    if (lane == 0) {
-      // G here holds G[a][b] = sum_i conj(W_ib) W_ia = (W^H W)[b][a]; factor
-      // the Hermitian matrix M = W^H W with M[a][b] = conj(G[a][b]).
-      for (int j = 0; j < r && ok; ++j) {
-        double s = C.G[j * kMaxR + j].x;
+    // G here holds G[a][b] = sum_i conj(W_ib) W_ia = (W^H W)[b][a]; factor the
+    // Hermitian matrix M = W^H W with M[a][b] = conj(G[a][b]), column j by the
+    // lanes i >= j at once (lane j's entry is the pivot)
+    bool ok = true;
+    for (int j = 0; j < r; ++j) {
+      double2 t = make_double2(0.0, 0.0);
+      if (lane >= j && lane < r) {
+        t = make_double2(C.G[lane * kMaxR + j].x, -C.G[lane * kMaxR + j].y);
         for (int p = 0; p < j; ++p) {
-          const double2 l = C.Lc[j * kMaxR + p];
-          s -= l.x * l.x + l.y * l.y;
-        }
-        if (!(s > 1e-13 * C.G[j * kMaxR + j].x) || !(s < 1e300)) { ok = 0; break; }
-        const double ij = rsqrt_newton(s);
-        C.Lc[j * kMaxR + j] = make_double2(s * ij, 0.0);
-        iL[j] = ij;
-        for (int i = j + 1; i < r; ++i) {
-          // M[i][j] = conj(G[i][j])
-          double2 t = make_double2(C.G[i * kMaxR + j].x, -C.G[i * kMaxR + j].y);
-          for (int p = 0; p < j; ++p) {
-            const double2 a = C.Lc[i * kMaxR + p], b = C.Lc[j * kMaxR + p];
-            // t -= L[i][p] * conj(L[j][p])
-            t.x -= a.x * b.x + a.y * b.y;
-            t.y -= a.y * b.x - a.x * b.y;
-          }
-          C.Lc[i * kMaxR + j] = make_double2(t.x * ij, t.y * ij);
+          const double2 x = C.Lc[lane * kMaxR + p], y = C.Lc[j * kMaxR + p];
+          // t -= L[i][p] * conj(L[j][p])
+          t.x -= x.x * y.x + x.y * y.y;
+          t.y -= x.y * y.x - x.x * y.y;
         }
       }
-      if (!ok) {
-        report_error(C.err, kErrNotSPD, C.k);
-        for (int i = 0; i < r; ++i) {
-          for (int p = 0; p < r; ++p) C.Lc[i * kMaxR + p] = make_double2(i == p ? 1.0 : 0.0, 0.0);
-          iL[i] = 1.0;
-        }
+      const double sj = __shfl_sync(0xffffffffu, t.x, j);
+      if (!(sj > 1e-13 * C.G[j * kMaxR + j].x) || !(sj < 1e300)) {
+        ok = false;
+        break;
+      }
+      const double ij = rsqrt_newton(sj);
+      if (lane == j) {
+        C.Lc[j * kMaxR + j] = make_double2(sj * ij, 0.0);
+        iL[j] = ij;
+      } else if (lane > j && lane < r) {
+        C.Lc[lane * kMaxR + j] = make_double2(t.x * ij, t.y * ij);
+      }
+      __syncwarp();
+    }
+    if (!ok && lane == 0) {
+      report_error(C.err, kErrNotSPD, C.k);
+      for (int i = 0; i < r; ++i) {
+        for (int p = 0; p < r; ++p) C.Lc[i * kMaxR + p] = make_double2(i == p ? 1.0 : 0.0, 0.0);
+        iL[i] = 1.0;
       }
     }
     __syncwarp();
@@ -676,16 +702,34 @@ __device__ void fhard_threshold(const FCtx& C, bool keep_values) {
     __syncthreads();
     const int cnt = info[5];
     if (cnt >= rho && cnt <= kCandCap) {
-      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        const int e = C.cl[t];
-        const unsigned ke = C.ck[t];
-        int rank = 0;
-        for (int u = 0; u < cnt; ++u) {
-          const unsigned ku = C.ck[u];
-          rank += (ku > ke) || (ku == ke && C.cl[u] < e);
+      // bitonic sort of the candidates, descending by (key, ~pixel): the
+      // order (key descending, pixel ascending); the 64-bit sort keys take
+      // the place of cl and ck (adjacent, 2 kCandCap words)
+      int P = 1;
+      while (P < cnt) P <<= 1;
+      const int t = threadIdx.x;  // blockDim.x >= kCandCap >= P
+      unsigned long long mine = 0ull;
+      if (t < cnt)
+        mine = (static_cast<unsigned long long>(C.ck[t]) << 32) |
+               static_cast<unsigned long long>(0xffffffffu - static_cast<unsigned>(C.cl[t]));
+      __syncthreads();
+      unsigned long long* K = reinterpret_cast<unsigned long long*>(C.cl);
+      if (t < P) K[t] = mine;
+      __syncthreads();
+      for (int kk = 2; kk <= P; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+          const int o = t ^ j;
+          if (t < P && o > t) {
+            const unsigned long long x = K[t], y = K[o];
+            if (((t & kk) == 0) ? (x < y) : (x > y)) {
+              K[t] = y;
+              K[o] = x;
+            }
+          }
+          __syncthreads();
         }
-        if (rank < rho) sel[rank] = e;
       }
+      if (t < rho) sel[t] = static_cast<int>(0xffffffffu - static_cast<unsigned>(K[t] & 0xffffffffull));
       __syncthreads();
       for (int t = threadIdx.x; t < rho; t += blockDim.x) {  // ascending by pixel
         const int e = sel[t];
@@ -822,6 +866,7 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
   C.cl = reinterpret_cast<int*>(sm + cv.cl);
   C.ck = reinterpret_cast<unsigned*>(sm + cv.ck);
   C.FU = a.FU;
+  C.Wk = a.Wk + static_cast<size_t>(blockIdx.x) * a.r * a.m;
   C.err = a.err;
   const int k = C.k, m = C.m, r = C.r, rho = C.rho, n = C.g.n, ld = C.g.ny + 1;
   for (int t = threadIdx.x; t < C.g.nx; t += blockDim.x) C.tx[t] = a.twx[t];
@@ -857,7 +902,29 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
     }
   };
   const bool project = (a.mode != kModeInit);
-  if (project) fgram_factor(C);
+  if (project) {
+    // W_k = (F2 U)[Omega_k] into the frame's contiguous copy (read
+    // coalesced by the Gram, the solves and the projections)
+    constexpr int kG = 8;  // gathers issued together per thread
+    for (int t0 = threadIdx.x; t0 < r * m; t0 += kG * blockDim.x) {
+      float2 g[kG];
+#pragma unroll
+      for (int u = 0; u < kG; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (t < r * m) {
+          const int l = t / m, i = t - l * m;
+          g[u] = __ldg(C.FU + static_cast<size_t>(l) * n + C.msk[i]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kG; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (t < r * m) C.Wk[t] = g[u];
+      }
+    }
+    __syncthreads();
+    fgram_factor(C);
+  }
   mark(0);
   const int tau = (a.mode == kModeLS || rho == 0) ? 0 : a.tau;
   // After a sweep whose HardThreshold kept the support, s_new = s - mu g_G on
@@ -1427,6 +1494,7 @@ struct FourierSolver {
   double* eta = nullptr;
   double* scal = nullptr;
   float2* vecs = nullptr;  // the sweep's m-vectors in global memory (large m)
+  float2* Wk = nullptr;    // q x r x m gathered W_k of the sweep
   unsigned long long* prof = nullptr;  // kFProf sweep cycle counters (profiling)
   size_t smem = 0;
 };
@@ -1525,6 +1593,8 @@ FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int 
             cudaMallocAsync(reinterpret_cast<void**>(&F->rfac), sizeof(double2) * 2 * rr, F->s) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&F->eta), sizeof(double), F->s) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&F->scal), sizeof(double) * 4, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->Wk),
+                            sizeof(float2) * static_cast<size_t>(r) * m * q, F->s) == cudaSuccess &&
             (!vglob || cudaMallocAsync(reinterpret_cast<void**>(&F->vecs),
                                        sizeof(float2) * 3 * static_cast<size_t>(m) * q, F->s) == cudaSuccess);
   if (!ok) {
@@ -1560,7 +1630,7 @@ void fourier_destroy(FourierSolver* F) {
   void* ps[] = {F->y, F->mask, F->U, F->FU, F->B, F->S_idx, F->S_val, F->RES, F->H, F->K, F->grad,
                 F->Z, F->Z2, F->twx, F->twy, F->twl, F->iptr, F->ilist, F->err, F->part, F->rfac, F->eta,
                 F->scal,
-                F->vecs, F->prof};
+                F->vecs, F->Wk, F->prof};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, F->s);
   cudaStreamSynchronize(F->s);
@@ -1635,6 +1705,7 @@ static cudaError_t launch_fsweep(FourierSolver* F, int mode, int tau) {
   a.twl = F->twl;
   a.err = F->err;
   a.vecs = F->vecs;
+  a.Wk = F->Wk;
   a.prof = F->prof;
   fsweep_kernel<<<F->q, kFT, F->smem, F->s>>>(a);
   return cudaGetLastError();
