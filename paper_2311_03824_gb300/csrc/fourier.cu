@@ -222,6 +222,10 @@ __device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const flo
       __syncthreads();
     }
   }
+  // the unitary scale 1/sqrt(n) is applied by the last column pass as it
+  // stores (the same multiply as a separate pass), else by a pass of its own
+  const float sc = rsqrtf(static_cast<float>(n));
+  bool scaled = false;
   if (lnx < 0) {
     dft_direct_smem(X, nx, ny, false, tx, inverse);
   } else {
@@ -239,12 +243,24 @@ __device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const flo
     int s = 0;
     for (; s + 1 < lnx; s += 2) {  // stages s and s + 1 in one pass
       const int h = 1 << s;
+      const float f = (s + 2 == lnx) ? sc : 1.f;  // the last pass scales
       for (int b = threadIdx.x; b < n / 4; b += blockDim.x) {
         const int t = lny >= 0 ? b >> lny : b / ny, col = b - t * ny;
         const int j = t & (h - 1), i0 = ((t >> s) << (s + 2)) + j;
-        stage_pair(X[i0 * ld + col], X[(i0 + h) * ld + col], X[(i0 + 2 * h) * ld + col],
-                   X[(i0 + 3 * h) * ld + col], tx[j * (nx >> (s + 1))], tx[j * (nx >> (s + 2))],
+        float2* p0 = X + i0 * ld + col;
+        float2 x0 = p0[0], x1 = p0[h * ld], x2 = p0[2 * h * ld], x3 = p0[3 * h * ld];
+        stage_pair(x0, x1, x2, x3, tx[j * (nx >> (s + 1))], tx[j * (nx >> (s + 2))],
                    tx[(j + h) * (nx >> (s + 2))], inverse);
+        if (s + 2 == lnx) {
+          x0 = make_float2(x0.x * f, x0.y * f);
+          x1 = make_float2(x1.x * f, x1.y * f);
+          x2 = make_float2(x2.x * f, x2.y * f);
+          x3 = make_float2(x3.x * f, x3.y * f);
+        }
+        p0[0] = x0;
+        p0[h * ld] = x1;
+        p0[2 * h * ld] = x2;
+        p0[3 * h * ld] = x3;
       }
       __syncthreads();
     }
@@ -256,19 +272,22 @@ __device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const flo
         float2 w = tx[j * step];
         if (inverse) w.y = -w.y;
         const float2 a = X[i1 * ld + col], c = cmul(X[i2 * ld + col], w);
-        X[i1 * ld + col] = cadd(a, c);
-        X[i2 * ld + col] = csub(a, c);
+        const float2 o1 = cadd(a, c), o2 = csub(a, c);
+        X[i1 * ld + col] = make_float2(o1.x * sc, o1.y * sc);
+        X[i2 * ld + col] = make_float2(o2.x * sc, o2.y * sc);
       }
       __syncthreads();
     }
+    scaled = lnx > 0;
   }
-  const float sc = rsqrtf(static_cast<float>(n));
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int row = e / ny, j = e - row * ny;
-    X[row * ld + j].x *= sc;
-    X[row * ld + j].y *= sc;
+  if (!scaled) {
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int row = e / ny, j = e - row * ny;
+      X[row * ld + j].x *= sc;
+      X[row * ld + j].y *= sc;
+    }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 struct Geo {
