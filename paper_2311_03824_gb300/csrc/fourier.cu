@@ -349,6 +349,8 @@ struct FArgs {
                         // they do not fit shared memory beside the frame
   float2* Wk;           // q x r x m: W_k = (F2 U)[Omega_k], gathered once per
                         // frame and sweep (row l of frame k contiguous)
+  float2* AS;           // q x m: A_k s_k of the last sweep's final stage
+  int* asv;             // q: 1 while AS[k] is A_k s_k of the current s_k
   unsigned long long* prof;  // optional kFProf cycle counters (thread 0 of each CTA)
 };
 
@@ -534,16 +536,35 @@ __device__ void fls_solve(const FCtx& C, const float2* v) {
   __syncthreads();
 }
 
-// v <- v - W x with x from fls_solve (float arithmetic)
+// v <- v - W x with x from fls_solve (float arithmetic).  A thread takes
+// kApPer rows at once, so that the loads of W for one l are independent.
+constexpr int kApPer = 4;
 __device__ void fapply_Wx(const FCtx& C, float2* v, float sign) {
-  for (int i = threadIdx.x; i < C.m; i += blockDim.x) {
-    float2 s = v[i];
+  const int bd = blockDim.x;
+  for (int i0 = threadIdx.x; i0 < C.m; i0 += kApPer * bd) {
+    float2 s[kApPer];
+#pragma unroll
+    for (int u = 0; u < kApPer; ++u) {
+      const int i = i0 + u * bd;
+      s[u] = i < C.m ? v[i] : make_float2(0.f, 0.f);
+    }
     for (int l = 0; l < C.r; ++l) {
       const double2 xd = C.vec[16 + l];
       const float2 x = make_float2(sign * static_cast<float>(xd.x), sign * static_cast<float>(xd.y));
-      s = cfma(W_at(C, i, l), x, s);
+      float2 wv[kApPer];
+#pragma unroll
+      for (int u = 0; u < kApPer; ++u) {
+        const int i = i0 + u * bd;
+        wv[u] = i < C.m ? W_at(C, i, l) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kApPer; ++u) s[u] = cfma(wv[u], x, s[u]);
     }
-    v[i] = s;
+#pragma unroll
+    for (int u = 0; u < kApPer; ++u) {
+      const int i = i0 + u * bd;
+      if (i < C.m) v[i] = s[u];
+    }
   }
   __syncthreads();
 }
@@ -920,6 +941,9 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
       tl = t;
     }
   };
+  // A_k s_k of this s_k from the previous sweep's final stage (the same
+  // sparse DFT of the same support, pixels and values in the same order)
+  const bool as_ok = a.asv[k] != 0;
   const bool project = (a.mode != kModeInit);
   if (project) {
     // W_k = (F2 U)[Omega_k] into the frame's contiguous copy (read
@@ -965,7 +989,11 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
       __syncthreads();
       mark(2);
     } else {
-      sparse_dft(C, C.sp, C.sv, rho, C.dv);
+      if (it == 0 && as_ok) {
+        for (int i = threadIdx.x; i < m; i += blockDim.x) C.dv[i] = a.AS[static_cast<size_t>(k) * m + i];
+      } else {
+        sparse_dft(C, C.sp, C.sv, rho, C.dv);
+      }
       __syncthreads();
       for (int i = threadIdx.x; i < m; i += blockDim.x) C.dv[i] = csub(C.dv[i], C.yv[i]);
       __syncthreads();
@@ -1048,9 +1076,19 @@ __global__ void __launch_bounds__(kFT, 1) fsweep_kernel(const FArgs a) {
     mark(4);
   }
   // ---- final stage ----
-  sparse_dft(C, C.sp, C.sv, rho, C.dv);  // A s
+  const bool as_kept = (tau == 0 && as_ok);  // s unchanged by this sweep
+  if (as_kept) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) C.dv[i] = a.AS[static_cast<size_t>(k) * m + i];
+  } else {
+    sparse_dft(C, C.sp, C.sv, rho, C.dv);  // A s
+  }
   __syncthreads();
-  for (int i = threadIdx.x; i < m; i += blockDim.x) C.dv[i] = csub(C.yv[i], C.dv[i]);  // y - A s
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {  // y - A s; A s kept for the next sweep
+    const float2 as = C.dv[i];
+    if (!as_kept) a.AS[static_cast<size_t>(k) * m + i] = as;
+    C.dv[i] = csub(C.yv[i], as);
+  }
+  if (threadIdx.x == 0) a.asv[k] = 1;
   __syncthreads();
   if (a.mode == kModeInit) {
     for (int e = threadIdx.x; e < C.g.nx * ld; e += blockDim.x) C.X[e] = make_float2(0.f, 0.f);
@@ -1514,6 +1552,8 @@ struct FourierSolver {
   double* scal = nullptr;
   float2* vecs = nullptr;  // the sweep's m-vectors in global memory (large m)
   float2* Wk = nullptr;    // q x r x m gathered W_k of the sweep
+  float2* AS = nullptr;    // q x m: A_k s_k from the last sweep's final stage
+  int* asv = nullptr;      // q flags: AS[k] matches the current s_k
   unsigned long long* prof = nullptr;  // kFProf sweep cycle counters (profiling)
   size_t smem = 0;
 };
@@ -1614,6 +1654,9 @@ FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int 
             cudaMallocAsync(reinterpret_cast<void**>(&F->scal), sizeof(double) * 4, F->s) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&F->Wk),
                             sizeof(float2) * static_cast<size_t>(r) * m * q, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->AS),
+                            sizeof(float2) * static_cast<size_t>(m) * q, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->asv), sizeof(int) * q, F->s) == cudaSuccess &&
             (!vglob || cudaMallocAsync(reinterpret_cast<void**>(&F->vecs),
                                        sizeof(float2) * 3 * static_cast<size_t>(m) * q, F->s) == cudaSuccess);
   if (!ok) {
@@ -1638,6 +1681,7 @@ FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int 
   }
   cudaMemcpyAsync(F->twl, twl.data(), sizeof(float2) * F->g.L, cudaMemcpyHostToDevice, F->s);
   cudaMemsetAsync(F->err, 0, 8, F->s);
+  cudaMemsetAsync(F->asv, 0, sizeof(int) * q, F->s);
   cudaMemsetAsync(F->S_idx, 0, sizeof(int) * q * std::max(1, rho), F->s);
   cudaMemsetAsync(F->S_val, 0, sizeof(float2) * q * std::max(1, rho), F->s);
   cudaStreamSynchronize(F->s);  // the twiddle tables' host staging ends here
@@ -1649,7 +1693,7 @@ void fourier_destroy(FourierSolver* F) {
   void* ps[] = {F->y, F->mask, F->U, F->FU, F->B, F->S_idx, F->S_val, F->RES, F->H, F->K, F->grad,
                 F->Z, F->Z2, F->twx, F->twy, F->twl, F->iptr, F->ilist, F->err, F->part, F->rfac, F->eta,
                 F->scal,
-                F->vecs, F->Wk, F->prof};
+                F->vecs, F->Wk, F->AS, F->asv, F->prof};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, F->s);
   cudaStreamSynchronize(F->s);
@@ -1692,6 +1736,7 @@ int fourier_set_measurements(FourierSolver* F, const void* y, const void* mask, 
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(F->y, y, sizeof(float2) * m * q,
                         mem_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, F->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(F->asv, 0, sizeof(int) * q, F->s);  // new A_k
   if (e == cudaSuccess) e = cudaStreamSynchronize(F->s);
   if (e != cudaSuccess) {
     *msg = cudaGetErrorString(e);
@@ -1725,6 +1770,8 @@ static cudaError_t launch_fsweep(FourierSolver* F, int mode, int tau) {
   a.err = F->err;
   a.vecs = F->vecs;
   a.Wk = F->Wk;
+  a.AS = F->AS;
+  a.asv = F->asv;
   a.prof = F->prof;
   fsweep_kernel<<<F->q, kFT, F->smem, F->s>>>(a);
   return cudaGetLastError();
@@ -1877,6 +1924,7 @@ int fourier_set_state(FourierSolver* F, const void* U, const void* B, const int*
     cudaMemcpyAsync(F->S_idx, S_idx, sizeof(int) * F->q * F->rho, k, F->s);
     cudaMemcpyAsync(F->S_val, S_val, sizeof(float2) * F->q * F->rho, k, F->s);
   }
+  cudaMemsetAsync(F->asv, 0, sizeof(int) * F->q, F->s);  // a new s_k
   cudaMemcpyAsync(F->eta, &eta, sizeof(double), cudaMemcpyHostToDevice, F->s);
   F->t = t;
   return cudaStreamSynchronize(F->s) == cudaSuccess ? 0 : 4;
