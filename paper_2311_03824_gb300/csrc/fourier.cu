@@ -486,6 +486,9 @@ __device__ void sparse_dft(const FCtx& C, const int* p, const float2* v, int nnz
   }
 }
 
+// rows of W a thread takes at once in the solves and projections
+constexpr int kApPer = 4;
+
 // x = G^{-1} W^H v (W^H v in FP32, block-summed in fixed order; solve FP64);
 // x in C.vec[16 + l] (double2)
 __device__ void fls_solve(const FCtx& C, const float2* v) {
@@ -493,11 +496,30 @@ __device__ void fls_solve(const FCtx& C, const float2* v) {
   float2 acc[kMaxR];
 #pragma unroll
   for (int l = 0; l < kMaxR; ++l) acc[l] = make_float2(0.f, 0.f);
-  for (int i = threadIdx.x; i < C.m; i += blockDim.x) {
-    const float2 vi = v[i];
+  // kApPer rows per thread at once (their W loads independent), each sum
+  // still over the thread's rows in increasing order
+  const int bd = blockDim.x;
+  for (int i0 = threadIdx.x; i0 < C.m; i0 += kApPer * bd) {
+    float2 vi[kApPer];
 #pragma unroll
-    for (int l = 0; l < kMaxR; ++l)
-      if (l < r) acc[l] = ccfma(W_at(C, i, l), vi, acc[l]);
+    for (int u = 0; u < kApPer; ++u) {
+      const int i = i0 + u * bd;
+      vi[u] = i < C.m ? v[i] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int l = 0; l < kMaxR; ++l) {
+      if (l < r) {
+        float2 wv[kApPer];
+#pragma unroll
+        for (int u = 0; u < kApPer; ++u) {
+          const int i = i0 + u * bd;
+          wv[u] = i < C.m ? W_at(C, i, l) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kApPer; ++u)
+          if (i0 + u * bd < C.m) acc[l] = ccfma(wv[u], vi[u], acc[l]);
+      }
+    }
   }
 #pragma unroll
   for (int l = 0; l < kMaxR; ++l) {
@@ -538,7 +560,6 @@ __device__ void fls_solve(const FCtx& C, const float2* v) {
 
 // v <- v - W x with x from fls_solve (float arithmetic).  A thread takes
 // kApPer rows at once, so that the loads of W for one l are independent.
-constexpr int kApPer = 4;
 __device__ void fapply_Wx(const FCtx& C, float2* v, float sign) {
   const int bd = blockDim.x;
   for (int i0 = threadIdx.x; i0 < C.m; i0 += kApPer * bd) {
