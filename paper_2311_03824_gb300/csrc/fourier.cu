@@ -290,6 +290,146 @@ __device__ void fft2_smem(float2* X, int nx, int ny, int lnx, int lny, const flo
   }
 }
 
+// g = log2 G consecutive radix-2 decimation-in-time stages s .. s + g - 1 on
+// the G elements x[t] at positions i0 + t h (h = 2^s, i0 = j mod h) of a block
+// of G h along a side of length N.  Stage s + u pairs x[t] with x[t + d]
+// (d = 2^u, bit u of t clear) with twiddle tw[(j + (t mod d) h) N / 2^(s+u+1)]:
+// the butterflies of g single-stage passes, in the same order, on registers.
+template <int G>
+__device__ __forceinline__ void dit_group(float2 (&x)[G], int j, int h, int s, int N,
+                                          const float2* tw, bool inverse) {
+#pragma unroll
+  for (int d = 1; d < G; d <<= 1) {
+    const int sig = s + __ffs(d) - 1;  // the global stage
+    const int step = N >> (sig + 1);
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      if (t & d) continue;
+      float2 w = tw[(j + (t & (d - 1)) * h) * step];
+      if (inverse) w.y = -w.y;
+      const float2 a = x[t], c = cmul(x[t + d], w);
+      x[t] = cadd(a, c);
+      x[t + d] = csub(a, c);
+    }
+  }
+}
+
+// One pass of g stages over every line of one side: nl lines of N elements,
+// element p of line l at X[l * ls + p * es].  Consecutive threads take the
+// same group of consecutive lines (distinct banks for the row stride ny + 1,
+// contiguous for columns; the twiddles are broadcasts).  With brev (the first
+// pass, when a round of the CTA's threads holds whole lines) the inputs come
+// from the bit-reversed positions: a round's reads all end before its writes.
+// f scales the outputs.
+template <int G>
+__device__ void dit_pass(float2* X, int nl, int ls, int es, int N, int lN, int s,
+                         const float2* tw, bool inverse, float f, bool brev) {
+  const int h = 1 << s, gpl = N / G, g = __ffs(G) - 1, bd = blockDim.x;
+  if (!brev) {
+    for (int b = threadIdx.x; b < nl * gpl; b += bd) {
+      const int line = b % nl, t = b / nl, j = t & (h - 1);
+      const int i0 = ((t >> s) << (s + g)) + j;
+      float2* L = X + line * ls;
+      float2 x[G];
+#pragma unroll
+      for (int u = 0; u < G; ++u) x[u] = L[(i0 + u * h) * es];
+      dit_group<G>(x, j, h, s, N, tw, inverse);
+#pragma unroll
+      for (int u = 0; u < G; ++u) L[(i0 + u * h) * es] = make_float2(x[u].x * f, x[u].y * f);
+    }
+    __syncthreads();
+    return;
+  }
+  const int lpr = min(nl, bd / gpl);  // lines per round (>= 1: checked by the caller)
+  for (int l0 = 0; l0 < nl; l0 += lpr) {
+    const int b = threadIdx.x;
+    const bool on = b < lpr * gpl && l0 + b % lpr < nl;
+    float2 x[G];
+    int line = 0, i0 = 0;
+    if (on) {
+      line = l0 + b % lpr;
+      i0 = (b / lpr) << g;  // s = 0: h = 1, j = 0
+      float2* L = X + line * ls;
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        const int src = static_cast<int>(__brev(static_cast<unsigned>(i0 + u)) >> (32 - lN));
+        x[u] = L[src * es];
+      }
+      dit_group<G>(x, 0, 1, 0, N, tw, inverse);
+    }
+    __syncthreads();
+    if (on) {
+      float2* L = X + line * ls;
+#pragma unroll
+      for (int u = 0; u < G; ++u) L[(i0 + u) * es] = make_float2(x[u].x * f, x[u].y * f);
+    }
+    __syncthreads();
+  }
+}
+
+// Radix-2 DIT transform of every line of one power-of-two side (lN = log2 N),
+// in passes of up to kDitMax stages (a register budget: 3 in the FFT kernel,
+// 2 inside the sweep); the last pass scales by f.  The bit reversal is read
+// by the first pass, or (lines longer than the CTA's threads hold) swapped in
+// a pass of its own.
+template <int kDitMax>
+__device__ __forceinline__ void dit_side(float2* X, int nl, int ls, int es, int N, int lN, const float2* tw,
+                         bool inverse, float f) {
+  if (lN <= 0) return;
+  const bool fused = (N >> min(kDitMax, lN)) <= static_cast<int>(blockDim.x);
+  if (!fused) {
+    for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
+      const int line = e % nl, p = e / nl;
+      const int q = static_cast<int>(__brev(static_cast<unsigned>(p)) >> (32 - lN));
+      if (q > p) {
+        float2* L = X + line * ls;
+        const float2 t = L[p * es];
+        L[p * es] = L[q * es];
+        L[q * es] = t;
+      }
+    }
+    __syncthreads();
+  }
+  for (int s = 0; s < lN;) {
+    const int g = min(kDitMax, lN - s);
+    const float fs = (s + g == lN) ? f : 1.f;
+    const bool br = fused && s == 0;
+    switch (g) {
+      case 1: dit_pass<2>(X, nl, ls, es, N, lN, s, tw, inverse, fs, br); break;
+      case 2: dit_pass<4>(X, nl, ls, es, N, lN, s, tw, inverse, fs, br); break;
+      default: dit_pass<(kDitMax >= 3 ? 8 : 4)>(X, nl, ls, es, N, lN, s, tw, inverse, fs, br); break;
+    }
+    s += g;
+  }
+}
+
+// The unitary 2D FFT of the frame kernel: as fft2_smem, with every side in
+// register passes of up to three stages (the bit reversal read by the first).
+__device__ void fft2_dit(float2* X, int nx, int ny, int lnx, int lny, const float2* tx,
+                         const float2* ty, bool inverse) {
+  const int ld = ny + 1, n = nx * ny;
+  const float sc = rsqrtf(static_cast<float>(n));
+  if (lny < 0)
+    dft_direct_smem(X, nx, ny, true, ty, inverse);
+  else
+    dit_side<3>(X, nx, ld, 1, ny, lny, ty, inverse, 1.f);  // rows
+  bool scaled = false;
+  if (lnx < 0) {
+    dft_direct_smem(X, nx, ny, false, tx, inverse);
+  } else {
+    dit_side<3>(X, ny, 1, ld, nx, lnx, tx, inverse, sc);  // columns
+    scaled = lnx > 0;
+  }
+  if (!scaled) {
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int row = e / ny, j = e - row * ny;
+      X[row * ld + j].x *= sc;
+      X[row * ld + j].y *= sc;
+    }
+    __syncthreads();
+  }
+}
+
 struct Geo {
   int nx, ny, lnx, lny, n;  // lnx / lny: log2 of a power-of-two side, else -1
   int L, sxL, syL, lL;      // L = lcm(nx, ny), L / nx, L / ny, log2 L (or -1)
@@ -322,7 +462,7 @@ __global__ void __launch_bounds__(kFT) fft_frames_kernel(Geo g, const float2* __
     X[row * (g.ny + 1) + j] = in[f * g.n + e];
   }
   __syncthreads();
-  fft2_smem(X, g.nx, g.ny, g.lnx, g.lny, tx, ty, inverse != 0);
+  fft2_dit(X, g.nx, g.ny, g.lnx, g.lny, tx, ty, inverse != 0);
   for (int e = threadIdx.x; e < g.n; e += blockDim.x) {
     const int row = e / g.ny, j = e - row * g.ny;
     out[f * g.n + e] = X[row * (g.ny + 1) + j];
