@@ -1322,34 +1322,19 @@ __global__ void kspace_kernel(int n, int m, int r, const int* __restrict__ ptr,
 
 // ---- complex column-reduced ops on r x n column-major matrices (l-major) ----
 // partial Hermitian Grams: part[blk][a][b] = sum_j conj(X_ja) X_jb (a >= b)
-__global__ void cgram_part_kernel(int n, int r, const float2* __restrict__ X,
-                                  const float2* __restrict__ G2, const double* __restrict__ eta,
-                                  float2* __restrict__ Xout, double2* __restrict__ part) {
-  const int rows = (n + gridDim.x - 1) / gridDim.x;
-  const int lo = blockIdx.x * rows, hi = min(n, lo + rows);
-  const float e = eta ? static_cast<float>(*eta) : 0.f;
-  if (Xout) {
-    for (int j = lo + threadIdx.x; j < hi; j += blockDim.x)
-      for (int l = 0; l < r; ++l) {
-        float2 v = X[static_cast<size_t>(l) * n + j];
-        if (G2) {
-          const float2 g = G2[static_cast<size_t>(l) * n + j];
-          v = make_float2(fmaf(-e, g.x, v.x), fmaf(-e, g.y, v.y));
-        }
-        Xout[static_cast<size_t>(l) * n + j] = v;
-      }
-    __syncthreads();
-  }
-  const float2* Y = Xout ? Xout : X;
-  // entry p of the lower triangle (row-major) and row group g: the block's
-  // rows g, g + ng, ... ; the groups are added in order afterwards
+// Gram partials of the rows [lo, hi) of the block Y (r x n column-major):
+// out[a * r + b] = sum_j conj(y_a[j]) y_b[j] (a >= b) in FP64.  Entry p of the
+// lower triangle (row-major) and row group g: the rows g, g + ng, ... of the
+// range; the groups are added in order afterwards.  All threads of the block.
+__device__ void cgram_rows(int n, int r, const float2* __restrict__ Y, int lo, int hi,
+                           double2* __restrict__ out) {
   __shared__ double2 red[256];
   const int npair = r * (r + 1) / 2, ng = max(1, static_cast<int>(blockDim.x) / npair);
   const int t = threadIdx.x, p = t % npair, g = t / npair;
   int a = 0, b = p;
   while (b > a) b -= ++a;
   double sx = 0, sy = 0;
-  if (g < ng) {
+  if (g < ng && t < 256) {
     for (int j = lo + g; j < hi; j += ng) {
       const float2 xa = Y[static_cast<size_t>(a) * n + j], xb = Y[static_cast<size_t>(b) * n + j];
       sx += static_cast<double>(xa.x) * xb.x + static_cast<double>(xa.y) * xb.y;  // conj(x_a) x_b
@@ -1364,14 +1349,38 @@ __global__ void cgram_part_kernel(int n, int r, const float2* __restrict__ X,
       s.x += red[gg * npair + t].x;
       s.y += red[gg * npair + t].y;
     }
-    part[static_cast<size_t>(blockIdx.x) * r * r + a * r + b] = s;
+    out[a * r + b] = s;
   }
+  __syncthreads();
+}
+// Z = X - eta G2 on the rows [lo, hi) (float32, as the sweep's update)
+__device__ void cstep_rows(int n, int r, const float2* __restrict__ X, const float2* __restrict__ G2,
+                           float e, float2* __restrict__ Xout, int lo, int hi) {
+  for (int j = lo + threadIdx.x; j < hi; j += blockDim.x)
+    for (int l = 0; l < r; ++l) {
+      float2 v = X[static_cast<size_t>(l) * n + j];
+      if (G2) {
+        const float2 g = G2[static_cast<size_t>(l) * n + j];
+        v = make_float2(fmaf(-e, g.x, v.x), fmaf(-e, g.y, v.y));
+      }
+      Xout[static_cast<size_t>(l) * n + j] = v;
+    }
+  __syncthreads();
+}
+__global__ void cgram_part_kernel(int n, int r, const float2* __restrict__ X,
+                                  const float2* __restrict__ G2, const double* __restrict__ eta,
+                                  float2* __restrict__ Xout, double2* __restrict__ part) {
+  const int rows = (n + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * rows, hi = min(n, lo + rows);
+  if (Xout) cstep_rows(n, r, X, G2, eta ? static_cast<float>(*eta) : 0.f, Xout, lo, hi);
+  cgram_rows(n, r, Xout ? Xout : X, lo, hi, part + static_cast<size_t>(blockIdx.x) * r * r);
 }
 // M = sum of partials (M[a][b] for a >= b = sum conj(x_a) x_b), Hermitian;
 // M = R^H R with R = L^H (L lower from the Cholesky of M^T... we factor the
 // matrix N[i][j] = sum conj(x_i) x_j directly: N = L L^H), Rinv = L^{-H}.
-__global__ void cchol_fin_kernel(int r, int nblk, const double2* __restrict__ part,
-                                 double2* __restrict__ Rinv, int* err) {
+// (All threads of the block; the partials read through L2.)
+__device__ void cchol_block(int r, int nblk, const double2* __restrict__ part,
+                            double2* __restrict__ Rinv, int* err) {
   __shared__ double2 N[kMaxR * kMaxR], Lw[kMaxR * kMaxR], Li[kMaxR * kMaxR];
   __shared__ double iL[kMaxR];
   // the partials of each entry: one warp per entry, lanes over the blocks,
@@ -1382,7 +1391,7 @@ __global__ void cchol_fin_kernel(int r, int nblk, const double2* __restrict__ pa
     if (b > a) continue;
     double sx = 0, sy = 0;
     for (int k = lane; k < nblk; k += 32) {
-      const double2 v = part[static_cast<size_t>(k) * r * r + a * r + b];
+      const double2 v = __ldcg(part + static_cast<size_t>(k) * r * r + a * r + b);
       sx += v.x;
       sy += v.y;
     }
@@ -1395,71 +1404,75 @@ __global__ void cchol_fin_kernel(int r, int nblk, const double2* __restrict__ pa
     }
   }
   __syncthreads();
-  if (threadIdx.x >= 32) return;
-  // (X^H X)[i][j] = sum conj(x_i) x_j = N[i][j]: factor N = L L^H, column j
-  // by the lanes i >= j at once (lane j's entry is the pivot)
-  bool ok = true;
-  for (int j = 0; j < r; ++j) {
-    double2 t = make_double2(0.0, 0.0);
-    if (lane >= j && lane < r) {
-      t = N[lane * kMaxR + j];
-      for (int p = 0; p < j; ++p) {
-        const double2 a = Lw[lane * kMaxR + p], b = Lw[j * kMaxR + p];
-        t.x -= a.x * b.x + a.y * b.y;
-        t.y -= a.y * b.x - a.x * b.y;
+  if (threadIdx.x < 32) {
+    // (X^H X)[i][j] = sum conj(x_i) x_j = N[i][j]: factor N = L L^H, column j
+    // by the lanes i >= j at once (lane j's entry is the pivot)
+    bool ok = true;
+    for (int j = 0; j < r; ++j) {
+      double2 t = make_double2(0.0, 0.0);
+      if (lane >= j && lane < r) {
+        t = N[lane * kMaxR + j];
+        for (int p = 0; p < j; ++p) {
+          const double2 a = Lw[lane * kMaxR + p], b = Lw[j * kMaxR + p];
+          t.x -= a.x * b.x + a.y * b.y;
+          t.y -= a.y * b.x - a.x * b.y;
+        }
       }
+      const double s = __shfl_sync(0xffffffffu, t.x, j);
+      if (!(s > 1e-13 * N[j * kMaxR + j].x) || !(s < 1e300)) {
+        ok = false;
+        break;
+      }
+      const double ij = rsqrt_newton(s);
+      if (lane == j) {
+        Lw[j * kMaxR + j] = make_double2(s * ij, 0);
+        iL[j] = ij;
+      } else if (lane > j && lane < r) {
+        Lw[lane * kMaxR + j] = make_double2(t.x * ij, t.y * ij);
+      }
+      __syncwarp();
     }
-    const double s = __shfl_sync(0xffffffffu, t.x, j);
-    if (!(s > 1e-13 * N[j * kMaxR + j].x) || !(s < 1e300)) {
-      ok = false;
-      break;
-    }
-    const double ij = rsqrt_newton(s);
-    if (lane == j) {
-      Lw[j * kMaxR + j] = make_double2(s * ij, 0);
-      iL[j] = ij;
-    } else if (lane > j && lane < r) {
-      Lw[lane * kMaxR + j] = make_double2(t.x * ij, t.y * ij);
+    if (!ok) {
+      if (lane == 0) {
+        report_error(err, kErrNotSPD, -1);
+        for (int i = 0; i < r; ++i) {
+          for (int p = 0; p < r; ++p) Lw[i * kMaxR + p] = make_double2(i == p ? 1.0 : 0.0, 0);
+          iL[i] = 1.0;
+        }
+      }
     }
     __syncwarp();
-  }
-  if (!ok) {
-    if (lane == 0) {
-      report_error(err, kErrNotSPD, -1);
+    if (lane < r) {
+      const int cc = lane;
       for (int i = 0; i < r; ++i) {
-        for (int p = 0; p < r; ++p) Lw[i * kMaxR + p] = make_double2(i == p ? 1.0 : 0.0, 0);
-        iL[i] = 1.0;
+        double2 t = make_double2(i == cc ? 1.0 : 0.0, 0.0);
+        for (int p = cc; p < i; ++p) {
+          const double2 q = dcmul(Lw[i * kMaxR + p], Li[p * kMaxR + cc]);
+          t.x -= q.x;
+          t.y -= q.y;
+        }
+        Li[i * kMaxR + cc] = (i < cc) ? make_double2(0, 0) : make_double2(t.x * iL[i], t.y * iL[i]);
       }
     }
-  }
-  __syncwarp();
-  if (lane < r) {
-    const int cc = lane;
-    for (int i = 0; i < r; ++i) {
-      double2 t = make_double2(i == cc ? 1.0 : 0.0, 0.0);
-      for (int p = cc; p < i; ++p) {
-        const double2 q = dcmul(Lw[i * kMaxR + p], Li[p * kMaxR + cc]);
-        t.x -= q.x;
-        t.y -= q.y;
-      }
-      Li[i * kMaxR + cc] = (i < cc) ? make_double2(0, 0) : make_double2(t.x * iL[i], t.y * iL[i]);
+    __syncwarp();
+    // X^H X = L L^H  ->  with R = L^H (upper), Q = X R^{-1} = X L^{-H}:
+    // Rinv[a][b] = (L^{-H})[a][b] = conj(Li[b][a])
+    for (int t = lane; t < r * r; t += 32) {
+      const int a = t / r, b = t - a * r;
+      const double2 v = Li[b * kMaxR + a];
+      Rinv[a * r + b] = make_double2(v.x, -v.y);
     }
   }
-  __syncwarp();
-  // X^H X = L L^H  ->  with R = L^H (upper), Q = X R^{-1} = X L^{-H}:
-  // Rinv[a][b] = (L^{-H})[a][b] = conj(Li[b][a])
-  for (int t = lane; t < r * r; t += 32) {
-    const int a = t / r, b = t - a * r;
-    const double2 v = Li[b * kMaxR + a];
-    Rinv[a * r + b] = make_double2(v.x, -v.y);
-  }
+  __syncthreads();
 }
-// Y = X Rinv (column-major complex, FP64 accumulation); optional float out
-__global__ void capply_kernel(int n, int r, const float2* __restrict__ X,
-                              const double2* __restrict__ Rinv, float2* __restrict__ Y) {
-  const size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
-  if (t >= static_cast<size_t>(n) * r) return;
-  const int l = static_cast<int>(t / n), j = static_cast<int>(t - static_cast<size_t>(l) * n);
+__global__ void cchol_fin_kernel(int r, int nblk, const double2* __restrict__ part,
+                                 double2* __restrict__ Rinv, int* err) {
+  cchol_block(r, nblk, part, Rinv, err);
+}
+// Y = X Rinv (column-major complex, FP64 accumulation) for the entries
+// (l, j), j in [lo, hi), of the block's range; Rinv r x r (row-major).
+__device__ __forceinline__ float2 capply_one(int n, int r, const float2* __restrict__ X,
+                                             const double2* __restrict__ Rinv, int l, int j) {
   double sx = 0, sy = 0;
   for (int p = 0; p <= l; ++p) {
     const float2 x = X[static_cast<size_t>(p) * n + j];
@@ -1467,8 +1480,82 @@ __global__ void capply_kernel(int n, int r, const float2* __restrict__ X,
     sx += x.x * q.x - x.y * q.y;
     sy += x.x * q.y + x.y * q.x;
   }
-  Y[t] = make_float2(static_cast<float>(sx), static_cast<float>(sy));
+  return make_float2(static_cast<float>(sx), static_cast<float>(sy));
 }
+__global__ void capply_kernel(int n, int r, const float2* __restrict__ X,
+                              const double2* __restrict__ Rinv, float2* __restrict__ Y) {
+  const size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (t >= static_cast<size_t>(n) * r) return;
+  const int l = static_cast<int>(t / n), j = static_cast<int>(t - static_cast<size_t>(l) * n);
+  Y[t] = capply_one(n, r, X, Rinv, l, j);
+}
+
+// Grid barrier of a cooperative launch (every block resident): thread 0
+// counts in and waits, bounded by wait_ns on the global timer, for
+// `target` arrivals; on expiry the launch's error flag records a timeout and
+// the block goes on (its results are then void, the host reports the error).
+__device__ void grid_barrier(unsigned* ctr, unsigned target, int* err, unsigned long long wait_ns) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+      if (v >= target) break;
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > wait_ns) {
+        report_error(err, kErrTimeout, -1);
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// The whole complex Cholesky-QR2 of Z = X - eta G2 (G2 null: Z = X) in one
+// cooperative launch of nblk blocks, block b on the same rows in every
+// phase: Z and its Gram partials; barrier; every block factors the Gram
+// (the same sums in the same order, so the same R^{-1}) and forms its rows of
+// Z2 = Z R^{-1} and their Gram partials; barrier; R2^{-1} and U = Z2 R2^{-1}.
+// The arithmetic is that of the separate kernels (gram, chol, apply twice).
+__global__ void __launch_bounds__(256) cqr2_fused_kernel(int n, int r, const float2* X,
+                                                         const float2* __restrict__ G2,
+                                                         const double* __restrict__ eta,
+                                                         float2* __restrict__ Z, float2* __restrict__ Z2,
+                                                         float2* Uout, double2* __restrict__ part,
+                                                         double2* __restrict__ part2, unsigned* bar,
+                                                         int* err, unsigned long long wait_ns) {
+  __shared__ double2 Rs[kMaxR * kMaxR];
+  const int nb = gridDim.x, rows = (n + nb - 1) / nb;
+  const int lo = blockIdx.x * rows, hi = min(n, lo + rows);
+  const float2* Y = X;
+  if (G2) {
+    cstep_rows(n, r, X, G2, static_cast<float>(*eta), Z, lo, hi);
+    Y = Z;
+  }
+  cgram_rows(n, r, Y, lo, hi, part + static_cast<size_t>(blockIdx.x) * r * r);
+  grid_barrier(bar, static_cast<unsigned>(nb), err, wait_ns);
+  cchol_block(r, nb, part, Rs, err);
+  for (int t = threadIdx.x; t < (hi - lo) * r; t += blockDim.x) {
+    const int l = t / (hi - lo), j = lo + (t - l * (hi - lo));
+    Z2[static_cast<size_t>(l) * n + j] = capply_one(n, r, Y, Rs, l, j);
+  }
+  __syncthreads();
+  cgram_rows(n, r, Z2, lo, hi, part2 + static_cast<size_t>(blockIdx.x) * r * r);
+  grid_barrier(bar, 2u * static_cast<unsigned>(nb), err, wait_ns);
+  cchol_block(r, nb, part2, Rs, err);
+  for (int t = threadIdx.x; t < (hi - lo) * r; t += blockDim.x) {
+    const int l = t / (hi - lo), j = lo + (t - l * (hi - lo));
+    Uout[static_cast<size_t>(l) * n + j] = capply_one(n, r, Z2, Rs, l, j);
+  }
+}
+
 // eta = c / sqrt(lambda_max(grad^H grad)), from the real 2r x 2r symmetric
 // embedding [[Re, -Im], [Im, Re]] of the Hermitian Gram (every eigenvalue of
 // the Gram appears twice).  The embedding is summed in FP64; a cyclic Jacobi
@@ -1708,6 +1795,9 @@ struct FourierSolver {
          *twy = nullptr;
   int *mask = nullptr, *S_idx = nullptr, *iptr = nullptr, *ilist = nullptr, *err = nullptr;
   double2* part = nullptr;
+  double2* part2 = nullptr;  // second Gram partials of the fused Cholesky-QR2
+  unsigned* qbar = nullptr;  // its grid-barrier counter
+  bool coop = false;         // the fused Cholesky-QR2 fits one cooperative launch
   double2* rfac = nullptr;
   double* eta = nullptr;
   double* scal = nullptr;
@@ -1774,6 +1864,14 @@ FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int 
   F->smem = fcarve(F->g, m, rho).total;
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
+  {  // the fused Cholesky-QR2 needs all its blocks resident at once
+    int coop = 0, nsm = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cqr2_fused_kernel, 256, 0) != cudaSuccess)
+      cudaGetLastError();
+    F->coop = coop != 0 && per_sm * nsm >= F->nblk;
+  }
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   // the m-vectors go to global memory when they do not fit beside the frame
   // (the sweep also holds kFStaticSmem bytes of static shared memory)
@@ -1810,6 +1908,8 @@ FourierSolver* fourier_create(int nx, int ny, int m, int q, int r, int rho, int 
             cudaMallocAsync(reinterpret_cast<void**>(&F->ilist), sizeof(int) * m * q, F->s) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&F->err), sizeof(int) * 2, F->s) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&F->part), sizeof(double2) * F->nblk * rr, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->part2), sizeof(double2) * F->nblk * rr, F->s) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&F->qbar), sizeof(unsigned), F->s) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&F->rfac), sizeof(double2) * 2 * rr, F->s) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&F->eta), sizeof(double), F->s) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&F->scal), sizeof(double) * 4, F->s) == cudaSuccess &&
@@ -1854,7 +1954,7 @@ void fourier_destroy(FourierSolver* F) {
   void* ps[] = {F->y, F->mask, F->U, F->FU, F->B, F->S_idx, F->S_val, F->RES, F->H, F->K, F->grad,
                 F->Z, F->Z2, F->twx, F->twy, F->twl, F->iptr, F->ilist, F->err, F->part, F->rfac, F->eta,
                 F->scal,
-                F->vecs, F->Wk, F->AS, F->asv, F->prof};
+                F->vecs, F->Wk, F->AS, F->asv, F->part2, F->qbar, F->prof};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, F->s);
   cudaStreamSynchronize(F->s);
@@ -1951,6 +2051,32 @@ static cudaError_t ccholqr2(FourierSolver* F, const float2* Zin, float2* Uout) {
   return cudaGetLastError();
 }
 
+// Z = X - eta G2 (G2 null: Z = X), then Uout = its Cholesky-QR2: one
+// cooperative launch when every block fits on the device at once, else the
+// separate kernels.  Uout may be X.
+static cudaError_t cqr2(FourierSolver* F, const float2* X, const float2* G2, const double* eta,
+                        float2* Uout) {
+  const int n = F->g.n, r = F->r;
+  if (F->coop) {
+    cudaError_t e = cudaMemsetAsync(F->qbar, 0, sizeof(unsigned), F->s);
+    if (e != cudaSuccess) return e;
+    float2* Z = F->Z;
+    float2* Z2 = F->Z2;
+    unsigned long long wait_ns = 10ull * 1000 * 1000 * 1000;
+    int nn = n, rr = r;
+    void* args[] = {&nn, &rr, const_cast<float2**>(&X), const_cast<float2**>(&G2),
+                    const_cast<double**>(&eta), &Z, &Z2, &Uout, &F->part, &F->part2, &F->qbar,
+                    &F->err, &wait_ns};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(cqr2_fused_kernel),
+                                       dim3(F->nblk), dim3(256), args, 0, F->s);
+  }
+  if (G2) {
+    cgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, X, G2, eta, F->Z, F->part);
+    return ccholqr2(F, F->Z, Uout);
+  }
+  return ccholqr2(F, X, Uout);
+}
+
 int fourier_check_error(FourierSolver* F, std::string* msg) {
   int e[2] = {0, 0};
   cudaMemcpyAsync(e, F->err, sizeof(e), cudaMemcpyDeviceToHost, F->s);
@@ -1999,14 +2125,14 @@ int fourier_init(FourierSolver* F, std::string* msg) {
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(Zf, st.data(), nr * 8, cudaMemcpyHostToDevice, F->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(F->s);  // the host block may go
-  if (e == cudaSuccess) e = ccholqr2(F, Zf, F->U);
+  if (e == cudaSuccess) e = cqr2(F, Zf, nullptr, nullptr, F->U);
   const double floor_tol = 4.0 * 0x1.0p-24 * std::sqrt(static_cast<double>(nr));
   const double tol = std::max(F->power_tol, floor_tol);
   for (int it = 0; it < F->power_iters && e == cudaSuccess; ++it) {
     e = cudaMemcpyAsync(Uo, F->U, nr * 8, cudaMemcpyDeviceToDevice, F->s);
     cproject_kernel<<<q, 256, 0, F->s>>>(n, q, r, F->H, Uo, Pf);
     cgrad_kernel<<<(n + 31) / 32, 256, 0, F->s>>>(n, q, r, F->H, Pf, Zf);
-    if (e == cudaSuccess) e = ccholqr2(F, Zf, F->U);
+    if (e == cudaSuccess) e = cqr2(F, Zf, nullptr, nullptr, F->U);
     if (e == cudaSuccess && ((it % 5) == 4 || it + 1 == F->power_iters)) {
       coverlap_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, Uo, F->U, F->part);
       cresid_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, F->nblk, F->part, Uo, F->U, rpart);
@@ -2052,8 +2178,7 @@ int fourier_iterate(FourierSolver* F, int iters, std::string* msg, cudaEvent_t* 
     }
     if (ev) cudaEventRecord(ev[2], F->s);
     // Z = U - eta grad, then complex Cholesky-QR2
-    cgram_part_kernel<<<F->nblk, 256, 0, F->s>>>(n, r, F->U, F->grad, F->eta, F->Z, F->part);
-    if (e == cudaSuccess) e = ccholqr2(F, F->Z, F->U);
+    if (e == cudaSuccess) e = cqr2(F, F->U, F->grad, F->eta, F->U);
     if (ev) cudaEventRecord(ev[3], F->s);
     if (e != cudaSuccess) {
       *msg = cudaGetErrorString(e);
