@@ -1645,38 +1645,55 @@ __global__ void ceta_kernel(int r, int nblk, const double2* __restrict__ part, d
 }
 
 // ---- subspace iteration of the initialisation: float32 products -----------
-// P[k][l] = sum_j conj(H[k][j]) U[l][j] (U column-major: column l contiguous):
-// one block per column k, threads over j with all r sums at once (H read
-// once), then the warps' sums added in warp order
-__global__ void __launch_bounds__(256) cproject_kernel(int n, int q, int r,
-                                                       const float2* __restrict__ H,
-                                                       const float2* __restrict__ U,
-                                                       float2* __restrict__ P) {
-  __shared__ float2 red[8][kMaxR];
-  const int k = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// P[k][l] = sum_j conj(H[k][j]) U[l][j] (U column-major: column l contiguous),
+// in two steps.  Partials: block (kb, c) takes the 8 columns k = 8 kb + w (one
+// per warp) over the chunk c of cs rows j; the chunk's U is staged in shared
+// memory 256 rows at a time and serves all 8 warps (H read once, U once per 8
+// columns); lanes over j, then a warp butterfly.  Then the chunks' partials
+// are added in chunk order.
+constexpr int kProjRows = 256;
+__global__ void __launch_bounds__(256) cproject_part_kernel(int n, int q, int r, int cs,
+                                                            const float2* __restrict__ H,
+                                                            const float2* __restrict__ U,
+                                                            float2* __restrict__ part) {
+  __shared__ float2 Us[kMaxR][kProjRows];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int k = blockIdx.x * 8 + w, c = blockIdx.y;
+  const int j0 = c * cs, j1 = min(n, j0 + cs);
   float2 acc[kMaxR];
 #pragma unroll
   for (int l = 0; l < kMaxR; ++l) acc[l] = make_float2(0.f, 0.f);
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const float2 h = H[static_cast<size_t>(k) * n + j];
+  for (int jb = j0; jb < j1; jb += kProjRows) {
+    const int nj = min(kProjRows, j1 - jb);
+    __syncthreads();
+    for (int t = threadIdx.x; t < r * kProjRows; t += blockDim.x) {
+      const int l = t / kProjRows, jj = t - l * kProjRows;
+      Us[l][jj] = jj < nj ? U[static_cast<size_t>(l) * n + jb + jj] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (k < q)
+      for (int jj = lane; jj < nj; jj += 32) {
+        const float2 h = H[static_cast<size_t>(k) * n + jb + jj];
 #pragma unroll
-    for (int l = 0; l < kMaxR; ++l)
-      if (l < r) acc[l] = ccfma(h, U[static_cast<size_t>(l) * n + j], acc[l]);
+        for (int l = 0; l < kMaxR; ++l)
+          if (l < r) acc[l] = ccfma(h, Us[l][jj], acc[l]);
+      }
   }
 #pragma unroll
   for (int l = 0; l < kMaxR; ++l) {
     if (l >= r) break;
     const float sx = warp_sumf(acc[l].x), sy = warp_sumf(acc[l].y);
-    if (lane == 0) red[w][l] = make_float2(sx, sy);
-  }
-  __syncthreads();
-  if (threadIdx.x < r) {
-    float2 s = make_float2(0.f, 0.f);
-    for (int ww = 0; ww < static_cast<int>(blockDim.x >> 5); ++ww) s = cadd(s, red[ww][threadIdx.x]);
-    P[static_cast<size_t>(k) * r + threadIdx.x] = s;
+    if (lane == 0 && k < q) part[(static_cast<size_t>(c) * q + k) * r + l] = make_float2(sx, sy);
   }
 }
-// Z[l][j] = sum_k H[k][j] P[k][l] (k in order)
+__global__ void cproject_sum_kernel(int q, int r, int nc, const float2* __restrict__ part,
+                                    float2* __restrict__ P) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= q * r) return;
+  float2 s = make_float2(0.f, 0.f);
+  for (int c = 0; c < nc; ++c) s = cadd(s, part[static_cast<size_t>(c) * q * r + t]);
+  P[t] = s;
+}
 // Z[l][j] = sum_k H[k][j] P[k][l]: a block holds 32 columns j; its 8 warps
 // take contiguous runs of k, and their sums are added in warp (k) order
 __global__ void __launch_bounds__(256) cgrad_kernel(int n, int q, int r,
@@ -2107,6 +2124,13 @@ int fourier_init(FourierSolver* F, std::string* msg) {
   if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Uo), nr * 8, F->s);
   if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Zf), nr * 8, F->s);
   if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Pf), static_cast<size_t>(q) * r * 8, F->s);
+  // the projection's row chunks: about two blocks per SM in all
+  const int kb = (q + 7) / 8;
+  int cs = (n + std::max(1, 304 / kb) - 1) / std::max(1, 304 / kb);
+  cs = (cs + kProjRows - 1) / kProjRows * kProjRows;
+  const int nc = (n + cs - 1) / cs;
+  float2* Pp = nullptr;
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&Pp), static_cast<size_t>(nc) * q * r * 8, F->s);
   if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&rpart), F->nblk * sizeof(double), F->s);
   // start: deterministic complex Gaussian block
   std::vector<float2> st(nr);
@@ -2130,7 +2154,8 @@ int fourier_init(FourierSolver* F, std::string* msg) {
   const double tol = std::max(F->power_tol, floor_tol);
   for (int it = 0; it < F->power_iters && e == cudaSuccess; ++it) {
     e = cudaMemcpyAsync(Uo, F->U, nr * 8, cudaMemcpyDeviceToDevice, F->s);
-    cproject_kernel<<<q, 256, 0, F->s>>>(n, q, r, F->H, Uo, Pf);
+    cproject_part_kernel<<<dim3(kb, nc), 256, 0, F->s>>>(n, q, r, cs, F->H, Uo, Pp);
+    cproject_sum_kernel<<<(q * r + 255) / 256, 256, 0, F->s>>>(q, r, nc, Pp, Pf);
     cgrad_kernel<<<(n + 31) / 32, 256, 0, F->s>>>(n, q, r, F->H, Pf, Zf);
     if (e == cudaSuccess) e = cqr2(F, Zf, nullptr, nullptr, F->U);
     if (e == cudaSuccess && ((it % 5) == 4 || it + 1 == F->power_iters)) {
@@ -2146,7 +2171,7 @@ int fourier_init(FourierSolver* F, std::string* msg) {
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(F->s);
   for (void* p : {static_cast<void*>(Uo), static_cast<void*>(Zf), static_cast<void*>(Pf),
-                  static_cast<void*>(rpart)})
+                  static_cast<void*>(Pp), static_cast<void*>(rpart)})
     if (p) cudaFreeAsync(p, F->s);
   // b_k = (A_k U0)^+ (y_k - A_k s_k)
   if (e == cudaSuccess) e = fft_frames(F, F->U, F->FU, r, false);

@@ -37,11 +37,14 @@ def test_alone_equals_mix():
     reqs = small_mix()
     budget = int(0.5 * torch.cuda.mem_get_info()[0])
     gen_a = bench.C4Inputs()
-    alone = S.Server(budget, slots=1, keep_outputs=True).run(reqs, gen_a)
+    inputs_a = {rq.rid: gen_a(rq) for rq in reqs}
+    alone = S.Server(budget, slots=1, keep_outputs=True).run(reqs, lambda rq: inputs_a[rq.rid])
     gen_a.score(alone, reqs)
     gen_m = bench.C4Inputs()
+    # made before: the submissions take no time, so the requests queue together
+    inputs_m = {rq.rid: gen_m(rq) for rq in reqs}
     srv = S.Server(budget, slots=4, keep_outputs=True)
-    mix = srv.run(reqs, gen_m)
+    mix = srv.run(reqs, lambda rq: inputs_m[rq.rid])
     assert srv.peak_running >= 2          # the requests did run concurrently
     for a, r in zip(alone, mix):
         assert a.error is None and r.error is None, (a.error, r.error)
