@@ -149,6 +149,7 @@ class Server:
         th = threading.Thread(target=submitter, daemon=True)
         th.start()
         results = {}
+        native = {}
         pending = [rq.rid for rq in order]
         while pending:
             rid = pending[0]
@@ -163,10 +164,8 @@ class Server:
                 continue
             res = L.lrs_server_wait(srv, tickets[rid], -1)
             rq = by_rid[rid]
-            # native times are seconds since the server's creation; place them
-            # on this clock through the submission time
-            base = submitted[rid] - res.submit_s
-            r = Result(rid, rq.kind, rq.arrival, base + res.start_s, base + res.end_s,
+            native[rid] = (res.submit_s, res.start_s, res.end_s)
+            r = Result(rid, rq.kind, rq.arrival, res.start_s, res.end_s,
                        footprint=int(res.footprint), grid=int(res.grid),
                        admitted=int(res.admitted), group=int(res.group),
                        group_size=int(res.group_size))
@@ -179,6 +178,15 @@ class Server:
             results[rid] = r
             pending.pop(0)
         th.join()
+        # native times are seconds since the server's creation: one offset
+        # places them all on this clock (the largest of submission time minus
+        # native submission time, the closest to the clocks' true offset), so
+        # that their order is the server's own
+        if native:
+            base = max(submitted[rid] - ns for rid, (ns, _, _) in native.items())
+            for rid, (_, st, en) in native.items():
+                results[rid].start = base + st
+                results[rid].end = base + en
         L.lrs_server_destroy(srv)
         del cb
         self.makespan = time.perf_counter() - t0

@@ -63,7 +63,7 @@ def test_reference_arm_other_ranks_leave_without_work(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("WORLD_SIZE", "2")
     called = []
-    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: called.append(1) or (1.0, 1.0))
+    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: called.append(1) or (1.0, 1.0, 1))
 
     class A:
         steps, warmup = 2, 3

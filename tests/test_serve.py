@@ -20,11 +20,12 @@ def dummy_inputs(rq):
 
 
 def overlaps_ok(res, slots, budget):
-    """At every start, the requests running (including it) fit the slots and
-    the budget."""
+    """At every start, the requests running (including it) fit the budget,
+    and their groups the slots (requests batched into one launch share a
+    slot; a queue that forms, e.g. on a loaded host, makes such batches)."""
     for r in res:
         running = [o for o in res if o.start <= r.start < o.end]
-        assert len(running) <= slots, (r.rid, len(running))
+        assert len({o.group for o in running}) <= slots, (r.rid, len(running))
         assert sum(o.footprint for o in running) <= budget
 
 
