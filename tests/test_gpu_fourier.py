@@ -59,6 +59,23 @@ def test_fourier_trajectory_and_init():
     assert rels[-1] <= 1e-3, rels[-1]     # 25 iterations: both still converging
 
 
+@pytest.mark.parametrize("nx,ny,m,rho,T", [(4, 256, 200, 4, 8), (2, 4096, 1000, 6, 6)])
+def test_fourier_long_sides_one_step(nx, ny, m, rho, T):
+    """Long power-of-two sides in the frame kernel's three-stage passes, the
+    bit reversal read by the first: 256-pixel rows (a round of threads takes
+    16 of them), and 4096-pixel rows (one row per round, two rounds).  One-step
+    parity from the oracle."""
+    inst = FourierInstance(nx=nx, ny=ny, q=12, r=2, m=m, rho=rho, seed=45 + nx,
+                           mask_law="uniform", b_law="gauss")
+    _, log = _oracle(inst, T)
+    s = new_fourier_solver(inst)
+    try:
+        recs = one_step(Problem.fourier(inst), s, log, range(T))
+    finally:
+        s.close()
+    check_records(recs, min_whole=T // 2)
+
+
 def test_fourier_table1_frames_one_step():
     """The Table 1 setting (Section III): 20 x 20 frames (n = 400), uniformly
     random DFT rows, S1 values, r = 4, rho = 2 with rho_max = 5; one-step
