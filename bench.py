@@ -420,6 +420,7 @@ def run_c3(args):
     s.set_measurements(Y, masks)
     s.init()
     s.iterate(args.warmup)
+    launches = int(L.lrs_describe(s.h).get("launches_per_iteration", 0))
     L.lrs_phase_times(s.h)
     with ClockSampler(0) as clk:
         torch.cuda.synchronize()
@@ -487,7 +488,7 @@ def run_c3(args):
                 "d2h_bytes_per_step": U_.nbytes + B_.nbytes + Si_.nbytes + Sv_.nbytes,
                 "iterations": T_e2e,
                 "includes": "lrs_set_measurements(pinned host) + lrs_init + lrs_iterate + lrs_get(host)"},
-        "gpu_launches": 11 * args.steps, "clocks": clocks, "cpu_baseline": cpu,
+        "gpu_launches": launches * args.steps, "clocks": clocks, "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
     return 0

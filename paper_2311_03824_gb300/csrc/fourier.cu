@@ -2249,6 +2249,12 @@ double fourier_eta(FourierSolver* F) {
 }
 int fourier_t(FourierSolver* F) { return F->t; }
 
+// Kernels one steady iteration launches: F2 U, the sweep, the k-space
+// reduction, F2^H K, and the step with its Cholesky-QR2 (one cooperative
+// launch, else the Gram partials and two factorisations and applications).
+int fourier_launches_per_iteration(FourierSolver* F) { return 4 + (F->coop ? 1 : 6); }
+int fourier_fused_qr(FourierSolver* F) { return F->coop ? 1 : 0; }
+
 // Sweep cycle counters: enable (allocate, zero) and read-and-zero.
 int fourier_prof_enable(FourierSolver* F) {
   if (F->prof) return 0;

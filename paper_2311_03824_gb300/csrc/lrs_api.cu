@@ -34,6 +34,8 @@ int fourier_set_state(FourierSolver* F, const void* U, const void* B, const int*
                       const void* S_val, int t, double eta, int mem_kind);
 double fourier_eta(FourierSolver* F);
 int fourier_t(FourierSolver* F);
+int fourier_launches_per_iteration(FourierSolver* F);
+int fourier_fused_qr(FourierSolver* F);
 int fourier_prof_enable(FourierSolver* F);
 int fourier_prof_read(FourierSolver* F, unsigned long long* out, int len);
 }  // namespace lrs
@@ -1634,8 +1636,10 @@ static int launches_per_iteration(const lrs_ctx* h) {
 lrs_status lrs_describe(lrs_t h, char* buf, int32_t len) {
   if (!h || !buf || len <= 0) return fail(LRS_ERR_ARG, "lrs_describe: bad argument");
   if (h->F) {
-    snprintf(buf, static_cast<size_t>(len), "{\"op\": \"dft2d\", \"nx\": %d, \"ny\": %d, \"cta_per_frame\": 1}",
-             h->opt.nx, h->opt.ny);
+    snprintf(buf, static_cast<size_t>(len),
+             "{\"op\": \"dft2d\", \"nx\": %d, \"ny\": %d, \"cta_per_frame\": 1, "
+             "\"fused_qr\": %d, \"launches_per_iteration\": %d}",
+             h->opt.nx, h->opt.ny, fourier_fused_qr(h->F), fourier_launches_per_iteration(h->F));
     return LRS_OK;
   }
   if (h->engine == 3) {
