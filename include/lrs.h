@@ -445,13 +445,19 @@ const char* lrs_server_last_error(void);
  * for pieces inside tasks, in the small steps after W / IHT / final passes,
  * producer waiting for a ticket, the numbers of tasks and small steps, then
  * the IHT step's parts: loads, mu, HardThreshold, next residual, publish.
+ * A DFT2D_MASK handle gives 8 counters (thread-0 cycles summed over the
+ * frames' CTAs): set-up and Gram, sparse DFTs, norms and updates, FFTs,
+ * HardThreshold, final stage, LS solves, projection applies.
  * len is the capacity of out in elements.  Counters restart at zero.
  * Errors: LRS_ERR_ARG, LRS_ERR_STATE (no trace buffer), LRS_ERR_CUDA. */
 lrs_status lrs_sweep_trace(lrs_t h, uint64_t* out, int64_t len);
 
-/* Write a one-line description of the handle's launch shape (operator,
- * CTAs per column, slab width, shared memory per CTA, resident clusters) into
- * buf (NUL-terminated, truncated to len bytes).  Errors: LRS_ERR_ARG. */
+/* Write a one-line JSON description of the handle's launch shape (operator,
+ * CTAs per column or frame, slab width, shared memory per CTA, resident
+ * clusters, and "launches_per_iteration": the kernels one steady iteration
+ * launches; DFT handles also give "fused_qr", 1 when the step and its
+ * Cholesky-QR2 run as one cooperative launch) into buf (NUL-terminated,
+ * truncated to len bytes).  Errors: LRS_ERR_ARG. */
 lrs_status lrs_describe(lrs_t h, char* buf, int32_t len);
 
 /* Release every resource of the handle (NULL is accepted). */
