@@ -275,14 +275,22 @@ def run_ours(args):
     A_h, Y_h = pinned_copy(A), pinned_copy(Y)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    s2 = L.Solver(n, m, q, r, rho, stream=stream, autotune=1,  # the shape chosen above (cached)
-                  engine=args.engine)
+    s2 = L.Solver(n, m, q, r, rho, stream=stream, use_graph=1, autotune=1,  # the shape chosen
+                  engine=args.engine)                                         # above (cached)
     s2.set_measurements(Y_h, A_h)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     s2.init()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
     s2.iterate(T_e2e)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
     U_, B_, Si_, Sv_ = s2.get()
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
+    e2e_parts = {"create_and_set_measurements": t1 - t0, "init": t2 - t1, "iterate": t3 - t2,
+                 "get": t0 + t_e2e - t3}
     s2.close()
     e2e_value = world * q * T_e2e / t_e2e
     h2d = A.nbytes + Y.nbytes
@@ -314,7 +322,8 @@ def run_ours(args):
             "phases_ms_per_step": {k: ph[k] / max(1, ph["iters"]) for k in ("sweep_ms", "grad_ms", "qr_ms")},
             "e2e": {"value": e2e_value, "unit": "column-iters/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "iterations": T_e2e,
-                    "includes": "lrs_set_measurements(pinned host) + lrs_init + lrs_iterate + lrs_get(host)"},
+                    "includes": "lrs_set_measurements(pinned host) + lrs_init + lrs_iterate + lrs_get(host)",
+                    "seconds": {k: round(v, 5) for k, v in e2e_parts.items()}},
             "gpu_launches": int(desc.get("launches_per_iteration", 0)) * args.steps,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
@@ -442,11 +451,19 @@ def run_c3(args):
     s2 = L.Solver(n, m, q, r, rho, kind=L.LRS_OP_DFT2D_MASK, nx=inst.nx, ny=inst.ny,
                   stream=stream)
     s2.set_measurements(Y_h, masks_h)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     s2.init()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
     s2.iterate(T_e2e)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
     U_, B_, Si_, Sv_ = s2.get()
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
+    e2e_parts = {"create_and_set_measurements": t1 - t0, "init": t2 - t1, "iterate": t3 - t2,
+                 "get": t0 + t_e2e - t3}
     s2.close()
     clocks = clk.summary()
     sweep_ms = ph["sweep_ms"] / max(1, ph["iters"])
@@ -487,7 +504,8 @@ def run_c3(args):
                 "h2d_bytes_per_step": Y.nbytes + masks.nbytes,
                 "d2h_bytes_per_step": U_.nbytes + B_.nbytes + Si_.nbytes + Sv_.nbytes,
                 "iterations": T_e2e,
-                "includes": "lrs_set_measurements(pinned host) + lrs_init + lrs_iterate + lrs_get(host)"},
+                "includes": "lrs_set_measurements(pinned host) + lrs_init + lrs_iterate + lrs_get(host)",
+                "seconds": {k: round(v, 5) for k, v in e2e_parts.items()}},
         "gpu_launches": launches * args.steps, "clocks": clocks, "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
